@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Benchmark of libchamfer's Chamfer-Estimate hot path on one GB300 per rank.
+
+Workload (one step = every stage of the path on one pair of point sets):
+  |A| = |B| = 100,000, d = 128, binary32, l2, eps = 0.1 (T = 4606 samples),
+  100-cluster Gaussian mixture (centres U[-10,10]^128, unit std; B's centres
+  moved by N(0, 0.5^2)), L = 10 scales, k = 16 embedding width.
+A step registers both sets from resident device memory (ingest), runs CrudeNN,
+the importance draws, the sampled scans and the combine, and ends with the
+estimate on the host (ch_set_create x2 + ch_estimate + ch_set_destroy x2).
+
+metric = (|A| + |B|) points per second of estimates within (1 +- 0.1) of the
+exact GPU brute force (ch_exact); steps outside that band count zero points.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank runs its own pair
+(independent replicas, no data-path collective); value = all points / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pts/s of (1±0.1) Chamfer est. vs exact GPU brute force; p50/p99 req latency"
+UNIT = "pts/s"
+NA = NB = 100_000
+DIM = 128
+EPS = 0.1
+LEVELS = 10
+PROJ = 16
+FLUSH_BYTES = 256 << 20  # > 126 MB L2
+
+
+def workload_config(T):
+    return {
+        "workload": "mid: |A|=|B|=100000, d=128, fp32, l2, eps=0.1, 100-cluster Gaussian mixture",
+        "nA": NA, "nB": NB, "d": DIM, "metric": "l2", "eps": EPS, "T": T, "levels": LEVELS,
+        "proj_dim": PROJ, "grouping": "hash tables per scale",
+        "l2_flush": "256 MiB write between timed steps, outside the timed events",
+    }
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--screen", default="auto", choices=["auto", "exact", "tf32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_oracle_step(A, B, T, seed, scan_fraction=1):
+    """One oracle Chamfer-Estimate on the full sets; with scan_fraction f > 1 only
+    T/f sampled scans run and their time is scaled by f.  Returns (seconds, eta)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.crude_nn(A, B, oracle.L2, hash_seed=seed, L=LEVELS, proj_dim=PROJ)
+    w, prefix, W, _ = oracle.weights(r["D"])
+    idx = oracle.draws(prefix, W, T, seed)
+    t1 = time.perf_counter()
+    Ts = int(math.ceil(T / scan_fraction))
+    m, _ = oracle.scan(A, idx[:Ts], B, oracle.L2)
+    t2 = time.perf_counter()
+    eta = oracle.combine(m, idx[:Ts], w, W)
+    return (t1 - t0) + (t2 - t1) * (T / Ts), eta
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2307_03043_gb300 import workloads
+    A, B = workloads.gaussian_mixture(NA, NB, DIM, 0)
+    T = oracle.default_T(NA, NB, EPS)
+    frac = 8
+    for w in range(args.warmup):
+        cpu_oracle_step(A, B, T, 1000 + w, frac)
+    times = []
+    for k in range(args.steps):
+        t, _ = cpu_oracle_step(A, B, T, k, frac)
+        times.append(t)
+    sec = float(np.mean(times))
+    value = (NA + NB) / sec
+    cores = oracle.num_threads()
+    sample = (f"each step: oracle CrudeNN + weights + draws on the full 100k x 100k sets, "
+              f"exact scans of T/{frac} samples timed and scaled by {frac}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(T),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2307_03043_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2307_03043_gb300 import binding as ch
+    from paper_2307_03043_gb300 import workloads
+
+    A_np, B_np = workloads.gaussian_mixture(NA, NB, DIM, rank)
+    A = torch.from_numpy(A_np).cuda()
+    B = torch.from_numpy(B_np).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = ch.ch_ctx_create(local, stream)
+    screen = {"auto": ch.CH_SCREEN_AUTO, "exact": ch.CH_SCREEN_EXACT, "tf32": ch.CH_SCREEN_TF32}[args.screen]
+
+    # exact reference value (untimed): GPU brute force
+    sA = ch.ch_set_create(ctx, A, 2, NA, DIM)
+    sB = ch.ch_set_create(ctx, B, 2, NB, DIM)
+    exact = ch.ch_exact(ctx, sA, sB, ch.CH_L2, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    exact_ms_ev = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ch.ch_exact(ctx, sA, sB, ch.CH_L2, 0)
+        e1.record(stream)
+        e1.synchronize()
+        exact_ms_ev.append(e0.elapsed_time(e1))
+    ch.ch_set_destroy(sA)
+    ch.ch_set_destroy(sB)
+    T = 0
+
+    def step(seed):
+        a = ch.ch_set_create(ctx, A, 2, NA, DIM)
+        b = ch.ch_set_create(ctx, B, 2, NB, DIM)
+        p = ch.est_params(ch.CH_L2, LEVELS, PROJ, None, seed, eps=EPS, T=0, sample_seed=seed, screen=screen)
+        eta, rep = ch.ch_estimate(ctx, a, b, p, report=True)
+        ch.ch_set_destroy(a)
+        ch.ch_set_destroy(b)
+        return eta, rep
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for w in range(args.warmup):
+        step(10_000 + w)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, scan_ms, ok = [], [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        eta, rep = step(k)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        scan_ms.append(rep.t_scan_ms)
+        ok.append(abs(eta / exact - 1.0) <= 0.1)
+        T = rep.T
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+
+    total_ms = float(np.sum(step_ms))
+    pts_ok = float(sum((NA + NB) for o in ok if o))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        pts = torch.tensor([pts_ok], device="cuda", dtype=torch.float64)
+        dist.all_reduce(pts, op=dist.ReduceOp.SUM)
+        total_ms, pts_ok = float(t.item()), float(pts.item())
+    value = pts_ok / (total_ms / 1e3)
+
+    # end to end through the public API from pinned host buffers
+    hA = torch.from_numpy(A_np).pin_memory()
+    hB = torch.from_numpy(B_np).pin_memory()
+    e2e_s = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a = ch.ch_set_create(ctx, hA, 0, NA, DIM)
+        b = ch.ch_set_create(ctx, hB, 0, NB, DIM)
+        eta = ch.ch_estimate(ctx, a, b, ch.est_params(ch.CH_L2, LEVELS, PROJ, None, 500 + k, eps=EPS,
+                                                      sample_seed=500 + k, screen=screen))
+        ch.ch_set_destroy(a)
+        ch.ch_set_destroy(b)
+        ch.ch_ctx_sync(ctx)
+        if k > 0:
+            e2e_s.append(time.perf_counter() - t0)
+    e2e_value = (NA + NB) / float(np.mean(e2e_s))
+
+    # roofline of the dominant kernel (the sampled scan)
+    scan_avg = float(np.mean(scan_ms))
+    sm_mhz = clk.get("sm_mhz") or 1455.0
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if args.screen == "exact" or True:
+        # CUDA-core canonical distances: 2 FP32 instructions per (sample, b, coordinate)
+        ops = 2.0 * T * NB * DIM
+        peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lanes x max clock, Tinst/s
+        roof = {"bound": "alu", "achieved": ops / (scan_avg / 1e3) / 1e12, "peak": peak, "unit": "Tinst/s",
+                "traffic": None, "kernel": "k_scan_exact (sampled scan, canonical fp32 distances)",
+                "peak_basis": "152 SMs x 128 FP32 lanes x sm_max_mhz (derived, not measured)"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        sec, _ = cpu_oracle_step(A_np, B_np, T, 0, 1)
+        cpu = {"value": (NA + NB) / sec, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "one full oracle Chamfer-Estimate of the 100k x 100k workload (all T scans)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(T),
+            "accuracy": {"steps_within_10pct": int(sum(ok)), "steps": len(ok), "exact_ch": exact},
+            "exact_gpu": {"ms": float(np.mean(exact_ms_ev)), "pts_per_s": (NA + NB) / (np.mean(exact_ms_ev) / 1e3),
+                          "speedup_estimate_vs_exact": float(np.mean(exact_ms_ev)) / (total_ms / args.steps)},
+            "stage_ms": {"scan": scan_avg},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (NA + NB) * DIM * 4,
+                    "d2h_bytes_per_step": 48},
+            "gpu_launches": None,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+    ch.ch_ctx_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

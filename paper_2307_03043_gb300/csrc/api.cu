@@ -1,0 +1,717 @@
+// api.cu -- the extern "C" entry points of libchamfer (include/chamfer.h).
+//
+// Host-side orchestration only: argument checks, workspace layout, kernel
+// launches on the context's stream, and the single device->host copy that
+// ends each synchronising call.  Every arithmetic step of the method runs in
+// the kernels of k_hash.cu, k_sample.cu, k_scan.cu and k_screen.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+using namespace chx;
+
+#include <atomic>
+
+namespace chx {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status,
+                         cudaStream_t s);
+void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
+                        uint8_t* level, cudaStream_t s);
+
+void Arena::reserve(size_t bytes) {
+  if (bytes <= cap) return;
+  if (base) {
+    CHX_CUDA(cudaDeviceSynchronize());
+    CHX_CUDA(cudaFree(base));
+    base = nullptr;
+    cap = 0;
+  }
+  const size_t want = bytes + bytes / 4 + (1 << 20);
+  if (cudaMalloc(&base, want) != cudaSuccess) {
+    cudaGetLastError();
+    base = nullptr;
+    throw Err{CH_ENOMEM, "workspace allocation of " + std::to_string(want) + " bytes failed"};
+  }
+  cap = want;
+}
+
+void Arena::release() {
+  if (base) cudaFree(base);
+  base = nullptr;
+  cap = used = 0;
+}
+
+// Two-pass layout: the same sequence of take() calls first measures, then carves.
+struct Layout {
+  bool measure = true;
+  size_t need = 0;
+  Arena* a = nullptr;
+  template <class T>
+  T* take(size_t count) {
+    const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (measure) {
+      need += bytes;
+      return nullptr;
+    }
+    return a->take<T>(count);
+  }
+};
+
+template <class F>
+static void carve(ch_ctx* c, F&& f) {
+  Layout m;
+  f(m);
+  c->ws.reserve(m.need + 256);
+  c->ws.reset();
+  Layout t;
+  t.measure = false;
+  t.a = &c->ws;
+  f(t);
+}
+
+// result block copied to the host at the end of a synchronising call
+struct ResBlock {
+  double eta;
+  double D_total;
+  uint64_t W;
+  int32_t e_top;
+  int32_t S;
+  uint32_t status;   // call status bits
+  uint32_t statusA;  // set A status bits
+  uint32_t statusB;  // set B status bits
+  uint32_t pad;
+};
+
+__global__ void k_collect(ResBlock* r, const uint32_t* sa, const uint32_t* sb, const double* out2,
+                          const uint64_t* W, const int32_t* S, const int32_t* e_top) {
+  if (threadIdx.x != 0) return;
+  r->statusA = sa ? *sa : 0u;
+  r->statusB = sb ? *sb : 0u;
+  if (out2) {
+    r->eta = out2[0];
+    r->D_total = out2[1];
+  }
+  if (W) r->W = *W;
+  if (S) r->S = *S;
+  if (e_top) r->e_top = *e_top;
+}
+
+static void finish(ch_ctx* c, ResBlock* dres, ResBlock* hres) {
+  CHX_CUDA(cudaMemcpyAsync(hres, dres, sizeof(ResBlock), cudaMemcpyDeviceToHost, c->stream));
+  CHX_CUDA(cudaStreamSynchronize(c->stream));
+  const uint32_t st = hres->status | hres->statusA | hres->statusB;
+  if (st & ST_NONFINITE) throw Err{CH_EINVAL, "point set holds a non-finite value"};
+  if (st & ST_RANGE) throw Err{CH_EINVAL, "scale exponents outside [-120, 120] (data range too large or too small)"};
+  if (st & ST_BAD_INDEX) throw Err{CH_EINVAL, "sample index out of range"};
+  if (st & ST_TABLE_FULL) throw Err{CH_ENOMEM, "bucket table overflow"};
+  if (st & ST_TIMEOUT) throw Err{CH_ETIMEOUT, "a bounded device wait gave up"};
+}
+
+static void check_hash(const ch_hash_params* hp) {
+  CHX_CHECK(hp, CH_EINVAL, "hash params NULL");
+  CHX_CHECK(hp->metric == CH_L1 || hp->metric == CH_L2, CH_EINVAL, "metric must be CH_L1 or CH_L2");
+  CHX_CHECK(hp->levels >= 1 && hp->levels <= uint32_t(kMaxLevels), CH_EINVAL, "levels must be in 1..32");
+  if (hp->metric == CH_L2)
+    CHX_CHECK(hp->proj_dim >= 1 && hp->proj_dim <= uint32_t(kMaxProj), CH_EINVAL, "proj_dim must be in 1..64");
+  CHX_CHECK(hp->group == CH_GROUP_HASH || hp->group == CH_GROUP_SORT, CH_EINVAL, "group must be HASH or SORT");
+}
+
+static void check_pair(ch_ctx* c, const ch_set* A, const ch_set* B) {
+  CHX_CHECK(A && B, CH_EINVAL, "set NULL");
+  CHX_CHECK(A->ctx == c && B->ctx == c, CH_EINVAL, "sets belong to another context");
+  CHX_CHECK(A->d == B->d, CH_EINVAL, "sets differ in dimension");
+  CHX_CHECK(A->dtype == B->dtype, CH_EINVAL, "sets differ in storage type");
+  CHX_CHECK(B->n >= 1, CH_EINVAL, "B must hold at least one point");
+}
+
+// hashed space of a set under hp: the set's own rows (l1) or its l2 embedding
+struct Hashed {
+  HashSrc src;
+  const uint32_t* box;
+  float* Y;        // l2 embedding (+ Gaussian matrix tail) in the workspace
+  uint32_t* boxY;  // l2 box in the workspace
+};
+
+static int proj_pad(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64; }
+
+template <class L>
+static void take_hashed(L& lay, const ch_set* X, const ch_hash_params* hp, Hashed* h) {
+  if (hp->metric == CH_L1) {
+    h->src = HashSrc{X->data, X->dtype, X->n, X->d, X->scales};
+    h->box = X->box_x;
+    h->Y = nullptr;
+    h->boxY = nullptr;
+  } else {
+    const int k = static_cast<int>(hp->proj_dim);
+    h->Y = lay.template take<float>(size_t(X->n) * k + size_t(proj_pad(k)) * X->d);
+    h->boxY = lay.template take<uint32_t>(size_t(2) * k);
+    h->src = HashSrc{h->Y, CH_F32, X->n, k, nullptr};
+    h->box = h->boxY;
+  }
+}
+
+static void run_hashed(ch_ctx* c, const ch_set* X, const ch_hash_params* hp, Hashed* h, uint32_t* status) {
+  if (hp->metric == CH_L2)
+    launch_project(X, hp->hash_seed, static_cast<int>(hp->proj_dim), h->Y, h->boxY, status, c->sm_count, c->stream);
+}
+
+template <class L>
+static ScaleTables take_tables(L& lay, int dd, int L_) {
+  ScaleTables t;
+  t.e_lo = lay.template take<int32_t>(1);
+  t.inv_r = lay.template take<float>(L_);
+  t.salt = lay.template take<uint64_t>(L_);
+  t.shift = lay.template take<float>(size_t(dd) * L_);
+  t.mult = lay.template take<uint64_t>(dd);
+  return t;
+}
+
+// bucket-table plan: one table of 2^log_cap 16-byte slots per scale, load <= 1/2,
+// scales grouped so that a group's tables stay L2-resident
+struct TablePlan {
+  uint32_t log_cap;
+  int per_group;
+};
+static TablePlan table_plan(int64_t nB, int L) {
+  TablePlan p;
+  p.log_cap = static_cast<uint32_t>(ceil_log2_i64(std::max<int64_t>(2 * nB, 1024)));
+  const size_t per_level = (size_t(1) << p.log_cap) * 16;
+  const size_t budget = size_t(48) << 20;
+  p.per_group = static_cast<int>(std::max<size_t>(1, std::min<size_t>(L, budget / per_level)));
+  return p;
+}
+
+struct CrudeBufs {
+  Hashed hA, hB;
+  ScaleTables tab;
+  int32_t* e_top;
+  ulonglong2* slots;
+  TablePlan plan;
+};
+
+template <class L>
+static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_params* hp, CrudeBufs* cb) {
+  take_hashed(lay, A, hp, &cb->hA);
+  take_hashed(lay, B, hp, &cb->hB);
+  const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
+  cb->tab = take_tables(lay, dd, static_cast<int>(hp->levels));
+  cb->e_top = lay.template take<int32_t>(1);
+  cb->plan = table_plan(B->n, static_cast<int>(hp->levels));
+  cb->slots = lay.template take<ulonglong2>(size_t(cb->plan.per_group) << cb->plan.log_cap);
+}
+
+// CrudeNN (Fig. 2): embedding, scales, per-scale bucket tables of B, probes of A,
+// then D_a = d(a, b(a)).
+static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash_params* hp, CrudeBufs* cb,
+                      int64_t* bidx, uint8_t* level, float* D, uint32_t* status) {
+  const int L = static_cast<int>(hp->levels);
+  const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
+  cudaStream_t s = c->stream;
+  run_hashed(c, A, hp, &cb->hA, status);
+  run_hashed(c, B, hp, &cb->hB, status);
+  launch_scale_tables(cb->hA.box, cb->hB.box, dd, L, hp->top_exp, hp->hash_seed, cb->tab, cb->e_top, status, s);
+  CHX_CUDA(cudaMemsetAsync(level, L, size_t(A->n), s));
+  CHX_CUDA(cudaMemsetAsync(bidx, 0, size_t(A->n) * sizeof(int64_t), s));
+  if (hp->group == CH_GROUP_SORT) throw Err{CH_ENOTSUP, "sort grouping not built"};
+  const size_t cap = size_t(1) << cb->plan.log_cap;
+  for (int L0 = 0; L0 < L; L0 += cb->plan.per_group) {
+    const int nl = std::min(cb->plan.per_group, L - L0);
+    CHX_CUDA(cudaMemsetAsync(cb->slots, 0, size_t(nl) * cap * sizeof(ulonglong2), s));
+    HashTable h{cb->slots, cb->plan.log_cap};
+    launch_group_insert(cb->hB.src, L, L0, nl, cb->tab, h, status, s);
+    launch_group_probe(cb->hA.src, L, L0, nl, cb->tab, h, bidx, level, s);
+  }
+  launch_crude_dist(A, B, hp->metric, bidx, D, s);
+}
+
+struct SampleBufs {
+  SampleWork sw;
+  uint64_t* prefix;
+};
+
+template <class L>
+static void take_sample(L& lay, int64_t nA, SampleBufs* sb) {
+  sb->sw.maxD = lay.template take<uint32_t>(1);
+  sb->sw.blocksum = lay.template take<uint64_t>(std::max<size_t>(sample_blocks(nA), 1));
+  sb->sw.W = lay.template take<uint64_t>(1);
+  sb->sw.S = lay.template take<int32_t>(1);
+  sb->prefix = lay.template take<uint64_t>(std::max<int64_t>(nA, 1));
+}
+
+static int screen_choice(int screen, int metric, const ch_set* A, const ch_set* B) {
+  if (metric == CH_L1) return CH_SCREEN_EXACT;
+  if (screen == CH_SCREEN_AUTO)
+    screen = A->dtype == CH_F32 ? CH_SCREEN_TF32 : A->dtype == CH_BF16 ? CH_SCREEN_BF16 : CH_SCREEN_FP8;
+  if (screen != CH_SCREEN_EXACT && !screen_supported(screen, A, B)) screen = CH_SCREEN_EXACT;
+  return screen;
+}
+
+struct ScanBufs {
+  ScanPart part;
+  void* screen_work;
+  int screen;
+};
+
+template <class L>
+static void take_scan(L& lay, ch_ctx* c, const ch_set* A, const ch_set* B, int64_t T, int metric, int screen,
+                      uint32_t R, ScanBufs* sb) {
+  sb->screen = screen_choice(screen, metric, A, B);
+  if (sb->screen == CH_SCREEN_EXACT) {
+    sb->part.chunks = scan_exact_chunks(T, B->n, A->d, c->sm_count);
+    sb->part.val = lay.template take<float>(size_t(sb->part.chunks) * std::max<int64_t>(T, 1));
+    sb->part.idx = lay.template take<int64_t>(size_t(sb->part.chunks) * std::max<int64_t>(T, 1));
+    sb->screen_work = nullptr;
+  } else {
+    sb->part = ScanPart{nullptr, nullptr, 0};
+    sb->screen_work =
+        lay.template take<char>(screen_workspace(T, B->n, A->d, static_cast<int>(R), c->sm_count, sb->screen));
+  }
+}
+
+static void run_scan(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t T, const ch_set* B, int metric,
+                     uint32_t R, ScanBufs* sb, float* m, int64_t* argmin, uint32_t* status) {
+  if (T == 0) return;
+  if (sb->screen == CH_SCREEN_EXACT) {
+    launch_scan_exact(A, idx, T, B, metric, sb->part, c->sm_count, c->stream);
+    launch_scan_merge(sb->part, T, idx, m, argmin, c->stream);
+  } else {
+    launch_screen_l2(A, idx, T, B, sb->screen, static_cast<int>(R), sb->screen_work, m, argmin, status, c->sm_count,
+                     c->stream);
+  }
+}
+
+static int64_t default_T(int64_t nA, int64_t nB, double eps) {
+  int64_t n = std::max<int64_t>(std::max(nA, nB), 2);
+  return static_cast<int64_t>(std::ceil(4.0 * std::log(static_cast<double>(n)) / (eps * eps)));
+}
+
+static ch_status fail(ch_ctx* c, const Err& e) {
+  if (c) c->err = e.msg;
+  return e.st;
+}
+
+}  // namespace chx
+
+#define CHX_GUARD_BEGIN(ctxp) \
+  ch_ctx* ctx_ = (ctxp);      \
+  try {
+#define CHX_GUARD_END                                  \
+  }                                                    \
+  catch (const ::chx::Err& e) {                        \
+    return ::chx::fail(ctx_, e);                       \
+  }                                                    \
+  catch (const std::bad_alloc&) {                      \
+    return ::chx::fail(ctx_, {CH_ENOMEM, "host allocation failed"}); \
+  }                                                    \
+  catch (...) {                                        \
+    return ::chx::fail(ctx_, {CH_ECUDA, "unexpected internal error"}); \
+  }
+
+extern "C" {
+
+int64_t ch_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void ch_default_params(ch_est_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->hash.metric = CH_L1;
+  p->hash.levels = 10;
+  p->hash.proj_dim = 16;
+  p->hash.top_exp = CH_TOP_EXP_AUTO;
+  p->hash.hash_seed = 0;
+  p->hash.group = CH_GROUP_HASH;
+  p->eps = 0.1;
+  p->T = 0;
+  p->sample_seed = 0;
+  p->screen = CH_SCREEN_AUTO;
+  p->rerank_k = 8;
+}
+
+ch_status ch_ctx_create(int device, void* stream, ch_ctx** out) {
+  if (!out) return CH_EINVAL;
+  ch_ctx* c = new (std::nothrow) ch_ctx();
+  if (!c) return CH_ENOMEM;
+  CHX_GUARD_BEGIN(c)
+  int ndev = 0;
+  CHX_CUDA(cudaGetDeviceCount(&ndev));
+  CHX_CHECK(device >= 0 && device < ndev, CH_EINVAL, "no such CUDA device");
+  c->device = device;
+  CHX_CUDA(cudaSetDevice(device));
+  CHX_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    CHX_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  CHX_CUDA(cudaMallocHost(&c->host_pin, 4096));
+  for (auto& e : c->ev) CHX_CUDA(cudaEventCreate(&e));
+  *out = c;
+  return CH_OK;
+  }
+  catch (const ::chx::Err& e) {
+    ch_ctx_destroy(c);
+    return e.st;
+  }
+  catch (...) {
+    ch_ctx_destroy(c);
+    return CH_ECUDA;
+  }
+}
+
+void ch_ctx_destroy(ch_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->ws.release();
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->host_pin) cudaFreeHost(c->host_pin);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* ch_last_error(const ch_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ch_status ch_ctx_sync(ch_ctx* c) {
+  if (!c) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  CHX_CUDA(cudaSetDevice(c->device));
+  CHX_CUDA(cudaStreamSynchronize(c->stream));
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+int64_t ch_ctx_workspace_bytes(const ch_ctx* c) { return c ? static_cast<int64_t>(c->ws.cap) : 0; }
+
+ch_status ch_set_create(ch_ctx* c, const void* data, int mode, int64_t n, int32_t d, int32_t dtype,
+                        const float* row_scales, ch_set** out) {
+  if (!c || !out) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  CHX_CHECK(n >= 0, CH_EINVAL, "n must be >= 0");
+  CHX_CHECK(d >= 1 && d <= kMaxDim, CH_EINVAL, "d must be in 1..4096");
+  CHX_CHECK(dtype == CH_F32 || dtype == CH_BF16 || dtype == CH_FP8E4M3, CH_EINVAL, "unknown dtype");
+  CHX_CHECK(mode >= 0 && mode <= 2, CH_EINVAL, "mode must be 0, 1 or 2");
+  CHX_CHECK(n == 0 || data, CH_EINVAL, "data NULL");
+  CHX_CHECK(dtype != CH_FP8E4M3 || n == 0 || row_scales, CH_EINVAL, "FP8 sets need row scales");
+  CHX_CUDA(cudaSetDevice(c->device));
+  ch_set* X = new ch_set();
+  X->ctx = c;
+  X->n = n;
+  X->d = d;
+  X->dtype = dtype;
+  const size_t bytes = size_t(n) * d * elem_size(dtype);
+  cudaStream_t s = c->stream;
+  try {
+    if (mode == 2) {
+      CHX_CHECK((reinterpret_cast<uintptr_t>(data) & 15) == 0, CH_EINVAL, "adopted data must be 16-byte aligned");
+      X->data = const_cast<void*>(data);
+      X->owned = false;
+    } else {
+      CHX_CUDA(cudaMallocAsync(&X->data, std::max<size_t>(bytes, 16), s));
+      X->owned = true;
+      if (bytes)
+        CHX_CUDA(cudaMemcpyAsync(X->data, data, bytes, mode == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                 s));
+    }
+    // aux: norms [n], status, box [2d], scales [n]
+    const size_t nb = (size_t(n) * 4 + 255) & ~size_t(255);
+    const size_t bb = (size_t(2) * d * 4 + 255) & ~size_t(255);
+    const size_t sb = dtype == CH_FP8E4M3 ? nb : 0;
+    char* aux = nullptr;
+    CHX_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&aux), nb + 256 + bb + sb, s));
+    X->norms = reinterpret_cast<float*>(aux);
+    X->status = reinterpret_cast<uint32_t*>(aux + nb);
+    X->box_x = reinterpret_cast<uint32_t*>(aux + nb + 256);
+    if (sb) {
+      X->scales = reinterpret_cast<float*>(aux + nb + 256 + bb);
+      if (n)
+        CHX_CUDA(cudaMemcpyAsync(X->scales, row_scales, size_t(n) * 4,
+                                 mode == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    }
+    CHX_CUDA(cudaMemsetAsync(X->status, 0, 4, s));
+    launch_ingest(X, s);
+  } catch (...) {
+    ch_set_destroy(X);
+    throw;
+  }
+  *out = X;
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+void ch_set_destroy(ch_set* X) {
+  if (!X) return;
+  ch_ctx* c = X->ctx;
+  cudaSetDevice(c->device);
+  if (X->owned && X->data) cudaFreeAsync(X->data, c->stream);
+  if (X->norms) cudaFreeAsync(X->norms, c->stream);
+  delete X;
+}
+
+int64_t ch_set_size(const ch_set* X) { return X ? X->n : -1; }
+int32_t ch_set_dim(const ch_set* X) { return X ? X->d : -1; }
+
+ch_status ch_top_exp(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash_params* hp, int32_t* e_top) {
+  if (!c || !e_top) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  check_hash(hp);
+  check_pair(c, A, B);
+  CHX_CUDA(cudaSetDevice(c->device));
+  Hashed hA, hB;
+  ScaleTables tab;
+  ResBlock* res = nullptr;
+  const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
+  int32_t* et = nullptr;
+  carve(c, [&](auto& lay) {
+    res = lay.template take<ResBlock>(1);
+    take_hashed(lay, A, hp, &hA);
+    take_hashed(lay, B, hp, &hB);
+    tab = take_tables(lay, dd, static_cast<int>(hp->levels));
+    et = lay.template take<int32_t>(1);
+  });
+  cudaStream_t s = c->stream;
+  CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
+  run_hashed(c, A, hp, &hA, &res->status);
+  run_hashed(c, B, hp, &hB, &res->status);
+  launch_scale_tables(hA.box, hB.box, dd, static_cast<int>(hp->levels), hp->top_exp, hp->hash_seed, tab, et,
+                      &res->status, s);
+  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, nullptr, nullptr, nullptr, et);
+  launch_check("collect");
+  ResBlock* h = static_cast<ResBlock*>(c->host_pin);
+  finish(c, res, h);
+  *e_top = h->e_top;
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+ch_status ch_hash_keys(ch_ctx* c, const ch_set* X, const ch_hash_params* hp, int32_t e_lo, uint64_t* keys) {
+  if (!c || !X || !keys) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  check_hash(hp);
+  CHX_CHECK(X->ctx == c, CH_EINVAL, "set belongs to another context");
+  const int L = static_cast<int>(hp->levels);
+  CHX_CHECK(e_lo >= -120 && e_lo + L - 1 <= 120, CH_EINVAL, "scale exponents outside [-120, 120]");
+  CHX_CUDA(cudaSetDevice(c->device));
+  Hashed h;
+  ScaleTables tab;
+  uint32_t* st = nullptr;
+  const int dd = hp->metric == CH_L1 ? X->d : static_cast<int>(hp->proj_dim);
+  carve(c, [&](auto& lay) {
+    st = lay.template take<uint32_t>(1);
+    take_hashed(lay, X, hp, &h);
+    tab = take_tables(lay, dd, L);
+  });
+  cudaStream_t s = c->stream;
+  CHX_CUDA(cudaMemsetAsync(st, 0, 4, s));
+  run_hashed(c, X, hp, &h, st);
+  launch_scale_tables(h.box, h.box, dd, L, e_lo + L - 1, hp->hash_seed, tab, nullptr, st, s);
+  launch_keys_write(h.src, L, tab, keys, s);
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+ch_status ch_crude_nn(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash_params* hp, int64_t* b_idx, float* D,
+                      uint8_t* level) {
+  if (!c) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  check_hash(hp);
+  check_pair(c, A, B);
+  CHX_CHECK(A->n == 0 || (b_idx && D), CH_EINVAL, "output NULL");
+  CHX_CUDA(cudaSetDevice(c->device));
+  if (A->n == 0) return CH_OK;
+  CrudeBufs cb;
+  uint32_t* st = nullptr;
+  uint8_t* lv = level;
+  carve(c, [&](auto& lay) {
+    st = lay.template take<uint32_t>(1);
+    take_crude(lay, A, B, hp, &cb);
+    uint8_t* tmp = lay.template take<uint8_t>(size_t(A->n));
+    if (!level) lv = tmp;
+  });
+  CHX_CUDA(cudaMemsetAsync(st, 0, 4, c->stream));
+  run_crude(c, A, B, hp, &cb, b_idx, lv, D, st);
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+ch_status ch_sample(ch_ctx* c, const float* D, int64_t nA, int64_t T, uint64_t seed, int64_t* idx, uint64_t* w,
+                    uint64_t* W_total) {
+  if (!c) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  CHX_CHECK(nA >= 0 && T >= 0, CH_EINVAL, "nA and T must be >= 0");
+  CHX_CHECK(nA == 0 || D, CH_EINVAL, "D NULL");
+  CHX_CHECK(T == 0 || idx, CH_EINVAL, "idx NULL");
+  CHX_CUDA(cudaSetDevice(c->device));
+  SampleBufs sb;
+  uint64_t* wbuf = w;
+  ResBlock* res = nullptr;
+  carve(c, [&](auto& lay) {
+    res = lay.template take<ResBlock>(1);
+    take_sample(lay, nA, &sb);
+    uint64_t* tmp = lay.template take<uint64_t>(std::max<int64_t>(nA, 1));
+    if (!w) wbuf = tmp;
+  });
+  cudaStream_t s = c->stream;
+  launch_weights(D, nA, wbuf, sb.prefix, sb.sw, s);
+  if (nA == 0) {
+    CHX_CUDA(cudaMemsetAsync(idx, 0xFF, size_t(T) * sizeof(int64_t), s));
+  } else {
+    launch_draws(sb.prefix, nA, sb.sw.W, T, seed, idx, s);
+  }
+  if (W_total) {
+    CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
+    k_collect<<<1, 32, 0, s>>>(res, nullptr, nullptr, nullptr, sb.sw.W, sb.sw.S, nullptr);
+    launch_check("collect");
+    ResBlock* h = static_cast<ResBlock*>(c->host_pin);
+    finish(c, res, h);
+    *W_total = h->W;
+  }
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+ch_status ch_sampled_nn(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t T, const ch_set* B, int32_t metric,
+                        int32_t screen, uint32_t rerank_k, float* min_d, int64_t* argmin) {
+  if (!c) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  check_pair(c, A, B);
+  CHX_CHECK(metric == CH_L1 || metric == CH_L2, CH_EINVAL, "metric must be CH_L1 or CH_L2");
+  CHX_CHECK(T >= 0, CH_EINVAL, "T must be >= 0");
+  CHX_CHECK(T == 0 || (idx && min_d), CH_EINVAL, "idx or min_d NULL");
+  CHX_CHECK(screen >= CH_SCREEN_AUTO && screen <= CH_SCREEN_FP8, CH_EINVAL, "unknown screen");
+  if (rerank_k == 0) rerank_k = 8;
+  CHX_CHECK(rerank_k <= 32, CH_EINVAL, "rerank_k must be in 1..32");
+  CHX_CUDA(cudaSetDevice(c->device));
+  ScanBufs sc;
+  uint32_t* st = nullptr;
+  carve(c, [&](auto& lay) {
+    st = lay.template take<uint32_t>(1);
+    take_scan(lay, c, A, B, T, metric, screen, rerank_k, &sc);
+  });
+  CHX_CUDA(cudaMemsetAsync(st, 0, 4, c->stream));
+  run_scan(c, A, idx, T, B, metric, rerank_k, &sc, min_d, argmin, st);
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, double* eta,
+                      ch_est_report* rep) {
+  if (!c || !p || !eta) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  check_hash(&p->hash);
+  check_pair(c, A, B);
+  CHX_CHECK(p->screen >= CH_SCREEN_AUTO && p->screen <= CH_SCREEN_FP8, CH_EINVAL, "unknown screen");
+  const uint32_t R = p->rerank_k ? p->rerank_k : 8;
+  CHX_CHECK(R <= 32, CH_EINVAL, "rerank_k must be in 1..32");
+  CHX_CHECK(p->T >= 0, CH_EINVAL, "T must be >= 0");
+  CHX_CHECK(p->T > 0 || (p->eps > 0.0 && p->eps < 1.0), CH_EINVAL, "eps must be in (0, 1)");
+  CHX_CUDA(cudaSetDevice(c->device));
+  const int64_t nA = A->n, nB = B->n;
+  const int64_t T = p->T > 0 ? p->T : default_T(nA, nB, p->eps);
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->T = T;
+  }
+  if (nA == 0) {
+    *eta = 0.0;
+    return CH_OK;
+  }
+  CrudeBufs cb;
+  SampleBufs sb;
+  ScanBufs sc;
+  ResBlock* res = nullptr;
+  int64_t *bidx = nullptr, *idx = nullptr;
+  uint8_t* level = nullptr;
+  float *D = nullptr, *m = nullptr;
+  uint64_t* w = nullptr;
+  double* out2 = nullptr;
+  carve(c, [&](auto& lay) {
+    res = lay.template take<ResBlock>(1);
+    out2 = lay.template take<double>(2);
+    take_crude(lay, A, B, &p->hash, &cb);
+    bidx = lay.template take<int64_t>(nA);
+    level = lay.template take<uint8_t>(nA);
+    D = lay.template take<float>(nA);
+    take_sample(lay, nA, &sb);
+    w = lay.template take<uint64_t>(nA);
+    idx = lay.template take<int64_t>(std::max<int64_t>(T, 1));
+    m = lay.template take<float>(std::max<int64_t>(T, 1));
+    take_scan(lay, c, A, B, T, p->hash.metric, p->screen, R, &sc);
+  });
+  cudaStream_t s = c->stream;
+  if (rep) CHX_CUDA(cudaEventRecord(c->ev[0], s));
+  CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
+  run_crude(c, A, B, &p->hash, &cb, bidx, level, D, &res->status);
+  if (rep) CHX_CUDA(cudaEventRecord(c->ev[1], s));
+  launch_weights(D, nA, w, sb.prefix, sb.sw, s);
+  launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, idx, s);
+  if (rep) CHX_CUDA(cudaEventRecord(c->ev[2], s));
+  run_scan(c, A, idx, T, B, p->hash.metric, R, &sc, m, nullptr, &res->status);
+  if (rep) CHX_CUDA(cudaEventRecord(c->ev[3], s));
+  launch_combine(m, idx, w, sb.sw.W, T, D, nA, out2, s);
+  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, out2, sb.sw.W, sb.sw.S, cb.e_top);
+  launch_check("collect");
+  if (rep) CHX_CUDA(cudaEventRecord(c->ev[4], s));
+  ResBlock* h = static_cast<ResBlock*>(c->host_pin);
+  finish(c, res, h);
+  *eta = h->eta;
+  if (rep) {
+    rep->eta = h->eta;
+    rep->D_total = h->D_total;
+    rep->W = h->W;
+    rep->top_exp = h->e_top;
+    rep->shift_S = h->S;
+    cudaEventElapsedTime(&rep->t_crude_ms, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&rep->t_sample_ms, c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&rep->t_scan_ms, c->ev[2], c->ev[3]);
+    cudaEventElapsedTime(&rep->t_total_ms, c->ev[0], c->ev[4]);
+  }
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+ch_status ch_exact(ch_ctx* c, const ch_set* A, const ch_set* B, int32_t metric, int32_t mode, double* ch,
+                   float* per_a_min) {
+  if (!c || !ch) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  check_pair(c, A, B);
+  CHX_CHECK(metric == CH_L1 || metric == CH_L2, CH_EINVAL, "metric must be CH_L1 or CH_L2");
+  CHX_CHECK(mode == 0 || mode == 1, CH_EINVAL, "mode must be 0 or 1");
+  CHX_CUDA(cudaSetDevice(c->device));
+  const int64_t nA = A->n;
+  ScanBufs sc;
+  ResBlock* res = nullptr;
+  float* mins = per_a_min;
+  double* out2 = nullptr;
+  carve(c, [&](auto& lay) {
+    res = lay.template take<ResBlock>(1);
+    out2 = lay.template take<double>(2);
+    take_scan(lay, c, A, B, nA, metric, mode == 0 ? CH_SCREEN_EXACT : CH_SCREEN_AUTO, 8, &sc);
+    float* tmp = lay.template take<float>(std::max<int64_t>(nA, 1));
+    if (!per_a_min) mins = tmp;
+  });
+  cudaStream_t s = c->stream;
+  CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
+  CHX_CUDA(cudaMemsetAsync(out2, 0, 2 * sizeof(double), s));
+  if (nA > 0) {
+    run_scan(c, A, nullptr, nA, B, metric, 8, &sc, mins, nullptr, &res->status);
+    launch_sum_f32(mins, nA, out2, s);
+  }
+  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, out2, nullptr, nullptr, nullptr);
+  launch_check("collect");
+  ResBlock* h = static_cast<ResBlock*>(c->host_pin);
+  finish(c, res, h);
+  *ch = h->D_total;
+  return CH_OK;
+  CHX_GUARD_END
+}
+
+}  // extern "C"

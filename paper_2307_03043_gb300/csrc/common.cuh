@@ -1,0 +1,303 @@
+// common.cuh -- shared definitions of libchamfer's CUDA sources.
+//
+// Exactness rules for every kernel whose result must match the canonical
+// definition bit for bit: binary32 round-to-nearest intrinsics only
+// (__fadd_rn, __fsub_rn, __fmul_rn, __fmaf_rn, __fsqrt_rn), which the
+// compiler never contracts or reassociates; no fast-math; denormals kept
+// (the library is built with -ftz=false -prec-div=true -prec-sqrt=true).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include <string>
+
+#include "../../include/chamfer.h"
+
+namespace chx {
+
+constexpr int kMaxLevels = 32;   // L <= 32 (keys kept in registers in blocks of 16)
+constexpr int kMaxProj = 64;     // l2 embedding width k <= 64
+constexpr int kMaxDim = 4096;    // point dimension supported by the kernels
+constexpr int kLevelBlock = 16;  // scales handled per register block
+
+// ------------------------------------------------------------------ errors
+struct Err {
+  ch_status st;
+  std::string msg;
+};
+
+#define CHX_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      throw ::chx::Err{CH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define CHX_CHECK(cond, code, text)                 \
+  do {                                              \
+    if (!(cond)) throw ::chx::Err{(code), (text)};  \
+  } while (0)
+
+// kernels launched by this process through the library (for launch accounting)
+void count_launch();
+
+inline void launch_check(const char* what) {
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Err{CH_ECUDA, std::string("launch ") + what + ": " + cudaGetErrorString(e)};
+}
+
+// device status bits (written by kernels, read back by synchronising calls)
+enum : uint32_t {
+  ST_NONFINITE = 1u << 0,   // a set holds NaN or Inf
+  ST_RANGE = 1u << 1,       // scale exponents outside the supported range
+  ST_TABLE_FULL = 1u << 2,  // a hash table probe sequence exceeded its bound
+  ST_TIMEOUT = 1u << 3,     // a bounded device wait gave up
+  ST_BAD_INDEX = 1u << 4,   // an index argument was out of range
+};
+
+// ------------------------------------------------------------------ workspace
+// Grow-only device arena; one per context (and one per serving slot).
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  void reserve(size_t bytes);  // synchronises the device if it must grow
+  void release();
+  void reset() { used = 0; }
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (used + bytes > cap) throw Err{CH_ENOMEM, "workspace arena overflow (internal sizing error)"};
+    T* p = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+};
+
+}  // namespace chx
+
+// hashed representation of a set for one (metric, seed, k)
+struct chx_hashed {
+  bool valid = false;
+  int metric = 0;
+  uint64_t seed = 0;
+  int k = 0;
+  float* Y = nullptr;         // l2: projection [n][k]; l1: unused (the set's own data)
+  uint32_t* box = nullptr;    // ordered-encoded [2][dd]: min then max per hashed coordinate
+};
+
+struct ch_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  chx::Arena ws;
+  void* host_pin = nullptr;   // pinned page for small readbacks
+  std::string err;
+  cudaEvent_t ev[8] = {};
+};
+
+struct ch_set {
+  ch_ctx* ctx = nullptr;
+  void* data = nullptr;
+  bool owned = false;
+  int64_t n = 0;
+  int32_t d = 0;
+  int32_t dtype = CH_F32;
+  float* scales = nullptr;     // FP8 row scales (device, owned)
+  float* norms = nullptr;      // |x|^2 per row (device, owned), binary32
+  uint32_t* status = nullptr;  // device status word (ST_* bits)
+  uint32_t* box_x = nullptr;   // ordered-encoded [2][d] bounding box of x (l1 hashed space)
+  chx_hashed hs;               // cached l2 embedding
+};
+
+namespace chx {
+
+// ------------------------------------------------------------------ RNG
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products of counter words 0 and 2 with the published
+// multipliers, the key advancing by the Weyl constants between rounds.
+struct P4 {
+  uint32_t x, y, z, w;
+};
+
+__host__ __device__ inline P4 philox10(P4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t m0 = 0xD2511F53ull * c.x;
+    const uint64_t m1 = 0xCD9E8D57ull * c.z;
+    P4 n;
+    n.x = static_cast<uint32_t>(m1 >> 32) ^ c.y ^ k0;
+    n.y = static_cast<uint32_t>(m1);
+    n.z = static_cast<uint32_t>(m0 >> 32) ^ c.w ^ k1;
+    n.w = static_cast<uint32_t>(m0);
+    c = n;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// splitmix64 finaliser (Steele, Lea, Flood 2014; Vigna's variant constants)
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------------ float helpers
+// order-preserving map binary32 -> uint32 (for atomic min / max of floats)
+__host__ __device__ inline uint32_t ord_enc(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float ord_dec(uint32_t u) {
+  uint32_t v = (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+  float f;
+  memcpy(&f, &v, 4);
+  return f;
+}
+
+// exact 2^e as binary32 for -126 <= e <= 127
+__device__ inline float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// E4M3 (OCP FP8, no infinities) code -> binary32, exact
+__device__ inline float e4m3_to_f32(uint8_t b) {
+  const uint32_t s = (b & 0x80u) << 24;
+  const uint32_t e = (b >> 3) & 0xFu;
+  const uint32_t m = b & 7u;
+  if (e == 0xFu && m == 7u) return __int_as_float(0x7FC00000u);
+  if (e == 0) {
+    float v = __fmul_rn(static_cast<float>(m), 1.0f / 512.0f);
+    return s ? -v : v;
+  }
+  return __int_as_float(s | ((e + 120u) << 23) | (m << 20));
+}
+
+__device__ inline float bf16_to_f32(uint16_t h) { return __int_as_float(static_cast<uint32_t>(h) << 16); }
+
+// element j of row r of a set stored as DT, widened to binary32 exactly
+template <int DT>
+__device__ inline float load_elem(const void* base, int64_t r, int d, int j, const float* scales) {
+  if constexpr (DT == CH_F32) {
+    return static_cast<const float*>(base)[r * d + j];
+  } else if constexpr (DT == CH_BF16) {
+    return bf16_to_f32(static_cast<const uint16_t*>(base)[r * d + j]);
+  } else {
+    return __fmul_rn(e4m3_to_f32(static_cast<const uint8_t*>(base)[r * d + j]), scales[r]);
+  }
+}
+
+__host__ __device__ inline int ceil_log2_i64(int64_t n) {
+  int c = 0;
+  while ((int64_t(1) << c) < n) ++c;
+  return c;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline uint32_t next_pow2_u32(uint64_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+size_t elem_size(int dtype);
+
+// ------------------------------------------------------------------ launchers
+// (defined in the kernel .cu files; all enqueue on `s` and never synchronise)
+
+// ingest: finite check, |x|^2, bounding box of x (ordered-encoded, [2][d])
+void launch_ingest(const ch_set* X, cudaStream_t s);
+
+// l2 embedding of X with G = Irwin-Hall Gaussian (k x d): Y [n][k], box [2][k]
+void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, uint32_t* status,
+                    int sm_count, cudaStream_t s);
+
+// Tables of one CrudeNN call (device): scales, shifts, multipliers
+struct ScaleTables {
+  int32_t* e_lo;         // [1] finest exponent
+  float* inv_r;          // [L] 2^-e
+  uint64_t* salt;        // [L] mix64((uint32)e ^ seed)
+  float* shift;          // [dd][L] z_{e,j}, coordinate-major
+  uint64_t* mult;        // [dd] odd multipliers
+};
+
+// computes e_top from the two boxes (or uses top_exp) then fills the tables
+void launch_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int dd, int L, int top_exp_in,
+                         uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status, cudaStream_t s);
+
+// hashed-space source of a set: DT-typed rows (l1) or the binary32 embedding (l2)
+struct HashSrc {
+  const void* base;
+  int dtype;
+  int64_t n;
+  int dd;
+  const float* scales;
+};
+
+struct HashTable {
+  ulonglong2* slots;  // [L][cap] : x = key (0 = empty), y = ~min b index
+  uint32_t log_cap;
+};
+
+// bucket tables of the scales [L0, L0+nl) (one table of 2^log_cap slots per scale)
+void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status,
+                         cudaStream_t s);
+void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
+                        uint8_t* level, cudaStream_t s);
+void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStream_t s);
+
+// radix-sort grouping (CH_GROUP_SORT): keys [L][nA] and [L][nB] -> bidx, level
+size_t sort_group_workspace(int64_t nA, int64_t nB, int L);
+void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L,
+                       void* work, int64_t* bidx, uint8_t* level, cudaStream_t s);
+
+// D_a = canonical d(a, B[b(a)])
+void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D,
+                       cudaStream_t s);
+
+// sampling
+struct SampleWork {
+  uint32_t* maxD;        // [1] ordered-encoded max
+  uint64_t* blocksum;    // [nblocks]
+  uint64_t* W;           // [1]
+  int32_t* S;            // [1]
+};
+size_t sample_blocks(int64_t nA);
+void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s);
+void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed,
+                  int64_t* idx, cudaStream_t s);
+
+// exact scan: per (sample, chunk) minima, then merge
+struct ScanPart {
+  float* val;
+  int64_t* idx;
+  int chunks;
+};
+void launch_scan_exact(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int metric, ScanPart part,
+                       int sm_count, cudaStream_t s);
+void launch_scan_merge(ScanPart part, int64_t T, const int64_t* qidx, float* min_d, int64_t* argmin,
+                       cudaStream_t s);
+int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count);
+
+// tensor-core screen + rerank (l2)
+bool screen_supported(int screen, const ch_set* A, const ch_set* B);
+size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int screen);
+void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R,
+                      void* work, float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s);
+
+// combine: eta = (1/T) sum m_l W / w_{x_l} (binary64) and sum D (binary64)
+void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
+                    const float* D, int64_t nA, double* out2, cudaStream_t s);
+// sum of per-a minima (binary64)
+void launch_sum_f32(const float* v, int64_t n, double* out2 /* out2[1] = sum */, cudaStream_t s);
+
+}  // namespace chx

@@ -1,0 +1,513 @@
+// k_hash.cu -- CrudeNN on the device (Fig. 2 of the paper): set ingest, the
+// l2 -> l1 Gaussian embedding, the shifted grids at every scale, bucket
+// tables of B probed by A in increasing scale order, and D_a = d(a, b(a)).
+#include <cstring>
+
+#include "common.cuh"
+
+namespace chx {
+
+size_t elem_size(int dtype) { return dtype == CH_F32 ? 4 : dtype == CH_BF16 ? 2 : 1; }
+
+// ------------------------------------------------------------------ ingest
+// One warp per row: finite check, |x|^2 (any order; used only by the tensor-core
+// screen), per-coordinate min/max of x.  CB = column blocks of 32 kept in
+// registers (0 = shared-memory atomics for large d).
+template <int DT, int CB>
+__global__ void __launch_bounds__(256) k_ingest(const void* X, const float* scales, int64_t n, int d,
+                                                float* norms, uint32_t* box, uint32_t* status) {
+  extern __shared__ uint32_t s_box[];  // [2][d]
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    s_box[c] = 0xFFFFFFFFu;
+    s_box[d + c] = 0u;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int warps = blockDim.x >> 5;
+  uint32_t lo[CB > 0 ? CB : 1], hi[CB > 0 ? CB : 1];
+#pragma unroll
+  for (int b = 0; b < (CB > 0 ? CB : 1); ++b) {
+    lo[b] = 0xFFFFFFFFu;
+    hi[b] = 0u;
+  }
+  bool bad = false;
+  for (int64_t r = int64_t(blockIdx.x) * warps + warp; r < n; r += int64_t(gridDim.x) * warps) {
+    float sq = 0.0f;
+    if constexpr (CB > 0) {
+#pragma unroll
+      for (int b = 0; b < CB; ++b) {
+        const int c = b * 32 + lane;
+        if (c < d) {
+          const float v = load_elem<DT>(X, r, d, c, scales);
+          bad |= !isfinite(v);
+          sq = fmaf(v, v, sq);
+          const uint32_t o = ord_enc(v);
+          lo[b] = min(lo[b], o);
+          hi[b] = max(hi[b], o);
+        }
+      }
+    } else {
+      for (int c = lane; c < d; c += 32) {
+        const float v = load_elem<DT>(X, r, d, c, scales);
+        bad |= !isfinite(v);
+        sq = fmaf(v, v, sq);
+        const uint32_t o = ord_enc(v);
+        atomicMin(&s_box[c], o);
+        atomicMax(&s_box[d + c], o);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xFFFFFFFFu, sq, o);
+    if (lane == 0) norms[r] = sq;
+  }
+  if constexpr (CB > 0) {
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int c = b * 32 + lane;
+      if (c < d && lo[b] <= hi[b]) {
+        atomicMin(&s_box[c], lo[b]);
+        atomicMax(&s_box[d + c], hi[b]);
+      }
+    }
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
+  __syncthreads();
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    if (s_box[c] <= s_box[d + c]) {
+      atomicMin(&box[c], s_box[c]);
+      atomicMax(&box[d + c], s_box[d + c]);
+    }
+  }
+}
+
+template <int DT>
+static void ingest_dt(const ch_set* X, cudaStream_t s, int grid) {
+  const int d = X->d;
+  const size_t smem = size_t(2) * d * sizeof(uint32_t);
+  const int cb = (d + 31) / 32;
+#define CHX_INGEST(CBV) \
+  k_ingest<DT, CBV><<<grid, 256, smem, s>>>(X->data, X->scales, X->n, d, X->norms, X->box_x, X->status)
+  if (cb <= 1) CHX_INGEST(1);
+  else if (cb <= 2) CHX_INGEST(2);
+  else if (cb <= 4) CHX_INGEST(4);
+  else if (cb <= 8) CHX_INGEST(8);
+  else if (cb <= 16) CHX_INGEST(16);
+  else CHX_INGEST(0);
+#undef CHX_INGEST
+}
+
+void launch_ingest(const ch_set* X, cudaStream_t s) {
+  CHX_CUDA(cudaMemsetAsync(X->box_x, 0xFF, size_t(X->d) * 4, s));
+  CHX_CUDA(cudaMemsetAsync(X->box_x + X->d, 0, size_t(X->d) * 4, s));
+  if (X->n == 0) return;
+  const int grid = static_cast<int>(std::min<int64_t>(ceil_div(X->n, 8), 152 * 8));
+  switch (X->dtype) {
+    case CH_F32: ingest_dt<CH_F32>(X, s, grid); break;
+    case CH_BF16: ingest_dt<CH_BF16>(X, s, grid); break;
+    default: ingest_dt<CH_FP8E4M3>(X, s, grid); break;
+  }
+  launch_check("ingest");
+}
+
+// ------------------------------------------------------------------ l2 embedding
+// Z_ij: 12-term Irwin-Hall normal from Philox counters (j, i, 2, m), m < 3,
+// summed exactly, centred, scaled by 2^-32 and rounded once to binary32
+// (the l2 -> l1 embedding theorem of App. A.2 with the 1/(beta k) factor left out).
+__global__ void k_gauss(uint64_t seed, int k, int kp, int d, float* G /* [d][kp], zero rows i >= k */) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(kp) * d) return;
+  const int i = static_cast<int>(t % kp);
+  const int j = static_cast<int>(t / kp);
+  float g = 0.0f;
+  if (i < k) {
+    uint64_t sum = 0;
+    for (uint32_t m = 0; m < 3; ++m) {
+      const P4 w = philox10(P4{uint32_t(j), uint32_t(i), 2u, m}, uint32_t(seed), uint32_t(seed >> 32));
+      sum += uint64_t(w.x) + w.y + w.z + w.w;
+    }
+    const int64_t centred = static_cast<int64_t>(sum) - int64_t(6) * 4294967296LL;
+    g = __double2float_rn(ldexp(static_cast<double>(centred), -32));
+  }
+  G[t] = g;
+}
+
+// Thread per row; rows staged through shared memory 32 coordinates at a time
+// (coalesced 128-byte row segments), y_i = fmaf chain over j in increasing order.
+template <int DT, int KP>
+__global__ void __launch_bounds__(128) k_project(const void* X, const float* scales, int64_t n, int d,
+                                                 const float* G, int k, float* Y, uint32_t* box) {
+  __shared__ float s_x[128][33];
+  __shared__ float s_g[32][KP];
+  const int64_t r0 = int64_t(blockIdx.x) * 128;
+  const int tid = threadIdx.x;
+  const int64_t r = r0 + tid;
+  float acc[KP];
+#pragma unroll
+  for (int i = 0; i < KP; ++i) acc[i] = 0.0f;
+  for (int j0 = 0; j0 < d; j0 += 32) {
+    const int jn = min(32, d - j0);
+    __syncthreads();
+    // stage: warp w loads rows w, w+4, ...; lane = coordinate within the segment
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int rr = warp; rr < 128; rr += 4) {
+      const int64_t row = r0 + rr;
+      float v = 0.0f;
+      if (row < n && lane < jn) v = load_elem<DT>(X, row, d, j0 + lane, scales);
+      s_x[rr][lane] = v;
+    }
+    for (int t = tid; t < 32 * KP; t += 128) {
+      const int jj = t / KP, ii = t % KP;
+      s_g[jj][ii] = (jj < jn) ? G[int64_t(j0 + jj) * KP + ii] : 0.0f;
+    }
+    __syncthreads();
+    for (int jj = 0; jj < jn; ++jj) {
+      const float xv = s_x[tid][jj];
+#pragma unroll
+      for (int i = 0; i < KP; ++i) acc[i] = __fmaf_rn(s_g[jj][i], xv, acc[i]);
+    }
+  }
+  const bool live = r < n;
+  if (live)
+    for (int i = 0; i < k; ++i) Y[r * k + i] = acc[i];
+  // bounding box of the embedding
+  const int lane = tid & 31;
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    if (i < k) {
+      uint32_t lo = live ? ord_enc(acc[i]) : 0xFFFFFFFFu;
+      uint32_t hi = live ? ord_enc(acc[i]) : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+      }
+      if (lane == 0 && lo <= hi) {
+        atomicMin(&box[i], lo);
+        atomicMax(&box[k + i], hi);
+      }
+    }
+  }
+}
+
+template <int DT>
+static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y, uint32_t* box, cudaStream_t s) {
+  const int grid = static_cast<int>(ceil_div(X->n, 128));
+#define CHX_PROJ(KPV) k_project<DT, KPV><<<grid, 128, 0, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box)
+  if (kp == 8) CHX_PROJ(8);
+  else if (kp == 16) CHX_PROJ(16);
+  else if (kp == 32) CHX_PROJ(32);
+  else CHX_PROJ(64);
+#undef CHX_PROJ
+}
+
+void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, uint32_t* status, int sm_count,
+                    cudaStream_t s) {
+  (void)status;
+  (void)sm_count;
+  const int kp = k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64;
+  CHX_CUDA(cudaMemsetAsync(box, 0xFF, size_t(k) * 4, s));
+  CHX_CUDA(cudaMemsetAsync(box + k, 0, size_t(k) * 4, s));
+  if (X->n == 0) return;
+  // the Gaussian matrix lives in the tail of Y's allocation
+  float* G = Y + X->n * k;
+  const int64_t gn = int64_t(kp) * X->d;
+  k_gauss<<<static_cast<int>(ceil_div(gn, 256)), 256, 0, s>>>(seed, k, kp, X->d, G);
+  launch_check("gauss");
+  switch (X->dtype) {
+    case CH_F32: project_dt<CH_F32>(X, G, k, kp, Y, box, s); break;
+    case CH_BF16: project_dt<CH_BF16>(X, G, k, kp, Y, box, s); break;
+    default: project_dt<CH_FP8E4M3>(X, G, k, kp, Y, box, s); break;
+  }
+  launch_check("project");
+}
+
+// ------------------------------------------------------------------ scales
+// Delta = sum_j (max_j - min_j) over the joint box (binary64, coordinate order),
+// e_top = ceil(log2 Delta) + 1 (0 if Delta = 0); scales 2^e, e = e_top-L+1..e_top.
+// Shift z_{e,j} = (w0 >> 8) 2^(e-24), w0 = Philox(j, e, 1, 0).x; multiplier
+// K_j = Philox(j, 0, 4, 0).(y:x) | 1; salt_e = mix64((uint32)e ^ seed).
+__global__ void k_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int dd, int L, int top_exp_in,
+                               uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status) {
+  __shared__ int s_elo;
+  if (threadIdx.x == 0) {
+    int e_top;
+    if (top_exp_in != CH_TOP_EXP_AUTO) {
+      e_top = top_exp_in;
+    } else {
+      double delta = 0.0;
+      for (int j = 0; j < dd; ++j) {
+        const uint32_t lo = min(boxA[j], boxB[j]);
+        const uint32_t hi = max(boxA[dd + j], boxB[dd + j]);
+        delta += static_cast<double>(ord_dec(hi)) - static_cast<double>(ord_dec(lo));
+      }
+      if (delta == 0.0) {
+        e_top = 0;
+      } else {
+        int E;
+        const double m = frexp(delta, &E);
+        e_top = (m == 0.5 ? E - 1 : E) + 1;
+      }
+    }
+    int e_lo = e_top - L + 1;
+    if (e_lo < -120 || e_top > 120) {
+      atomicOr(status, ST_RANGE);
+      e_lo = 0;  // keep the tables well defined; the call reports CH_EINVAL
+    }
+    s_elo = e_lo;
+    t.e_lo[0] = e_lo;
+    if (e_top_out) *e_top_out = e_lo + L - 1;
+  }
+  __syncthreads();
+  const int e_lo = s_elo;
+  const uint32_t k0 = uint32_t(seed), k1 = uint32_t(seed >> 32);
+  for (int idx = threadIdx.x; idx < dd * L; idx += blockDim.x) {
+    const int j = idx / L, l = idx % L;
+    const int e = e_lo + l;
+    const P4 w = philox10(P4{uint32_t(j), uint32_t(e), 1u, 0u}, k0, k1);
+    t.shift[idx] = __double2float_rn(ldexp(static_cast<double>(w.x >> 8), e - 24));
+  }
+  for (int j = threadIdx.x; j < dd; j += blockDim.x) {
+    const P4 w = philox10(P4{uint32_t(j), 0u, 4u, 0u}, k0, k1);
+    t.mult[j] = ((uint64_t(w.y) << 32) | w.x) | 1ull;
+  }
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    const int e = e_lo + l;
+    t.inv_r[l] = pow2f(-e);
+    t.salt[l] = mix64(uint64_t(uint32_t(e)) ^ seed);
+  }
+}
+
+void launch_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int dd, int L, int top_exp_in, uint64_t seed,
+                         ScaleTables t, int32_t* e_top_out, uint32_t* status, cudaStream_t s) {
+  k_scale_tables<<<1, 256, 0, s>>>(boxA, boxB, dd, L, top_exp_in, seed, t, e_top_out, status);
+  launch_check("scale_tables");
+}
+
+// ------------------------------------------------------------------ keys
+// Keys of one point at scales L0 .. L0+nl-1 (nl <= 16):
+//   c_j = ceil((y_j + z_{e,j}) * 2^-e) + 0, h = sum_j bits(c_j) K_j mod 2^64,
+//   key = mix64(h + salt_e), 0 -> 1.
+template <int DT>
+__device__ inline void point_keys(const HashSrc& src, int64_t r, int L, int L0, int nl, const ScaleTables& t,
+                                  uint64_t (&key)[kLevelBlock]) {
+  uint64_t h[kLevelBlock];
+  float inv_r[kLevelBlock];
+#pragma unroll
+  for (int l = 0; l < kLevelBlock; ++l) {
+    h[l] = 0;
+    inv_r[l] = (l < nl) ? __ldg(&t.inv_r[L0 + l]) : 1.0f;
+  }
+  const int dd = src.dd;
+  for (int j = 0; j < dd; ++j) {
+    const float y = load_elem<DT>(src.base, r, dd, j, src.scales);
+    const uint64_t K = __ldg(reinterpret_cast<const unsigned long long*>(&t.mult[j]));
+    const uint32_t klo = uint32_t(K), khi = uint32_t(K >> 32);
+    const float* zrow = t.shift + int64_t(j) * L + L0;
+#pragma unroll
+    for (int l = 0; l < kLevelBlock; ++l) {
+      if (l < nl) {
+        const float z = __ldg(&zrow[l]);
+        float c = ceilf(__fmul_rn(__fadd_rn(y, z), inv_r[l]));
+        c = __fadd_rn(c, 0.0f);
+        const uint32_t bits = __float_as_uint(c);
+        h[l] += uint64_t(bits) * klo + (uint64_t(bits * khi) << 32);
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < kLevelBlock; ++l) {
+    if (l < nl) {
+      uint64_t k = mix64(h[l] + __ldg(reinterpret_cast<const unsigned long long*>(&t.salt[L0 + l])));
+      key[l] = k == 0 ? 1 : k;
+    }
+  }
+}
+
+__device__ inline uint32_t slot_home(uint64_t key, uint32_t log_cap) {
+  return log_cap == 0 ? 0u : static_cast<uint32_t>(key >> (64 - log_cap));
+}
+
+// Insert every b at every scale of the group [L0, L0+nl): bucket key -> min b.
+template <int DT>
+__global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0, int nl, ScaleTables t,
+                                                      HashTable h, uint32_t* status) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= src.n) return;
+  const uint32_t cap = 1u << h.log_cap;
+  for (int b0 = 0; b0 < nl; b0 += kLevelBlock) {
+    uint64_t key[kLevelBlock];
+    const int nb = min(kLevelBlock, nl - b0);
+    point_keys<DT>(src, r, L, L0 + b0, nb, t, key);
+    const unsigned long long want = ~static_cast<unsigned long long>(r);
+#pragma unroll
+    for (int l = 0; l < kLevelBlock; ++l) {
+      if (l >= nb) continue;
+      ulonglong2* tab = h.slots + size_t(b0 + l) * cap;
+      uint32_t pos = slot_home(key[l], h.log_cap);
+      bool done = false;
+      for (uint32_t it = 0; it < cap; ++it) {
+        unsigned long long* kp = &tab[pos].x;
+        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(kp);
+        if (cur == 0ull) {
+          cur = atomicCAS(kp, 0ull, static_cast<unsigned long long>(key[l]));
+          if (cur == 0ull) cur = key[l];
+        }
+        if (cur == key[l]) {
+          unsigned long long* vp = &tab[pos].y;
+          if (*reinterpret_cast<volatile unsigned long long*>(vp) < want) atomicMax(vp, want);
+          done = true;
+          break;
+        }
+        pos = (pos + 1) & (cap - 1);
+      }
+      if (!done) atomicOr(status, ST_TABLE_FULL);
+    }
+  }
+}
+
+// Each unresolved a walks the scales of the group in increasing order and stops
+// at the first bucket that holds a b (Fig. 2, step 3).
+template <int DT>
+__global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0, int nl, ScaleTables t,
+                                                     HashTable h, int64_t* bidx, uint8_t* level) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= src.n) return;
+  if (level[r] < L) return;  // resolved at a finer scale group
+  const uint32_t cap = 1u << h.log_cap;
+  for (int b0 = 0; b0 < nl; b0 += kLevelBlock) {
+    uint64_t key[kLevelBlock];
+    const int nb = min(kLevelBlock, nl - b0);
+    point_keys<DT>(src, r, L, L0 + b0, nb, t, key);
+#pragma unroll
+    for (int l = 0; l < kLevelBlock; ++l) {
+      if (l >= nb) continue;
+      const ulonglong2* tab = h.slots + size_t(b0 + l) * cap;
+      uint32_t pos = slot_home(key[l], h.log_cap);
+      for (uint32_t it = 0; it < cap; ++it) {
+        const ulonglong2 sl = tab[pos];
+        if (sl.x == key[l]) {
+          bidx[r] = static_cast<int64_t>(~sl.y);
+          level[r] = static_cast<uint8_t>(L0 + b0 + l);
+          return;
+        }
+        if (sl.x == 0ull) break;
+        pos = (pos + 1) & (cap - 1);
+      }
+    }
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(128) k_keys_write(HashSrc src, int L, ScaleTables t, uint64_t* keys) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= src.n) return;
+  for (int b0 = 0; b0 < L; b0 += kLevelBlock) {
+    uint64_t key[kLevelBlock];
+    const int nb = min(kLevelBlock, L - b0);
+    point_keys<DT>(src, r, L, b0, nb, t, key);
+#pragma unroll
+    for (int l = 0; l < kLevelBlock; ++l)
+      if (l < nb) keys[size_t(b0 + l) * src.n + r] = key[l];
+  }
+}
+
+void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStream_t s) {
+  if (X.n == 0) return;
+  const int grid = static_cast<int>(ceil_div(X.n, 128));
+  switch (X.dtype) {
+    case CH_F32: k_keys_write<CH_F32><<<grid, 128, 0, s>>>(X, L, t, keys); break;
+    case CH_BF16: k_keys_write<CH_BF16><<<grid, 128, 0, s>>>(X, L, t, keys); break;
+    default: k_keys_write<CH_FP8E4M3><<<grid, 128, 0, s>>>(X, L, t, keys); break;
+  }
+  launch_check("keys_write");
+}
+
+// group launchers used by the API (scales [L0, L0+nl) in one table set)
+void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status,
+                         cudaStream_t s) {
+  if (B.n == 0) return;
+  const int grid = static_cast<int>(ceil_div(B.n, 128));
+  switch (B.dtype) {
+    case CH_F32: k_table_insert<CH_F32><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
+    case CH_BF16: k_table_insert<CH_BF16><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
+    default: k_table_insert<CH_FP8E4M3><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
+  }
+  launch_check("table_insert");
+}
+
+void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
+                        uint8_t* level, cudaStream_t s) {
+  if (A.n == 0) return;
+  const int grid = static_cast<int>(ceil_div(A.n, 128));
+  switch (A.dtype) {
+    case CH_F32: k_table_probe<CH_F32><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
+    case CH_BF16: k_table_probe<CH_BF16><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
+    default: k_table_probe<CH_FP8E4M3><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
+  }
+  launch_check("table_probe");
+}
+
+// ------------------------------------------------------------------ crude distance
+// D_a = canonical d(a, B[b(a)]): G lanes per a (G = min(32, next pow2 of d)),
+// lane q sums coordinates j = q, q+32, ... in increasing j; then p_q += p_{q+s}
+// for s = G/2 .. 1 via shuffles (steps s >= G would add +0).
+template <int DTA, int DTB, int METRIC>
+__global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* scA, int64_t nA, const void* B,
+                                                    const float* scB, int d, int G, const int64_t* bidx,
+                                                    float* D) {
+  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t a = gt / G;
+  const int q = static_cast<int>(gt % G);
+  const bool live = a < nA;
+  float p = 0.0f;
+  if (live) {
+    const int64_t b = bidx[a];
+    for (int j = q; j < d; j += 32) {
+      const float t = __fsub_rn(load_elem<DTA>(A, a, d, j, scA), load_elem<DTB>(B, b, d, j, scB));
+      if (METRIC == CH_L1)
+        p = __fadd_rn(p, fabsf(t));
+      else
+        p = __fmaf_rn(t, t, p);
+    }
+  }
+  for (int s = G >> 1; s >= 1; s >>= 1) {
+    const float o = __shfl_down_sync(0xFFFFFFFFu, p, s, G);
+    p = __fadd_rn(p, o);
+  }
+  if (live && q == 0) D[a] = (METRIC == CH_L1) ? p : __fsqrt_rn(p);
+}
+
+template <int DTA, int DTB>
+static void crude_dist_2(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, int G,
+                         int grid, cudaStream_t s) {
+  if (metric == CH_L1)
+    k_crude_dist<DTA, DTB, CH_L1><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D);
+  else
+    k_crude_dist<DTA, DTB, CH_L2><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D);
+}
+
+template <int DTA>
+static void crude_dist_1(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, int G,
+                         int grid, cudaStream_t s) {
+  switch (B->dtype) {
+    case CH_F32: crude_dist_2<DTA, CH_F32>(A, B, metric, bidx, D, G, grid, s); break;
+    case CH_BF16: crude_dist_2<DTA, CH_BF16>(A, B, metric, bidx, D, G, grid, s); break;
+    default: crude_dist_2<DTA, CH_FP8E4M3>(A, B, metric, bidx, D, G, grid, s); break;
+  }
+}
+
+void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, cudaStream_t s) {
+  if (A->n == 0) return;
+  int G = 1;
+  while (G < A->d && G < 32) G <<= 1;
+  const int grid = static_cast<int>(ceil_div(A->n * G, 256));
+  switch (A->dtype) {
+    case CH_F32: crude_dist_1<CH_F32>(A, B, metric, bidx, D, G, grid, s); break;
+    case CH_BF16: crude_dist_1<CH_BF16>(A, B, metric, bidx, D, G, grid, s); break;
+    default: crude_dist_1<CH_FP8E4M3>(A, B, metric, bidx, D, G, grid, s); break;
+  }
+  launch_check("crude_dist");
+}
+
+}  // namespace chx

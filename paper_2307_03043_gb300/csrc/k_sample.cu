@@ -1,0 +1,216 @@
+// k_sample.cu -- importance sampling (Fig. 1, steps 2-3) and the estimate
+// (Fig. 1, step 4) on the device.
+//
+// Pr[x = a] = D_a / D is realised with 64-bit fixed-point weights
+// w_a = ceil(D_a 2^S), S = 62 - ceil(log2 nA) - e_M (max D_a < 2^e_M), an exact
+// integer inclusive prefix, and inverse-CDF draws from 128-bit Philox words.
+#include "common.cuh"
+
+namespace chx {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;  // elements per block
+
+size_t sample_blocks(int64_t nA) { return static_cast<size_t>(ceil_div(nA, kScanTile)); }
+
+__global__ void k_max_d(const float* D, int64_t n, uint32_t* maxD) {
+  uint32_t m = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    m = max(m, ord_enc(D[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxD, m);
+}
+
+__device__ inline int weight_shift(const uint32_t* maxD, int64_t nA, bool* zero) {
+  const float M = ord_dec(*maxD);
+  if (!(M > 0.0f)) {
+    *zero = true;
+    return 0;
+  }
+  *zero = false;
+  int eM;
+  frexp(static_cast<double>(M), &eM);
+  return 62 - ceil_log2_i64(nA) - eM;
+}
+
+// block-local inclusive scan of u64 weights; writes w, the local prefix and the block sum
+__global__ void __launch_bounds__(kScanThreads) k_weights(const float* D, int64_t nA, const uint32_t* maxD,
+                                                          uint64_t* w, uint64_t* prefix, uint64_t* blocksum,
+                                                          int32_t* S_out) {
+  __shared__ uint64_t s_warp[kScanThreads / 32];
+  bool zero;
+  const int S = weight_shift(maxD, nA, &zero);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *S_out = S;
+  const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
+  uint64_t v[kScanItems];
+  uint64_t run = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t a = base + i;
+    uint64_t wa = 0;
+    if (a < nA && !zero) {
+      const float Da = D[a];
+      if (Da > 0.0f) wa = static_cast<uint64_t>(ceil(ldexp(static_cast<double>(Da), S)));
+    }
+    if (a < nA) w[a] = wa;
+    run += wa;
+    v[i] = run;
+  }
+  // exclusive offset of this thread within the block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint64_t woff = 0;
+  for (int i = 0; i < warp; ++i) woff += s_warp[i];
+  const uint64_t off = woff + x - run;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t a = base + i;
+    if (a < nA) prefix[a] = v[i] + off;
+  }
+  if (threadIdx.x == kScanThreads - 1) blocksum[blockIdx.x] = off + run;
+}
+
+// exclusive scan of the block sums (one block, sequential chunks of 1024)
+__global__ void k_scan_blocksums(uint64_t* blocksum, int64_t nb, uint64_t* W) {
+  __shared__ uint64_t s_warp[32];
+  __shared__ uint64_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+    const int64_t i = c0 + threadIdx.x;
+    const uint64_t v = i < nb ? blocksum[i] : 0;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint64_t woff = 0;
+    for (int k = 0; k < warp; ++k) woff += s_warp[k];
+    const uint64_t carry = s_carry;
+    if (i < nb) blocksum[i] = carry + woff + x - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = carry + woff + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *W = s_carry;
+}
+
+__global__ void k_add_offsets(uint64_t* prefix, int64_t nA, const uint64_t* blockoff) {
+  const int64_t a = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (a < nA) prefix[a] += blockoff[a / kScanTile];
+}
+
+void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s) {
+  CHX_CUDA(cudaMemsetAsync(sw.maxD, 0, sizeof(uint32_t), s));
+  if (nA == 0) {
+    CHX_CUDA(cudaMemsetAsync(sw.W, 0, sizeof(uint64_t), s));
+    CHX_CUDA(cudaMemsetAsync(sw.S, 0, sizeof(int32_t), s));
+    return;
+  }
+  const int gmax = static_cast<int>(std::min<int64_t>(ceil_div(nA, 256), 152 * 4));
+  k_max_d<<<gmax, 256, 0, s>>>(D, nA, sw.maxD);
+  launch_check("max_d");
+  const int64_t nb = static_cast<int64_t>(sample_blocks(nA));
+  k_weights<<<static_cast<int>(nb), kScanThreads, 0, s>>>(D, nA, sw.maxD, w, prefix, sw.blocksum, sw.S);
+  launch_check("weights");
+  k_scan_blocksums<<<1, 1024, 0, s>>>(sw.blocksum, nb, sw.W);
+  launch_check("scan_blocksums");
+  if (nb > 1) {
+    k_add_offsets<<<static_cast<int>(ceil_div(nA, 256)), 256, 0, s>>>(prefix, nA, sw.blocksum);
+    launch_check("add_offsets");
+  }
+}
+
+// x_l = first a with prefix_a > floor(u W / 2^128), u = Philox(l_lo, l_hi, 3, 0)
+__global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, int64_t T, uint64_t seed,
+                        int64_t* idx) {
+  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= T) return;
+  const uint64_t W = *Wp;
+  if (W == 0) {
+    idx[l] = -1;
+    return;
+  }
+  const P4 u = philox10(P4{uint32_t(l), uint32_t(uint64_t(l) >> 32), 3u, 0u}, uint32_t(seed), uint32_t(seed >> 32));
+  const uint64_t ulo = (uint64_t(u.y) << 32) | u.x;
+  const uint64_t uhi = (uint64_t(u.w) << 32) | u.z;
+  const uint64_t plo_hi = __umul64hi(ulo, W);
+  const uint64_t phi_lo = uhi * W;
+  const uint64_t phi_hi = __umul64hi(uhi, W);
+  const uint64_t mid = phi_lo + plo_hi;
+  const uint64_t t = phi_hi + (mid < phi_lo ? 1 : 0);
+  int64_t lo = 0, hi = nA;  // first a with prefix[a] > t
+  while (lo < hi) {
+    const int64_t m = lo + ((hi - lo) >> 1);
+    if (prefix[m] > t)
+      hi = m;
+    else
+      lo = m + 1;
+  }
+  idx[l] = lo;
+}
+
+void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed, int64_t* idx,
+                  cudaStream_t s) {
+  if (T == 0) return;
+  k_draws<<<static_cast<int>(ceil_div(T, 256)), 256, 0, s>>>(prefix, nA, W, T, seed, idx);
+  launch_check("draws");
+}
+
+// ------------------------------------------------------------------ combine
+// out[0] = (1/T) sum_l m_l W / w_{x_l}; out[1] = sum_a D_a   (binary64, fixed tree order)
+__global__ void __launch_bounds__(1024) k_combine(const float* m, const int64_t* idx, const uint64_t* w,
+                                                  const uint64_t* Wp, int64_t T, const float* D, int64_t nA,
+                                                  double* out) {
+  __shared__ double s_a[1024], s_b[1024];
+  const uint64_t W = Wp ? *Wp : 0;
+  double acc = 0.0, accD = 0.0;
+  if (W != 0)
+    for (int64_t l = threadIdx.x; l < T; l += blockDim.x) {
+      const int64_t x = idx[l];
+      acc += static_cast<double>(m[l]) * (static_cast<double>(W) / static_cast<double>(w[x]));
+    }
+  if (D)
+    for (int64_t a = threadIdx.x; a < nA; a += blockDim.x) accD += static_cast<double>(D[a]);
+  s_a[threadIdx.x] = acc;
+  s_b[threadIdx.x] = accD;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      s_a[threadIdx.x] += s_a[threadIdx.x + st];
+      s_b[threadIdx.x] += s_b[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = (W != 0 && T > 0) ? s_a[0] / static_cast<double>(T) : 0.0;
+    out[1] = s_b[0];
+  }
+}
+
+void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
+                    const float* D, int64_t nA, double* out2, cudaStream_t s) {
+  k_combine<<<1, 1024, 0, s>>>(m, idx, w, W, T, D, nA, out2);
+  launch_check("combine");
+}
+
+void launch_sum_f32(const float* v, int64_t n, double* out2, cudaStream_t s) {
+  // out2[1] = sum v (binary64), out2[0] = 0; the combine reduction with no samples
+  k_combine<<<1, 1024, 0, s>>>(nullptr, nullptr, nullptr, nullptr, 0, v, n, out2);
+  launch_check("sum_f32");
+}
+
+}  // namespace chx

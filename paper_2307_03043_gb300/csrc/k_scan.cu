@@ -1,0 +1,284 @@
+// k_scan.cu -- exact sampled nearest-neighbour scan (Fig. 1, step 3) and the
+// exact brute force (Section 1) on CUDA cores.
+//
+// Every (q, b) pair is evaluated with the canonical binary32 distance: 32
+// strided partials p_r = sum_{j = r mod 32} term_j in increasing j, combined
+// by the halving tree p_r += p_{r+s}, s = 16, 8, 4, 2, 1.  A thread holds a
+// PQ x PB block of pairs and walks the tree depth first (leaves in bit-reversed
+// order), so each pair needs ~6 live registers instead of 32; subtrees whose
+// leaves are all beyond d are +0 and skipped (adding +0 to a non-negative
+// partial is exact).  The result is bit-identical to the definition, for both
+// the minimum and the smallest-index argmin.
+#include "common.cuh"
+
+namespace chx {
+
+template <int METRIC, int PQ, int PB, int QS, int BS>
+struct Tree {
+  // leaf r: sum over j = r, r+32, ... of |q_j - b_j| or (q_j - b_j)^2
+  template <int R>
+  static __device__ __forceinline__ void leaf(float (&acc)[PQ][PB], const float* __restrict__ Qt,
+                                              const float* __restrict__ Bt, int d) {
+#pragma unroll
+    for (int p = 0; p < PQ; ++p)
+#pragma unroll
+      for (int b = 0; b < PB; ++b) acc[p][b] = 0.0f;
+    for (int j = R; j < d; j += 32) {
+      float qv[PQ], bv[PB];
+      if constexpr (PQ == 2) {
+        const float2 t = *reinterpret_cast<const float2*>(Qt + j * QS);
+        qv[0] = t.x;
+        qv[1] = t.y;
+      } else {
+#pragma unroll
+        for (int p = 0; p < PQ; ++p) qv[p] = Qt[j * QS + p];
+      }
+      if constexpr (PB == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(Bt + j * BS);
+        bv[0] = t.x;
+        bv[1] = t.y;
+        bv[2] = t.z;
+        bv[3] = t.w;
+      } else if constexpr (PB == 2) {
+        const float2 t = *reinterpret_cast<const float2*>(Bt + j * BS);
+        bv[0] = t.x;
+        bv[1] = t.y;
+      } else {
+#pragma unroll
+        for (int b = 0; b < PB; ++b) bv[b] = Bt[j * BS + b];
+      }
+#pragma unroll
+      for (int p = 0; p < PQ; ++p)
+#pragma unroll
+        for (int b = 0; b < PB; ++b) {
+          const float t = __fsub_rn(qv[p], bv[b]);
+          if constexpr (METRIC == CH_L1)
+            acc[p][b] = __fadd_rn(acc[p][b], fabsf(t));
+          else
+            acc[p][b] = __fmaf_rn(t, t, acc[p][b]);
+        }
+    }
+  }
+
+  // value of partial R after tree steps 16 .. S  (S = 32: the leaf itself)
+  template <int R, int S>
+  static __device__ __forceinline__ void node(float (&out)[PQ][PB], const float* __restrict__ Qt,
+                                              const float* __restrict__ Bt, int d) {
+    if constexpr (S == 32) {
+      leaf<R>(out, Qt, Bt, d);
+    } else {
+      node<R, 2 * S>(out, Qt, Bt, d);
+      if (R + S < d) {
+        float tmp[PQ][PB];
+        node<R + S, 2 * S>(tmp, Qt, Bt, d);
+#pragma unroll
+        for (int p = 0; p < PQ; ++p)
+#pragma unroll
+          for (int b = 0; b < PB; ++b) out[p][b] = __fadd_rn(out[p][b], tmp[p][b]);
+      }
+    }
+  }
+};
+
+template <int DT, int METRIC, int QT, int BT, int PQ, int PB>
+__global__ void __launch_bounds__(256) k_scan_exact(const void* __restrict__ A, const float* __restrict__ scA,
+                                                    const int64_t* __restrict__ qidx, int64_t T, int64_t nA,
+                                                    const void* __restrict__ B, const float* __restrict__ scB,
+                                                    int64_t nB, int d, int64_t chunk_len, float* part_val,
+                                                    int64_t* part_idx) {
+  constexpr int NTQ = QT / PQ, NTB = BT / PB;
+  static_assert(NTQ * NTB == 256, "256 threads");
+  constexpr int QS = QT + 4, BS = BT + 4;
+  extern __shared__ __align__(16) float smem[];
+  float* Qs = smem;
+  float* Bs = smem + size_t(d) * QS;
+  __shared__ float r_val[NTB][QT];
+  __shared__ int64_t r_idx[NTB][QT];
+
+  const int tid = threadIdx.x;
+  const int tq = tid % NTQ, tb = tid / NTQ;
+  const int64_t q0 = int64_t(blockIdx.x) * QT;
+  const int64_t b_begin = int64_t(blockIdx.y) * chunk_len;
+  const int64_t b_end = min(nB, b_begin + chunk_len);
+
+  for (int f = tid; f < QT * d; f += 256) {
+    const int q = f / d, j = f - q * d;
+    const int64_t l = q0 + q;
+    float v = 0.0f;
+    if (l < T) {
+      const int64_t a = qidx ? qidx[l] : l;
+      if (a >= 0 && a < nA) v = load_elem<DT>(A, a, d, j, scA);
+    }
+    Qs[j * QS + q] = v;
+  }
+
+  float best_val[PQ], best_p0[PQ];
+  int64_t best_idx[PQ];
+#pragma unroll
+  for (int p = 0; p < PQ; ++p) {
+    best_val[p] = __int_as_float(0x7F800000);
+    best_p0[p] = __int_as_float(0x7F800000);
+    best_idx[p] = INT64_MAX;
+  }
+  const float* Qt = Qs + tq * PQ;
+  const float* Bt = Bs + tb * PB;
+
+  for (int64_t b0 = b_begin; b0 < b_end; b0 += BT) {
+    __syncthreads();
+    const int64_t rows = min(static_cast<int64_t>(BT), b_end - b0);
+    for (int f = tid; f < BT * d; f += 256) {
+      const int r = f / d, j = f - r * d;
+      Bs[j * BS + r] = (r < rows) ? load_elem<DT>(B, b0 + r, d, j, scB) : 0.0f;
+    }
+    __syncthreads();
+    float out[PQ][PB];
+    Tree<METRIC, PQ, PB, QS, BS>::template node<0, 1>(out, Qt, Bt, d);
+#pragma unroll
+    for (int p = 0; p < PQ; ++p)
+#pragma unroll
+      for (int b = 0; b < PB; ++b) {
+        const int r = tb * PB + b;
+        if (r < rows) {
+          const float v = out[p][b];
+          if constexpr (METRIC == CH_L1) {
+            if (v < best_val[p]) {
+              best_val[p] = v;
+              best_idx[p] = b0 + r;
+            }
+          } else if (v < best_p0[p]) {
+            best_p0[p] = v;
+            const float sv = __fsqrt_rn(v);
+            if (sv < best_val[p]) {
+              best_val[p] = sv;
+              best_idx[p] = b0 + r;
+            }
+          }
+        }
+      }
+  }
+#pragma unroll
+  for (int p = 0; p < PQ; ++p) {
+    r_val[tb][tq * PQ + p] = best_val[p];
+    r_idx[tb][tq * PQ + p] = best_idx[p];
+  }
+  __syncthreads();
+  if (tid < QT) {
+    float bv = r_val[0][tid];
+    int64_t bi = r_idx[0][tid];
+    for (int k = 1; k < NTB; ++k) {
+      const float v = r_val[k][tid];
+      const int64_t i = r_idx[k][tid];
+      if (v < bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+      }
+    }
+    const int64_t l = q0 + tid;
+    if (l < T) {
+      part_val[int64_t(blockIdx.y) * T + l] = bv;
+      part_idx[int64_t(blockIdx.y) * T + l] = bi;
+    }
+  }
+}
+
+__global__ void k_scan_merge(const float* part_val, const int64_t* part_idx, int chunks, int64_t T,
+                             const int64_t* qidx, float* min_d, int64_t* argmin) {
+  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= T) return;
+  float bv = part_val[l];
+  int64_t bi = part_idx[l];
+  for (int c = 1; c < chunks; ++c) {
+    const float v = part_val[int64_t(c) * T + l];
+    const int64_t i = part_idx[int64_t(c) * T + l];
+    if (v < bv || (v == bv && i < bi)) {
+      bv = v;
+      bi = i;
+    }
+  }
+  const bool none = qidx && qidx[l] < 0;
+  min_d[l] = none ? 0.0f : bv;
+  if (argmin) argmin[l] = none ? -1 : bi;
+}
+
+struct TileShape {
+  int QT, BT;
+};
+
+static TileShape tile_for(int d) {
+  if (d <= 192) return {32, 64};
+  if (d <= 768) return {32, 32};
+  return {16, 16};
+}
+
+static size_t scan_smem(int d) {
+  const TileShape t = tile_for(d);
+  return size_t(d) * ((t.QT + 4) + (t.BT + 4)) * sizeof(float);
+}
+
+int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
+  const TileShape t = tile_for(d);
+  const int64_t qtiles = ceil_div(std::max<int64_t>(T, 1), t.QT);
+  const int64_t target = int64_t(sm_count) * 4;
+  int64_t chunks = ceil_div(target, qtiles);
+  chunks = std::min<int64_t>(chunks, ceil_div(nB, int64_t(t.BT) * 4));
+  return static_cast<int>(std::max<int64_t>(chunks, 1));
+}
+
+template <int DT, int METRIC, int QT, int BT, int PQ, int PB>
+static void scan_launch(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, ScanPart part,
+                        cudaStream_t s) {
+  auto kern = k_scan_exact<DT, METRIC, QT, BT, PQ, PB>;
+  const size_t smem = scan_smem(A->d);
+  static bool attr_set = false;  // one attribute call per instantiation
+  if (!attr_set) {
+    CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 20 * 1024));
+    attr_set = true;
+  }
+  const int64_t chunk_len = ceil_div(ceil_div(B->n, part.chunks), BT) * BT;
+  dim3 grid(static_cast<unsigned>(ceil_div(T, QT)), static_cast<unsigned>(part.chunks));
+  kern<<<grid, 256, smem, s>>>(A->data, A->scales, qidx, T, A->n, B->data, B->scales, B->n, A->d, chunk_len,
+                               part.val, part.idx);
+}
+
+template <int DT, int METRIC>
+static void scan_shape(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, ScanPart part,
+                       cudaStream_t s) {
+  const TileShape t = tile_for(A->d);
+  if (t.BT == 64)
+    scan_launch<DT, METRIC, 32, 64, 2, 4>(A, qidx, T, B, part, s);
+  else if (t.BT == 32)
+    scan_launch<DT, METRIC, 32, 32, 2, 2>(A, qidx, T, B, part, s);
+  else
+    scan_launch<DT, METRIC, 16, 16, 1, 1>(A, qidx, T, B, part, s);
+}
+
+template <int DT>
+static void scan_metric(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int metric, ScanPart part,
+                        cudaStream_t s) {
+  if (metric == CH_L1)
+    scan_shape<DT, CH_L1>(A, qidx, T, B, part, s);
+  else
+    scan_shape<DT, CH_L2>(A, qidx, T, B, part, s);
+}
+
+void launch_scan_exact(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int metric, ScanPart part,
+                       int sm_count, cudaStream_t s) {
+  (void)sm_count;
+  if (T == 0) return;
+  CHX_CHECK(scan_smem(A->d) <= 220 * 1024, CH_ENOTSUP, "dimension too large for the exact scan");
+  switch (A->dtype) {
+    case CH_F32: scan_metric<CH_F32>(A, qidx, T, B, metric, part, s); break;
+    case CH_BF16: scan_metric<CH_BF16>(A, qidx, T, B, metric, part, s); break;
+    default: scan_metric<CH_FP8E4M3>(A, qidx, T, B, metric, part, s); break;
+  }
+  launch_check("scan_exact");
+}
+
+void launch_scan_merge(ScanPart part, int64_t T, const int64_t* qidx, float* min_d, int64_t* argmin, cudaStream_t s) {
+  if (T == 0) return;
+  k_scan_merge<<<static_cast<int>(ceil_div(T, 256)), 256, 0, s>>>(part.val, part.idx, part.chunks, T, qidx, min_d,
+                                                                  argmin);
+  launch_check("scan_merge");
+}
+
+}  // namespace chx

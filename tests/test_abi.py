@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+symbol include/chamfer.h declares, and shares no code with the oracle."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "chamfer.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(ch_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2307_03043_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_path(built):
+    names = _declared()
+    for n in ("ch_crude_nn", "ch_sample", "ch_sampled_nn", "ch_estimate", "ch_exact", "ch_serve_create",
+              "ch_serve_submit", "ch_serve_wait", "ch_hash_keys"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\b(ch_[a-z0-9_]+)\b", out))
+    missing = _declared() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+
+
+def test_library_loads_and_binding_covers_header(built):
+    from paper_2307_03043_gb300 import binding
+    so = binding.lib()
+    for n in _declared():
+        assert hasattr(so, n)
+    assert set(binding.SIGNATURES) == _declared()
+
+
+def test_library_shares_no_code_with_oracle(built):
+    out = subprocess.run(["nm", "-D", built], capture_output=True, text=True, check=True).stdout
+    assert not re.search(r"\bor_[a-z0-9_]+\b", out)
+    ldd = subprocess.run(["ldd", built], capture_output=True, text=True).stdout
+    assert "oracle" not in ldd
+    csrc = os.path.join(ROOT, "paper_2307_03043_gb300", "csrc")
+    for f in os.listdir(csrc):
+        txt = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in txt.lower(), f
+
+
+def test_build_targets_sm_103a_only():
+    from paper_2307_03043_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert "-use_fast_math" not in build.NVCC_FLAGS and "-ftz=false" in build.NVCC_FLAGS
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    from paper_2307_03043_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(binding.ChamferError):
+        binding.lib()

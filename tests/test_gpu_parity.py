@@ -1,0 +1,306 @@
+"""GPU (libchamfer through its C ABI) versus the CPU oracle, element by element.
+
+Bit-exact: bucket keys, scale exponents, b(a), level, D_a, weights w_a, W and
+the sample indices, the exact-scan minima and argmins.  Estimates: within
+1e-5 relative (the binary64 sums differ only in order).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_03043_gb300 import binding as ch
+from paper_2307_03043_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+L1, L2 = ch.CH_L1, ch.CH_L2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_03043_gb300 import build
+    build.build()
+    c = ch.ch_ctx_create(0, torch.cuda.current_stream())
+    yield c
+    ch.ch_ctx_destroy(c)
+
+
+def dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    return t.cuda() if dtype is None else t.to(dtype).cuda()
+
+
+class Pair:
+    """Device copies of A and B registered as libchamfer sets (adopted)."""
+
+    def __init__(self, ctx, A, B):
+        self.ctx = ctx
+        self.A_np, self.B_np = A, B
+        self.A, self.B = dev(A), dev(B)
+        self.sA = ch.ch_set_create(ctx, self.A, 2, A.shape[0], A.shape[1])
+        self.sB = ch.ch_set_create(ctx, self.B, 2, B.shape[0], B.shape[1])
+
+    def close(self):
+        ch.ch_set_destroy(self.sA)
+        ch.ch_set_destroy(self.sB)
+        torch.cuda.synchronize()
+
+
+@pytest.fixture
+def pair_factory(ctx):
+    made = []
+
+    def make(A, B):
+        p = Pair(ctx, A, B)
+        made.append(p)
+        return p
+
+    yield make
+    for p in made:
+        p.close()
+
+
+def gpu_crude(ctx, p, metric, seed, L=10, k=16, top_exp=None):
+    nA = p.A_np.shape[0]
+    bidx = torch.zeros(nA, dtype=torch.int64, device="cuda")
+    D = torch.zeros(nA, dtype=torch.float32, device="cuda")
+    lv = torch.zeros(nA, dtype=torch.uint8, device="cuda")
+    ch.ch_crude_nn(ctx, p.sA, p.sB, ch.hash_params(metric, L, k, top_exp, seed), bidx, D, lv)
+    return bidx.cpu().numpy(), D.cpu().numpy(), lv.cpu().numpy()
+
+
+# ------------------------------------------------------------------ hashing
+@pytest.mark.parametrize("metric", [L1, L2])
+@pytest.mark.parametrize("n,d", [(1037, 16), (517, 3), (300, 33), (260, 128)])
+def test_keys_bit_exact(ctx, pair_factory, metric, n, d):
+    A, B = workloads.gaussian_mixture(n, 50, d, n + d, clusters=7)
+    p = pair_factory(A, B)
+    for L, e_lo in ((10, -6), (3, 2), (17, -12)):
+        hp = ch.hash_params(metric, L, 16, None, 1234 + L)
+        keys = torch.zeros((L, n), dtype=torch.int64, device="cuda")
+        ch.ch_hash_keys(ctx, p.sA, hp, e_lo, keys)
+        got = keys.cpu().numpy().view(np.uint64)
+        Y = oracle.hashed(A, metric, 1234 + L, 16)
+        want = oracle.keys(Y, e_lo, L, 1234 + L)
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_top_exp_matches(ctx, pair_factory, metric):
+    for seed, scale in ((1, 1.0), (2, 1e-3), (3, 300.0)):
+        A, B = workloads.uniform(333, 211, 7, seed)
+        p = pair_factory(A * scale, B * scale + 0.5)
+        hp = ch.hash_params(metric, 10, 16, None, seed)
+        YA = oracle.hashed(A * scale, metric, seed, 16)
+        YB = oracle.hashed(B * scale + 0.5, metric, seed, 16)
+        assert ch.ch_top_exp(ctx, p.sA, p.sB, hp) == oracle.top_exp(YA, YB)
+
+
+# ------------------------------------------------------------------ CrudeNN
+@pytest.mark.parametrize("metric", [L1, L2])
+@pytest.mark.parametrize("shape", ["tiny", "ragged", "dup", "one_b", "d3"])
+def test_crude_nn_bit_exact(ctx, pair_factory, metric, shape):
+    if shape == "tiny":
+        A, B = workloads.uniform(2000, 2000, 16, 0)
+    elif shape == "ragged":
+        A, B = workloads.gaussian_mixture(1531, 977, 37, 1, clusters=11)
+    elif shape == "dup":
+        A, B = workloads.uniform(700, 900, 8, 2)
+        B[100:800] = A
+    elif shape == "one_b":
+        A, B = workloads.uniform(513, 1, 5, 3)
+    else:
+        A, B = workloads.shape_surface(3001, 2999, 4)
+    p = pair_factory(A, B)
+    for seed in (0, 7):
+        bidx, D, lv = gpu_crude(ctx, p, metric, seed)
+        r = oracle.crude_nn(A, B, metric, hash_seed=seed)
+        assert np.array_equal(bidx, r["bidx"])
+        assert np.array_equal(lv, r["level"])
+        assert np.array_equal(D.view(np.uint32), r["D"].view(np.uint32))
+
+
+def test_crude_nn_few_levels_and_fallback(ctx, pair_factory):
+    A, B = workloads.uniform(400, 600, 6, 5)
+    p = pair_factory(A, B)
+    for L, top in ((1, None), (2, -8), (32, None), (5, 40)):
+        bidx, D, lv = gpu_crude(ctx, p, L1, 3, L=L, top_exp=top)
+        r = oracle.crude_nn(A, B, L1, hash_seed=3, L=L, top_exp=top)
+        assert np.array_equal(bidx, r["bidx"]) and np.array_equal(lv, r["level"])
+        assert np.array_equal(D, r["D"])
+
+
+# ------------------------------------------------------------------ sampling
+def gpu_sample(ctx, D, T, seed):
+    n = D.size
+    Dd = dev(D.astype(np.float32))
+    idx = torch.zeros(max(T, 1), dtype=torch.int64, device="cuda")
+    w = torch.zeros(max(n, 1), dtype=torch.int64, device="cuda")
+    W = ch.ch_sample(ctx, Dd, n, T, seed, idx, w, want_total=True)
+    return idx.cpu().numpy()[:T], w.cpu().numpy()[:n].view(np.uint64), W
+
+
+@pytest.mark.parametrize("case", ["random", "zeros_mixed", "single", "one", "wide_range", "big"])
+def test_sample_bit_exact(ctx, case):
+    g = np.random.default_rng(11)
+    if case == "random":
+        D = g.random(5003).astype(np.float32)
+    elif case == "zeros_mixed":
+        D = g.random(3000).astype(np.float32)
+        D[g.random(3000) < 0.4] = 0
+    elif case == "single":
+        D = np.zeros(777, np.float32)
+        D[300] = 2.5
+    elif case == "one":
+        D = np.array([0.25], np.float32)
+    elif case == "wide_range":
+        D = (10.0 ** g.uniform(-30, 30, 4000)).astype(np.float32)
+    else:
+        D = g.random(300_001).astype(np.float32) * 50
+    T = 4097
+    idx, w, W = gpu_sample(ctx, D, T, 99)
+    w_o, prefix_o, W_o, _ = oracle.weights(D)
+    assert W == W_o
+    assert np.array_equal(w, w_o)
+    if D.size <= 5003:
+        assert np.array_equal(idx, oracle.draws(prefix_o, W_o, T, 99))
+    else:  # linear-search oracle: check a sample of draws by big-integer arithmetic
+        for l in range(0, T, 97):
+            u = oracle.philox([l, 0, 3, 0], [99, 0])
+            U = int(u[0]) | int(u[1]) << 32 | int(u[2]) << 64 | int(u[3]) << 96
+            t = (U * W_o) >> 128
+            assert idx[l] == int(np.searchsorted(prefix_o, np.uint64(t), side="right"))
+
+
+def test_sample_all_zero(ctx):
+    idx, w, W = gpu_sample(ctx, np.zeros(100, np.float32), 10, 1)
+    assert W == 0 and np.all(idx == -1) and np.all(w == 0)
+
+
+# ------------------------------------------------------------------ scans
+@pytest.mark.parametrize("metric", [L1, L2])
+@pytest.mark.parametrize("nA,nB,d,T", [(500, 2000, 16, 777), (300, 4099, 3, 301), (200, 1500, 128, 97),
+                                       (120, 700, 200, 65), (64, 333, 768, 33), (50, 123, 1, 40)])
+def test_sampled_nn_exact_bit_exact(ctx, pair_factory, metric, nA, nB, d, T):
+    A, B = workloads.gaussian_mixture(nA, nB, d, nA + d, clusters=9)
+    p = pair_factory(A, B)
+    g = np.random.default_rng(d)
+    idx = g.integers(0, nA, T).astype(np.int64)
+    idx[::17] = -1
+    m = torch.zeros(T, dtype=torch.float32, device="cuda")
+    am = torch.zeros(T, dtype=torch.int64, device="cuda")
+    ch.ch_sampled_nn(ctx, p.sA, dev(idx), T, p.sB, metric, ch.CH_SCREEN_EXACT, 8, m, am)
+    m, am = m.cpu().numpy(), am.cpu().numpy()
+    ok = idx >= 0
+    mo, amo = oracle.scan(A, idx[ok], B, metric)
+    assert np.array_equal(m[ok].view(np.uint32), mo.view(np.uint32))
+    assert np.array_equal(am[ok], amo)
+    assert np.all(m[~ok] == 0) and np.all(am[~ok] == -1)
+
+
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_exact_matches_oracle(ctx, pair_factory, metric):
+    A, B = workloads.uniform(1500, 1300, 16, 21)
+    p = pair_factory(A, B)
+    mins = torch.zeros(1500, dtype=torch.float32, device="cuda")
+    v = ch.ch_exact(ctx, p.sA, p.sB, metric, 0, mins)
+    vo, mo = oracle.exact_canonical(A, B, metric)
+    assert np.array_equal(mins.cpu().numpy(), mo)
+    assert abs(v / vo - 1) < 1e-12
+    assert abs(v / oracle.exact_fp64(A, B, metric) - 1) < 1e-5
+
+
+# ------------------------------------------------------------------ estimate
+@pytest.mark.parametrize("metric", [L1, L2])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_estimate_tiny_matches_oracle(ctx, pair_factory, metric, seed):
+    A, B = workloads.uniform(2000, 2000, 16, seed)
+    p = pair_factory(A, B)
+    prm = ch.est_params(metric, 10, 16, None, seed, eps=0.2, T=2000, sample_seed=seed + 5,
+                        screen=ch.CH_SCREEN_EXACT)
+    eta, rep = ch.ch_estimate(ctx, p.sA, p.sB, prm, report=True)
+    eta_o, det = oracle.estimate(A, B, metric, seed, seed + 5, T=2000, details=True)
+    assert abs(eta / eta_o - 1) < 1e-5
+    assert rep.W == det["W"] and rep.top_exp == det["top_exp"] and rep.shift_S == det["S"]
+    assert abs(rep.D_total / det["D_total"] - 1) < 1e-12
+    ch_x = oracle.exact_fp64(A, B, metric)
+    assert abs(eta / ch_x - 1) < 0.2
+
+
+def test_estimate_edge_cases(ctx, pair_factory):
+    A, B = workloads.uniform(10, 20, 4, 1)
+    p = pair_factory(A, B)
+    # A empty -> 0
+    e = np.zeros((0, 4), np.float32)
+    sE = ch.ch_set_create(ctx, e, 0, 0, 4)
+    assert ch.ch_estimate(ctx, sE, p.sB, ch.est_params(T=10)) == 0.0
+    # B empty -> EINVAL
+    with pytest.raises(ch.ChamferError) as ei:
+        ch.ch_estimate(ctx, p.sA, sE, ch.est_params(T=10))
+    assert ei.value.status == ch.CH_EINVAL
+    ch.ch_set_destroy(sE)
+    # non-finite data -> EINVAL at the next synchronising call
+    bad = A.copy()
+    bad[3, 2] = np.nan
+    sBad = ch.ch_set_create(ctx, bad, 0, 10, 4)
+    with pytest.raises(ch.ChamferError) as ei:
+        ch.ch_estimate(ctx, sBad, p.sB, ch.est_params(T=10))
+    assert ei.value.status == ch.CH_EINVAL
+    ch.ch_set_destroy(sBad)
+    # bad parameters
+    with pytest.raises(ch.ChamferError):
+        ch.ch_estimate(ctx, p.sA, p.sB, ch.est_params(eps=1.5))
+    with pytest.raises(ch.ChamferError):
+        ch.ch_estimate(ctx, p.sA, p.sB, ch.est_params(levels=0, T=5))
+    # |A| = 1: eta = its nearest-neighbour distance
+    s1 = ch.ch_set_create(ctx, A[:1].copy(), 0, 1, 4)
+    for metric in (L1, L2):
+        eta = ch.ch_estimate(ctx, s1, p.sB, ch.est_params(metric, T=7))
+        _, mins = oracle.exact_canonical(A[:1], B, metric)
+        assert eta == float(mins[0])
+    ch.ch_set_destroy(s1)
+    # subset -> exactly 0
+    B2 = np.vstack([B, A])
+    s2 = ch.ch_set_create(ctx, B2, 0, B2.shape[0], 4)
+    assert ch.ch_estimate(ctx, p.sA, s2, ch.est_params(L2, T=50)) == 0.0
+    ch.ch_set_destroy(s2)
+
+
+def test_host_mode_sets_match_device_sets(ctx, pair_factory):
+    A, B = workloads.uniform(900, 1100, 12, 8)
+    p = pair_factory(A, B)
+    sA = ch.ch_set_create(ctx, A, 0, 900, 12)
+    sB = ch.ch_set_create(ctx, p.B, 1, 1100, 12)
+    prm = ch.est_params(L2, T=300, hash_seed=4, sample_seed=4, screen=ch.CH_SCREEN_EXACT)
+    assert ch.ch_estimate(ctx, sA, sB, prm) == ch.ch_estimate(ctx, p.sA, p.sB, prm)
+    ch.ch_set_destroy(sA)
+    ch.ch_set_destroy(sB)
+
+
+# ------------------------------------------------------------------ mid-size workload
+def test_mid_workload_sampled_parity(ctx, pair_factory):
+    """The benchmark's 100k x 100k, d = 128 Gaussian-mixture l2 workload: CrudeNN
+    bit-exact in full; sampled scan minima checked against the oracle on a sample."""
+    A, B = workloads.gaussian_mixture(100_000, 100_000, 128, 0)
+    p = pair_factory(A, B)
+    bidx, D, lv = gpu_crude(ctx, p, L2, 0)
+    r = oracle.crude_nn(A, B, L2, hash_seed=0)
+    assert np.array_equal(bidx, r["bidx"]) and np.array_equal(lv, r["level"])
+    assert np.array_equal(D.view(np.uint32), r["D"].view(np.uint32))
+    T = oracle.default_T(100_000, 100_000, 0.1)
+    idx, w, W = gpu_sample(ctx, D, T, 1)
+    w_o, prefix_o, W_o, _ = oracle.weights(r["D"])
+    assert W == W_o and np.array_equal(w, w_o)
+    sub = np.arange(0, T, 23)
+    assert np.array_equal(idx[sub], oracle.draws(prefix_o, W_o, T, 1)[sub])
+    m = torch.zeros(T, dtype=torch.float32, device="cuda")
+    ch.ch_sampled_nn(ctx, p.sA, dev(idx), T, p.sB, L2, ch.CH_SCREEN_AUTO, 8, m)
+    m = m.cpu().numpy()
+    mo, _ = oracle.scan(A, idx[sub], B, L2)
+    assert np.array_equal(m[sub], mo)
+    eta = ch.ch_estimate(ctx, p.sA, p.sB, ch.est_params(L2, eps=0.1, hash_seed=0, sample_seed=1))
+    eta_o = oracle.combine(np.asarray(m), idx, w_o, W_o)
+    assert abs(eta / eta_o - 1) < 1e-5
