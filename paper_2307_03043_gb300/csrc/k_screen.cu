@@ -1,24 +1,654 @@
-// k_screen.cu -- tensor-core screen of the sampled l2 scan (placeholder until
-// the tcgen05 kernel lands: reports no support, so callers use the exact scan).
+// k_screen.cu -- tensor-core screen for the sampled l2 scan (Fig. 1, step 3).
+//
+// For each sample q and every b: s(q, b) = |b|^2 - 2 q.b ranks b exactly like
+// |q - b|^2 (|q|^2 is constant per sample).  The dot products are a dense
+// contraction S = Q B^T run on the 5th-generation tensor cores:
+//   * TMA (cp.async.bulk.tensor, 128-byte swizzle) stages Q (128 samples x d,
+//     resident per work item) and B tiles (256 points x one 128-byte K block)
+//     through a ring of shared-memory stages;
+//   * one elected thread issues tcgen05.mma (kind::tf32 for binary32 data,
+//     kind::f16 with bf16 operands, kind::f8f6f4 with e4m3 operands) into a
+//     double-buffered 128 x 256 binary32 accumulator in tensor memory;
+//   * four epilogue warps read the accumulator with tcgen05.ld (one row per
+//     thread), form s and keep each row's R smallest (s, b) in registers.
+// Work items are (128-sample tile, chunk of B) pairs spread over a persistent
+// grid; a rerank kernel then takes each sample's R best screened candidates
+// over all chunks and evaluates the canonical binary32 distance on them, so the
+// reported minimum is exact whenever the true nearest point survives the screen.
+//
+// Every mbarrier wait is bounded (about 2 s of SM clock); on expiry the CTA
+// raises ST_TIMEOUT, stops issuing work, lets in-flight copies and MMAs drain
+// and frees its tensor memory before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 namespace chx {
 
+namespace {
+
+constexpr int kBM = 128;          // samples per tile (TMEM lanes)
+constexpr int kBN = 256;          // B points per tile (accumulator columns)
+constexpr int kKB = 128;          // bytes of K per stage (one 128B swizzle row)
+constexpr int kThreads = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kMaxChunks = 32;
+constexpr int kMaxCand = 256;  // screened candidates per sample handed to the rerank
+constexpr long long kTimeoutCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false if this or another role gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kTimeoutCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                  // leading byte offset (unused for SW128 K-major)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;          // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                  // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                  // SWIZZLE_128B
+  return d;
+}
+
+// instruction descriptor: D f32, A/B K-major, M = 128, N = 256
+template <int SCREEN>
+__host__ __device__ constexpr uint32_t idesc() {
+  // operand format: tf32 = 2 (kind::tf32), bf16 = 1 (kind::f16), e4m3 = 0 (kind::f8f6f4)
+  constexpr uint32_t fmt = SCREEN == CH_SCREEN_TF32 ? 2u : SCREEN == CH_SCREEN_BF16 ? 1u : 0u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(kBN >> 3) << 17) |
+         (static_cast<uint32_t>(kBM >> 4) << 24);
+}
+
+template <int SCREEN>
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  constexpr uint32_t id = idesc<SCREEN>();
+  if constexpr (SCREEN == CH_SCREEN_TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate));
+  } else if constexpr (SCREEN == CH_SCREEN_BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct ScreenArgs {
+  int64_t T;          // samples (rows of Q)
+  int64_t nB;
+  int kblocks;        // ceil(d * elem / 128)
+  int row_tiles;
+  int chunks;
+  int64_t chunk_len;  // B points per chunk (multiple of kBN)
+  int stages;
+  const float* normB;   // |b|^2 [nB]
+  const float* scaleB;  // FP8 row scales [nB] or null
+  const float* scaleQ;  // FP8 sample scales [T] or null
+  float* part_s;        // [chunks][T][R]
+  int32_t* part_i;
+  uint32_t* status;
+};
+
+template <int SCREEN, int R>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_screen(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmB, ScreenArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int KB = args.kblocks;
+  const int S = args.stages;
+  uint8_t* q_smem = smem;                                 // KB x (128 rows x 128 B)
+  uint8_t* b_smem = q_smem + size_t(KB) * kBM * kKB;      // S x (256 rows x 128 B)
+  float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [4 warps][2][256] |b|^2
+  float* sb_s = nb_s + 8 * kBN;                                            // [4 warps][2][256] -2 x FP8 scale
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sb_s + 8 * kBN);
+  uint64_t* full = bars;            // [S]
+  uint64_t* empty = bars + S;       // [S]
+  uint64_t* q_full = bars + 2 * S;  // [1]
+  uint64_t* q_empty = q_full + 1;   // [1]
+  uint64_t* acc_full = q_empty + 1; // [2]
+  uint64_t* acc_empty = acc_full + 2;  // [2]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(q_full, 1);
+    mbar_init(q_empty, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 128);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
+                 "r"(2 * kBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  const int n_items = args.row_tiles * args.chunks;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, qphase = 0;
+      for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+        const int mt = item % args.row_tiles, ck = item / args.row_tiles;
+        const int64_t b_begin = int64_t(ck) * args.chunk_len;
+        const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
+        if (!mbar_wait(q_empty, qphase ^ 1, abort_flag)) break;
+        qphase ^= 1;
+        mbar_expect_tx(q_full, uint32_t(KB) * kBM * kKB);
+        for (int kb = 0; kb < KB; ++kb)
+          tma_load_2d(q_smem + size_t(kb) * kBM * kKB, &tmQ, kb * kKB / (SCREEN == CH_SCREEN_TF32 ? 4 : SCREEN == CH_SCREEN_BF16 ? 2 : 1),
+                      mt * kBM, q_full);
+        bool ok = true;
+        for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += kBN) {
+          for (int kb = 0; kb < KB; ++kb) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&full[stage], uint32_t(kBN) * kKB);
+            tma_load_2d(b_smem + size_t(stage) * kBN * kKB, &tmB,
+                        kb * kKB / (SCREEN == CH_SCREEN_TF32 ? 4 : SCREEN == CH_SCREEN_BF16 ? 2 : 1),
+                        static_cast<int>(b0), &full[stage]);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, qphase = 0;
+      uint32_t acc = 0, accphase = 0;
+      for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+        const int ck = item / args.row_tiles;
+        const int64_t b_begin = int64_t(ck) * args.chunk_len;
+        const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
+        if (!mbar_wait(q_full, qphase, abort_flag)) break;
+        qphase ^= 1;
+        tc_fence_after();
+        bool ok = true;
+        for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += kBN) {
+          if (!mbar_wait(&acc_empty[acc], accphase ^ 1, abort_flag)) break;
+          tc_fence_after();
+          const uint32_t dtmem = tmem_base + acc * kBN;
+          for (int kb = 0; kb < KB; ++kb) {
+            if (!mbar_wait(&full[stage], phase, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t qa = su32(q_smem + size_t(kb) * kBM * kKB);
+            const uint32_t ba = su32(b_smem + size_t(stage) * kBN * kKB);
+#pragma unroll
+            for (int k = 0; k < kKB / 32; ++k)  // 32 bytes of K per instruction
+              tc_mma<SCREEN>(dtmem, sdesc(qa + k * 32), sdesc(ba + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&empty[stage]);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+          if (!ok) break;
+          tc_commit(&acc_full[acc]);
+          acc ^= 1;
+          if (acc == 0) accphase ^= 1;
+        }
+        tc_commit(q_empty);
+        if (!ok) break;
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue: one sample row per thread
+    const int ew = warp & 3;  // TMEM lane quadrant this warp may access
+    const int row = ew * 32 + lane;
+    uint32_t acc = 0, accphase = 0;
+    for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+      const int mt = item % args.row_tiles, ck = item / args.row_tiles;
+      const int64_t b_begin = int64_t(ck) * args.chunk_len;
+      const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
+      const int64_t grow = int64_t(mt) * kBM + row;
+      float sq = 1.0f;
+      if constexpr (SCREEN == CH_SCREEN_FP8) sq = (grow < args.T) ? args.scaleQ[grow] : 1.0f;
+      float top_s[R];
+      int32_t top_i[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        top_s[i] = __int_as_float(0x7F800000);
+        top_i[i] = -1;
+      }
+      bool ok = true;
+      for (int64_t b0 = b_begin; b0 < b_end; b0 += kBN) {
+        // stage |b|^2 (and -2 x FP8 scale) of this tile in this warp's own buffer;
+        // +inf past the end of B.  Only __syncwarp is used inside the epilogue, so
+        // a warp that gives up on a wait can never strand another one.
+        float* nb = nb_s + ((warp - 2) * 2 + acc) * kBN;
+        float* sb = sb_s + ((warp - 2) * 2 + acc) * kBN;
+        for (int c = lane; c < kBN; c += 32) {
+          const int64_t b = b0 + c;
+          nb[c] = (b < b_end) ? args.normB[b] : __int_as_float(0x7F800000);
+          if constexpr (SCREEN == CH_SCREEN_FP8) sb[c] = (b < b_end) ? -2.0f * args.scaleB[b] : 0.0f;
+        }
+        __syncwarp();
+        const bool got = mbar_wait(&acc_full[acc], accphase, abort_flag);
+        if (!__all_sync(0xFFFFFFFFu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN;
+#pragma unroll 1
+        for (int ch = 0; ch < kBN / 32; ++ch) {
+          uint32_t r[32];
+          tmem_ld32(taddr + ch * 32, r);
+          const float thr0 = top_s[R - 1];
+          // cheap pass: any candidate below the current R-th best?
+          float mn = __int_as_float(0x7F800000);
+          float sv[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float a = __uint_as_float(r[i]);
+            if constexpr (SCREEN == CH_SCREEN_FP8)
+              sv[i] = fmaf(sb[ch * 32 + i] * sq, a, nb[ch * 32 + i]);
+            else
+              sv[i] = fmaf(-2.0f, a, nb[ch * 32 + i]);
+            mn = fminf(mn, sv[i]);
+          }
+          if (mn < thr0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              if (sv[i] < top_s[R - 1]) {
+                float cs = sv[i];
+                int32_t ci = static_cast<int32_t>(b0 + ch * 32 + i);
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                  if (cs < top_s[k]) {
+                    const float ts = top_s[k];
+                    const int32_t ti = top_i[k];
+                    top_s[k] = cs;
+                    top_i[k] = ci;
+                    cs = ts;
+                    ci = ti;
+                  }
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[acc]);
+        acc ^= 1;
+        if (acc == 0) accphase ^= 1;
+        __syncwarp();  // this warp's staging buffer is rewritten two tiles later
+      }
+      if (!ok) break;
+      if (grow < args.T) {
+        const size_t base = (size_t(ck) * args.T + grow) * R;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          args.part_s[base + i] = top_s[i];
+          args.part_i[base + i] = top_i[i];
+        }
+      }
+    }
+  }
+
+  // ------------------------------------------------ teardown
+  __syncwarp();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) atomicOr(args.status, ST_TIMEOUT);
+    // let in-flight copies and MMAs drain before the CTA's memory is released
+    const long long t0 = clock64();
+    while (clock64() - t0 < 20000000ll) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * kBN) : "memory");
+  }
+}
+
+// Gathers the sampled rows A[idx] into a dense [T][d] operand (raw storage type)
+// and, for FP8, their scales; idx < 0 gives a zero row.
+__global__ void k_gather_rows(const uint8_t* A, const float* scA, int64_t nA, int row_bytes, const int64_t* idx,
+                              int64_t T, uint8_t* Q, float* sQ) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int words = row_bytes / 16;
+  const int64_t row = t / words;
+  const int w = static_cast<int>(t % words);
+  if (row >= T) return;
+  const int64_t a = idx ? idx[row] : row;
+  uint4 v = make_uint4(0, 0, 0, 0);
+  if (a >= 0 && a < nA) v = reinterpret_cast<const uint4*>(A + a * row_bytes)[w];
+  reinterpret_cast<uint4*>(Q + row * row_bytes)[w] = v;
+  if (sQ && w == 0) sQ[row] = (a >= 0 && a < nA) ? scA[a] : 1.0f;
+}
+
+// One warp per sample: the R best screened candidates over all chunks (by s,
+// then index), the canonical binary32 distance of each, and their minimum.
+template <int DT, int METRIC>
+__global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA, int64_t nA, const void* B,
+                                                const float* scB, int d, const int64_t* idx, int64_t T,
+                                                const float* part_s, const int32_t* part_i, int chunks, int R,
+                                                float* min_d, int64_t* argmin) {
+  __shared__ float s_s[8][kMaxCand];
+  __shared__ int32_t s_i[8][kMaxCand];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t l = int64_t(blockIdx.x) * 8 + wib;
+  if (l >= T) return;
+  const int64_t a = idx ? idx[l] : l;
+  if (a < 0 || a >= nA) {
+    if (lane == 0) {
+      min_d[l] = 0.0f;
+      if (argmin) argmin[l] = -1;
+    }
+    return;
+  }
+  const int nc = chunks * R;
+  for (int p = lane; p < nc; p += 32) {
+    const int c = p / R, k = p % R;
+    const size_t off = (size_t(c) * T + l) * R + k;
+    s_s[wib][p] = part_s[off];
+    s_i[wib][p] = part_i[off];
+  }
+  __syncwarp();
+  float best = __int_as_float(0x7F800000);
+  int64_t bidx = INT64_MAX;
+  for (int round = 0; round < R; ++round) {
+    float ms = __int_as_float(0x7F800000);
+    int32_t mi = INT32_MAX;
+    int mp = -1;
+    for (int p = lane; p < nc; p += 32) {
+      const float v = s_s[wib][p];
+      const int32_t i = s_i[wib][p];
+      if (i >= 0 && (v < ms || (v == ms && i < mi))) {
+        ms = v;
+        mi = i;
+        mp = p;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(0xFFFFFFFFu, ms, o);
+      const int32_t oi = __shfl_xor_sync(0xFFFFFFFFu, mi, o);
+      const int op = __shfl_xor_sync(0xFFFFFFFFu, mp, o);
+      if (os < ms || (os == ms && oi < mi)) {
+        ms = os;
+        mi = oi;
+        mp = op;
+      }
+    }
+    if (mi == INT32_MAX || mi < 0) break;  // fewer than R candidates
+    if (lane == (mp & 31)) s_i[wib][mp] = -1;  // taken
+    __syncwarp();
+    // canonical distance to candidate mi (lane r sums coordinates j = r mod 32)
+    float part = 0.0f;
+    for (int j = lane; j < d; j += 32) {
+      const float t = __fsub_rn(load_elem<DT>(A, a, d, j, scA), load_elem<DT>(B, mi, d, j, scB));
+      part = (METRIC == CH_L1) ? __fadd_rn(part, fabsf(t)) : __fmaf_rn(t, t, part);
+    }
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) part = __fadd_rn(part, __shfl_down_sync(0xFFFFFFFFu, part, s));
+    const float dist = __shfl_sync(0xFFFFFFFFu, (METRIC == CH_L1) ? part : __fsqrt_rn(part), 0);
+    if (dist < best || (dist == best && mi < bidx)) {
+      best = dist;
+      bidx = mi;
+    }
+  }
+  if (lane == 0) {
+    min_d[l] = best;
+    if (argmin) argmin[l] = bidx;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CHX_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    CHX_CHECK(p && q == cudaDriverEntryPointSuccess, CH_ENOTSUP, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+CUtensorMap make_map(const void* base, int dtype, int64_t rows, int d, int box_rows) {
+  CUtensorMap m;
+  const int es = static_cast<int>(elem_size(dtype));
+  const CUtensorMapDataType t = dtype == CH_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                : dtype == CH_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(d), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(d) * es};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kKB / es), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, t, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CHX_CHECK(r == CUDA_SUCCESS, CH_ECUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+struct Plan {
+  int kblocks, row_tiles, chunks, stages, R;
+  int64_t chunk_len, T;
+  size_t smem;
+  int grid;
+};
+
+int screen_dtype(int screen) { return screen == CH_SCREEN_TF32 ? CH_F32 : screen == CH_SCREEN_BF16 ? CH_BF16 : CH_FP8E4M3; }
+
+Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
+  Plan p;
+  const int es = static_cast<int>(elem_size(screen_dtype(screen)));
+  p.T = T;
+  p.R = R <= 8 ? 8 : R <= 16 ? 16 : 32;
+  p.kblocks = static_cast<int>(ceil_div(int64_t(d) * es, kKB));
+  p.row_tiles = static_cast<int>(ceil_div(std::max<int64_t>(T, 1), kBM));
+  const size_t fixed = 1024 + size_t(p.kblocks) * kBM * kKB + 16 * kBN * sizeof(float) + 256;
+  const size_t per_stage = size_t(kBN) * kKB;
+  const size_t limit = 227 * 1024;
+  p.stages = static_cast<int>(std::min<size_t>(6, (limit - std::min(limit, fixed)) / per_stage));
+  p.smem = fixed + size_t(p.stages) * per_stage;
+  // chunks: smallest count whose items fill the SMs to >= 90 % (at most kMaxChunks)
+  const int64_t btiles = ceil_div(nB, kBN);
+  int best_c = 1;
+  double best_eff = 0.0;
+  for (int c = 1; c <= kMaxChunks && c <= btiles; ++c) {
+    if (c * p.R > kMaxCand) break;
+    const int64_t items = int64_t(p.row_tiles) * c;
+    const int64_t rounds = ceil_div(items, sm_count);
+    const double eff = double(items) / double(rounds * sm_count);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best_c = c;
+    }
+    if (eff >= 0.9) break;
+  }
+  p.chunks = best_c;
+  p.chunk_len = ceil_div(ceil_div(nB, p.chunks), kBN) * kBN;
+  p.chunks = static_cast<int>(ceil_div(nB, p.chunk_len));
+  p.grid = static_cast<int>(std::min<int64_t>(int64_t(p.row_tiles) * p.chunks, sm_count));
+  return p;
+}
+
+}  // namespace
+
 bool screen_supported(int screen, const ch_set* A, const ch_set* B) {
-  (void)screen; (void)A; (void)B;
-  return false;
+  if (screen != CH_SCREEN_TF32 && screen != CH_SCREEN_BF16 && screen != CH_SCREEN_FP8) return false;
+  if (A->dtype != screen_dtype(screen) || B->dtype != screen_dtype(screen)) return false;
+  const int es = static_cast<int>(elem_size(A->dtype));
+  if ((int64_t(A->d) * es) % 16 != 0) return false;     // TMA row stride
+  if (int64_t(A->d) * es < kKB) return false;            // at least one full 128-byte swizzle row
+  if (int64_t(A->d) * es > 96 * 1024 / kBM) return false; // resident sample tile <= 96 KB
+  if (B->n >= (int64_t(1) << 31)) return false;
+  return true;
 }
 
 size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
-  (void)T; (void)nB; (void)d; (void)R; (void)sm_count; (void)screen;
-  return 256;
+  const Plan p = make_plan(T, nB, d, R, sm_count, screen);
+  const int es = static_cast<int>(elem_size(screen_dtype(screen)));
+  const size_t q = ((size_t(T) * d * es + 255) & ~size_t(255)) + ((size_t(T) * 4 + 255) & ~size_t(255));
+  const size_t parts = size_t(p.chunks) * T * p.R * 8 + 512;
+  return q + parts + 1024;
 }
 
-void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R,
-                      void* work, float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s) {
-  (void)A; (void)qidx; (void)T; (void)B; (void)screen; (void)R; (void)work; (void)min_d; (void)argmin;
-  (void)status; (void)sm_count; (void)s;
-  throw Err{CH_ENOTSUP, "tensor-core screen not built"};
+void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R, void* work,
+                      float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s) {
+  if (T == 0) return;
+  const Plan p = make_plan(T, B->n, A->d, R, sm_count, screen);
+  const int es = static_cast<int>(elem_size(A->dtype));
+  const int row_bytes = A->d * es;
+  uint8_t* w = static_cast<uint8_t*>(work);
+  uint8_t* Q = w;
+  w += (size_t(T) * row_bytes + 255) & ~size_t(255);
+  float* sQ = reinterpret_cast<float*>(w);
+  w += (size_t(T) * 4 + 255) & ~size_t(255);
+  float* part_s = reinterpret_cast<float*>(w);
+  w += (size_t(p.chunks) * T * p.R * 4 + 255) & ~size_t(255);
+  int32_t* part_i = reinterpret_cast<int32_t*>(w);
+
+  const int64_t words = T * (row_bytes / 16);
+  k_gather_rows<<<static_cast<int>(ceil_div(words, 256)), 256, 0, s>>>(
+      static_cast<const uint8_t*>(A->data), A->scales, A->n, row_bytes, qidx, T, Q,
+      screen == CH_SCREEN_FP8 ? sQ : nullptr);
+  launch_check("gather_rows");
+
+  const CUtensorMap tmQ = make_map(Q, A->dtype, T, A->d, kBM);
+  const CUtensorMap tmB = make_map(B->data, B->dtype, B->n, B->d, kBN);
+  ScreenArgs a;
+  a.T = T;
+  a.nB = B->n;
+  a.kblocks = p.kblocks;
+  a.row_tiles = p.row_tiles;
+  a.chunks = p.chunks;
+  a.chunk_len = p.chunk_len;
+  a.stages = p.stages;
+  a.normB = B->norms;
+  a.scaleB = B->scales;
+  a.scaleQ = sQ;
+  a.part_s = part_s;
+  a.part_i = part_i;
+  a.status = status;
+
+#define CHX_SCREEN_LAUNCH(SCR, RR)                                                                          \
+  do {                                                                                                      \
+    auto kern = k_screen<SCR, RR>;                                                                          \
+    CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem))); \
+    kern<<<p.grid, kThreads, p.smem, s>>>(tmQ, tmB, a);                                                     \
+  } while (0)
+#define CHX_SCREEN_R(SCR)                   \
+  do {                                      \
+    if (p.R == 8) CHX_SCREEN_LAUNCH(SCR, 8); \
+    else if (p.R == 16) CHX_SCREEN_LAUNCH(SCR, 16); \
+    else CHX_SCREEN_LAUNCH(SCR, 32);        \
+  } while (0)
+  if (screen == CH_SCREEN_TF32) CHX_SCREEN_R(CH_SCREEN_TF32);
+  else if (screen == CH_SCREEN_BF16) CHX_SCREEN_R(CH_SCREEN_BF16);
+  else CHX_SCREEN_R(CH_SCREEN_FP8);
+#undef CHX_SCREEN_R
+#undef CHX_SCREEN_LAUNCH
+  launch_check("screen");
+
+  const int blocks = static_cast<int>(ceil_div(T, 8));
+  if (A->dtype == CH_F32)
+    k_rerank<CH_F32, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T, part_s,
+                                                   part_i, p.chunks, p.R, min_d, argmin);
+  else if (A->dtype == CH_BF16)
+    k_rerank<CH_BF16, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
+                                                    part_s, part_i, p.chunks, p.R, min_d, argmin);
+  else
+    k_rerank<CH_FP8E4M3, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
+                                                       part_s, part_i, p.chunks, p.R, min_d, argmin);
+  launch_check("rerank");
 }
 
 }  // namespace chx
