@@ -222,7 +222,9 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, scan_ms, ok = [], [], []
+    step_ms, scan_ms, kern_ms, ok = [], [], [], []
+    screen_used = None
+    launches0 = ch.ch_kernel_launches()
     for k in range(args.steps):
         flush.fill_(float(k))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -232,9 +234,12 @@ def main():
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         scan_ms.append(rep.t_scan_ms)
+        kern_ms.append(rep.t_kernel_ms)
+        screen_used = rep.screen
         ok.append(abs(eta / exact - 1.0) <= 0.1)
         T = rep.T
     torch.cuda.synchronize()
+    launches = ch.ch_kernel_launches() - launches0
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -267,20 +272,27 @@ def main():
             e2e_s.append(time.perf_counter() - t0)
     e2e_value = (NA + NB) / float(np.mean(e2e_s))
 
-    # roofline of the dominant kernel (the sampled scan)
+    # roofline of the dominant kernel (the sampled scan's main kernel), timed with
+    # CUDA events on the library's stream inside ch_estimate
     scan_avg = float(np.mean(scan_ms))
-    sm_mhz = clk.get("sm_mhz") or 1455.0
+    kern_avg = float(np.mean(kern_ms))
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if args.screen == "exact" or True:
-        # CUDA-core canonical distances: 2 FP32 instructions per (sample, b, coordinate)
-        ops = 2.0 * T * NB * DIM
+    flops = 2.0 * T * NB * DIM  # algorithmic: one multiply-add per (sample, b, coordinate)
+    if screen_used == ch.CH_SCREEN_EXACT:
         peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lanes x max clock, Tinst/s
-        roof = {"bound": "alu", "achieved": ops / (scan_avg / 1e3) / 1e12, "peak": peak, "unit": "Tinst/s",
-                "traffic": None, "kernel": "k_scan_exact (sampled scan, canonical fp32 distances)",
+        roof = {"bound": "alu", "achieved": flops / (kern_avg / 1e3) / 1e12, "peak": peak, "unit": "Tinst/s",
+                "traffic": None, "kernel": "k_scan_exact (canonical fp32 distances on CUDA cores)",
                 "peak_basis": "152 SMs x 128 FP32 lanes x sm_max_mhz (derived, not measured)"}
-        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        bf16 = peaks.get("bf16_tflops", 1910.1)
+        peak = bf16 * (1.1 / 2.25)  # TF32 dense = measured BF16 burst x nominal TF32/BF16 ratio
+        roof = {"bound": "tensor", "achieved": flops / (kern_avg / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "traffic": None, "kernel": "k_screen<TF32> (tcgen05 screen, 2*T*nB*d flops)",
+                "peak_basis": "of measured: bf16_tflops (burst) x 1.1/2.25 nominal tf32:bf16"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel_ms"] = kern_avg
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -298,10 +310,10 @@ def main():
             "accuracy": {"steps_within_10pct": int(sum(ok)), "steps": len(ok), "exact_ch": exact},
             "exact_gpu": {"ms": float(np.mean(exact_ms_ev)), "pts_per_s": (NA + NB) / (np.mean(exact_ms_ev) / 1e3),
                           "speedup_estimate_vs_exact": float(np.mean(exact_ms_ev)) / (total_ms / args.steps)},
-            "stage_ms": {"scan": scan_avg},
+            "stage_ms": {"scan": scan_avg, "scan_main_kernel": kern_avg},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (NA + NB) * DIM * 4,
                     "d2h_bytes_per_step": 48},
-            "gpu_launches": None,
+            "gpu_launches": launches,
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -110,6 +110,8 @@ typedef struct {
     int32_t top_exp;  /* finest..coarsest scales are 2^(top_exp-L+1) .. 2^top_exp */
     int32_t shift_S;  /* weights are ceil(D_a * 2^S) */
     float t_crude_ms, t_sample_ms, t_scan_ms, t_total_ms; /* device time per stage */
+    float t_kernel_ms;  /* device time of the scan's main kernel (screen or exact scan) */
+    int32_t screen;     /* ch_screen the scan actually used */
 } ch_est_report;
 
 /* Fill defaults: L1, 10 levels, k = 16, auto scales, HASH grouping, seeds 0,

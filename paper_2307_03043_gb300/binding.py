@@ -48,7 +48,7 @@ class ch_est_report(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("D_total", ctypes.c_double), ("W", ctypes.c_uint64),
                 ("T", ctypes.c_int64), ("top_exp", ctypes.c_int32), ("shift_S", ctypes.c_int32),
                 ("t_crude_ms", ctypes.c_float), ("t_sample_ms", ctypes.c_float), ("t_scan_ms", ctypes.c_float),
-                ("t_total_ms", ctypes.c_float)]
+                ("t_total_ms", ctypes.c_float), ("t_kernel_ms", ctypes.c_float), ("screen", ctypes.c_int32)]
 
 
 class ch_serve_config(ctypes.Structure):

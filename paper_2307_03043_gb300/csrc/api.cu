@@ -276,14 +276,17 @@ static void take_scan(L& lay, ch_ctx* c, const ch_set* A, const ch_set* B, int64
 }
 
 static void run_scan(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t T, const ch_set* B, int metric,
-                     uint32_t R, ScanBufs* sb, float* m, int64_t* argmin, uint32_t* status) {
+                     uint32_t R, ScanBufs* sb, float* m, int64_t* argmin, uint32_t* status,
+                     const KernelTimer& timer = KernelTimer()) {
   if (T == 0) return;
   if (sb->screen == CH_SCREEN_EXACT) {
+    timer.start(c->stream);
     launch_scan_exact(A, idx, T, B, metric, sb->part, c->sm_count, c->stream);
+    timer.stop(c->stream);
     launch_scan_merge(sb->part, T, idx, m, argmin, c->stream);
   } else {
     launch_screen_l2(A, idx, T, B, sb->screen, static_cast<int>(R), sb->screen_work, m, argmin, status, c->sm_count,
-                     c->stream);
+                     c->stream, timer);
   }
 }
 
@@ -654,7 +657,12 @@ ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_
   launch_weights(D, nA, w, sb.prefix, sb.sw, s);
   launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, idx, s);
   if (rep) CHX_CUDA(cudaEventRecord(c->ev[2], s));
-  run_scan(c, A, idx, T, B, p->hash.metric, R, &sc, m, nullptr, &res->status);
+  KernelTimer kt;
+  if (rep) {
+    kt.before = c->ev[5];
+    kt.after = c->ev[6];
+  }
+  run_scan(c, A, idx, T, B, p->hash.metric, R, &sc, m, nullptr, &res->status, kt);
   if (rep) CHX_CUDA(cudaEventRecord(c->ev[3], s));
   launch_combine(m, idx, w, sb.sw.W, T, D, nA, out2, s);
   k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, out2, sb.sw.W, sb.sw.S, cb.e_top);
@@ -673,6 +681,9 @@ ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_
     cudaEventElapsedTime(&rep->t_sample_ms, c->ev[1], c->ev[2]);
     cudaEventElapsedTime(&rep->t_scan_ms, c->ev[2], c->ev[3]);
     cudaEventElapsedTime(&rep->t_total_ms, c->ev[0], c->ev[4]);
+    rep->t_kernel_ms = 0.0f;
+    if (T > 0) cudaEventElapsedTime(&rep->t_kernel_ms, c->ev[5], c->ev[6]);
+    rep->screen = sc.screen;
   }
   return CH_OK;
   CHX_GUARD_END

@@ -276,6 +276,17 @@ void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, S
 void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed,
                   int64_t* idx, cudaStream_t s);
 
+// optional CUDA events recorded around a stage's main kernel
+struct KernelTimer {
+  cudaEvent_t before = nullptr, after = nullptr;
+  void start(cudaStream_t s) const {
+    if (before) cudaEventRecord(before, s);
+  }
+  void stop(cudaStream_t s) const {
+    if (after) cudaEventRecord(after, s);
+  }
+};
+
 // exact scan: per (sample, chunk) minima, then merge
 struct ScanPart {
   float* val;
@@ -292,7 +303,8 @@ int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count);
 bool screen_supported(int screen, const ch_set* A, const ch_set* B);
 size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int screen);
 void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R,
-                      void* work, float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s);
+                      void* work, float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s,
+                      const KernelTimer& timer);
 
 // combine: eta = (1/T) sum m_l W / w_{x_l} (binary64) and sum D (binary64)
 void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,

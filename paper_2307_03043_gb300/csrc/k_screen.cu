@@ -582,7 +582,8 @@ size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int s
 }
 
 void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R, void* work,
-                      float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s) {
+                      float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s,
+                      const KernelTimer& timer) {
   if (T == 0) return;
   const Plan p = make_plan(T, B->n, A->d, R, sm_count, screen);
   const int es = static_cast<int>(elem_size(A->dtype));
@@ -623,7 +624,9 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   do {                                                                                                      \
     auto kern = k_screen<SCR, RR>;                                                                          \
     CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem))); \
+    timer.start(s);                                                                                         \
     kern<<<p.grid, kThreads, p.smem, s>>>(tmQ, tmB, a);                                                     \
+    timer.stop(s);                                                                                          \
   } while (0)
 #define CHX_SCREEN_R(SCR)                   \
   do {                                      \
