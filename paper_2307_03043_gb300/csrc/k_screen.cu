@@ -9,7 +9,7 @@
 //   * one elected thread issues tcgen05.mma (kind::tf32 for binary32 data,
 //     kind::f16 with bf16 operands, kind::f8f6f4 with e4m3 operands) into a
 //     double-buffered 128 x 256 binary32 accumulator in tensor memory;
-//   * four epilogue warps read the accumulator with tcgen05.ld (one row per
+//   * eight epilogue warps read the accumulator with tcgen05.ld (one row per
 //     thread), form s and keep each row's R smallest (s, b) in registers.
 // Work items are (128-sample tile, chunk of B) pairs spread over a persistent
 // grid; a rerank kernel then takes each sample's R best screened candidates
@@ -31,7 +31,7 @@ namespace {
 constexpr int kBM = 128;          // samples per tile (TMEM lanes)
 constexpr int kBN = 256;          // B points per tile (accumulator columns)
 constexpr int kKB = 128;          // bytes of K per stage (one 128B swizzle row)
-constexpr int kThreads = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kThreads = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kMaxChunks = 32;
 constexpr int kMaxCand = 256;  // screened candidates per sample handed to the rerank
 constexpr long long kTimeoutCycles = 4000000000ll;  // ~2 s at 2 GHz
@@ -166,9 +166,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int S = args.stages;
   uint8_t* q_smem = smem;                                 // KB x (128 rows x 128 B)
   uint8_t* b_smem = q_smem + size_t(KB) * kBM * kKB;      // S x (256 rows x 128 B)
-  float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [4 warps][2][256] |b|^2
-  float* sb_s = nb_s + 8 * kBN;                                            // [4 warps][2][256] -2 x FP8 scale
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sb_s + 8 * kBN);
+  float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [8 warps][2][128] |b|^2
+  float* sb_s = nb_s + 8 * kBN;                                            // [8 warps][2][128] -2 x FP8 scale
+  float* cand_s = sb_s + 8 * kBN;                                          // [8 warps][32 lanes][33] spill rows
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cand_s + 8 * 32 * 33);
   uint64_t* full = bars;            // [S]
   uint64_t* empty = bars + S;       // [S]
   uint64_t* q_full = bars + 2 * S;  // [1]
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(q_empty, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 128);
+      mbar_init(&acc_empty[i], 256);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -285,8 +286,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------ epilogue: one sample row per thread
-    const int ew = warp & 3;  // TMEM lane quadrant this warp may access
+    // Eight warps: warp w reads TMEM lane quadrant w % 4 (the only one it may
+    // access) and one half (128 columns) of each accumulator tile.
+    const int ew = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = ew * 32 + lane;
+    float* cbuf = cand_s + size_t(warp - 2) * 32 * 33 + lane * 33;  // this lane's spill row
     uint32_t acc = 0, accphase = 0;
     for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
       const int mt = item % args.row_tiles, ck = item / args.row_tiles;
@@ -307,10 +312,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // stage |b|^2 (and -2 x FP8 scale) of this tile in this warp's own buffer;
         // +inf past the end of B.  Only __syncwarp is used inside the epilogue, so
         // a warp that gives up on a wait can never strand another one.
-        float* nb = nb_s + ((warp - 2) * 2 + acc) * kBN;
-        float* sb = sb_s + ((warp - 2) * 2 + acc) * kBN;
-        for (int c = lane; c < kBN; c += 32) {
-          const int64_t b = b0 + c;
+        const int64_t c0 = b0 + half * (kBN / 2);  // first B index of this warp's half
+        float* nb = nb_s + ((warp - 2) * 2 + acc) * (kBN / 2);
+        float* sb = sb_s + ((warp - 2) * 2 + acc) * (kBN / 2);
+        for (int c = lane; c < kBN / 2; c += 32) {
+          const int64_t b = c0 + c;
           nb[c] = (b < b_end) ? args.normB[b] : __int_as_float(0x7F800000);
           if constexpr (SCREEN == CH_SCREEN_FP8) sb[c] = (b < b_end) ? -2.0f * args.scaleB[b] : 0.0f;
         }
@@ -321,39 +327,55 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN;
+        const uint32_t taddr =
+            tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + half * (kBN / 2);
 #pragma unroll 1
-        for (int ch = 0; ch < kBN / 32; ++ch) {
+        for (int ch = 0; ch < kBN / 64; ++ch) {
           uint32_t r[32];
           tmem_ld32(taddr + ch * 32, r);
-          const float thr0 = top_s[R - 1];
-          // cheap pass: any candidate below the current R-th best?
+          // fast pass: scores of 32 columns and their minimum
           float mn = __int_as_float(0x7F800000);
-          float sv[32];
+          const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 32);
+          const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 32);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float a = __uint_as_float(r[i]);
-            if constexpr (SCREEN == CH_SCREEN_FP8)
-              sv[i] = fmaf(sb[ch * 32 + i] * sq, a, nb[ch * 32 + i]);
-            else
-              sv[i] = fmaf(-2.0f, a, nb[ch * 32 + i]);
-            mn = fminf(mn, sv[i]);
+          for (int q = 0; q < 8; ++q) {
+            const float4 n = nb4[q];
+            float4 m = make_float4(-2.0f, -2.0f, -2.0f, -2.0f);
+            if constexpr (SCREEN == CH_SCREEN_FP8) {
+              m = sb4[q];  // -2 x column scale, times this row's sample scale
+              m.x *= sq;
+              m.y *= sq;
+              m.z *= sq;
+              m.w *= sq;
+            }
+            float* rr = reinterpret_cast<float*>(&r[4 * q]);
+            rr[0] = fmaf(m.x, rr[0], n.x);
+            rr[1] = fmaf(m.y, rr[1], n.y);
+            rr[2] = fmaf(m.z, rr[2], n.z);
+            rr[3] = fmaf(m.w, rr[3], n.w);
+            mn = fminf(mn, fminf(fminf(rr[0], rr[1]), fminf(rr[2], rr[3])));
           }
-          if (mn < thr0) {
+          // slow pass, only when some lane of the warp has a candidate: spill the
+          // chunk to this lane's shared-memory row and insert sequentially
+          const bool cand = mn < top_s[R - 1];
+          if (__any_sync(0xFFFFFFFFu, cand)) {
+            if (cand) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              if (sv[i] < top_s[R - 1]) {
-                float cs = sv[i];
-                int32_t ci = static_cast<int32_t>(b0 + ch * 32 + i);
+              for (int i = 0; i < 32; ++i) cbuf[i] = __uint_as_float(r[i]);
+#pragma unroll 1
+              for (int i = 0; i < 32; ++i) {
+                float cs = cbuf[i];
+                if (cs < top_s[R - 1]) {
+                  int32_t ci = static_cast<int32_t>(c0 + ch * 32 + i);
 #pragma unroll
-                for (int k = 0; k < R; ++k) {
-                  if (cs < top_s[k]) {
+                  for (int k = 0; k < R; ++k) {
+                    const bool sw = cs < top_s[k];
                     const float ts = top_s[k];
                     const int32_t ti = top_i[k];
-                    top_s[k] = cs;
-                    top_i[k] = ci;
-                    cs = ts;
-                    ci = ti;
+                    top_s[k] = sw ? cs : ts;
+                    top_i[k] = sw ? ci : ti;
+                    cs = sw ? ts : cs;
+                    ci = sw ? ti : ci;
                   }
                 }
               }
@@ -368,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       if (grow < args.T) {
-        const size_t base = (size_t(ck) * args.T + grow) * R;
+        const size_t base = (size_t(ck * 2 + half) * args.T + grow) * R;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
           args.part_s[base + i] = top_s[i];
@@ -533,7 +555,7 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   p.R = R <= 8 ? 8 : R <= 16 ? 16 : 32;
   p.kblocks = static_cast<int>(ceil_div(int64_t(d) * es, kKB));
   p.row_tiles = static_cast<int>(ceil_div(std::max<int64_t>(T, 1), kBM));
-  const size_t fixed = 1024 + size_t(p.kblocks) * kBM * kKB + 16 * kBN * sizeof(float) + 256;
+  const size_t fixed = 1024 + size_t(p.kblocks) * kBM * kKB + 16 * kBN * sizeof(float) + 8 * 32 * 33 * sizeof(float) + 256;
   const size_t per_stage = size_t(kBN) * kKB;
   const size_t limit = 227 * 1024;
   p.stages = static_cast<int>(std::min<size_t>(6, (limit - std::min(limit, fixed)) / per_stage));
@@ -543,7 +565,7 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   int best_c = 1;
   double best_eff = 0.0;
   for (int c = 1; c <= kMaxChunks && c <= btiles; ++c) {
-    if (c * p.R > kMaxCand) break;
+    if (2 * c * p.R > kMaxCand) break;  // two column halves per chunk
     const int64_t items = int64_t(p.row_tiles) * c;
     const int64_t rounds = ceil_div(items, sm_count);
     const double eff = double(items) / double(rounds * sm_count);
@@ -577,7 +599,7 @@ size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int s
   const Plan p = make_plan(T, nB, d, R, sm_count, screen);
   const int es = static_cast<int>(elem_size(screen_dtype(screen)));
   const size_t q = ((size_t(T) * d * es + 255) & ~size_t(255)) + ((size_t(T) * 4 + 255) & ~size_t(255));
-  const size_t parts = size_t(p.chunks) * T * p.R * 8 + 512;
+  const size_t parts = size_t(2 * p.chunks) * T * p.R * 8 + 512;
   return q + parts + 1024;
 }
 
@@ -594,7 +616,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   float* sQ = reinterpret_cast<float*>(w);
   w += (size_t(T) * 4 + 255) & ~size_t(255);
   float* part_s = reinterpret_cast<float*>(w);
-  w += (size_t(p.chunks) * T * p.R * 4 + 255) & ~size_t(255);
+  w += (size_t(2 * p.chunks) * T * p.R * 4 + 255) & ~size_t(255);
   int32_t* part_i = reinterpret_cast<int32_t*>(w);
 
   const int64_t words = T * (row_bytes / 16);
@@ -644,13 +666,13 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   const int blocks = static_cast<int>(ceil_div(T, 8));
   if (A->dtype == CH_F32)
     k_rerank<CH_F32, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T, part_s,
-                                                   part_i, p.chunks, p.R, min_d, argmin);
+                                                   part_i, 2 * p.chunks, p.R, min_d, argmin);
   else if (A->dtype == CH_BF16)
     k_rerank<CH_BF16, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
-                                                    part_s, part_i, p.chunks, p.R, min_d, argmin);
+                                                    part_s, part_i, 2 * p.chunks, p.R, min_d, argmin);
   else
     k_rerank<CH_FP8E4M3, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
-                                                       part_s, part_i, p.chunks, p.R, min_d, argmin);
+                                                       part_s, part_i, 2 * p.chunks, p.R, min_d, argmin);
   launch_check("rerank");
 }
 
