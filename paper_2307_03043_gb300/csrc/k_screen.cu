@@ -33,7 +33,8 @@ constexpr int kBN = 256;          // B points per tile (accumulator columns)
 constexpr int kKB = 128;          // bytes of K per stage (one 128B swizzle row)
 constexpr int kThreads = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kMaxChunks = 32;
-constexpr int kMaxCand = 256;  // screened candidates per sample handed to the rerank
+constexpr int kClasses = 32;   // running minima per row and column partition (column mod 32)
+constexpr int kMaxCand = 512;  // screened candidates per sample handed to the rerank
 constexpr long long kTimeoutCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -157,7 +158,7 @@ struct ScreenArgs {
   uint32_t* status;
 };
 
-template <int SCREEN, int R>
+template <int SCREEN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_screen(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmB, ScreenArgs args) {
   extern __shared__ uint8_t smem_raw[];
@@ -168,8 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* b_smem = q_smem + size_t(KB) * kBM * kKB;      // S x (256 rows x 128 B)
   float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [8 warps][2][128] |b|^2
   float* sb_s = nb_s + 8 * kBN;                                            // [8 warps][2][128] -2 x FP8 scale
-  float* cand_s = sb_s + 8 * kBN;                                          // [8 warps][32 lanes][33] spill rows
-  uint64_t* bars = reinterpret_cast<uint64_t*>(cand_s + 8 * 32 * 33);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sb_s + 8 * kBN);
   uint64_t* full = bars;            // [S]
   uint64_t* empty = bars + S;       // [S]
   uint64_t* q_full = bars + 2 * S;  // [1]
@@ -291,7 +291,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ew = warp & 3;
     const int half = (warp - 2) >> 2;
     const int row = ew * 32 + lane;
-    float* cbuf = cand_s + size_t(warp - 2) * 32 * 33 + lane * 33;  // this lane's spill row
     uint32_t acc = 0, accphase = 0;
     for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
       const int mt = item % args.row_tiles, ck = item / args.row_tiles;
@@ -300,13 +299,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t grow = int64_t(mt) * kBM + row;
       float sq = 1.0f;
       if constexpr (SCREEN == CH_SCREEN_FP8) sq = (grow < args.T) ? args.scaleQ[grow] : 1.0f;
-      float top_s[R];
-      int32_t top_i[R];
+      // 32 running minima per row, one per residue class (column mod 32) of this
+      // warp's half-columns; best_c holds the 32-column group of each minimum.
+      float best_s[32];
+      int32_t best_c[32];
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        top_s[i] = __int_as_float(0x7F800000);
-        top_i[i] = -1;
+      for (int i = 0; i < 32; ++i) {
+        best_s[i] = __int_as_float(0x7F800000);
+        best_c[i] = -1;
       }
+      int32_t group = 0;  // running 32-column group index within this half
       bool ok = true;
       for (int64_t b0 = b_begin; b0 < b_end; b0 += kBN) {
         // stage |b|^2 (and -2 x FP8 scale) of this tile in this warp's own buffer;
@@ -333,8 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int ch = 0; ch < kBN / 64; ++ch) {
           uint32_t r[32];
           tmem_ld32(taddr + ch * 32, r);
-          // fast pass: scores of 32 columns and their minimum
-          float mn = __int_as_float(0x7F800000);
+          // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 32 columns
           const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 32);
           const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 32);
 #pragma unroll
@@ -348,39 +349,20 @@ __global__ void __launch_bounds__(kThreads, 1)
               m.z *= sq;
               m.w *= sq;
             }
-            float* rr = reinterpret_cast<float*>(&r[4 * q]);
-            rr[0] = fmaf(m.x, rr[0], n.x);
-            rr[1] = fmaf(m.y, rr[1], n.y);
-            rr[2] = fmaf(m.z, rr[2], n.z);
-            rr[3] = fmaf(m.w, rr[3], n.w);
-            mn = fminf(mn, fminf(fminf(rr[0], rr[1]), fminf(rr[2], rr[3])));
+            r[4 * q + 0] = __float_as_uint(fmaf(m.x, __uint_as_float(r[4 * q + 0]), n.x));
+            r[4 * q + 1] = __float_as_uint(fmaf(m.y, __uint_as_float(r[4 * q + 1]), n.y));
+            r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
+            r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
           }
-          // slow pass, only when some lane of the warp has a candidate: spill the
-          // chunk to this lane's shared-memory row and insert sequentially
-          const bool cand = mn < top_s[R - 1];
-          if (__any_sync(0xFFFFFFFFu, cand)) {
-            if (cand) {
+          // branch-free update of the residue-class minima
 #pragma unroll
-              for (int i = 0; i < 32; ++i) cbuf[i] = __uint_as_float(r[i]);
-#pragma unroll 1
-              for (int i = 0; i < 32; ++i) {
-                float cs = cbuf[i];
-                if (cs < top_s[R - 1]) {
-                  int32_t ci = static_cast<int32_t>(c0 + ch * 32 + i);
-#pragma unroll
-                  for (int k = 0; k < R; ++k) {
-                    const bool sw = cs < top_s[k];
-                    const float ts = top_s[k];
-                    const int32_t ti = top_i[k];
-                    top_s[k] = sw ? cs : ts;
-                    top_i[k] = sw ? ci : ti;
-                    cs = sw ? ts : cs;
-                    ci = sw ? ti : ci;
-                  }
-                }
-              }
-            }
+          for (int i = 0; i < 32; ++i) {
+            const float v = __uint_as_float(r[i]);
+            const bool lt = v < best_s[i];
+            best_s[i] = lt ? v : best_s[i];
+            best_c[i] = lt ? group : best_c[i];
           }
+          ++group;
         }
         tc_fence_before();
         mbar_arrive(&acc_empty[acc]);
@@ -390,11 +372,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       if (grow < args.T) {
-        const size_t base = (size_t(ck * 2 + half) * args.T + grow) * R;
+        // group g of class i is column b_begin + (g/4)*256 + half*128 + (g%4)*32 + i
+        const size_t base = (size_t(ck * 2 + half) * args.T + grow) * kClasses;
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-          args.part_s[base + i] = top_s[i];
-          args.part_i[base + i] = top_i[i];
+        for (int i = 0; i < kClasses; ++i) {
+          const int32_t g = best_c[i];
+          args.part_s[base + i] = best_s[i];
+          args.part_i[base + i] =
+              g < 0 ? -1
+                    : static_cast<int32_t>(b_begin + int64_t(g >> 2) * kBN + half * (kBN / 2) + (g & 3) * 32 + i);
         }
       }
     }
@@ -438,8 +424,8 @@ __global__ void k_gather_rows(const uint8_t* A, const float* scA, int64_t nA, in
 template <int DT, int METRIC>
 __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA, int64_t nA, const void* B,
                                                 const float* scB, int d, const int64_t* idx, int64_t T,
-                                                const float* part_s, const int32_t* part_i, int chunks, int R,
-                                                float* min_d, int64_t* argmin) {
+                                                const float* part_s, const int32_t* part_i, int parts, int per,
+                                                int R, float* min_d, int64_t* argmin) {
   __shared__ float s_s[8][kMaxCand];
   __shared__ int32_t s_i[8][kMaxCand];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -453,10 +439,10 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
     }
     return;
   }
-  const int nc = chunks * R;
+  const int nc = parts * per;
   for (int p = lane; p < nc; p += 32) {
-    const int c = p / R, k = p % R;
-    const size_t off = (size_t(c) * T + l) * R + k;
+    const int c = p / per, k = p % per;
+    const size_t off = (size_t(c) * T + l) * per + k;
     s_s[wib][p] = part_s[off];
     s_i[wib][p] = part_i[off];
   }
@@ -552,10 +538,10 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   Plan p;
   const int es = static_cast<int>(elem_size(screen_dtype(screen)));
   p.T = T;
-  p.R = R <= 8 ? 8 : R <= 16 ? 16 : 32;
+  p.R = std::max(1, std::min(R, 32));  // candidates the rerank evaluates exactly
   p.kblocks = static_cast<int>(ceil_div(int64_t(d) * es, kKB));
   p.row_tiles = static_cast<int>(ceil_div(std::max<int64_t>(T, 1), kBM));
-  const size_t fixed = 1024 + size_t(p.kblocks) * kBM * kKB + 16 * kBN * sizeof(float) + 8 * 32 * 33 * sizeof(float) + 256;
+  const size_t fixed = 1024 + size_t(p.kblocks) * kBM * kKB + 16 * kBN * sizeof(float) + 256;
   const size_t per_stage = size_t(kBN) * kKB;
   const size_t limit = 227 * 1024;
   p.stages = static_cast<int>(std::min<size_t>(6, (limit - std::min(limit, fixed)) / per_stage));
@@ -565,7 +551,7 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   int best_c = 1;
   double best_eff = 0.0;
   for (int c = 1; c <= kMaxChunks && c <= btiles; ++c) {
-    if (2 * c * p.R > kMaxCand) break;  // two column halves per chunk
+    if (2 * c * kClasses > kMaxCand) break;  // two column halves per chunk
     const int64_t items = int64_t(p.row_tiles) * c;
     const int64_t rounds = ceil_div(items, sm_count);
     const double eff = double(items) / double(rounds * sm_count);
@@ -599,7 +585,7 @@ size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int s
   const Plan p = make_plan(T, nB, d, R, sm_count, screen);
   const int es = static_cast<int>(elem_size(screen_dtype(screen)));
   const size_t q = ((size_t(T) * d * es + 255) & ~size_t(255)) + ((size_t(T) * 4 + 255) & ~size_t(255));
-  const size_t parts = size_t(2 * p.chunks) * T * p.R * 8 + 512;
+  const size_t parts = size_t(2 * p.chunks) * T * kClasses * 8 + 512;
   return q + parts + 1024;
 }
 
@@ -616,7 +602,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   float* sQ = reinterpret_cast<float*>(w);
   w += (size_t(T) * 4 + 255) & ~size_t(255);
   float* part_s = reinterpret_cast<float*>(w);
-  w += (size_t(2 * p.chunks) * T * p.R * 4 + 255) & ~size_t(255);
+  w += (size_t(2 * p.chunks) * T * kClasses * 4 + 255) & ~size_t(255);
   int32_t* part_i = reinterpret_cast<int32_t*>(w);
 
   const int64_t words = T * (row_bytes / 16);
@@ -642,37 +628,30 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   a.part_i = part_i;
   a.status = status;
 
-#define CHX_SCREEN_LAUNCH(SCR, RR)                                                                          \
+#define CHX_SCREEN_LAUNCH(SCR)                                                                              \
   do {                                                                                                      \
-    auto kern = k_screen<SCR, RR>;                                                                          \
+    auto kern = k_screen<SCR>;                                                                              \
     CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem))); \
     timer.start(s);                                                                                         \
     kern<<<p.grid, kThreads, p.smem, s>>>(tmQ, tmB, a);                                                     \
     timer.stop(s);                                                                                          \
   } while (0)
-#define CHX_SCREEN_R(SCR)                   \
-  do {                                      \
-    if (p.R == 8) CHX_SCREEN_LAUNCH(SCR, 8); \
-    else if (p.R == 16) CHX_SCREEN_LAUNCH(SCR, 16); \
-    else CHX_SCREEN_LAUNCH(SCR, 32);        \
-  } while (0)
-  if (screen == CH_SCREEN_TF32) CHX_SCREEN_R(CH_SCREEN_TF32);
-  else if (screen == CH_SCREEN_BF16) CHX_SCREEN_R(CH_SCREEN_BF16);
-  else CHX_SCREEN_R(CH_SCREEN_FP8);
-#undef CHX_SCREEN_R
+  if (screen == CH_SCREEN_TF32) CHX_SCREEN_LAUNCH(CH_SCREEN_TF32);
+  else if (screen == CH_SCREEN_BF16) CHX_SCREEN_LAUNCH(CH_SCREEN_BF16);
+  else CHX_SCREEN_LAUNCH(CH_SCREEN_FP8);
 #undef CHX_SCREEN_LAUNCH
   launch_check("screen");
 
   const int blocks = static_cast<int>(ceil_div(T, 8));
   if (A->dtype == CH_F32)
     k_rerank<CH_F32, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T, part_s,
-                                                   part_i, 2 * p.chunks, p.R, min_d, argmin);
+                                                   part_i, 2 * p.chunks, kClasses, p.R, min_d, argmin);
   else if (A->dtype == CH_BF16)
     k_rerank<CH_BF16, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
-                                                    part_s, part_i, 2 * p.chunks, p.R, min_d, argmin);
+                                                    part_s, part_i, 2 * p.chunks, kClasses, p.R, min_d, argmin);
   else
     k_rerank<CH_FP8E4M3, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
-                                                       part_s, part_i, 2 * p.chunks, p.R, min_d, argmin);
+                                                       part_s, part_i, 2 * p.chunks, kClasses, p.R, min_d, argmin);
   launch_check("rerank");
 }
 
