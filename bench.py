@@ -222,7 +222,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, scan_ms, kern_ms, ok = [], [], [], []
+    step_ms, scan_ms, kern_ms, ok, stages = [], [], [], [], []
     screen_used = None
     launches0 = ch.ch_kernel_launches()
     for k in range(args.steps):
@@ -235,6 +235,7 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
         scan_ms.append(rep.t_scan_ms)
         kern_ms.append(rep.t_kernel_ms)
+        stages.append((rep.t_crude_ms, rep.t_sample_ms, rep.t_scan_ms, rep.t_total_ms))
         screen_used = rep.screen
         ok.append(abs(eta / exact - 1.0) <= 0.1)
         T = rep.T
@@ -310,7 +311,11 @@ def main():
             "accuracy": {"steps_within_10pct": int(sum(ok)), "steps": len(ok), "exact_ch": exact},
             "exact_gpu": {"ms": float(np.mean(exact_ms_ev)), "pts_per_s": (NA + NB) / (np.mean(exact_ms_ev) / 1e3),
                           "speedup_estimate_vs_exact": float(np.mean(exact_ms_ev)) / (total_ms / args.steps)},
-            "stage_ms": {"scan": scan_avg, "scan_main_kernel": kern_avg},
+            "stage_ms": {"crude_nn": float(np.mean([s[0] for s in stages])),
+                         "sample": float(np.mean([s[1] for s in stages])),
+                         "scan": scan_avg, "scan_main_kernel": kern_avg,
+                         "estimate_total": float(np.mean([s[3] for s in stages])),
+                         "step": total_ms / args.steps},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (NA + NB) * DIM * 4,
                     "d2h_bytes_per_step": 48},
             "gpu_launches": launches,

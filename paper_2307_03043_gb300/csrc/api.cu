@@ -638,7 +638,7 @@ ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_
   double* out2 = nullptr;
   carve(c, [&](auto& lay) {
     res = lay.template take<ResBlock>(1);
-    out2 = lay.template take<double>(2);
+    out2 = lay.template take<double>(kCombineDoubles);
     take_crude(lay, A, B, &p->hash, &cb);
     bidx = lay.template take<int64_t>(nA);
     level = lay.template take<uint8_t>(nA);
@@ -704,7 +704,7 @@ ch_status ch_exact(ch_ctx* c, const ch_set* A, const ch_set* B, int32_t metric, 
   double* out2 = nullptr;
   carve(c, [&](auto& lay) {
     res = lay.template take<ResBlock>(1);
-    out2 = lay.template take<double>(2);
+    out2 = lay.template take<double>(kCombineDoubles);
     take_scan(lay, c, A, B, nA, metric, mode == 0 ? CH_SCREEN_EXACT : CH_SCREEN_AUTO, 8, &sc);
     float* tmp = lay.template take<float>(std::max<int64_t>(nA, 1));
     if (!per_a_min) mins = tmp;

@@ -203,6 +203,7 @@ __host__ __device__ inline int ceil_log2_i64(int64_t n) {
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__device__ inline int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline uint32_t next_pow2_u32(uint64_t x) {
   uint32_t p = 1;
   while (p < x) p <<= 1;
@@ -306,10 +307,15 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
                       void* work, float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s,
                       const KernelTimer& timer);
 
-// combine: eta = (1/T) sum m_l W / w_{x_l} (binary64) and sum D (binary64)
+// combine: eta = (1/T) sum m_l W / w_{x_l} (binary64) and sum D (binary64).
+// out must hold kCombineDoubles doubles: out[0] = eta, out[1] = sum D, then
+// per-block partials.  The block count is fixed, so the summation order (and
+// the result's bits) do not depend on the GPU.
+constexpr int kCombineBlocks = 128;
+constexpr int kCombineDoubles = 2 + 2 * kCombineBlocks;
 void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
-                    const float* D, int64_t nA, double* out2, cudaStream_t s);
-// sum of per-a minima (binary64)
-void launch_sum_f32(const float* v, int64_t n, double* out2 /* out2[1] = sum */, cudaStream_t s);
+                    const float* D, int64_t nA, double* out, cudaStream_t s);
+// sum of per-a minima (binary64): out[1] = sum (same layout as launch_combine)
+void launch_sum_f32(const float* v, int64_t n, double* out, cudaStream_t s);
 
 }  // namespace chx

@@ -32,22 +32,42 @@ __global__ void __launch_bounds__(256) k_ingest(const void* X, const float* scal
     hi[b] = 0u;
   }
   bool bad = false;
-  for (int64_t r = int64_t(blockIdx.x) * warps + warp; r < n; r += int64_t(gridDim.x) * warps) {
-    float sq = 0.0f;
-    if constexpr (CB > 0) {
+  if constexpr (CB > 0) {
+    // four rows per warp iteration; every load of the four rows is issued first
+    constexpr int RPW = 4;
+    for (int64_t r0 = (int64_t(blockIdx.x) * warps + warp) * RPW; r0 < n; r0 += int64_t(gridDim.x) * warps * RPW) {
+      float v[RPW][CB];
 #pragma unroll
-      for (int b = 0; b < CB; ++b) {
-        const int c = b * 32 + lane;
-        if (c < d) {
-          const float v = load_elem<DT>(X, r, d, c, scales);
-          bad |= !isfinite(v);
-          sq = fmaf(v, v, sq);
-          const uint32_t o = ord_enc(v);
-          lo[b] = min(lo[b], o);
-          hi[b] = max(hi[b], o);
+      for (int q = 0; q < RPW; ++q)
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+          const int c = b * 32 + lane;
+          v[q][b] = (r0 + q < n && c < d) ? load_elem<DT>(X, r0 + q, d, c, scales) : 0.0f;
         }
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        float sq = 0.0f;
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+          const int c = b * 32 + lane;
+          if (r0 + q < n && c < d) {
+            const float x = v[q][b];
+            bad |= !isfinite(x);
+            sq = fmaf(x, x, sq);
+            const uint32_t o = ord_enc(x);
+            lo[b] = min(lo[b], o);
+            hi[b] = max(hi[b], o);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xFFFFFFFFu, sq, o);
+        if (lane == 0 && r0 + q < n) norms[r0 + q] = sq;
       }
-    } else {
+    }
+  }
+  for (int64_t r = int64_t(blockIdx.x) * warps + warp; CB == 0 && r < n; r += int64_t(gridDim.x) * warps) {
+    float sq = 0.0f;
+    {
       for (int c = lane; c < d; c += 32) {
         const float v = load_elem<DT>(X, r, d, c, scales);
         bad |= !isfinite(v);
@@ -148,14 +168,17 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
   for (int j0 = 0; j0 < d; j0 += 32) {
     const int jn = min(32, d - j0);
     __syncthreads();
-    // stage: warp w loads rows w, w+4, ...; lane = coordinate within the segment
+    // stage: warp w holds rows w, w+4, ..., lane = coordinate within the 32-wide
+    // segment (coalesced); all 32 loads of a thread are issued before any store
     const int lane = tid & 31, warp = tid >> 5;
-    for (int rr = warp; rr < 128; rr += 4) {
-      const int64_t row = r0 + rr;
-      float v = 0.0f;
-      if (row < n && lane < jn) v = load_elem<DT>(X, row, d, j0 + lane, scales);
-      s_x[rr][lane] = v;
+    float v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int64_t row = r0 + warp + 4 * q;
+      v[q] = (row < n && lane < jn) ? load_elem<DT>(X, row, d, j0 + lane, scales) : 0.0f;
     }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) s_x[warp + 4 * q][lane] = v[q];
     for (int t = tid; t < 32 * KP; t += 128) {
       const int jj = t / KP, ii = t % KP;
       s_g[jj][ii] = (jj < jn) ? G[int64_t(j0 + jj) * KP + ii] : 0.0f;
@@ -168,8 +191,11 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
     }
   }
   const bool live = r < n;
-  if (live)
-    for (int i = 0; i < k; ++i) Y[r * k + i] = acc[i];
+  if (live) {
+#pragma unroll
+    for (int i = 0; i < KP; ++i)
+      if (i < k) Y[r * k + i] = acc[i];
+  }
   // bounding box of the embedding
   const int lane = tid & 31;
 #pragma unroll
@@ -299,8 +325,7 @@ __device__ inline void point_keys(const HashSrc& src, int64_t r, int L, int L0, 
     inv_r[l] = (l < nl) ? __ldg(&t.inv_r[L0 + l]) : 1.0f;
   }
   const int dd = src.dd;
-  for (int j = 0; j < dd; ++j) {
-    const float y = load_elem<DT>(src.base, r, dd, j, src.scales);
+  auto accumulate = [&](int j, float y) {
     const uint64_t K = __ldg(reinterpret_cast<const unsigned long long*>(&t.mult[j]));
     const uint32_t klo = uint32_t(K), khi = uint32_t(K >> 32);
     const float* zrow = t.shift + int64_t(j) * L + L0;
@@ -314,6 +339,17 @@ __device__ inline void point_keys(const HashSrc& src, int64_t r, int L, int L0, 
         h[l] += uint64_t(bits) * klo + (uint64_t(bits * khi) << 32);
       }
     }
+  };
+  if (dd <= 32) {
+    // narrow rows (always the case for the l2 embedding): issue every load first
+    float y[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) y[j] = (j < dd) ? load_elem<DT>(src.base, r, dd, j, src.scales) : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < dd) accumulate(j, y[j]);
+  } else {
+    for (int j = 0; j < dd; ++j) accumulate(j, load_elem<DT>(src.base, r, dd, j, src.scales));
   }
 #pragma unroll
   for (int l = 0; l < kLevelBlock; ++l) {

@@ -171,46 +171,71 @@ void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t
 }
 
 // ------------------------------------------------------------------ combine
-// out[0] = (1/T) sum_l m_l W / w_{x_l}; out[1] = sum_a D_a   (binary64, fixed tree order)
-__global__ void __launch_bounds__(1024) k_combine(const float* m, const int64_t* idx, const uint64_t* w,
-                                                  const uint64_t* Wp, int64_t T, const float* D, int64_t nA,
-                                                  double* out) {
-  __shared__ double s_a[1024], s_b[1024];
-  const uint64_t W = Wp ? *Wp : 0;
-  double acc = 0.0, accD = 0.0;
-  if (W != 0)
-    for (int64_t l = threadIdx.x; l < T; l += blockDim.x) {
-      const int64_t x = idx[l];
-      acc += static_cast<double>(m[l]) * (static_cast<double>(W) / static_cast<double>(w[x]));
-    }
-  if (D)
-    for (int64_t a = threadIdx.x; a < nA; a += blockDim.x) accD += static_cast<double>(D[a]);
-  s_a[threadIdx.x] = acc;
-  s_b[threadIdx.x] = accD;
+// Two fixed-shape passes (kCombineBlocks blocks of 256, then one block), so the
+// binary64 summation order is the same on every GPU:
+//   out[0] = (1/T) sum_l m_l W / w_{x_l};  out[1] = sum_a D_a.
+// Block b sums the contiguous slices [b*len, (b+1)*len) of the samples and of D.
+__device__ inline void block_sum2(double& a, double& b, double* sa, double* sb) {
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
   __syncthreads();
   for (int st = blockDim.x / 2; st > 0; st >>= 1) {
     if (threadIdx.x < st) {
-      s_a[threadIdx.x] += s_a[threadIdx.x + st];
-      s_b[threadIdx.x] += s_b[threadIdx.x + st];
+      sa[threadIdx.x] += sa[threadIdx.x + st];
+      sb[threadIdx.x] += sb[threadIdx.x + st];
     }
     __syncthreads();
   }
+  a = sa[0];
+  b = sb[0];
+}
+
+__global__ void __launch_bounds__(256) k_combine_part(const float* m, const int64_t* idx, const uint64_t* w,
+                                                      const uint64_t* Wp, int64_t T, const float* D, int64_t nA,
+                                                      double* out) {
+  __shared__ double s_a[256], s_b[256];
+  const uint64_t W = Wp ? *Wp : 0;
+  const int64_t lt = ceil_div_dev(T, kCombineBlocks), la = ceil_div_dev(nA, kCombineBlocks);
+  double acc = 0.0, accD = 0.0;
+  if (W != 0) {
+    const double Wd = static_cast<double>(W);
+    const int64_t end = min(T, (blockIdx.x + 1) * lt);
+    for (int64_t l = blockIdx.x * lt + threadIdx.x; l < end; l += blockDim.x)
+      acc += static_cast<double>(m[l]) * (Wd / static_cast<double>(w[idx[l]]));
+  }
+  if (D) {
+    const int64_t end = min(nA, (blockIdx.x + 1) * la);
+    for (int64_t a = blockIdx.x * la + threadIdx.x; a < end; a += blockDim.x) accD += static_cast<double>(D[a]);
+  }
+  block_sum2(acc, accD, s_a, s_b);
   if (threadIdx.x == 0) {
-    out[0] = (W != 0 && T > 0) ? s_a[0] / static_cast<double>(T) : 0.0;
-    out[1] = s_b[0];
+    out[2 + 2 * blockIdx.x] = acc;
+    out[3 + 2 * blockIdx.x] = accD;
+  }
+}
+
+__global__ void __launch_bounds__(kCombineBlocks) k_combine_final(const uint64_t* Wp, int64_t T, double* out) {
+  __shared__ double s_a[kCombineBlocks], s_b[kCombineBlocks];
+  double a = out[2 + 2 * threadIdx.x], b = out[3 + 2 * threadIdx.x];
+  block_sum2(a, b, s_a, s_b);
+  if (threadIdx.x == 0) {
+    const uint64_t W = Wp ? *Wp : 0;
+    out[0] = (W != 0 && T > 0) ? a / static_cast<double>(T) : 0.0;
+    out[1] = b;
   }
 }
 
 void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
-                    const float* D, int64_t nA, double* out2, cudaStream_t s) {
-  k_combine<<<1, 1024, 0, s>>>(m, idx, w, W, T, D, nA, out2);
-  launch_check("combine");
+                    const float* D, int64_t nA, double* out, cudaStream_t s) {
+  k_combine_part<<<kCombineBlocks, 256, 0, s>>>(m, idx, w, W, T, D, nA, out);
+  launch_check("combine_part");
+  k_combine_final<<<1, kCombineBlocks, 0, s>>>(W, T, out);
+  launch_check("combine_final");
 }
 
-void launch_sum_f32(const float* v, int64_t n, double* out2, cudaStream_t s) {
-  // out2[1] = sum v (binary64), out2[0] = 0; the combine reduction with no samples
-  k_combine<<<1, 1024, 0, s>>>(nullptr, nullptr, nullptr, nullptr, 0, v, n, out2);
-  launch_check("sum_f32");
+void launch_sum_f32(const float* v, int64_t n, double* out, cudaStream_t s) {
+  // out[1] = sum v (binary64), out[0] = 0: the combine reduction with no samples
+  launch_combine(nullptr, nullptr, nullptr, nullptr, 0, v, n, out, s);
 }
 
 }  // namespace chx
