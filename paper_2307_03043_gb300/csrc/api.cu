@@ -355,6 +355,17 @@ ch_status ch_ctx_create(int device, void* stream, ch_ctx** out) {
     c->own_stream = true;
   }
   CHX_CUDA(cudaMallocHost(&c->host_pin, 4096));
+  {
+    // sets come and go per request: a private pool that keeps freed memory
+    // (release threshold = max) makes their allocation a stream-ordered reuse
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    CHX_CUDA(cudaMemPoolCreate(&c->pool, &props));
+    uint64_t keep = ~uint64_t(0);
+    CHX_CUDA(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  }
   for (auto& e : c->ev) CHX_CUDA(cudaEventCreate(&e));
   *out = c;
   return CH_OK;
@@ -374,6 +385,7 @@ void ch_ctx_destroy(ch_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   c->ws.release();
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->host_pin) cudaFreeHost(c->host_pin);
@@ -418,7 +430,7 @@ ch_status ch_set_create(ch_ctx* c, const void* data, int mode, int64_t n, int32_
       X->data = const_cast<void*>(data);
       X->owned = false;
     } else {
-      CHX_CUDA(cudaMallocAsync(&X->data, std::max<size_t>(bytes, 16), s));
+      CHX_CUDA(cudaMallocFromPoolAsync(&X->data, std::max<size_t>(bytes, 16), c->pool, s));
       X->owned = true;
       if (bytes)
         CHX_CUDA(cudaMemcpyAsync(X->data, data, bytes, mode == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
@@ -429,7 +441,7 @@ ch_status ch_set_create(ch_ctx* c, const void* data, int mode, int64_t n, int32_
     const size_t bb = (size_t(2) * d * 4 + 255) & ~size_t(255);
     const size_t sb = dtype == CH_FP8E4M3 ? nb : 0;
     char* aux = nullptr;
-    CHX_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&aux), nb + 256 + bb + sb, s));
+    CHX_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&aux), nb + 256 + bb + sb, c->pool, s));
     X->norms = reinterpret_cast<float*>(aux);
     X->status = reinterpret_cast<uint32_t*>(aux + nb);
     X->box_x = reinterpret_cast<uint32_t*>(aux + nb + 256);

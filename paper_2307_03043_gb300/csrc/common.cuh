@@ -97,6 +97,7 @@ struct ch_ctx {
   bool own_stream = false;
   int sm_count = 0;
   chx::Arena ws;
+  cudaMemPool_t pool = nullptr;  // stream-ordered pool for sets; keeps freed memory
   void* host_pin = nullptr;   // pinned page for small readbacks
   std::string err;
   cudaEvent_t ev[8] = {};

@@ -157,52 +157,80 @@ __global__ void k_gauss(uint64_t seed, int k, int kp, int d, float* G /* [d][kp]
 template <int DT, int KP>
 __global__ void __launch_bounds__(128) k_project(const void* X, const float* scales, int64_t n, int d,
                                                  const float* G, int k, float* Y, uint32_t* box) {
-  __shared__ float s_x[128][33];
-  __shared__ float s_g[32][KP];
-  const int64_t r0 = int64_t(blockIdx.x) * 128;
+  // RPT rows per thread (rows tid and tid + 128) so that each G value read from
+  // shared memory feeds RPT fused multiply-adds
+  constexpr int RPT = KP <= 16 ? 2 : 1;
+  __shared__ float s_x[128 * RPT][33];
+  __shared__ __align__(16) float s_g[32][KP];
+  const int64_t r0 = int64_t(blockIdx.x) * 128 * RPT;
   const int tid = threadIdx.x;
-  const int64_t r = r0 + tid;
-  float acc[KP];
+  float acc[RPT][KP];
 #pragma unroll
-  for (int i = 0; i < KP; ++i) acc[i] = 0.0f;
+  for (int p = 0; p < RPT; ++p)
+#pragma unroll
+    for (int i = 0; i < KP; ++i) acc[p][i] = 0.0f;
   for (int j0 = 0; j0 < d; j0 += 32) {
     const int jn = min(32, d - j0);
     __syncthreads();
     // stage: warp w holds rows w, w+4, ..., lane = coordinate within the 32-wide
-    // segment (coalesced); all 32 loads of a thread are issued before any store
+    // segment (coalesced); the 32 loads of a pass are issued before any store
     const int lane = tid & 31, warp = tid >> 5;
-    float v[32];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int64_t row = r0 + warp + 4 * q;
-      v[q] = (row < n && lane < jn) ? load_elem<DT>(X, row, d, j0 + lane, scales) : 0.0f;
+    for (int p = 0; p < RPT; ++p) {
+      float v[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int64_t row = r0 + p * 128 + warp + 4 * q;
+        v[q] = (row < n && lane < jn) ? load_elem<DT>(X, row, d, j0 + lane, scales) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 32; ++q) s_x[p * 128 + warp + 4 * q][lane] = v[q];
     }
-#pragma unroll
-    for (int q = 0; q < 32; ++q) s_x[warp + 4 * q][lane] = v[q];
     for (int t = tid; t < 32 * KP; t += 128) {
       const int jj = t / KP, ii = t % KP;
       s_g[jj][ii] = (jj < jn) ? G[int64_t(j0 + jj) * KP + ii] : 0.0f;
     }
     __syncthreads();
     for (int jj = 0; jj < jn; ++jj) {
-      const float xv = s_x[tid][jj];
+      float xv[RPT];
 #pragma unroll
-      for (int i = 0; i < KP; ++i) acc[i] = __fmaf_rn(s_g[jj][i], xv, acc[i]);
+      for (int p = 0; p < RPT; ++p) xv[p] = s_x[p * 128 + tid][jj];
+      const float4* g4 = reinterpret_cast<const float4*>(&s_g[jj][0]);
+#pragma unroll
+      for (int i4 = 0; i4 < KP / 4; ++i4) {
+        const float4 g = g4[i4];
+#pragma unroll
+        for (int p = 0; p < RPT; ++p) {
+          acc[p][4 * i4 + 0] = __fmaf_rn(g.x, xv[p], acc[p][4 * i4 + 0]);
+          acc[p][4 * i4 + 1] = __fmaf_rn(g.y, xv[p], acc[p][4 * i4 + 1]);
+          acc[p][4 * i4 + 2] = __fmaf_rn(g.z, xv[p], acc[p][4 * i4 + 2]);
+          acc[p][4 * i4 + 3] = __fmaf_rn(g.w, xv[p], acc[p][4 * i4 + 3]);
+        }
+      }
     }
   }
-  const bool live = r < n;
-  if (live) {
 #pragma unroll
-    for (int i = 0; i < KP; ++i)
-      if (i < k) Y[r * k + i] = acc[i];
+  for (int p = 0; p < RPT; ++p) {
+    const int64_t r = r0 + p * 128 + tid;
+    if (r < n) {
+#pragma unroll
+      for (int i = 0; i < KP; ++i)
+        if (i < k) Y[r * k + i] = acc[p][i];
+    }
   }
   // bounding box of the embedding
   const int lane = tid & 31;
 #pragma unroll
   for (int i = 0; i < KP; ++i) {
     if (i < k) {
-      uint32_t lo = live ? ord_enc(acc[i]) : 0xFFFFFFFFu;
-      uint32_t hi = live ? ord_enc(acc[i]) : 0u;
+      uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+#pragma unroll
+      for (int p = 0; p < RPT; ++p) {
+        if (r0 + p * 128 + tid < n) {
+          lo = min(lo, ord_enc(acc[p][i]));
+          hi = max(hi, ord_enc(acc[p][i]));
+        }
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
@@ -218,7 +246,8 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
 
 template <int DT>
 static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y, uint32_t* box, cudaStream_t s) {
-  const int grid = static_cast<int>(ceil_div(X->n, 128));
+  const int rows_per_block = kp <= 16 ? 256 : 128;
+  const int grid = static_cast<int>(ceil_div(X->n, rows_per_block));
 #define CHX_PROJ(KPV) k_project<DT, KPV><<<grid, 128, 0, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box)
   if (kp == 8) CHX_PROJ(8);
   else if (kp == 16) CHX_PROJ(16);
@@ -308,180 +337,6 @@ void launch_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int dd, int
                          ScaleTables t, int32_t* e_top_out, uint32_t* status, cudaStream_t s) {
   k_scale_tables<<<1, 256, 0, s>>>(boxA, boxB, dd, L, top_exp_in, seed, t, e_top_out, status);
   launch_check("scale_tables");
-}
-
-// ------------------------------------------------------------------ keys
-// Keys of one point at scales L0 .. L0+nl-1 (nl <= 16):
-//   c_j = ceil((y_j + z_{e,j}) * 2^-e) + 0, h = sum_j bits(c_j) K_j mod 2^64,
-//   key = mix64(h + salt_e), 0 -> 1.
-template <int DT>
-__device__ inline void point_keys(const HashSrc& src, int64_t r, int L, int L0, int nl, const ScaleTables& t,
-                                  uint64_t (&key)[kLevelBlock]) {
-  uint64_t h[kLevelBlock];
-  float inv_r[kLevelBlock];
-#pragma unroll
-  for (int l = 0; l < kLevelBlock; ++l) {
-    h[l] = 0;
-    inv_r[l] = (l < nl) ? __ldg(&t.inv_r[L0 + l]) : 1.0f;
-  }
-  const int dd = src.dd;
-  auto accumulate = [&](int j, float y) {
-    const uint64_t K = __ldg(reinterpret_cast<const unsigned long long*>(&t.mult[j]));
-    const uint32_t klo = uint32_t(K), khi = uint32_t(K >> 32);
-    const float* zrow = t.shift + int64_t(j) * L + L0;
-#pragma unroll
-    for (int l = 0; l < kLevelBlock; ++l) {
-      if (l < nl) {
-        const float z = __ldg(&zrow[l]);
-        float c = ceilf(__fmul_rn(__fadd_rn(y, z), inv_r[l]));
-        c = __fadd_rn(c, 0.0f);
-        const uint32_t bits = __float_as_uint(c);
-        h[l] += uint64_t(bits) * klo + (uint64_t(bits * khi) << 32);
-      }
-    }
-  };
-  if (dd <= 32) {
-    // narrow rows (always the case for the l2 embedding): issue every load first
-    float y[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) y[j] = (j < dd) ? load_elem<DT>(src.base, r, dd, j, src.scales) : 0.0f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < dd) accumulate(j, y[j]);
-  } else {
-    for (int j = 0; j < dd; ++j) accumulate(j, load_elem<DT>(src.base, r, dd, j, src.scales));
-  }
-#pragma unroll
-  for (int l = 0; l < kLevelBlock; ++l) {
-    if (l < nl) {
-      uint64_t k = mix64(h[l] + __ldg(reinterpret_cast<const unsigned long long*>(&t.salt[L0 + l])));
-      key[l] = k == 0 ? 1 : k;
-    }
-  }
-}
-
-__device__ inline uint32_t slot_home(uint64_t key, uint32_t log_cap) {
-  return log_cap == 0 ? 0u : static_cast<uint32_t>(key >> (64 - log_cap));
-}
-
-// Insert every b at every scale of the group [L0, L0+nl): bucket key -> min b.
-template <int DT>
-__global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0, int nl, ScaleTables t,
-                                                      HashTable h, uint32_t* status) {
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= src.n) return;
-  const uint32_t cap = 1u << h.log_cap;
-  for (int b0 = 0; b0 < nl; b0 += kLevelBlock) {
-    uint64_t key[kLevelBlock];
-    const int nb = min(kLevelBlock, nl - b0);
-    point_keys<DT>(src, r, L, L0 + b0, nb, t, key);
-    const unsigned long long want = ~static_cast<unsigned long long>(r);
-#pragma unroll
-    for (int l = 0; l < kLevelBlock; ++l) {
-      if (l >= nb) continue;
-      ulonglong2* tab = h.slots + size_t(b0 + l) * cap;
-      uint32_t pos = slot_home(key[l], h.log_cap);
-      bool done = false;
-      for (uint32_t it = 0; it < cap; ++it) {
-        unsigned long long* kp = &tab[pos].x;
-        unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(kp);
-        if (cur == 0ull) {
-          cur = atomicCAS(kp, 0ull, static_cast<unsigned long long>(key[l]));
-          if (cur == 0ull) cur = key[l];
-        }
-        if (cur == key[l]) {
-          unsigned long long* vp = &tab[pos].y;
-          if (*reinterpret_cast<volatile unsigned long long*>(vp) < want) atomicMax(vp, want);
-          done = true;
-          break;
-        }
-        pos = (pos + 1) & (cap - 1);
-      }
-      if (!done) atomicOr(status, ST_TABLE_FULL);
-    }
-  }
-}
-
-// Each unresolved a walks the scales of the group in increasing order and stops
-// at the first bucket that holds a b (Fig. 2, step 3).
-template <int DT>
-__global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0, int nl, ScaleTables t,
-                                                     HashTable h, int64_t* bidx, uint8_t* level) {
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= src.n) return;
-  if (level[r] < L) return;  // resolved at a finer scale group
-  const uint32_t cap = 1u << h.log_cap;
-  for (int b0 = 0; b0 < nl; b0 += kLevelBlock) {
-    uint64_t key[kLevelBlock];
-    const int nb = min(kLevelBlock, nl - b0);
-    point_keys<DT>(src, r, L, L0 + b0, nb, t, key);
-#pragma unroll
-    for (int l = 0; l < kLevelBlock; ++l) {
-      if (l >= nb) continue;
-      const ulonglong2* tab = h.slots + size_t(b0 + l) * cap;
-      uint32_t pos = slot_home(key[l], h.log_cap);
-      for (uint32_t it = 0; it < cap; ++it) {
-        const ulonglong2 sl = tab[pos];
-        if (sl.x == key[l]) {
-          bidx[r] = static_cast<int64_t>(~sl.y);
-          level[r] = static_cast<uint8_t>(L0 + b0 + l);
-          return;
-        }
-        if (sl.x == 0ull) break;
-        pos = (pos + 1) & (cap - 1);
-      }
-    }
-  }
-}
-
-template <int DT>
-__global__ void __launch_bounds__(128) k_keys_write(HashSrc src, int L, ScaleTables t, uint64_t* keys) {
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= src.n) return;
-  for (int b0 = 0; b0 < L; b0 += kLevelBlock) {
-    uint64_t key[kLevelBlock];
-    const int nb = min(kLevelBlock, L - b0);
-    point_keys<DT>(src, r, L, b0, nb, t, key);
-#pragma unroll
-    for (int l = 0; l < kLevelBlock; ++l)
-      if (l < nb) keys[size_t(b0 + l) * src.n + r] = key[l];
-  }
-}
-
-void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStream_t s) {
-  if (X.n == 0) return;
-  const int grid = static_cast<int>(ceil_div(X.n, 128));
-  switch (X.dtype) {
-    case CH_F32: k_keys_write<CH_F32><<<grid, 128, 0, s>>>(X, L, t, keys); break;
-    case CH_BF16: k_keys_write<CH_BF16><<<grid, 128, 0, s>>>(X, L, t, keys); break;
-    default: k_keys_write<CH_FP8E4M3><<<grid, 128, 0, s>>>(X, L, t, keys); break;
-  }
-  launch_check("keys_write");
-}
-
-// group launchers used by the API (scales [L0, L0+nl) in one table set)
-void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status,
-                         cudaStream_t s) {
-  if (B.n == 0) return;
-  const int grid = static_cast<int>(ceil_div(B.n, 128));
-  switch (B.dtype) {
-    case CH_F32: k_table_insert<CH_F32><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
-    case CH_BF16: k_table_insert<CH_BF16><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
-    default: k_table_insert<CH_FP8E4M3><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
-  }
-  launch_check("table_insert");
-}
-
-void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
-                        uint8_t* level, cudaStream_t s) {
-  if (A.n == 0) return;
-  const int grid = static_cast<int>(ceil_div(A.n, 128));
-  switch (A.dtype) {
-    case CH_F32: k_table_probe<CH_F32><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
-    case CH_BF16: k_table_probe<CH_BF16><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
-    default: k_table_probe<CH_FP8E4M3><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
-  }
-  launch_check("table_probe");
 }
 
 // ------------------------------------------------------------------ crude distance
