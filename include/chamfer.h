@@ -141,9 +141,11 @@ int64_t ch_ctx_workspace_bytes(const ch_ctx* ctx);
  * mode 2: data is DEVICE memory, adopted without a copy (must stay valid and
  *         unchanged until ch_set_destroy; rows must be 16-byte aligned).
  * n >= 0, d >= 1; dtype ch_dtype; row_scales: n binary32 scales (FP8 only, same
- * memory kind as data, copied), NULL otherwise.  Non-finite values are
- * detected on the device and make the first call that uses the set return
- * CH_EINVAL. */
+ * memory kind as data, copied), NULL otherwise.  The set's own passes (bounding
+ * box, |x|^2, finite check) run lazily, fused into the first call that reads
+ * the set for hashing or screening; a non-finite value found there makes the
+ * next synchronising call on the set (ch_estimate, ch_exact, ch_top_exp)
+ * return CH_EINVAL. */
 ch_status ch_set_create(ch_ctx* ctx, const void* data, int mode, int64_t n, int32_t d, int32_t dtype,
                         const float* row_scales, ch_set** out);
 void ch_set_destroy(ch_set* set);

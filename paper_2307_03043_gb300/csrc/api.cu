@@ -157,9 +157,13 @@ static void take_hashed(L& lay, const ch_set* X, const ch_hash_params* hp, Hashe
   }
 }
 
+// the hashed space's pass over a set: the l2 projection (which also yields
+// |x|^2 and the finite check) or, for l1, the ingest pass (box of x)
 static void run_hashed(ch_ctx* c, const ch_set* X, const ch_hash_params* hp, Hashed* h, uint32_t* status) {
   if (hp->metric == CH_L2)
     launch_project(X, hp->hash_seed, static_cast<int>(hp->proj_dim), h->Y, h->boxY, status, c->sm_count, c->stream);
+  else
+    ensure_ingest(const_cast<ch_set*>(X), c->stream);
 }
 
 template <class L>
@@ -217,8 +221,6 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
   run_hashed(c, A, hp, &cb->hA, status);
   run_hashed(c, B, hp, &cb->hB, status);
   launch_scale_tables(cb->hA.box, cb->hB.box, dd, L, hp->top_exp, hp->hash_seed, cb->tab, cb->e_top, status, s);
-  CHX_CUDA(cudaMemsetAsync(level, L, size_t(A->n), s));
-  CHX_CUDA(cudaMemsetAsync(bidx, 0, size_t(A->n) * sizeof(int64_t), s));
   if (hp->group == CH_GROUP_SORT) throw Err{CH_ENOTSUP, "sort grouping not built"};
   const size_t cap = size_t(1) << cb->plan.log_cap;
   for (int L0 = 0; L0 < L; L0 += cb->plan.per_group) {
@@ -285,6 +287,7 @@ static void run_scan(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t T, 
     timer.stop(c->stream);
     launch_scan_merge(sb->part, T, idx, m, argmin, c->stream);
   } else {
+    ensure_norms(const_cast<ch_set*>(B), c->stream);
     launch_screen_l2(A, idx, T, B, sb->screen, static_cast<int>(R), sb->screen_work, m, argmin, status, c->sm_count,
                      c->stream, timer);
   }
@@ -452,7 +455,8 @@ ch_status ch_set_create(ch_ctx* c, const void* data, int mode, int64_t n, int32_
                                  mode == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     }
     CHX_CUDA(cudaMemsetAsync(X->status, 0, 4, s));
-    launch_ingest(X, s);
+    // the set's passes (bounding box, |x|^2 and the finite check) run lazily with
+    // the first call that needs them, fused with that call's own read of the set
   } catch (...) {
     ch_set_destroy(X);
     throw;
@@ -724,6 +728,8 @@ ch_status ch_exact(ch_ctx* c, const ch_set* A, const ch_set* B, int32_t metric, 
   cudaStream_t s = c->stream;
   CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
   CHX_CUDA(cudaMemsetAsync(out2, 0, 2 * sizeof(double), s));
+  ensure_ingest(const_cast<ch_set*>(A), s);  // finite check of both sets
+  ensure_ingest(const_cast<ch_set*>(B), s);
   if (nA > 0) {
     run_scan(c, A, nullptr, nA, B, metric, 8, &sc, mins, nullptr, &res->status);
     launch_sum_f32(mins, nA, out2, s);

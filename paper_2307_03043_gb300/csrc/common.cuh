@@ -115,7 +115,19 @@ struct ch_set {
   uint32_t* status = nullptr;  // device status word (ST_* bits)
   uint32_t* box_x = nullptr;   // ordered-encoded [2][d] bounding box of x (l1 hashed space)
   chx_hashed hs;               // cached l2 embedding
+  uint32_t ready = 0;          // READY_* passes already enqueued on the context's stream
 };
+
+namespace chx {
+enum : uint32_t {
+  READY_BOX_X = 1u << 0,  // box_x computed (and the finite check done)
+  READY_NORMS = 1u << 1,  // norms computed (and the finite check done)
+};
+// ingest pass (box of x, finite check) unless already done
+void ensure_ingest(ch_set* X, cudaStream_t s);
+// |x|^2 per row (sequential fmaf chain over j) unless already done
+void ensure_norms(ch_set* X, cudaStream_t s);
+}  // namespace chx
 
 namespace chx {
 

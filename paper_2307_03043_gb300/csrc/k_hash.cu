@@ -46,40 +46,28 @@ __global__ void __launch_bounds__(256) k_ingest(const void* X, const float* scal
         }
 #pragma unroll
       for (int q = 0; q < RPW; ++q) {
-        float sq = 0.0f;
 #pragma unroll
         for (int b = 0; b < CB; ++b) {
           const int c = b * 32 + lane;
           if (r0 + q < n && c < d) {
             const float x = v[q][b];
             bad |= !isfinite(x);
-            sq = fmaf(x, x, sq);
             const uint32_t o = ord_enc(x);
             lo[b] = min(lo[b], o);
             hi[b] = max(hi[b], o);
           }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xFFFFFFFFu, sq, o);
-        if (lane == 0 && r0 + q < n) norms[r0 + q] = sq;
       }
     }
   }
   for (int64_t r = int64_t(blockIdx.x) * warps + warp; CB == 0 && r < n; r += int64_t(gridDim.x) * warps) {
-    float sq = 0.0f;
-    {
-      for (int c = lane; c < d; c += 32) {
-        const float v = load_elem<DT>(X, r, d, c, scales);
-        bad |= !isfinite(v);
-        sq = fmaf(v, v, sq);
-        const uint32_t o = ord_enc(v);
-        atomicMin(&s_box[c], o);
-        atomicMax(&s_box[d + c], o);
-      }
+    for (int c = lane; c < d; c += 32) {
+      const float v = load_elem<DT>(X, r, d, c, scales);
+      bad |= !isfinite(v);
+      const uint32_t o = ord_enc(v);
+      atomicMin(&s_box[c], o);
+      atomicMax(&s_box[d + c], o);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xFFFFFFFFu, sq, o);
-    if (lane == 0) norms[r] = sq;
   }
   if constexpr (CB > 0) {
 #pragma unroll
@@ -130,6 +118,44 @@ void launch_ingest(const ch_set* X, cudaStream_t s) {
   launch_check("ingest");
 }
 
+void ensure_ingest(ch_set* X, cudaStream_t s) {
+  if (X->ready & READY_BOX_X) return;
+  launch_ingest(X, s);
+  X->ready |= READY_BOX_X;
+}
+
+// |x|^2 per row as the fmaf chain over j in increasing order (the order the l2
+// projection pass uses, so the norms never depend on which pass made them)
+template <int DT>
+__global__ void __launch_bounds__(256) k_norms(const void* X, const float* scales, int64_t n, int d, float* norms,
+                                               uint32_t* status) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (r < n) {
+    float sq = 0.0f;
+    for (int j = 0; j < d; ++j) {
+      const float x = load_elem<DT>(X, r, d, j, scales);
+      bad |= !isfinite(x);
+      sq = fmaf(x, x, sq);
+    }
+    norms[r] = sq;
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+}
+
+void ensure_norms(ch_set* X, cudaStream_t s) {
+  if (X->ready & READY_NORMS) return;
+  X->ready |= READY_NORMS;
+  if (X->n == 0) return;
+  const int grid = static_cast<int>(ceil_div(X->n, 256));
+  switch (X->dtype) {
+    case CH_F32: k_norms<CH_F32><<<grid, 256, 0, s>>>(X->data, X->scales, X->n, X->d, X->norms, X->status); break;
+    case CH_BF16: k_norms<CH_BF16><<<grid, 256, 0, s>>>(X->data, X->scales, X->n, X->d, X->norms, X->status); break;
+    default: k_norms<CH_FP8E4M3><<<grid, 256, 0, s>>>(X->data, X->scales, X->n, X->d, X->norms, X->status); break;
+  }
+  launch_check("norms");
+}
+
 // ------------------------------------------------------------------ l2 embedding
 // Z_ij: 12-term Irwin-Hall normal from Philox counters (j, i, 2, m), m < 3,
 // summed exactly, centred, scaled by 2^-32 and rounded once to binary32
@@ -154,9 +180,12 @@ __global__ void k_gauss(uint64_t seed, int k, int kp, int d, float* G /* [d][kp]
 
 // Thread per row; rows staged through shared memory 32 coordinates at a time
 // (coalesced 128-byte row segments), y_i = fmaf chain over j in increasing order.
+// The same pass also writes |x|^2 (norms, when non-null) and raises ST_NONFINITE
+// in the set's status word, so an l2 set is read from HBM once.
 template <int DT, int KP>
 __global__ void __launch_bounds__(128) k_project(const void* X, const float* scales, int64_t n, int d,
-                                                 const float* G, int k, float* Y, uint32_t* box) {
+                                                 const float* G, int k, float* Y, uint32_t* box, float* norms,
+                                                 uint32_t* status) {
   // RPT rows per thread (rows tid and tid + 128) so that each G value read from
   // shared memory feeds RPT fused multiply-adds
   constexpr int RPT = KP <= 16 ? 2 : 1;
@@ -165,10 +194,14 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
   const int64_t r0 = int64_t(blockIdx.x) * 128 * RPT;
   const int tid = threadIdx.x;
   float acc[RPT][KP];
+  float sq[RPT];
+  bool bad = false;
 #pragma unroll
-  for (int p = 0; p < RPT; ++p)
+  for (int p = 0; p < RPT; ++p) {
+    sq[p] = 0.0f;
 #pragma unroll
     for (int i = 0; i < KP; ++i) acc[p][i] = 0.0f;
+  }
   for (int j0 = 0; j0 < d; j0 += 32) {
     const int jn = min(32, d - j0);
     __syncthreads();
@@ -194,7 +227,11 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
     for (int jj = 0; jj < jn; ++jj) {
       float xv[RPT];
 #pragma unroll
-      for (int p = 0; p < RPT; ++p) xv[p] = s_x[p * 128 + tid][jj];
+      for (int p = 0; p < RPT; ++p) {
+        xv[p] = s_x[p * 128 + tid][jj];
+        sq[p] = fmaf(xv[p], xv[p], sq[p]);
+        bad |= !isfinite(xv[p]);
+      }
       const float4* g4 = reinterpret_cast<const float4*>(&s_g[jj][0]);
 #pragma unroll
       for (int i4 = 0; i4 < KP / 4; ++i4) {
@@ -216,8 +253,10 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
 #pragma unroll
       for (int i = 0; i < KP; ++i)
         if (i < k) Y[r * k + i] = acc[p][i];
+      if (norms) norms[r] = sq[p];
     }
   }
+  if (__any_sync(0xFFFFFFFFu, bad) && (tid & 31) == 0) atomicOr(status, ST_NONFINITE);
   // bounding box of the embedding
   const int lane = tid & 31;
 #pragma unroll
@@ -245,10 +284,12 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
 }
 
 template <int DT>
-static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y, uint32_t* box, cudaStream_t s) {
+static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y, uint32_t* box, float* norms,
+                       cudaStream_t s) {
   const int rows_per_block = kp <= 16 ? 256 : 128;
   const int grid = static_cast<int>(ceil_div(X->n, rows_per_block));
-#define CHX_PROJ(KPV) k_project<DT, KPV><<<grid, 128, 0, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box)
+#define CHX_PROJ(KPV) \
+  k_project<DT, KPV><<<grid, 128, 0, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box, norms, X->status)
   if (kp == 8) CHX_PROJ(8);
   else if (kp == 16) CHX_PROJ(16);
   else if (kp == 32) CHX_PROJ(32);
@@ -261,6 +302,10 @@ void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* b
   (void)status;
   (void)sm_count;
   const int kp = k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64;
+  // the set's |x|^2 and finite check come for free with this pass
+  ch_set* mut = const_cast<ch_set*>(X);
+  float* norms = (X->ready & READY_NORMS) ? nullptr : X->norms;
+  mut->ready |= READY_NORMS;
   CHX_CUDA(cudaMemsetAsync(box, 0xFF, size_t(k) * 4, s));
   CHX_CUDA(cudaMemsetAsync(box + k, 0, size_t(k) * 4, s));
   if (X->n == 0) return;
@@ -270,9 +315,9 @@ void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* b
   k_gauss<<<static_cast<int>(ceil_div(gn, 256)), 256, 0, s>>>(seed, k, kp, X->d, G);
   launch_check("gauss");
   switch (X->dtype) {
-    case CH_F32: project_dt<CH_F32>(X, G, k, kp, Y, box, s); break;
-    case CH_BF16: project_dt<CH_BF16>(X, G, k, kp, Y, box, s); break;
-    default: project_dt<CH_FP8E4M3>(X, G, k, kp, Y, box, s); break;
+    case CH_F32: project_dt<CH_F32>(X, G, k, kp, Y, box, norms, s); break;
+    case CH_BF16: project_dt<CH_BF16>(X, G, k, kp, Y, box, norms, s); break;
+    default: project_dt<CH_FP8E4M3>(X, G, k, kp, Y, box, norms, s); break;
   }
   launch_check("project");
 }

@@ -90,15 +90,11 @@ __device__ inline void table_insert(ulonglong2* tab, uint32_t log_cap, uint64_t 
   const unsigned long long want = ~static_cast<unsigned long long>(b);
   uint32_t pos = slot_home(key, log_cap);
   for (uint32_t it = 0; it < cap; ++it) {
-    unsigned long long* kp = &tab[pos].x;
-    unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(kp);
-    if (cur == 0ull) {
-      cur = atomicCAS(kp, 0ull, static_cast<unsigned long long>(key));
-      if (cur == 0ull) cur = key;
-    }
-    if (cur == key) {
-      unsigned long long* vp = &tab[pos].y;
-      if (*reinterpret_cast<volatile unsigned long long*>(vp) < want) atomicMax(vp, want);
+    // one round trip: claim the slot or learn its owner; the min-update is a
+    // fire-and-forget reduction
+    const unsigned long long cur = atomicCAS(&tab[pos].x, 0ull, static_cast<unsigned long long>(key));
+    if (cur == 0ull || cur == key) {
+      atomicMax(&tab[pos].y, want);
       return;
     }
     pos = (pos + 1) & (cap - 1);
@@ -119,18 +115,28 @@ __device__ inline int64_t table_find(const ulonglong2* tab, uint32_t log_cap, ui
   return -1;
 }
 
+// Narrow rows: one thread per (point, scale), thread t = l * n + r, so the
+// scales' insert round trips overlap instead of forming one chain per point.
+template <int DT>
+__global__ void __launch_bounds__(128) k_table_insert_ps(HashSrc src, int L, int L0, int nl, ScaleTables t,
+                                                         HashTable h, uint32_t* status) {
+  const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g >= src.n * nl) return;
+  const int l = static_cast<int>(g / src.n);
+  const int64_t r = g - int64_t(l) * src.n;
+  float y[kRegRow];
+  load_row<DT>(src, r, y);
+  const size_t cap = size_t(1) << h.log_cap;
+  table_insert(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t), r, status);
+}
+
 template <int DT>
 __global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
                                                       uint32_t* status) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= src.n) return;
   const size_t cap = size_t(1) << h.log_cap;
-  if (src.dd <= kRegRow) {
-    float y[kRegRow];
-    load_row<DT>(src, r, y);
-    for (int l = 0; l < nl; ++l)
-      table_insert(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t), r, status);
-  } else {
+  {
     for (int b0 = 0; b0 < nl; b0 += kLevelBlock) {
       uint64_t key[kLevelBlock];
       const int nb = min(kLevelBlock, nl - b0);
@@ -149,7 +155,12 @@ __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0,
                                                      int64_t* bidx, uint8_t* level) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= src.n) return;
-  if (level[r] < L) return;  // resolved at a finer scale group
+  if (L0 > 0 && level[r] < L) return;  // resolved at a finer scale group
+  if (L0 == 0) {
+    // first group: start from "no scale collides" (b = 0, level = L)
+    bidx[r] = 0;
+    level[r] = static_cast<uint8_t>(L);
+  }
   const size_t cap = size_t(1) << h.log_cap;
   if (src.dd <= kRegRow) {
     float y[kRegRow];
@@ -217,6 +228,16 @@ void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStre
 void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status,
                          cudaStream_t s) {
   if (B.n == 0) return;
+  if (B.dd <= kRegRow) {
+    const int grid_ps = static_cast<int>(ceil_div(B.n * nl, 128));
+    switch (B.dtype) {
+      case CH_F32: k_table_insert_ps<CH_F32><<<grid_ps, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
+      case CH_BF16: k_table_insert_ps<CH_BF16><<<grid_ps, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
+      default: k_table_insert_ps<CH_FP8E4M3><<<grid_ps, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
+    }
+    launch_check("table_insert");
+    return;
+  }
   const int grid = static_cast<int>(ceil_div(B.n, 128));
   switch (B.dtype) {
     case CH_F32: k_table_insert<CH_F32><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
