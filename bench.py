@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--screen", default="auto", choices=["auto", "exact", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--serve-requests", type=int, default=200, help="0 skips the serving sample")
     return ap.parse_args()
 
 
@@ -123,6 +124,64 @@ def cpu_oracle_step(A, B, T, seed, scan_fraction=1):
     t2 = time.perf_counter()
     eta = oracle.combine(m, idx[:Ts], w, W)
     return (t1 - t0) + (t2 - t1) * (T / Ts), eta
+
+
+def serving_sample(ch, ctx, rank, n_req=200, seed=7):
+    """Request loop on a bounded sample of the serving workload: 12 resident sets,
+    sizes log-uniform in [1k, 100k], d in {3, 128}, fp32, l2, eps = 0.1.  A closed
+    burst measures saturation throughput; then n_req requests arrive as a Poisson
+    process at 0.8x that rate.  Returns p50/p99 submit->result latency."""
+    from paper_2307_03043_gb300 import workloads
+    rng = np.random.default_rng(seed + rank)
+    srv = ch.ch_serve_create(ctx, 32 << 30, 8, 4096)
+    by_dim = {3: [], 128: []}
+    sizes = workloads.log_uniform_sizes(12, 1000, 100_000, seed + rank)
+    for i, n in enumerate(sizes):
+        d = 3 if i % 2 == 0 else 128
+        X, _ = workloads.gaussian_mixture(int(n), 1, d, seed * 1000 + i, clusters=20)
+        by_dim[d].append((ch.ch_serve_register(srv, X, 0, X.shape[0], d), int(n)))
+
+    def req(k):
+        pool = by_dim[3] if rng.random() < 0.5 else by_dim[128]
+        a, b = pool[rng.integers(len(pool))], pool[rng.integers(len(pool))]
+        p = ch.est_params(ch.CH_L2, LEVELS, PROJ, None, k, eps=EPS, sample_seed=k)
+        st, t = ch.ch_serve_submit(srv, a[0], b[0], p)
+        return st, t, a[1] + b[1]
+
+    t0 = time.perf_counter()
+    burst = [req(k) for k in range(48)]
+    for st, t, _ in burst:
+        ch.ch_serve_wait(srv, t, 120000)
+    rate = len(burst) / (time.perf_counter() - t0)
+    ch.ch_serve_destroy(srv)
+    srv = ch.ch_serve_create(ctx, 32 << 30, 8, 4096)
+    by_dim = {3: [], 128: []}
+    for i, n in enumerate(sizes):
+        d = 3 if i % 2 == 0 else 128
+        X, _ = workloads.gaussian_mixture(int(n), 1, d, seed * 1000 + i, clusters=20)
+        by_dim[d].append((ch.ch_serve_register(srv, X, 0, X.shape[0], d), int(n)))
+    arrivals = np.cumsum(rng.exponential(1.0 / (0.8 * rate), n_req))
+    tickets, pts = [], 0
+    t0 = time.perf_counter()
+    for k, at in enumerate(arrivals):
+        while time.perf_counter() - t0 < at:
+            time.sleep(0.0002)
+        st, t, n = req(1000 + k)
+        if st == ch.CH_OK:
+            tickets.append(t)
+            pts += n
+    ok = 0
+    for t in tickets:
+        st, eta, rs = ch.ch_serve_wait(srv, t, 120000)
+        ok += int(st == ch.CH_OK and rs == ch.CH_OK)
+    wall = time.perf_counter() - t0
+    s = ch.ch_serve_stats_get(srv)
+    ch.ch_serve_destroy(srv)
+    return {"workload": "12 resident sets, log-uniform 1k-100k points, d in {3,128}, fp32, l2, eps=0.1, "
+                        "Poisson arrivals at 0.8x saturation, 8 slots",
+            "requests": n_req, "completed": ok, "p50_us": s.p50_us, "p99_us": s.p99_us,
+            "saturation_rps": rate, "offered_rps": 0.8 * rate, "throughput_rps": ok / wall,
+            "pts_per_s": pts / wall, "peak_bytes": s.peak_bytes}
 
 
 def run_reference(args):
@@ -295,6 +354,7 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel_ms"] = kern_avg
 
+    serving = serving_sample(ch, ctx, rank, args.serve_requests) if args.serve_requests > 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -322,6 +382,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "serving": serving,
         }
         print(json.dumps(out))
     ch.ch_ctx_destroy(ctx)

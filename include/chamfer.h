@@ -149,6 +149,12 @@ int64_t ch_ctx_workspace_bytes(const ch_ctx* ctx);
 ch_status ch_set_create(ch_ctx* ctx, const void* data, int mode, int64_t n, int32_t d, int32_t dtype,
                         const float* row_scales, ch_set** out);
 void ch_set_destroy(ch_set* set);
+/* Runs the set's lazy passes now (bounding box, |x|^2, finite check) and
+ * synchronises; CH_EINVAL if the set holds a non-finite value.  A prepared set
+ * is never written again, so contexts on the same device may read it
+ * concurrently (every call only requires the set to live on the context's
+ * device). */
+ch_status ch_set_prepare(ch_ctx* ctx, ch_set* set);
 int64_t ch_set_size(const ch_set* set);
 int32_t ch_set_dim(const ch_set* set);
 

@@ -79,6 +79,7 @@ SIGNATURES = {
     "ch_kernel_launches": (_i64, []),
     "ch_set_create": (_i32, [_vp, _vp, ctypes.c_int, _i64, _i32, _i32, _vp, _P(_vp)]),
     "ch_set_destroy": (None, [_vp]),
+    "ch_set_prepare": (_i32, [_vp, _vp]),
     "ch_set_size": (_i64, [_vp]),
     "ch_set_dim": (_i32, [_vp]),
     "ch_top_exp": (_i32, [_vp, _vp, _vp, _P(ch_hash_params), _P(_i32)]),
@@ -196,6 +197,10 @@ def ch_set_create(ctx, data, mode: int, n: int, d: int, dtype: int = CH_F32, row
 
 def ch_set_destroy(s):
     lib().ch_set_destroy(s)
+
+
+def ch_set_prepare(ctx, s):
+    _check(lib().ch_set_prepare(ctx, s), "ch_set_prepare", ctx)
 
 
 def ch_set_size(s) -> int:

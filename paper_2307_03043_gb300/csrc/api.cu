@@ -27,6 +27,7 @@ void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTab
 
 void Arena::reserve(size_t bytes) {
   if (bytes <= cap) return;
+  if (borrowed) throw Err{CH_ENOMEM, "lent workspace smaller than the call needs"};
   if (base) {
     CHX_CUDA(cudaDeviceSynchronize());
     CHX_CUDA(cudaFree(base));
@@ -43,7 +44,7 @@ void Arena::reserve(size_t bytes) {
 }
 
 void Arena::release() {
-  if (base) cudaFree(base);
+  if (base && !borrowed) cudaFree(base);
   base = nullptr;
   cap = used = 0;
 }
@@ -125,7 +126,8 @@ static void check_hash(const ch_hash_params* hp) {
 
 static void check_pair(ch_ctx* c, const ch_set* A, const ch_set* B) {
   CHX_CHECK(A && B, CH_EINVAL, "set NULL");
-  CHX_CHECK(A->ctx == c && B->ctx == c, CH_EINVAL, "sets belong to another context");
+  CHX_CHECK(A->ctx->device == c->device && B->ctx->device == c->device, CH_EINVAL,
+            "sets live on another device");
   CHX_CHECK(A->d == B->d, CH_EINVAL, "sets differ in dimension");
   CHX_CHECK(A->dtype == B->dtype, CH_EINVAL, "sets differ in storage type");
   CHX_CHECK(B->n >= 1, CH_EINVAL, "B must hold at least one point");
@@ -293,9 +295,49 @@ static void run_scan(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t T, 
   }
 }
 
-static int64_t default_T(int64_t nA, int64_t nB, double eps) {
+int64_t default_T(int64_t nA, int64_t nB, double eps) {
   int64_t n = std::max<int64_t>(std::max(nA, nB), 2);
   return static_cast<int64_t>(std::ceil(4.0 * std::log(static_cast<double>(n)) / (eps * eps)));
+}
+
+// every workspace buffer of one ch_estimate call
+struct EstBufs {
+  CrudeBufs cb;
+  SampleBufs sb;
+  ScanBufs sc;
+  ResBlock* res = nullptr;
+  int64_t *bidx = nullptr, *idx = nullptr;
+  uint8_t* level = nullptr;
+  float *D = nullptr, *m = nullptr;
+  uint64_t* w = nullptr;
+  double* out2 = nullptr;
+};
+
+template <class L>
+static void take_estimate(L& lay, ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t T,
+                          uint32_t R, EstBufs* eb) {
+  const int64_t nA = A->n;
+  eb->res = lay.template take<ResBlock>(1);
+  eb->out2 = lay.template take<double>(kCombineDoubles);
+  take_crude(lay, A, B, &p->hash, &eb->cb);
+  eb->bidx = lay.template take<int64_t>(nA);
+  eb->level = lay.template take<uint8_t>(nA);
+  eb->D = lay.template take<float>(nA);
+  take_sample(lay, nA, &eb->sb);
+  eb->w = lay.template take<uint64_t>(nA);
+  eb->idx = lay.template take<int64_t>(std::max<int64_t>(T, 1));
+  eb->m = lay.template take<float>(std::max<int64_t>(T, 1));
+  take_scan(lay, c, A, B, T, p->hash.metric, p->screen, R, &eb->sc);
+}
+
+// device workspace bytes ch_estimate(A, B, p) needs on a context like c
+size_t estimate_footprint(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p) {
+  const uint32_t R = p->rerank_k ? p->rerank_k : 8;
+  const int64_t T = p->T > 0 ? p->T : default_T(A->n, B->n, p->eps);
+  Layout m;
+  EstBufs eb;
+  take_estimate(m, c, A, B, p, T, R, &eb);
+  return m.need + 256;
 }
 
 static ch_status fail(ch_ctx* c, const Err& e) {
@@ -475,6 +517,24 @@ void ch_set_destroy(ch_set* X) {
   delete X;
 }
 
+ch_status ch_set_prepare(ch_ctx* c, ch_set* X) {
+  if (!c || !X) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  CHX_CHECK(X->ctx->device == c->device, CH_EINVAL, "set lives on another device");
+  CHX_CUDA(cudaSetDevice(c->device));
+  ResBlock* res = nullptr;
+  carve(c, [&](auto& lay) { res = lay.template take<ResBlock>(1); });
+  cudaStream_t s = c->stream;
+  CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
+  ensure_ingest(X, s);
+  ensure_norms(X, s);
+  k_collect<<<1, 32, 0, s>>>(res, X->status, nullptr, nullptr, nullptr, nullptr, nullptr);
+  launch_check("collect");
+  finish(c, res, static_cast<ResBlock*>(c->host_pin));
+  return CH_OK;
+  CHX_GUARD_END
+}
+
 int64_t ch_set_size(const ch_set* X) { return X ? X->n : -1; }
 int32_t ch_set_dim(const ch_set* X) { return X ? X->d : -1; }
 
@@ -643,28 +703,17 @@ ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_
     *eta = 0.0;
     return CH_OK;
   }
-  CrudeBufs cb;
-  SampleBufs sb;
-  ScanBufs sc;
-  ResBlock* res = nullptr;
-  int64_t *bidx = nullptr, *idx = nullptr;
-  uint8_t* level = nullptr;
-  float *D = nullptr, *m = nullptr;
-  uint64_t* w = nullptr;
-  double* out2 = nullptr;
-  carve(c, [&](auto& lay) {
-    res = lay.template take<ResBlock>(1);
-    out2 = lay.template take<double>(kCombineDoubles);
-    take_crude(lay, A, B, &p->hash, &cb);
-    bidx = lay.template take<int64_t>(nA);
-    level = lay.template take<uint8_t>(nA);
-    D = lay.template take<float>(nA);
-    take_sample(lay, nA, &sb);
-    w = lay.template take<uint64_t>(nA);
-    idx = lay.template take<int64_t>(std::max<int64_t>(T, 1));
-    m = lay.template take<float>(std::max<int64_t>(T, 1));
-    take_scan(lay, c, A, B, T, p->hash.metric, p->screen, R, &sc);
-  });
+  EstBufs eb;
+  carve(c, [&](auto& lay) { take_estimate(lay, c, A, B, p, T, R, &eb); });
+  CrudeBufs& cb = eb.cb;
+  SampleBufs& sb = eb.sb;
+  ScanBufs& sc = eb.sc;
+  ResBlock* res = eb.res;
+  int64_t *bidx = eb.bidx, *idx = eb.idx;
+  uint8_t* level = eb.level;
+  float *D = eb.D, *m = eb.m;
+  uint64_t* w = eb.w;
+  double* out2 = eb.out2;
   cudaStream_t s = c->stream;
   if (rep) CHX_CUDA(cudaEventRecord(c->ev[0], s));
   CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));

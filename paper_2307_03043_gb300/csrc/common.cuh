@@ -66,6 +66,7 @@ struct Arena {
   char* base = nullptr;
   size_t cap = 0;
   size_t used = 0;
+  bool borrowed = false;  // base is lent by the caller: never freed or regrown here
   void reserve(size_t bytes);  // synchronises the device if it must grow
   void release();
   void reset() { used = 0; }

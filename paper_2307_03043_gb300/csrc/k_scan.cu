@@ -229,11 +229,8 @@ static void scan_launch(const ch_set* A, const int64_t* qidx, int64_t T, const c
                         cudaStream_t s) {
   auto kern = k_scan_exact<DT, METRIC, QT, BT, PQ, PB>;
   const size_t smem = scan_smem(A->d);
-  static bool attr_set = false;  // one attribute call per instantiation
-  if (!attr_set) {
-    CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 20 * 1024));
-    attr_set = true;
-  }
+  // a constant value, so concurrent callers on other threads never race on it
+  CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
   const int64_t chunk_len = ceil_div(ceil_div(B->n, part.chunks), BT) * BT;
   dim3 grid(static_cast<unsigned>(ceil_div(T, QT)), static_cast<unsigned>(part.chunks));
   kern<<<grid, 256, smem, s>>>(A->data, A->scales, qidx, T, A->n, B->data, B->scales, B->n, A->d, chunk_len,
