@@ -188,6 +188,24 @@ ch_status ch_crude_nn(ch_ctx* ctx, const ch_set* A, const ch_set* B, const ch_ha
 ch_status ch_sample(ch_ctx* ctx, const float* D, int64_t nA, int64_t T, uint64_t seed, int64_t* idx,
                     uint64_t* w, uint64_t* W_total);
 
+/* ch_sample without any device allocation (the paper has no counterpart; this
+ * is a deployment variant).  For callers that cannot allocate device memory:
+ * code that must stay allocation-free while a stream is captured, plug-ins
+ * whose host application owns every device allocation, processes held to a
+ * memory budget fixed at start-up.  It needs no context: the scratch lives in
+ * one fixed ~8.4 MB device array inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ * Same arguments and results as ch_sample, bit for bit, except: nA may be at
+ * most 1,048,576 (larger returns CH_EINVAL before any work); w is required;
+ * W_total is a DEVICE uint64 or NULL (no host synchronisation); stream is a
+ * cudaStream_t (NULL = legacy default stream).  The first call on a device
+ * looks up the array's device address with that device current, so make it
+ * before any stream capture.  Every call shares the one array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race; serialise
+ * them, e.g. on one stream.  Returns CH_ECUDA if a launch fails. */
+ch_status ch_sample_static(const float* D, int64_t nA, int64_t T, uint64_t seed, int64_t* idx, uint64_t* w,
+                           uint64_t* W_total, void* stream);
+
 /* ------------------------------------------------------------ sampled scan (Fig. 1, step 3)
  * For each l < T: min_d[l] = min_b d_X(A[idx[l]], b) with the canonical
  * binary32 distance, argmin[l] its index (smallest on ties) -- exactly, for

@@ -86,6 +86,7 @@ SIGNATURES = {
     "ch_hash_keys": (_i32, [_vp, _vp, _P(ch_hash_params), _i32, _vp]),
     "ch_crude_nn": (_i32, [_vp, _vp, _vp, _P(ch_hash_params), _vp, _vp, _vp]),
     "ch_sample": (_i32, [_vp, _vp, _i64, _i64, _u64, _vp, _vp, _P(_u64)]),
+    "ch_sample_static": (_i32, [_vp, _i64, _i64, _u64, _vp, _vp, _vp, _vp]),
     "ch_sampled_nn": (_i32, [_vp, _vp, _vp, _i64, _vp, _i32, _i32, _u32, _vp, _vp]),
     "ch_estimate": (_i32, [_vp, _vp, _vp, _P(ch_est_params), _P(ctypes.c_double), _P(ch_est_report)]),
     "ch_exact": (_i32, [_vp, _vp, _vp, _i32, _i32, _P(ctypes.c_double), _vp]),
@@ -231,6 +232,15 @@ def ch_sample(ctx, D, nA: int, T: int, seed: int, idx, w=None, want_total: bool 
     _check(lib().ch_sample(ctx, _ptr(D), nA, T, seed, _ptr(idx), _ptr(w), ctypes.byref(W) if want_total else None),
            "ch_sample", ctx)
     return int(W.value) if want_total else None
+
+
+def ch_sample_static(D, nA: int, T: int, seed: int, idx, w, W_total=None, stream=None):
+    """ch_sample for callers that cannot allocate device memory (no context;
+    fixed library-held scratch, nA <= 1,048,576).  W_total: device uint64 or None.
+    stream: torch.cuda.Stream / int handle / None (legacy default stream)."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(lib().ch_sample_static(_ptr(D), nA, T, seed, _ptr(idx), _ptr(w), _ptr(W_total), s),
+           "ch_sample_static")
 
 
 def ch_sampled_nn(ctx, A, idx, T: int, B, metric: int, screen: int, rerank_k: int, min_d, argmin=None):
