@@ -42,12 +42,53 @@ EPS = 0.1
 LEVELS = 10
 PROJ = 16
 FLUSH_BYTES = 256 << 20  # > 126 MB L2
+DTYPE = "f32"            # storage type of the sets ("f32", "bf16", "fp8")
+CONFIG = "mid"
+
+WORKLOADS = {
+    "mid": dict(n=100_000, d=128, dtype="f32",
+                desc="mid: |A|=|B|=100000, d=128, fp32, l2, eps=0.1, 100-cluster Gaussian mixture"),
+    "precision": dict(n=1_000_000, d=384, dtype="bf16",
+                      desc="precision: |A|=|B|=1000000, d=384, bf16, l2, eps=0.1, 1000-cluster unit-norm mixture"),
+    "precision_fp8": dict(n=1_000_000, d=384, dtype="fp8",
+                          desc="precision: |A|=|B|=1000000, d=384, fp8 e4m3 + row scale, l2, eps=0.1, "
+                               "1000-cluster unit-norm mixture"),
+}
+
+
+def select_workload(name):
+    global NA, NB, DIM, DTYPE, CONFIG
+    w = WORKLOADS[name]
+    NA = NB = w["n"]
+    DIM = w["d"]
+    DTYPE = w["dtype"]
+    CONFIG = name
+
+
+def make_data(rank):
+    """Returns (A32, B32, A_store, B_store, sA, sB): the binary32 values the oracle
+    sees, the stored arrays and FP8 row scales (None otherwise)."""
+    from paper_2307_03043_gb300 import workloads
+    if CONFIG == "mid":
+        A, B = workloads.gaussian_mixture(NA, NB, DIM, rank)
+        return A, B, A, B, None, None
+    A, B = workloads.unit_mixture(NA, NB, DIM, rank)
+    if DTYPE == "bf16":
+        Ah, Bh = workloads.to_bf16_bits(A), workloads.to_bf16_bits(B)
+        return workloads.bf16_bits_to_f32(Ah), workloads.bf16_bits_to_f32(Bh), Ah, Bh, None, None
+    ca, sa = workloads.to_fp8_e4m3(A)
+    cb, sb = workloads.to_fp8_e4m3(B)
+    return workloads.fp8_dequant(ca, sa), workloads.fp8_dequant(cb, sb), ca, cb, sa, sb
+
+
+def elem_bytes():
+    return {"f32": 4, "bf16": 2, "fp8": 1}[DTYPE]
 
 
 def workload_config(T):
     return {
-        "workload": "mid: |A|=|B|=100000, d=128, fp32, l2, eps=0.1, 100-cluster Gaussian mixture",
-        "nA": NA, "nB": NB, "d": DIM, "metric": "l2", "eps": EPS, "T": T, "levels": LEVELS,
+        "workload": WORKLOADS[CONFIG]["desc"],
+        "nA": NA, "nB": NB, "d": DIM, "storage": DTYPE, "metric": "l2", "eps": EPS, "T": T, "levels": LEVELS,
         "proj_dim": PROJ, "grouping": "hash tables per scale",
         "l2_flush": "256 MiB write between timed steps, outside the timed events",
     }
@@ -63,6 +104,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=200, help="0 skips the serving sample")
+    ap.add_argument("--config", default="mid", choices=sorted(WORKLOADS))
     return ap.parse_args()
 
 
@@ -108,6 +150,22 @@ class Clocks:
                           if len(s) > 5 + i and s[5 + i].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.samples)}
+
+
+def screen_traffic(kind):
+    """DRAM bytes per launch of k_screen<kind> on this workload from the committed
+    ncu summary (profiles/screen_traffic.json), or None when the kernel source has
+    changed since those counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "screen_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2307_03043_gb300", "csrc", "k_screen.cu"), "rb").read()
+        ent = rec.get(f"{CONFIG}/{kind}")
+        if ent and ent["k_screen_sha256"] == hashlib.sha256(src).hexdigest():
+            return ent["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
 
 
 def cpu_oracle_step(A, B, T, seed, scan_fraction=1):
@@ -217,6 +275,7 @@ def run_reference(args):
 
 def main():
     args = parse()
+    select_workload(args.config)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -237,24 +296,32 @@ def main():
     from paper_2307_03043_gb300 import binding as ch
     from paper_2307_03043_gb300 import workloads
 
-    A_np, B_np = workloads.gaussian_mixture(NA, NB, DIM, rank)
-    A = torch.from_numpy(A_np).cuda()
-    B = torch.from_numpy(B_np).cuda()
+    A_np, B_np, A_st, B_st, scA_np, scB_np = make_data(rank)
+    A = torch.from_numpy(A_st).cuda()
+    B = torch.from_numpy(B_st).cuda()
+    scA = torch.from_numpy(scA_np).cuda() if scA_np is not None else None
+    scB = torch.from_numpy(scB_np).cuda() if scB_np is not None else None
+    cdt = {"f32": ch.CH_F32, "bf16": ch.CH_BF16, "fp8": ch.CH_FP8E4M3}[DTYPE]
     stream = torch.cuda.current_stream()
     ctx = ch.ch_ctx_create(local, stream)
     screen = {"auto": ch.CH_SCREEN_AUTO, "exact": ch.CH_SCREEN_EXACT, "tf32": ch.CH_SCREEN_TF32}[args.screen]
+    exact_mode = 0 if CONFIG == "mid" else 1  # 1M x 1M: tensor-core screen + canonical rerank
+
+    def mkset(X, sc, mode=2):
+        # mode 2 adopts device memory; FP8 scales (device) are copied
+        return ch.ch_set_create(ctx, X, mode if sc is None else 1, NA if X is A else NB, DIM, cdt, sc)
 
     # exact reference value (untimed): GPU brute force
-    sA = ch.ch_set_create(ctx, A, 2, NA, DIM)
-    sB = ch.ch_set_create(ctx, B, 2, NB, DIM)
-    exact = ch.ch_exact(ctx, sA, sB, ch.CH_L2, 0)
+    sA = mkset(A, scA)
+    sB = mkset(B, scB)
+    exact = ch.ch_exact(ctx, sA, sB, ch.CH_L2, exact_mode)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     exact_ms_ev = []
     for _ in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ch.ch_exact(ctx, sA, sB, ch.CH_L2, 0)
+        ch.ch_exact(ctx, sA, sB, ch.CH_L2, exact_mode)
         e1.record(stream)
         e1.synchronize()
         exact_ms_ev.append(e0.elapsed_time(e1))
@@ -263,8 +330,8 @@ def main():
     T = 0
 
     def step(seed):
-        a = ch.ch_set_create(ctx, A, 2, NA, DIM)
-        b = ch.ch_set_create(ctx, B, 2, NB, DIM)
+        a = mkset(A, scA)
+        b = mkset(B, scB)
         p = ch.est_params(ch.CH_L2, LEVELS, PROJ, None, seed, eps=EPS, T=0, sample_seed=seed, screen=screen)
         eta, rep = ch.ch_estimate(ctx, a, b, p, report=True)
         ch.ch_set_destroy(a)
@@ -315,14 +382,16 @@ def main():
     value = pts_ok / (total_ms / 1e3)
 
     # end to end through the public API from pinned host buffers
-    hA = torch.from_numpy(A_np).pin_memory()
-    hB = torch.from_numpy(B_np).pin_memory()
+    hA = torch.from_numpy(A_st).pin_memory()
+    hB = torch.from_numpy(B_st).pin_memory()
+    hsA = torch.from_numpy(scA_np).pin_memory() if scA_np is not None else None
+    hsB = torch.from_numpy(scB_np).pin_memory() if scB_np is not None else None
     e2e_s = []
     for k in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        a = ch.ch_set_create(ctx, hA, 0, NA, DIM)
-        b = ch.ch_set_create(ctx, hB, 0, NB, DIM)
+        a = ch.ch_set_create(ctx, hA, 0, NA, DIM, cdt, hsA)
+        b = ch.ch_set_create(ctx, hB, 0, NB, DIM, cdt, hsB)
         eta = ch.ch_estimate(ctx, a, b, ch.est_params(ch.CH_L2, LEVELS, PROJ, None, 500 + k, eps=EPS,
                                                       sample_seed=500 + k, screen=screen))
         ch.ch_set_destroy(a)
@@ -347,10 +416,14 @@ def main():
                 "peak_basis": "152 SMs x 128 FP32 lanes x sm_max_mhz (derived, not measured)"}
     else:
         bf16 = peaks.get("bf16_tflops", 1910.1)
-        peak = bf16 * (1.1 / 2.25)  # TF32 dense = measured BF16 burst x nominal TF32/BF16 ratio
-        roof = {"bound": "tensor", "achieved": flops / (kern_avg / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "traffic": None, "kernel": "k_screen<TF32> (tcgen05 screen, 2*T*nB*d flops)",
-                "peak_basis": "of measured: bf16_tflops (burst) x 1.1/2.25 nominal tf32:bf16"}
+        # tensor peak for the screen's own operand type: measured BF16 burst, scaled by the
+        # nominal dense ratio for TF32 (1.1/2.25) and FP8 (4.5/2.25)
+        ratio, kind = {ch.CH_SCREEN_TF32: (1.1 / 2.25, "TF32"), ch.CH_SCREEN_BF16: (1.0, "BF16"),
+                       ch.CH_SCREEN_FP8: (2.0, "FP8")}[screen_used]
+        roof = {"bound": "tensor", "achieved": flops / (kern_avg / 1e3) / 1e12, "peak": bf16 * ratio,
+                "unit": "TFLOP/s", "traffic": screen_traffic(kind),
+                "kernel": f"k_screen<{kind}> (tcgen05 screen, 2*T*nB*d flops)",
+                "peak_basis": f"of measured: bf16_tflops (burst) x {ratio:.3f} nominal {kind.lower()}:bf16"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel_ms"] = kern_avg
 
@@ -358,25 +431,31 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        sec, _ = cpu_oracle_step(A_np, B_np, T, 0, 1)
+        frac = 1 if CONFIG == "mid" else 32
+        sec, _ = cpu_oracle_step(A_np, B_np, T, 0, frac)
         cpu = {"value": (NA + NB) / sec, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": "one full oracle Chamfer-Estimate of the 100k x 100k workload (all T scans)"}
+               "sample": ("one full oracle Chamfer-Estimate of the 100k x 100k workload (all T scans)"
+                          if frac == 1 else
+                          f"oracle CrudeNN + weights + draws on the full sets (dequantised values), "
+                          f"exact scans of T/{frac} samples timed and scaled by {frac}")}
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
             "config": workload_config(T),
             "accuracy": {"steps_within_10pct": int(sum(ok)), "steps": len(ok), "exact_ch": exact},
-            "exact_gpu": {"ms": float(np.mean(exact_ms_ev)), "pts_per_s": (NA + NB) / (np.mean(exact_ms_ev) / 1e3),
+            "exact_gpu": {"mode": "canonical fp32, all pairs" if exact_mode == 0 else
+                          "tensor-core screen + canonical fp32 rerank, all of A", "ms": float(np.mean(exact_ms_ev)), "pts_per_s": (NA + NB) / (np.mean(exact_ms_ev) / 1e3),
                           "speedup_estimate_vs_exact": float(np.mean(exact_ms_ev)) / (total_ms / args.steps)},
             "stage_ms": {"crude_nn": float(np.mean([s[0] for s in stages])),
                          "sample": float(np.mean([s[1] for s in stages])),
                          "scan": scan_avg, "scan_main_kernel": kern_avg,
                          "estimate_total": float(np.mean([s[3] for s in stages])),
                          "step": total_ms / args.steps},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (NA + NB) * DIM * 4,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": (NA + NB) * DIM * elem_bytes() + (0 if scA_np is None else (NA + NB) * 4),
                     "d2h_bytes_per_step": 48},
             "gpu_launches": launches,
             "roofline": roof,

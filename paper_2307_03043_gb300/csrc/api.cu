@@ -152,7 +152,7 @@ static void take_hashed(L& lay, const ch_set* X, const ch_hash_params* hp, Hashe
     h->boxY = nullptr;
   } else {
     const int k = static_cast<int>(hp->proj_dim);
-    h->Y = lay.template take<float>(size_t(X->n) * k + size_t(proj_pad(k)) * X->d);
+    h->Y = lay.template take<float>(size_t(X->n) * k + 4 + size_t(proj_pad(k)) * X->d);
     h->boxY = lay.template take<uint32_t>(size_t(2) * k);
     h->src = HashSrc{h->Y, CH_F32, X->n, k, nullptr};
     h->box = h->boxY;

@@ -283,11 +283,205 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
   }
 }
 
+// Asynchronous variant for rows whose byte length is a multiple of 16: each
+// 32-coordinate slice of the block's rows (and of G) is copied with 16-byte
+// cp.async into a double buffer, so the next slice is in flight while the
+// current one is multiplied.  Same arithmetic and order as k_project.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(static_cast<uint32_t>(
+                   __cvta_generic_to_shared(smem))),
+               "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int DT, int KP>
+__global__ void __launch_bounds__(128) k_project_async(const void* X, const float* scales, int64_t n, int d,
+                                                       const float* G, int k, float* Y, uint32_t* box, float* norms,
+                                                       uint32_t* status) {
+  constexpr int RPT = KP <= 16 ? 2 : 1;
+  constexpr int ROWS = 128 * RPT;
+  constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
+  constexpr int PER = 16 / ES;       // coordinates per 16-byte chunk
+  constexpr int CH = 32 / PER;       // chunks per 32-coordinate slice of a row
+  constexpr int STR = CH + 1;        // padded row stride in chunks (odd: conflict-free)
+  extern __shared__ __align__(16) uint4 dyn[];
+  uint4* s_x = dyn;                                                    // [2][ROWS][STR]
+  float* s_g = reinterpret_cast<float*>(dyn + 2 * ROWS * STR);         // [2][32][KP]
+  const int64_t r0 = int64_t(blockIdx.x) * ROWS;
+  const int tid = threadIdx.x;
+  const int row_bytes = d * ES;
+  const int slices = (d + 31) / 32;
+  auto issue = [&](int sl, int buf) {
+    const int j0 = sl * 32;
+    // rows: ROWS x CH chunks; chunk (rr, c) covers coordinates j0 + c*PER .. +PER
+    for (int t = tid; t < ROWS * CH; t += 128) {
+      const int rr = t / CH, c = t % CH;
+      const int64_t row = r0 + rr;
+      const int jb = (j0 + c * PER) * ES;
+      const bool ok = row < n && jb < row_bytes;
+      const char* src = static_cast<const char*>(X) + (ok ? row * row_bytes + jb : 0);
+      cp_async16(&s_x[(buf * ROWS + rr) * STR + c], src, ok ? 16u : 0u);
+    }
+    // G rows j0 .. j0+31 (KP floats each), zero past d
+    for (int t = tid; t < 32 * KP / 4; t += 128) {
+      const int jj = t / (KP / 4), c = t % (KP / 4);
+      const bool ok = j0 + jj < d;
+      const float* src = G + (ok ? int64_t(j0 + jj) * KP + c * 4 : 0);
+      cp_async16(&s_g[(buf * 32 + jj) * KP + c * 4], src, ok ? 16u : 0u);
+    }
+    cp_async_commit();
+  };
+
+  float acc[RPT][KP];
+  float sq[RPT];
+  bool bad = false;
+#pragma unroll
+  for (int p = 0; p < RPT; ++p) {
+    sq[p] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < KP; ++i) acc[p][i] = 0.0f;
+  }
+  float scl[RPT];
+#pragma unroll
+  for (int p = 0; p < RPT; ++p) {
+    const int64_t r = r0 + p * 128 + tid;
+    scl[p] = (DT == CH_FP8E4M3 && r < n) ? scales[r] : 1.0f;
+  }
+  issue(0, 0);
+  for (int sl = 0; sl < slices; ++sl) {
+    const int buf = sl & 1;
+    if (sl + 1 < slices) {
+      issue(sl + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int jn = min(32, d - sl * 32);
+    const float* g = s_g + buf * 32 * KP;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      float xv[RPT][PER];
+#pragma unroll
+      for (int p = 0; p < RPT; ++p) {
+        const uint4 raw = s_x[(buf * ROWS + p * 128 + tid) * STR + c];
+        if constexpr (DT == CH_F32) {
+          xv[p][0] = __uint_as_float(raw.x);
+          xv[p][1] = __uint_as_float(raw.y);
+          xv[p][2] = __uint_as_float(raw.z);
+          xv[p][3] = __uint_as_float(raw.w);
+        } else if constexpr (DT == CH_BF16) {
+          const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            xv[p][2 * e] = bf16_to_f32(static_cast<uint16_t>(w4[e] & 0xFFFFu));
+            xv[p][2 * e + 1] = bf16_to_f32(static_cast<uint16_t>(w4[e] >> 16));
+          }
+        } else {
+          const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            xv[p][e] = __fmul_rn(e4m3_to_f32(static_cast<uint8_t>(w4[e / 4] >> (8 * (e % 4)))), scl[p]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        const int jj = c * PER + e;
+        if (jj < jn) {
+#pragma unroll
+          for (int p = 0; p < RPT; ++p) {
+            sq[p] = fmaf(xv[p][e], xv[p][e], sq[p]);
+            bad |= !isfinite(xv[p][e]);
+          }
+          const float4* g4 = reinterpret_cast<const float4*>(g + jj * KP);
+#pragma unroll
+          for (int i4 = 0; i4 < KP / 4; ++i4) {
+            const float4 gv = g4[i4];
+#pragma unroll
+            for (int p = 0; p < RPT; ++p) {
+              acc[p][4 * i4 + 0] = __fmaf_rn(gv.x, xv[p][e], acc[p][4 * i4 + 0]);
+              acc[p][4 * i4 + 1] = __fmaf_rn(gv.y, xv[p][e], acc[p][4 * i4 + 1]);
+              acc[p][4 * i4 + 2] = __fmaf_rn(gv.z, xv[p][e], acc[p][4 * i4 + 2]);
+              acc[p][4 * i4 + 3] = __fmaf_rn(gv.w, xv[p][e], acc[p][4 * i4 + 3]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // the buffer is refilled two slices from now
+  }
+  const int lane = tid & 31;
+#pragma unroll
+  for (int p = 0; p < RPT; ++p) {
+    const int64_t r = r0 + p * 128 + tid;
+    if (r < n) {
+#pragma unroll
+      for (int i = 0; i < KP; ++i)
+        if (i < k) Y[r * k + i] = acc[p][i];
+      if (norms) norms[r] = sq[p];
+    }
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    if (i < k) {
+      uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+#pragma unroll
+      for (int p = 0; p < RPT; ++p) {
+        if (r0 + p * 128 + tid < n) {
+          lo = min(lo, ord_enc(acc[p][i]));
+          hi = max(hi, ord_enc(acc[p][i]));
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+      }
+      if (lane == 0 && lo <= hi) {
+        atomicMin(&box[i], lo);
+        atomicMax(&box[k + i], hi);
+      }
+    }
+  }
+}
+
+template <int DT, int KP>
+static size_t project_async_smem() {
+  constexpr int RPT = KP <= 16 ? 2 : 1;
+  constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
+  constexpr int CH = 32 * ES / 16;
+  return size_t(2) * 128 * RPT * (CH + 1) * 16 + size_t(2) * 32 * KP * 4;
+}
+
 template <int DT>
 static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y, uint32_t* box, float* norms,
                        cudaStream_t s) {
   const int rows_per_block = kp <= 16 ? 256 : 128;
   const int grid = static_cast<int>(ceil_div(X->n, rows_per_block));
+  const bool aligned = (int64_t(X->d) * int64_t(elem_size(DT))) % 16 == 0 &&
+                       (reinterpret_cast<uintptr_t>(X->data) & 15) == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
+  if (aligned) {
+#define CHX_PROJA(KPV)                                                                                       \
+  do {                                                                                                       \
+    const size_t sm = project_async_smem<DT, KPV>();                                                         \
+    CHX_CUDA(cudaFuncSetAttribute(k_project_async<DT, KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                  static_cast<int>(project_async_smem<DT, KPV>())));                         \
+    k_project_async<DT, KPV><<<grid, 128, sm, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box, norms,      \
+                                                   X->status);                                               \
+  } while (0)
+    if (kp == 8) CHX_PROJA(8);
+    else if (kp == 16) CHX_PROJA(16);
+    else if (kp == 32) CHX_PROJA(32);
+    else CHX_PROJA(64);
+#undef CHX_PROJA
+    return;
+  }
 #define CHX_PROJ(KPV) \
   k_project<DT, KPV><<<grid, 128, 0, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box, norms, X->status)
   if (kp == 8) CHX_PROJ(8);
@@ -310,7 +504,7 @@ void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* b
   CHX_CUDA(cudaMemsetAsync(box + k, 0, size_t(k) * 4, s));
   if (X->n == 0) return;
   // the Gaussian matrix lives in the tail of Y's allocation
-  float* G = Y + X->n * k;
+  float* G = Y + ((X->n * k + 3) & ~int64_t(3));  // 16-byte aligned
   const int64_t gn = int64_t(kp) * X->d;
   k_gauss<<<static_cast<int>(ceil_div(gn, 256)), 256, 0, s>>>(seed, k, kp, X->d, G);
   launch_check("gauss");

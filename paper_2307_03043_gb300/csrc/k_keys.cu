@@ -10,6 +10,8 @@
 // Bucket tables: one open-addressing table (linear probing, 16-byte slots
 // {key, ~min b}) per scale; B inserts, then each a probes its scales in
 // increasing order and stops at the first bucket that holds a b.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace chx {
@@ -21,10 +23,25 @@ namespace {
 // once and accumulate up to 16 scales together.
 constexpr int kRegRow = 32;
 
-template <int DT>
-__device__ inline void load_row(const HashSrc& src, int64_t r, float (&y)[kRegRow]) {
+// row of width dd <= W into registers (float4 loads for aligned binary32 rows of width W)
+template <int DT, int W>
+__device__ inline void load_row(const HashSrc& src, int64_t r, float (&y)[W]) {
+  if constexpr (DT == CH_F32) {
+    if (src.dd == W && (reinterpret_cast<uintptr_t>(src.base) & 15) == 0) {
+      const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(src.base) + r * W);
 #pragma unroll
-  for (int j = 0; j < kRegRow; ++j) y[j] = (j < src.dd) ? load_elem<DT>(src.base, r, src.dd, j, src.scales) : 0.0f;
+      for (int q = 0; q < W / 4; ++q) {
+        const float4 v = p[q];
+        y[4 * q] = v.x;
+        y[4 * q + 1] = v.y;
+        y[4 * q + 2] = v.z;
+        y[4 * q + 3] = v.w;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < W; ++j) y[j] = (j < src.dd) ? load_elem<DT>(src.base, r, src.dd, j, src.scales) : 0.0f;
 }
 
 __device__ inline void cell_acc(float y, float z, float inv_r, uint64_t K, uint64_t& h) {
@@ -40,11 +57,12 @@ __device__ inline uint64_t finish_key(uint64_t h, const ScaleTables& t, int lvl)
 }
 
 // key of a register-resident row at absolute scale index lvl
-__device__ inline uint64_t reg_key(const float (&y)[kRegRow], int dd, int L, int lvl, const ScaleTables& t) {
+template <int W>
+__device__ inline uint64_t reg_key(const float (&y)[W], int dd, int L, int lvl, const ScaleTables& t) {
   const float inv_r = __ldg(&t.inv_r[lvl]);
   uint64_t h = 0;
 #pragma unroll
-  for (int j = 0; j < kRegRow; ++j)
+  for (int j = 0; j < W; ++j)
     if (j < dd)
       cell_acc(y[j], __ldg(&t.shift[j * L + lvl]), inv_r,
                __ldg(reinterpret_cast<const unsigned long long*>(&t.mult[j])), h);
@@ -117,15 +135,15 @@ __device__ inline int64_t table_find(const ulonglong2* tab, uint32_t log_cap, ui
 
 // Narrow rows: one thread per (point, scale), thread t = l * n + r, so the
 // scales' insert round trips overlap instead of forming one chain per point.
-template <int DT>
+template <int DT, int W>
 __global__ void __launch_bounds__(128) k_table_insert_ps(HashSrc src, int L, int L0, int nl, ScaleTables t,
                                                          HashTable h, uint32_t* status) {
   const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (g >= src.n * nl) return;
   const int l = static_cast<int>(g / src.n);
   const int64_t r = g - int64_t(l) * src.n;
-  float y[kRegRow];
-  load_row<DT>(src, r, y);
+  float y[W];
+  load_row<DT, W>(src, r, y);
   const size_t cap = size_t(1) << h.log_cap;
   table_insert(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t), r, status);
 }
@@ -150,7 +168,7 @@ __global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0
 
 // Each unresolved a walks the scales of the group in increasing order and
 // stops at the first bucket that holds a b (Fig. 2, step 3).
-template <int DT>
+template <int DT, int W>
 __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
                                                      int64_t* bidx, uint8_t* level) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -162,9 +180,9 @@ __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0,
     level[r] = static_cast<uint8_t>(L);
   }
   const size_t cap = size_t(1) << h.log_cap;
-  if (src.dd <= kRegRow) {
-    float y[kRegRow];
-    load_row<DT>(src, r, y);
+  if (src.dd <= W) {
+    float y[W];
+    load_row<DT, W>(src, r, y);
     for (int l = 0; l < nl; ++l) {
       const int64_t b = table_find(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t));
       if (b >= 0) {
@@ -192,13 +210,13 @@ __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0,
   }
 }
 
-template <int DT>
+template <int DT, int W>
 __global__ void __launch_bounds__(128) k_keys_write(HashSrc src, int L, ScaleTables t, uint64_t* keys) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= src.n) return;
-  if (src.dd <= kRegRow) {
-    float y[kRegRow];
-    load_row<DT>(src, r, y);
+  if (src.dd <= W) {
+    float y[W];
+    load_row<DT, W>(src, r, y);
     for (int l = 0; l < L; ++l) keys[size_t(l) * src.n + r] = reg_key(y, src.dd, L, l, t);
   } else {
     for (int b0 = 0; b0 < L; b0 += kLevelBlock) {
@@ -212,16 +230,30 @@ __global__ void __launch_bounds__(128) k_keys_write(HashSrc src, int L, ScaleTab
   }
 }
 
+// calls f(dtype constant, register row width constant) for a hashed source
+template <class F>
+void dispatch_dt_w(int dtype, int dd, F&& f) {
+  auto with_w = [&](auto dtc) {
+    if (dd <= 16)
+      f(dtc, std::integral_constant<int, 16>{});
+    else
+      f(dtc, std::integral_constant<int, kRegRow>{});
+  };
+  switch (dtype) {
+    case CH_F32: with_w(std::integral_constant<int, CH_F32>{}); break;
+    case CH_BF16: with_w(std::integral_constant<int, CH_BF16>{}); break;
+    default: with_w(std::integral_constant<int, CH_FP8E4M3>{}); break;
+  }
+}
+
 }  // namespace
 
 void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStream_t s) {
   if (X.n == 0) return;
   const int grid = static_cast<int>(ceil_div(X.n, 128));
-  switch (X.dtype) {
-    case CH_F32: k_keys_write<CH_F32><<<grid, 128, 0, s>>>(X, L, t, keys); break;
-    case CH_BF16: k_keys_write<CH_BF16><<<grid, 128, 0, s>>>(X, L, t, keys); break;
-    default: k_keys_write<CH_FP8E4M3><<<grid, 128, 0, s>>>(X, L, t, keys); break;
-  }
+  dispatch_dt_w(X.dtype, X.dd, [&](auto dtc, auto wc) {
+    k_keys_write<decltype(dtc)::value, decltype(wc)::value><<<grid, 128, 0, s>>>(X, L, t, keys);
+  });
   launch_check("keys_write");
 }
 
@@ -230,11 +262,10 @@ void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTa
   if (B.n == 0) return;
   if (B.dd <= kRegRow) {
     const int grid_ps = static_cast<int>(ceil_div(B.n * nl, 128));
-    switch (B.dtype) {
-      case CH_F32: k_table_insert_ps<CH_F32><<<grid_ps, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
-      case CH_BF16: k_table_insert_ps<CH_BF16><<<grid_ps, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
-      default: k_table_insert_ps<CH_FP8E4M3><<<grid_ps, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
-    }
+    dispatch_dt_w(B.dtype, B.dd, [&](auto dtc, auto wc) {
+      k_table_insert_ps<decltype(dtc)::value, decltype(wc)::value><<<grid_ps, 128, 0, s>>>(B, L, L0, nl, t, h,
+                                                                                            status);
+    });
     launch_check("table_insert");
     return;
   }
@@ -251,11 +282,9 @@ void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTab
                         cudaStream_t s) {
   if (A.n == 0) return;
   const int grid = static_cast<int>(ceil_div(A.n, 128));
-  switch (A.dtype) {
-    case CH_F32: k_table_probe<CH_F32><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
-    case CH_BF16: k_table_probe<CH_BF16><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
-    default: k_table_probe<CH_FP8E4M3><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level); break;
-  }
+  dispatch_dt_w(A.dtype, A.dd, [&](auto dtc, auto wc) {
+    k_table_probe<decltype(dtc)::value, decltype(wc)::value><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level);
+  });
   launch_check("table_probe");
 }
 

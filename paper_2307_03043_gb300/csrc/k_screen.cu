@@ -130,6 +130,30 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, u
   }
 }
 
+// 32 columns of this warp's 32 TMEM lanes; the registers are valid only after
+// tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 16 columns; valid after tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -309,20 +333,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         best_c[i] = -1;
       }
       int32_t group = 0;  // running 32-column group index within this half
+      // |b|^2 (and -2 x FP8 scale) of this lane's 4 columns of a tile half,
+      // fetched one tile ahead so the load latency hides behind a tile of work;
+      // +inf past the end of the chunk
+      float pn[4], ps[4];
+      auto prefetch_norms = [&](int64_t t0) {
+        const int64_t base = t0 + half * (kBN / 2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t b = base + lane + 32 * k;
+          pn[k] = (b < b_end) ? __ldg(&args.normB[b]) : __int_as_float(0x7F800000);
+          ps[k] = 0.0f;
+          if constexpr (SCREEN == CH_SCREEN_FP8) ps[k] = (b < b_end) ? -2.0f * __ldg(&args.scaleB[b]) : 0.0f;
+        }
+      };
+      prefetch_norms(b_begin);
       bool ok = true;
       for (int64_t b0 = b_begin; b0 < b_end; b0 += kBN) {
         // stage |b|^2 (and -2 x FP8 scale) of this tile in this warp's own buffer;
         // +inf past the end of B.  Only __syncwarp is used inside the epilogue, so
         // a warp that gives up on a wait can never strand another one.
-        const int64_t c0 = b0 + half * (kBN / 2);  // first B index of this warp's half
         float* nb = nb_s + ((warp - 2) * 2 + acc) * (kBN / 2);
         float* sb = sb_s + ((warp - 2) * 2 + acc) * (kBN / 2);
-        for (int c = lane; c < kBN / 2; c += 32) {
-          const int64_t b = c0 + c;
-          nb[c] = (b < b_end) ? args.normB[b] : __int_as_float(0x7F800000);
-          if constexpr (SCREEN == CH_SCREEN_FP8) sb[c] = (b < b_end) ? -2.0f * args.scaleB[b] : 0.0f;
+        // this tile's norms were fetched into registers during the previous tile
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          nb[lane + 32 * k] = pn[k];
+          if constexpr (SCREEN == CH_SCREEN_FP8) sb[lane + 32 * k] = ps[k];
         }
         __syncwarp();
+        prefetch_norms(b0 + kBN);  // next tile's, consumed one tile from now
         const bool got = mbar_wait(&acc_full[acc], accphase, abort_flag);
         if (!__all_sync(0xFFFFFFFFu, got)) {
           ok = false;
@@ -331,15 +371,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t taddr =
             tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + half * (kBN / 2);
-#pragma unroll 1
-        for (int ch = 0; ch < kBN / 64; ++ch) {
-          uint32_t r[32];
-          tmem_ld32(taddr + ch * 32, r);
-          // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 32 columns
-          const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 32);
-          const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 32);
+        // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 32 columns, then
+        // the branch-free update of the residue-class minima
+        // chunk ch = columns ch*16 .. ch*16+15 of this warp's half: residue
+        // classes (ch%2)*16 + i, 32-column group (tile, ch/2)
+        auto process = [&](uint32_t(&r)[16], int ch) {
+          const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 16);
+          const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 16);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 4; ++q) {
             const float4 n = nb4[q];
             float4 m = make_float4(-2.0f, -2.0f, -2.0f, -2.0f);
             if constexpr (SCREEN == CH_SCREEN_FP8) {
@@ -354,16 +394,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
             r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
           }
-          // branch-free update of the residue-class minima
+          const int cls = (ch & 1) * 16;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < 16; ++i) {
             const float v = __uint_as_float(r[i]);
-            const bool lt = v < best_s[i];
-            best_s[i] = lt ? v : best_s[i];
-            best_c[i] = lt ? group : best_c[i];
+            const bool lt = v < best_s[cls + i];
+            best_s[cls + i] = lt ? v : best_s[cls + i];
+            best_c[cls + i] = lt ? group + (ch >> 1) : best_c[cls + i];
           }
-          ++group;
+        };
+        // two 16-column register buffers: the next chunk loads while this one is processed
+        uint32_t ra[16], rb[16];
+        tmem_ld16_async(taddr, ra);
+        tmem_wait_ld();
+#pragma unroll
+        for (int ch = 0; ch < 8; ch += 2) {
+          tmem_ld16_async(taddr + (ch + 1) * 16, rb);
+          process(ra, ch);
+          tmem_wait_ld();
+          if (ch + 2 < 8) tmem_ld16_async(taddr + (ch + 2) * 16, ra);
+          process(rb, ch + 1);
+          tmem_wait_ld();
         }
+        group += kBN / 64;
         tc_fence_before();
         mbar_arrive(&acc_empty[acc]);
         acc ^= 1;
