@@ -10,9 +10,9 @@ namespace chx {
 size_t elem_size(int dtype) { return dtype == CH_F32 ? 4 : dtype == CH_BF16 ? 2 : 1; }
 
 // ------------------------------------------------------------------ ingest
-// One warp per row: finite check, |x|^2 (any order; used only by the tensor-core
-// screen), per-coordinate min/max of x.  CB = column blocks of 32 kept in
-// registers (0 = shared-memory atomics for large d).
+// One warp per row: finite check and per-coordinate min/max of x (the l1 hashed
+// space's bounding box).  CB = column blocks of 32 kept in registers (0 =
+// shared-memory atomics for large d).
 template <int DT, int CB>
 __global__ void __launch_bounds__(256) k_ingest(const void* X, const float* scales, int64_t n, int d,
                                                 float* norms, uint32_t* box, uint32_t* status) {
@@ -287,6 +287,8 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
 // 32-coordinate slice of the block's rows (and of G) is copied with 16-byte
 // cp.async into a double buffer, so the next slice is in flight while the
 // current one is multiplied.  Same arithmetic and order as k_project.
+constexpr int kProjThreads = 64;  // small blocks: ~5 resident per SM, about one wave
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, uint32_t bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(static_cast<uint32_t>(
                    __cvta_generic_to_shared(smem))),
@@ -300,11 +302,11 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 template <int DT, int KP>
-__global__ void __launch_bounds__(128) k_project_async(const void* X, const float* scales, int64_t n, int d,
+__global__ void __launch_bounds__(kProjThreads) k_project_async(const void* X, const float* scales, int64_t n, int d,
                                                        const float* G, int k, float* Y, uint32_t* box, float* norms,
                                                        uint32_t* status) {
   constexpr int RPT = KP <= 16 ? 2 : 1;
-  constexpr int ROWS = 128 * RPT;
+  constexpr int ROWS = kProjThreads * RPT;
   constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
   constexpr int PER = 16 / ES;       // coordinates per 16-byte chunk
   constexpr int CH = 32 / PER;       // chunks per 32-coordinate slice of a row
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(128) k_project_async(const void* X, const floa
   auto issue = [&](int sl, int buf) {
     const int j0 = sl * 32;
     // rows: ROWS x CH chunks; chunk (rr, c) covers coordinates j0 + c*PER .. +PER
-    for (int t = tid; t < ROWS * CH; t += 128) {
+    for (int t = tid; t < ROWS * CH; t += kProjThreads) {
       const int rr = t / CH, c = t % CH;
       const int64_t row = r0 + rr;
       const int jb = (j0 + c * PER) * ES;
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(128) k_project_async(const void* X, const floa
       cp_async16(&s_x[(buf * ROWS + rr) * STR + c], src, ok ? 16u : 0u);
     }
     // G rows j0 .. j0+31 (KP floats each), zero past d
-    for (int t = tid; t < 32 * KP / 4; t += 128) {
+    for (int t = tid; t < 32 * KP / 4; t += kProjThreads) {
       const int jj = t / (KP / 4), c = t % (KP / 4);
       const bool ok = j0 + jj < d;
       const float* src = G + (ok ? int64_t(j0 + jj) * KP + c * 4 : 0);
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(128) k_project_async(const void* X, const floa
   float scl[RPT];
 #pragma unroll
   for (int p = 0; p < RPT; ++p) {
-    const int64_t r = r0 + p * 128 + tid;
+    const int64_t r = r0 + p * kProjThreads + tid;
     scl[p] = (DT == CH_FP8E4M3 && r < n) ? scales[r] : 1.0f;
   }
   issue(0, 0);
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(128) k_project_async(const void* X, const floa
       float xv[RPT][PER];
 #pragma unroll
       for (int p = 0; p < RPT; ++p) {
-        const uint4 raw = s_x[(buf * ROWS + p * 128 + tid) * STR + c];
+        const uint4 raw = s_x[(buf * ROWS + p * kProjThreads + tid) * STR + c];
         if constexpr (DT == CH_F32) {
           xv[p][0] = __uint_as_float(raw.x);
           xv[p][1] = __uint_as_float(raw.y);
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(128) k_project_async(const void* X, const floa
   const int lane = tid & 31;
 #pragma unroll
   for (int p = 0; p < RPT; ++p) {
-    const int64_t r = r0 + p * 128 + tid;
+    const int64_t r = r0 + p * kProjThreads + tid;
     if (r < n) {
 #pragma unroll
       for (int i = 0; i < KP; ++i)
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(128) k_project_async(const void* X, const floa
       uint32_t lo = 0xFFFFFFFFu, hi = 0u;
 #pragma unroll
       for (int p = 0; p < RPT; ++p) {
-        if (r0 + p * 128 + tid < n) {
+        if (r0 + p * kProjThreads + tid < n) {
           lo = min(lo, ord_enc(acc[p][i]));
           hi = max(hi, ord_enc(acc[p][i]));
         }
@@ -456,7 +458,7 @@ static size_t project_async_smem() {
   constexpr int RPT = KP <= 16 ? 2 : 1;
   constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
   constexpr int CH = 32 * ES / 16;
-  return size_t(2) * 128 * RPT * (CH + 1) * 16 + size_t(2) * 32 * KP * 4;
+  return size_t(2) * kProjThreads * RPT * (CH + 1) * 16 + size_t(2) * 32 * KP * 4;
 }
 
 template <int DT>
@@ -467,12 +469,13 @@ static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y,
   const bool aligned = (int64_t(X->d) * int64_t(elem_size(DT))) % 16 == 0 &&
                        (reinterpret_cast<uintptr_t>(X->data) & 15) == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
   if (aligned) {
+    const int grid_a = static_cast<int>(ceil_div(X->n, int64_t(kProjThreads) * (kp <= 16 ? 2 : 1)));
 #define CHX_PROJA(KPV)                                                                                       \
   do {                                                                                                       \
     const size_t sm = project_async_smem<DT, KPV>();                                                         \
     CHX_CUDA(cudaFuncSetAttribute(k_project_async<DT, KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                   static_cast<int>(project_async_smem<DT, KPV>())));                         \
-    k_project_async<DT, KPV><<<grid, 128, sm, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box, norms,      \
+    k_project_async<DT, KPV><<<grid_a, kProjThreads, sm, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box, norms,      \
                                                    X->status);                                               \
   } while (0)
     if (kp == 8) CHX_PROJA(8);
