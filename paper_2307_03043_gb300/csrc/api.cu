@@ -198,8 +198,10 @@ struct CrudeBufs {
   Hashed hA, hB;
   ScaleTables tab;
   int32_t* e_top;
-  ulonglong2* slots;
+  ulonglong2* slots;   // CH_GROUP_HASH: bucket tables of one scale group
   TablePlan plan;
+  uint64_t *keysA, *keysB;  // CH_GROUP_SORT: keys [L][n] and the sort's scratch
+  void* sort_work;
 };
 
 template <class L>
@@ -209,8 +211,20 @@ static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_p
   const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
   cb->tab = take_tables(lay, dd, static_cast<int>(hp->levels));
   cb->e_top = lay.template take<int32_t>(1);
-  cb->plan = table_plan(B->n, static_cast<int>(hp->levels));
+  const int nl = static_cast<int>(hp->levels);
+  if (hp->group == CH_GROUP_SORT) {
+    CHX_CHECK(sort_group_supported(A->n, B->n, nl), CH_EINVAL, "sort grouping: (nA + nB) * levels must be below 2^31");
+    cb->plan = TablePlan{0, 0};
+    cb->slots = nullptr;
+    cb->keysA = lay.template take<uint64_t>(std::max<size_t>(size_t(nl) * A->n, 1));
+    cb->keysB = lay.template take<uint64_t>(size_t(nl) * B->n);
+    cb->sort_work = lay.template take<char>(sort_group_workspace(A->n, B->n, nl));
+    return;
+  }
+  cb->plan = table_plan(B->n, nl);
   cb->slots = lay.template take<ulonglong2>(size_t(cb->plan.per_group) << cb->plan.log_cap);
+  cb->keysA = cb->keysB = nullptr;
+  cb->sort_work = nullptr;
 }
 
 // CrudeNN (Fig. 2): embedding, scales, per-scale bucket tables of B, probes of A,
@@ -223,7 +237,13 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
   run_hashed(c, A, hp, &cb->hA, status);
   run_hashed(c, B, hp, &cb->hB, status);
   launch_scale_tables(cb->hA.box, cb->hB.box, dd, L, hp->top_exp, hp->hash_seed, cb->tab, cb->e_top, status, s);
-  if (hp->group == CH_GROUP_SORT) throw Err{CH_ENOTSUP, "sort grouping not built"};
+  if (hp->group == CH_GROUP_SORT) {
+    launch_keys_write(cb->hB.src, L, cb->tab, cb->keysB, s);
+    launch_keys_write(cb->hA.src, L, cb->tab, cb->keysA, s);
+    launch_sort_group(cb->keysA, A->n, cb->keysB, B->n, L, cb->sort_work, bidx, level, s);
+    launch_crude_dist(A, B, hp->metric, bidx, D, s);
+    return;
+  }
   const size_t cap = size_t(1) << cb->plan.log_cap;
   for (int L0 = 0; L0 < L; L0 += cb->plan.per_group) {
     const int nl = std::min(cb->plan.per_group, L - L0);

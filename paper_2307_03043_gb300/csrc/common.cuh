@@ -272,6 +272,7 @@ void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStre
 
 // radix-sort grouping (CH_GROUP_SORT): keys [L][nA] and [L][nB] -> bidx, level
 size_t sort_group_workspace(int64_t nA, int64_t nB, int L);
+bool sort_group_supported(int64_t nA, int64_t nB, int L);
 void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L,
                        void* work, int64_t* bidx, uint8_t* level, cudaStream_t s);
 

@@ -63,12 +63,12 @@ def pair_factory(ctx):
         p.close()
 
 
-def gpu_crude(ctx, p, metric, seed, L=10, k=16, top_exp=None):
+def gpu_crude(ctx, p, metric, seed, L=10, k=16, top_exp=None, group=ch.CH_GROUP_HASH):
     nA = p.A_np.shape[0]
-    bidx = torch.zeros(nA, dtype=torch.int64, device="cuda")
-    D = torch.zeros(nA, dtype=torch.float32, device="cuda")
-    lv = torch.zeros(nA, dtype=torch.uint8, device="cuda")
-    ch.ch_crude_nn(ctx, p.sA, p.sB, ch.hash_params(metric, L, k, top_exp, seed), bidx, D, lv)
+    bidx = torch.full((nA,), -5, dtype=torch.int64, device="cuda")
+    D = torch.full((nA,), -1.0, dtype=torch.float32, device="cuda")
+    lv = torch.full((nA,), 255, dtype=torch.uint8, device="cuda")
+    ch.ch_crude_nn(ctx, p.sA, p.sB, ch.hash_params(metric, L, k, top_exp, seed, group), bidx, D, lv)
     return bidx.cpu().numpy(), D.cpu().numpy(), lv.cpu().numpy()
 
 
@@ -100,9 +100,13 @@ def test_top_exp_matches(ctx, pair_factory, metric):
 
 
 # ------------------------------------------------------------------ CrudeNN
+GROUPS = [ch.CH_GROUP_HASH, ch.CH_GROUP_SORT]
+
+
+@pytest.mark.parametrize("group", GROUPS, ids=["hash", "sort"])
 @pytest.mark.parametrize("metric", [L1, L2])
 @pytest.mark.parametrize("shape", ["tiny", "ragged", "dup", "one_b", "d3"])
-def test_crude_nn_bit_exact(ctx, pair_factory, metric, shape):
+def test_crude_nn_bit_exact(ctx, pair_factory, metric, shape, group):
     if shape == "tiny":
         A, B = workloads.uniform(2000, 2000, 16, 0)
     elif shape == "ragged":
@@ -116,21 +120,48 @@ def test_crude_nn_bit_exact(ctx, pair_factory, metric, shape):
         A, B = workloads.shape_surface(3001, 2999, 4)
     p = pair_factory(A, B)
     for seed in (0, 7):
-        bidx, D, lv = gpu_crude(ctx, p, metric, seed)
+        bidx, D, lv = gpu_crude(ctx, p, metric, seed, group=group)
         r = oracle.crude_nn(A, B, metric, hash_seed=seed)
         assert np.array_equal(bidx, r["bidx"])
         assert np.array_equal(lv, r["level"])
         assert np.array_equal(D.view(np.uint32), r["D"].view(np.uint32))
 
 
-def test_crude_nn_few_levels_and_fallback(ctx, pair_factory):
+@pytest.mark.parametrize("group", GROUPS, ids=["hash", "sort"])
+def test_crude_nn_few_levels_and_fallback(ctx, pair_factory, group):
     A, B = workloads.uniform(400, 600, 6, 5)
     p = pair_factory(A, B)
     for L, top in ((1, None), (2, -8), (32, None), (5, 40)):
-        bidx, D, lv = gpu_crude(ctx, p, L1, 3, L=L, top_exp=top)
+        bidx, D, lv = gpu_crude(ctx, p, L1, 3, L=L, top_exp=top, group=group)
         r = oracle.crude_nn(A, B, L1, hash_seed=3, L=L, top_exp=top)
         assert np.array_equal(bidx, r["bidx"]) and np.array_equal(lv, r["level"])
         assert np.array_equal(D, r["D"])
+
+
+def test_sort_grouping_long_runs(ctx, pair_factory):
+    """Radix-sort grouping over many tiles: runs of equal keys that cross sort
+    tiles and head-scan blocks (B holds few distinct points, A many copies)."""
+    rng = np.random.default_rng(11)
+    base = rng.standard_normal((37, 8)).astype(np.float32)
+    B = base[rng.integers(0, 37, 60_000)]
+    A = np.vstack([base[rng.integers(0, 37, 30_000)], rng.standard_normal((20_000, 8)).astype(np.float32)])
+    p = pair_factory(A, B)
+    for metric in (L1, L2):
+        bh, Dh, lh = gpu_crude(ctx, p, metric, 2)
+        bs, Ds, ls = gpu_crude(ctx, p, metric, 2, group=ch.CH_GROUP_SORT)
+        assert np.array_equal(bh, bs) and np.array_equal(lh, ls)
+        assert np.array_equal(Dh.view(np.uint32), Ds.view(np.uint32))
+        r = oracle.crude_nn(A, B, metric, hash_seed=2)
+        assert np.array_equal(bs, r["bidx"]) and np.array_equal(ls, r["level"])
+
+
+def test_estimate_sort_equals_hash(ctx, pair_factory):
+    A, B = workloads.gaussian_mixture(5000, 7000, 24, 3, clusters=9)
+    p = pair_factory(A, B)
+    for metric in (L1, L2):
+        e = [ch.ch_estimate(ctx, p.sA, p.sB, ch.est_params(metric, T=3000, group=g, hash_seed=1, sample_seed=2))
+             for g in GROUPS]
+        assert e[0] == e[1]
 
 
 # ------------------------------------------------------------------ sampling
