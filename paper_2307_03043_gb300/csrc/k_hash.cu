@@ -3,7 +3,7 @@
 // tables of B probed by A in increasing scale order, and D_a = d(a, b(a)).
 #include <cstring>
 
-#include "common.cuh"
+#include "tma.cuh"
 
 namespace chx {
 
@@ -160,22 +160,24 @@ void ensure_norms(ch_set* X, cudaStream_t s) {
 // Z_ij: 12-term Irwin-Hall normal from Philox counters (j, i, 2, m), m < 3,
 // summed exactly, centred, scaled by 2^-32 and rounded once to binary32
 // (the l2 -> l1 embedding theorem of App. A.2 with the 1/(beta k) factor left out).
+// entry (j, i) of the Gaussian matrix: Irwin-Hall sum of 12 Philox words
+// (counter (j, i, 2, m), m = 0..2), centred and scaled by 2^-32 in binary64,
+// rounded once to binary32; zero for i >= k
+__device__ inline float gauss_entry(uint64_t seed, int k, int j, int i) {
+  if (i >= k) return 0.0f;
+  uint64_t sum = 0;
+  for (uint32_t m = 0; m < 3; ++m) {
+    const P4 w = philox10(P4{uint32_t(j), uint32_t(i), 2u, m}, uint32_t(seed), uint32_t(seed >> 32));
+    sum += uint64_t(w.x) + w.y + w.z + w.w;
+  }
+  const int64_t centred = static_cast<int64_t>(sum) - int64_t(6) * 4294967296LL;
+  return __double2float_rn(ldexp(static_cast<double>(centred), -32));
+}
+
 __global__ void k_gauss(uint64_t seed, int k, int kp, int d, float* G /* [d][kp], zero rows i >= k */) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(kp) * d) return;
-  const int i = static_cast<int>(t % kp);
-  const int j = static_cast<int>(t / kp);
-  float g = 0.0f;
-  if (i < k) {
-    uint64_t sum = 0;
-    for (uint32_t m = 0; m < 3; ++m) {
-      const P4 w = philox10(P4{uint32_t(j), uint32_t(i), 2u, m}, uint32_t(seed), uint32_t(seed >> 32));
-      sum += uint64_t(w.x) + w.y + w.z + w.w;
-    }
-    const int64_t centred = static_cast<int64_t>(sum) - int64_t(6) * 4294967296LL;
-    g = __double2float_rn(ldexp(static_cast<double>(centred), -32));
-  }
-  G[t] = g;
+  G[t] = gauss_entry(seed, k, static_cast<int>(t / kp), static_cast<int>(t % kp));
 }
 
 // Thread per row; rows staged through shared memory 32 coordinates at a time
@@ -461,6 +463,216 @@ static size_t project_async_smem() {
   return size_t(2) * kProjThreads * RPT * (CH + 1) * 16 + size_t(2) * 32 * KP * 4;
 }
 
+// TMA-streamed projection (rows whose byte length is a multiple of 16, KP <= 16).
+// A persistent grid of one block per SM; every warp is its own pipeline over
+// 32-row tiles: lane 0 streams 128-byte slices of the tile's rows (one TMA box
+// of 32 rows x 128 bytes, 128-byte swizzle) through two stages, each lane owns
+// one row.  The Gaussian matrix is generated into shared memory by each block
+// (same entries as k_gauss) while the first slices are in flight.  Per row:
+// y_i = fmaf chain over j in increasing order, |x|^2 likewise, so the results
+// are those of k_project bit for bit.  The box of y is kept per lane in
+// registers and merged once per warp at the end.
+// warps per block: 20 for binary32 rows (96 registers a thread), 16 for the
+// narrower types, whose unpacking needs more registers
+template <int DT>
+constexpr int pt_max_warps() { return DT == CH_F32 ? 20 : 16; }
+constexpr int kPTBox = 128;            // bytes of a row per slice
+constexpr int kPTStage = 32 * kPTBox;  // one 32-row box
+
+template <int DT, int KP>
+__global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
+    k_project_tma(const __grid_constant__ CUtensorMap map, const void* X, const float* scales, int64_t n, int d,
+                  uint64_t seed, int k, float* Y, uint32_t* box, float* norms, uint32_t* status) {
+  constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
+  constexpr int PER = 16 / ES;          // coordinates per 16-byte chunk
+  constexpr int SLICE = kPTBox / ES;    // coordinates per slice
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* stage = base + size_t(warp) * 2 * kPTStage;
+  float* sG = reinterpret_cast<float*>(base + size_t(warps) * 2 * kPTStage);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sG + size_t(d) * KP) + 2 * warp;
+
+  const int64_t ntiles = (n + 31) >> 5;
+  const int slices = (d + SLICE - 1) / SLICE;
+  const int64_t gw = int64_t(blockIdx.x) * warps + warp, stride = int64_t(gridDim.x) * warps;
+  const int64_t my_tiles = gw < ntiles ? (ntiles - gw + stride - 1) / stride : 0;
+  const int64_t items = my_tiles * slices;
+
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  auto issue = [&](int64_t it) {  // lane 0: item it -> stage it & 1
+    const int64_t t = gw + (it / slices) * stride;
+    const int sl = static_cast<int>(it % slices);
+    uint64_t* b = &bar[it & 1];
+    mbar_expect_tx(b, kPTStage);
+    tma_load_2d(stage + (it & 1) * kPTStage, &map, sl * kPTBox, static_cast<int>(t * 32), b);
+  };
+  if (lane == 0) {
+    if (items > 0) issue(0);
+    if (items > 1) issue(1);
+  }
+  for (int t = threadIdx.x; t < d * KP; t += blockDim.x) sG[t] = gauss_entry(seed, k, t / KP, t % KP);
+  __syncthreads();
+
+  float lo[KP], hi[KP], acc[KP];
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    lo[i] = __int_as_float(0x7F800000);
+    hi[i] = __int_as_float(0xFF800000);
+    acc[i] = 0.0f;
+  }
+  float sq = 0.0f;
+  bool ok = true;
+  int64_t it = 0;
+  for (; it < items; ++it) {
+    const int64_t t = gw + (it / slices) * stride;
+    const int sl = static_cast<int>(it % slices);
+    const float scl = (DT == CH_FP8E4M3 && t * 32 + lane < n) ? scales[t * 32 + lane] : 1.0f;
+    ok = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(&bar[it & 1], static_cast<uint32_t>((it >> 1) & 1)));
+    if (!ok) break;
+    const uint4* row = reinterpret_cast<const uint4*>(stage + (it & 1) * kPTStage + lane * kPTBox);
+    const int j0 = sl * SLICE;
+    const int jn = min(SLICE, d - j0);
+    auto chunk = [&](int c, int lim) {
+      const uint4 raw = row[c ^ (lane & 7)];
+      float xv[PER];
+      if constexpr (DT == CH_F32) {
+        xv[0] = __uint_as_float(raw.x);
+        xv[1] = __uint_as_float(raw.y);
+        xv[2] = __uint_as_float(raw.z);
+        xv[3] = __uint_as_float(raw.w);
+      } else if constexpr (DT == CH_BF16) {
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          xv[2 * e] = __uint_as_float(w4[e] << 16);
+          xv[2 * e + 1] = __uint_as_float(w4[e] & 0xFFFF0000u);
+        }
+      } else {
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int e = 0; e < 16; ++e) xv[e] = __fmul_rn(e4m3_to_f32(static_cast<uint8_t>(w4[e / 4] >> (8 * (e % 4)))), scl);
+      }
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        if (e < lim) {
+          sq = fmaf(xv[e], xv[e], sq);
+          const float4* g4 = reinterpret_cast<const float4*>(sG + (j0 + c * PER + e) * KP);
+#pragma unroll
+          for (int i4 = 0; i4 < KP / 4; ++i4) {
+            const float4 gv = g4[i4];
+            acc[4 * i4 + 0] = __fmaf_rn(gv.x, xv[e], acc[4 * i4 + 0]);
+            acc[4 * i4 + 1] = __fmaf_rn(gv.y, xv[e], acc[4 * i4 + 1]);
+            acc[4 * i4 + 2] = __fmaf_rn(gv.z, xv[e], acc[4 * i4 + 2]);
+            acc[4 * i4 + 3] = __fmaf_rn(gv.w, xv[e], acc[4 * i4 + 3]);
+          }
+        }
+      }
+    };
+    if (jn == SLICE) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) chunk(c, PER);
+    } else {
+      for (int c = 0; c * PER < jn; ++c) chunk(c, min(PER, jn - c * PER));
+    }
+    __syncwarp();
+    if (lane == 0 && it + 2 < items) {
+      fence_proxy_async_smem();
+      issue(it + 2);
+    }
+    if (sl == slices - 1) {  // the tile's rows are complete
+      const int64_t r = t * 32 + lane;
+      if (r < n) {
+        if (KP == 16 && k == 16) {
+          float4* y4 = reinterpret_cast<float4*>(Y + r * 16);
+#pragma unroll
+          for (int i4 = 0; i4 < 4; ++i4)
+            y4[i4] = make_float4(acc[4 * i4], acc[4 * i4 + 1], acc[4 * i4 + 2], acc[4 * i4 + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < KP; ++i)
+            if (i < k) Y[r * k + i] = acc[i];
+        }
+        if (norms) norms[r] = sq;
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+          lo[i] = fminf(lo[i], acc[i]);
+          hi[i] = fmaxf(hi[i], acc[i]);
+        }
+        if (!isfinite(sq)) {  // a non-finite coordinate, or only an overflowing square: look again
+          bool bad = false;
+          for (int j = 0; j < d; ++j) bad |= !isfinite(load_elem<DT>(X, r, d, j, scales));
+          if (bad) atomicOr(status, ST_NONFINITE);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < KP; ++i) acc[i] = 0.0f;
+      sq = 0.0f;
+    }
+  }
+  if (!ok) {
+    if (lane == 0) atomicOr(status, ST_TIMEOUT);
+    // let the copies still in flight (items it and it + 1) land before the
+    // block's shared memory is released
+    for (int64_t j = it; j < items && j < it + 2; ++j)
+      mbar_wait_bounded(&bar[j & 1], static_cast<uint32_t>((j >> 1) & 1));
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    if (i < k) {
+      float l = lo[i], h = hi[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        l = fminf(l, __shfl_xor_sync(0xFFFFFFFFu, l, o));
+        h = fmaxf(h, __shfl_xor_sync(0xFFFFFFFFu, h, o));
+      }
+      if (lane == 0 && l <= h) {
+        atomicMin(&box[i], ord_enc(l));
+        atomicMax(&box[k + i], ord_enc(h));
+      }
+    }
+  }
+}
+
+template <int DT>
+static size_t project_tma_smem(int warps, int d, int kp) {
+  return 1024 + size_t(warps) * 2 * kPTStage + size_t(d) * kp * 4 + size_t(warps) * 16;
+}
+
+// the launch shape for the TMA projection, or 0 warps when it does not apply
+template <int DT>
+static int project_tma_warps(const ch_set* X, int kp) {
+  if (kp > 16) return 0;
+  if ((int64_t(X->d) * int64_t(elem_size(DT))) % 16 != 0 || (reinterpret_cast<uintptr_t>(X->data) & 15) != 0) return 0;
+  if (X->n >= (int64_t(1) << 31) - 32) return 0;
+  const size_t budget = 227 * 1024;
+  for (int w = pt_max_warps<DT>(); w >= 4; w -= 2)
+    if (project_tma_smem<DT>(w, X->d, kp) <= budget) return w;
+  return 0;
+}
+
+template <int DT>
+static CUtensorMap project_map(const ch_set* X) {
+  CUtensorMap m;
+  const cuuint64_t rb = static_cast<cuuint64_t>(X->d) * elem_size(DT);
+  cuuint64_t dims[2] = {rb, static_cast<cuuint64_t>(X->n)};
+  cuuint64_t strides[1] = {rb};
+  cuuint32_t boxd[2] = {static_cast<cuuint32_t>(kPTBox), 32u};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(X->data), dims, strides, boxd, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CHX_CHECK(r == CUDA_SUCCESS, CH_ECUDA, "cuTensorMapEncodeTiled failed (projection)");
+  return m;
+}
+
 template <int DT>
 static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y, uint32_t* box, float* norms,
                        cudaStream_t s) {
@@ -494,10 +706,41 @@ static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y,
 #undef CHX_PROJ
 }
 
+template <int DT, int KP>
+static void launch_project_tma(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, float* norms,
+                               int warps, int sm_count, cudaStream_t s) {
+  static const bool attr = [] {
+    CHX_CUDA(cudaFuncSetAttribute(k_project_tma<DT, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    return true;
+  }();
+  (void)attr;
+  const CUtensorMap map = project_map<DT>(X);
+  const int64_t ntiles = ceil_div(X->n, 32);
+  const int grid = static_cast<int>(std::min<int64_t>(sm_count, ceil_div(ntiles, warps)));
+  k_project_tma<DT, KP><<<grid, warps * 32, project_tma_smem<DT>(warps, X->d, KP), s>>>(
+      map, X->data, X->scales, X->n, X->d, seed, k, Y, box, norms, X->status);
+}
+
+template <int DT>
+static void project_any(const ch_set* X, uint64_t seed, int k, int kp, float* Y, uint32_t* box, float* norms,
+                        int sm_count, cudaStream_t s) {
+  const int warps = project_tma_warps<DT>(X, kp);
+  if (warps > 0) {
+    if (kp == 8) launch_project_tma<DT, 8>(X, seed, k, Y, box, norms, warps, sm_count, s);
+    else launch_project_tma<DT, 16>(X, seed, k, Y, box, norms, warps, sm_count, s);
+    return;
+  }
+  // the Gaussian matrix lives in the tail of Y's allocation
+  float* G = Y + ((X->n * k + 3) & ~int64_t(3));  // 16-byte aligned
+  const int64_t gn = int64_t(kp) * X->d;
+  k_gauss<<<static_cast<int>(ceil_div(gn, 256)), 256, 0, s>>>(seed, k, kp, X->d, G);
+  launch_check("gauss");
+  project_dt<DT>(X, G, k, kp, Y, box, norms, s);
+}
+
 void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, uint32_t* status, int sm_count,
                     cudaStream_t s) {
   (void)status;
-  (void)sm_count;
   const int kp = k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64;
   // the set's |x|^2 and finite check come for free with this pass
   ch_set* mut = const_cast<ch_set*>(X);
@@ -506,15 +749,10 @@ void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* b
   CHX_CUDA(cudaMemsetAsync(box, 0xFF, size_t(k) * 4, s));
   CHX_CUDA(cudaMemsetAsync(box + k, 0, size_t(k) * 4, s));
   if (X->n == 0) return;
-  // the Gaussian matrix lives in the tail of Y's allocation
-  float* G = Y + ((X->n * k + 3) & ~int64_t(3));  // 16-byte aligned
-  const int64_t gn = int64_t(kp) * X->d;
-  k_gauss<<<static_cast<int>(ceil_div(gn, 256)), 256, 0, s>>>(seed, k, kp, X->d, G);
-  launch_check("gauss");
   switch (X->dtype) {
-    case CH_F32: project_dt<CH_F32>(X, G, k, kp, Y, box, norms, s); break;
-    case CH_BF16: project_dt<CH_BF16>(X, G, k, kp, Y, box, norms, s); break;
-    default: project_dt<CH_FP8E4M3>(X, G, k, kp, Y, box, norms, s); break;
+    case CH_F32: project_any<CH_F32>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
+    case CH_BF16: project_any<CH_BF16>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
+    default: project_any<CH_FP8E4M3>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
   }
   launch_check("project");
 }

@@ -88,6 +88,55 @@ def test_keys_bit_exact(ctx, pair_factory, metric, n, d):
         assert np.array_equal(got, want)
 
 
+def _typed_set(ctx, X32, dtype, keep):
+    """A set of X32 stored as dtype; returns (set, dequantised binary32 values)."""
+    if dtype == ch.CH_F32:
+        t = dev(X32)
+        keep.append(t)
+        return ch.ch_set_create(ctx, t, 2, X32.shape[0], X32.shape[1]), X32
+    if dtype == ch.CH_BF16:
+        h = workloads.to_bf16_bits(X32)
+        t = dev(h)
+        keep.append(t)
+        return ch.ch_set_create(ctx, t, 2, X32.shape[0], X32.shape[1], dtype), workloads.bf16_bits_to_f32(h)
+    c, sc = workloads.to_fp8_e4m3(X32)
+    t, tsc = dev(c), dev(sc)
+    keep += [t, tsc]
+    return ch.ch_set_create(ctx, t, 1, X32.shape[0], X32.shape[1], dtype, tsc), workloads.fp8_dequant(c, sc)
+
+
+@pytest.mark.parametrize("dtype", [ch.CH_F32, ch.CH_BF16, ch.CH_FP8E4M3], ids=["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("n,d", [(1000, 16), (4097, 128), (333, 384), (70, 40), (129, 24), (2500, 200)])
+def test_projection_keys_all_types(ctx, dtype, n, d):
+    """l2 keys (projection, |x|^2 pass, scales, fingerprints) for every storage
+    type against the oracle on the dequantised values: row lengths that are and
+    are not multiples of 16 bytes and of one 128-byte slice, ragged tiles."""
+    keep = []
+    A32, B32 = workloads.gaussian_mixture(n, 300, d, n + d, clusters=5)
+    sA, Ad = _typed_set(ctx, A32, dtype, keep)
+    sB, Bd = _typed_set(ctx, B32, dtype, keep)
+    for L, k, seed in ((10, 16, 3), (6, 8, 4), (4, 12, 5)):
+        hp = ch.hash_params(L2, L, k, None, seed)
+        Y = oracle.hashed(Ad, L2, seed, k)
+        YB = oracle.hashed(Bd, L2, seed, k)
+        assert ch.ch_top_exp(ctx, sA, sB, hp) == oracle.top_exp(Y, YB)
+        keys = torch.zeros((L, n), dtype=torch.int64, device="cuda")
+        ch.ch_hash_keys(ctx, sA, hp, -3, keys)
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), oracle.keys(Y, -3, L, seed))
+    ch.ch_set_destroy(sA)
+    ch.ch_set_destroy(sB)
+
+
+def test_projection_many_tiles(ctx, pair_factory):
+    """More 32-row tiles than resident warps (each warp streams several tiles)."""
+    A, B = workloads.gaussian_mixture(131_101, 20_000, 64, 9, clusters=40)
+    p = pair_factory(A, B)
+    bidx, D, lv = gpu_crude(ctx, p, L2, 6)
+    r = oracle.crude_nn(A, B, L2, hash_seed=6)
+    assert np.array_equal(bidx, r["bidx"]) and np.array_equal(lv, r["level"])
+    assert np.array_equal(D.view(np.uint32), r["D"].view(np.uint32))
+
+
 @pytest.mark.parametrize("metric", [L1, L2])
 def test_top_exp_matches(ctx, pair_factory, metric):
     for seed, scale in ((1, 1.0), (2, 1e-3), (3, 300.0)):
