@@ -171,7 +171,10 @@ __device__ inline float gauss_entry(uint64_t seed, int k, int j, int i) {
     sum += uint64_t(w.x) + w.y + w.z + w.w;
   }
   const int64_t centred = static_cast<int64_t>(sum) - int64_t(6) * 4294967296LL;
-  return __double2float_rn(ldexp(static_cast<double>(centred), -32));
+  // one round-to-nearest of the integer to binary32, then an exact scaling by
+  // 2^-32 (|centred| >= 1 keeps it normal): the single rounding of
+  // centred * 2^-32, without binary64 arithmetic
+  return __ll2float_rn(centred) * 0x1p-32f;
 }
 
 __global__ void k_gauss(uint64_t seed, int k, int kp, int d, float* G /* [d][kp], zero rows i >= k */) {
@@ -506,12 +509,18 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
     mbar_init_fence();
   }
   __syncwarp();
+  // item it = (tile gw + (it / slices) * stride, slice it % slices); the
+  // producer (lane 0) runs two items ahead of the consumers
+  int64_t pt = gw;  // producer's next tile and slice
+  int psl = 0;
   auto issue = [&](int64_t it) {  // lane 0: item it -> stage it & 1
-    const int64_t t = gw + (it / slices) * stride;
-    const int sl = static_cast<int>(it % slices);
     uint64_t* b = &bar[it & 1];
     mbar_expect_tx(b, kPTStage);
-    tma_load_2d(stage + (it & 1) * kPTStage, &map, sl * kPTBox, static_cast<int>(t * 32), b);
+    tma_load_2d(stage + (it & 1) * kPTStage, &map, psl * kPTBox, static_cast<int>(pt * 32), b);
+    if (++psl == slices) {
+      psl = 0;
+      pt += stride;
+    }
   };
   if (lane == 0) {
     if (items > 0) issue(0);
@@ -530,9 +539,9 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
   float sq = 0.0f;
   bool ok = true;
   int64_t it = 0;
+  int64_t t = gw;  // consumer's tile and slice
+  int sl = 0;
   for (; it < items; ++it) {
-    const int64_t t = gw + (it / slices) * stride;
-    const int sl = static_cast<int>(it % slices);
     const float scl = (DT == CH_FP8E4M3 && t * 32 + lane < n) ? scales[t * 32 + lane] : 1.0f;
     ok = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(&bar[it & 1], static_cast<uint32_t>((it >> 1) & 1)));
     if (!ok) break;
@@ -614,6 +623,10 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
 #pragma unroll
       for (int i = 0; i < KP; ++i) acc[i] = 0.0f;
       sq = 0.0f;
+    }
+    if (++sl == slices) {
+      sl = 0;
+      t += stride;
     }
   }
   if (!ok) {
