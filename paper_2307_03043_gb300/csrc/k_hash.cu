@@ -490,7 +490,9 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
   constexpr int PER = 16 / ES;          // coordinates per 16-byte chunk
   constexpr int SLICE = kPTBox / ES;    // coordinates per slice
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned by an offset from the shared array itself, so that the
+  // compiler keeps every access below in the shared state space
+  unsigned char* base = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int warps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* stage = base + size_t(warp) * 2 * kPTStage;

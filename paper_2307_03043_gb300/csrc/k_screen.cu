@@ -138,7 +138,9 @@ template <int SCREEN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_screen(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmB, ScreenArgs args) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned by an offset from the shared array itself, so that the
+  // compiler keeps every access below in the shared state space
+  uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int KB = args.kblocks;
   const int S = args.stages;
   uint8_t* q_smem = smem;                                 // KB x (128 rows x 128 B)
