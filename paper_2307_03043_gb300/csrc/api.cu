@@ -136,9 +136,10 @@ static void check_pair(ch_ctx* c, const ch_set* A, const ch_set* B) {
 // hashed space of a set under hp: the set's own rows (l1) or its l2 embedding
 struct Hashed {
   HashSrc src;
-  const uint32_t* box;
+  const uint32_t* box;  // [box_parts][2][dd] partial boxes of the hashed space
+  int box_parts;
   float* Y;        // l2 embedding (+ Gaussian matrix tail) in the workspace
-  uint32_t* boxY;  // l2 box in the workspace
+  uint32_t* boxY;  // l2 partial boxes in the workspace
 };
 
 static int proj_pad(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64; }
@@ -148,14 +149,16 @@ static void take_hashed(L& lay, const ch_set* X, const ch_hash_params* hp, Hashe
   if (hp->metric == CH_L1) {
     h->src = HashSrc{X->data, X->dtype, X->n, X->d, X->scales};
     h->box = X->box_x;
+    h->box_parts = 1;
     h->Y = nullptr;
     h->boxY = nullptr;
   } else {
     const int k = static_cast<int>(hp->proj_dim);
     h->Y = lay.template take<float>(size_t(X->n) * k + 4 + size_t(proj_pad(k)) * X->d);
-    h->boxY = lay.template take<uint32_t>(size_t(2) * k);
+    h->boxY = lay.template take<uint32_t>(size_t(2) * k * kMaxBoxParts);
     h->src = HashSrc{h->Y, CH_F32, X->n, k, nullptr};
     h->box = h->boxY;
+    h->box_parts = 1;  // set by the projection
   }
 }
 
@@ -163,7 +166,8 @@ static void take_hashed(L& lay, const ch_set* X, const ch_hash_params* hp, Hashe
 // |x|^2 and the finite check) or, for l1, the ingest pass (box of x)
 static void run_hashed(ch_ctx* c, const ch_set* X, const ch_hash_params* hp, Hashed* h, uint32_t* status) {
   if (hp->metric == CH_L2)
-    launch_project(X, hp->hash_seed, static_cast<int>(hp->proj_dim), h->Y, h->boxY, status, c->sm_count, c->stream);
+    h->box_parts = launch_project(X, hp->hash_seed, static_cast<int>(hp->proj_dim), h->Y, h->boxY, status,
+                                  c->sm_count, c->stream);
   else
     ensure_ingest(const_cast<ch_set*>(X), c->stream);
 }
@@ -230,18 +234,19 @@ static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_p
 // CrudeNN (Fig. 2): embedding, scales, per-scale bucket tables of B, probes of A,
 // then D_a = d(a, b(a)).
 static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash_params* hp, CrudeBufs* cb,
-                      int64_t* bidx, uint8_t* level, float* D, uint32_t* status) {
+                      int64_t* bidx, uint8_t* level, float* D, uint32_t* status, uint32_t* maxD = nullptr) {
   const int L = static_cast<int>(hp->levels);
   const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
   cudaStream_t s = c->stream;
   run_hashed(c, A, hp, &cb->hA, status);
   run_hashed(c, B, hp, &cb->hB, status);
-  launch_scale_tables(cb->hA.box, cb->hB.box, dd, L, hp->top_exp, hp->hash_seed, cb->tab, cb->e_top, status, s);
+  launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp, hp->hash_seed,
+                      cb->tab, cb->e_top, status, s);
   if (hp->group == CH_GROUP_SORT) {
     launch_keys_write(cb->hB.src, L, cb->tab, cb->keysB, s);
     launch_keys_write(cb->hA.src, L, cb->tab, cb->keysA, s);
     launch_sort_group(cb->keysA, A->n, cb->keysB, B->n, L, cb->sort_work, bidx, level, s);
-    launch_crude_dist(A, B, hp->metric, bidx, D, s);
+    launch_crude_dist(A, B, hp->metric, bidx, D, maxD, c->sm_count, s);
     return;
   }
   const size_t cap = size_t(1) << cb->plan.log_cap;
@@ -252,7 +257,7 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
     launch_group_insert(cb->hB.src, L, L0, nl, cb->tab, h, status, s);
     launch_group_probe(cb->hA.src, L, L0, nl, cb->tab, h, bidx, level, s);
   }
-  launch_crude_dist(A, B, hp->metric, bidx, D, s);
+  launch_crude_dist(A, B, hp->metric, bidx, D, maxD, c->sm_count, s);
 }
 
 struct SampleBufs {
@@ -580,7 +585,8 @@ ch_status ch_top_exp(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash_
   CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
   run_hashed(c, A, hp, &hA, &res->status);
   run_hashed(c, B, hp, &hB, &res->status);
-  launch_scale_tables(hA.box, hB.box, dd, static_cast<int>(hp->levels), hp->top_exp, hp->hash_seed, tab, et,
+  launch_scale_tables(hA.box, hA.box_parts, hB.box, hB.box_parts, dd, static_cast<int>(hp->levels), hp->top_exp,
+                      hp->hash_seed, tab, et,
                       &res->status, s);
   k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, nullptr, nullptr, nullptr, et);
   launch_check("collect");
@@ -611,7 +617,8 @@ ch_status ch_hash_keys(ch_ctx* c, const ch_set* X, const ch_hash_params* hp, int
   cudaStream_t s = c->stream;
   CHX_CUDA(cudaMemsetAsync(st, 0, 4, s));
   run_hashed(c, X, hp, &h, st);
-  launch_scale_tables(h.box, h.box, dd, L, e_lo + L - 1, hp->hash_seed, tab, nullptr, st, s);
+  launch_scale_tables(h.box, h.box_parts, h.box, h.box_parts, dd, L, e_lo + L - 1, hp->hash_seed, tab, nullptr, st,
+                      s);
   launch_keys_write(h.src, L, tab, keys, s);
   return CH_OK;
   CHX_GUARD_END
@@ -737,9 +744,9 @@ ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_
   cudaStream_t s = c->stream;
   if (rep) CHX_CUDA(cudaEventRecord(c->ev[0], s));
   CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
-  run_crude(c, A, B, &p->hash, &cb, bidx, level, D, &res->status);
+  run_crude(c, A, B, &p->hash, &cb, bidx, level, D, &res->status, sb.sw.maxD);
   if (rep) CHX_CUDA(cudaEventRecord(c->ev[1], s));
-  launch_weights(D, nA, w, sb.prefix, sb.sw, s);
+  launch_weights(D, nA, w, sb.prefix, sb.sw, s, true);
   launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, idx, s);
   if (rep) CHX_CUDA(cudaEventRecord(c->ev[2], s));
   KernelTimer kt;

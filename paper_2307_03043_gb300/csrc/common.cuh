@@ -232,9 +232,12 @@ size_t elem_size(int dtype);
 // ingest: finite check, |x|^2, bounding box of x (ordered-encoded, [2][d])
 void launch_ingest(const ch_set* X, cudaStream_t s);
 
-// l2 embedding of X with G = Irwin-Hall Gaussian (k x d): Y [n][k], box [2][k]
-void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, uint32_t* status,
-                    int sm_count, cudaStream_t s);
+// l2 embedding of X with G = Irwin-Hall Gaussian (k x d): Y [n][k] and the box
+// of Y as P partial boxes [P][2][k] (ordered-encoded; P <= kMaxBoxParts), whose
+// elementwise min / max is the box.  Returns P.
+constexpr int kMaxBoxParts = 256;
+int launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, uint32_t* status,
+                   int sm_count, cudaStream_t s);
 
 // Tables of one CrudeNN call (device): scales, shifts, multipliers
 struct ScaleTables {
@@ -245,9 +248,11 @@ struct ScaleTables {
   uint64_t* mult;        // [dd] odd multipliers
 };
 
-// computes e_top from the two boxes (or uses top_exp) then fills the tables
-void launch_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int dd, int L, int top_exp_in,
-                         uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status, cudaStream_t s);
+// computes e_top from the two boxes, each given as partial boxes [parts][2][dd]
+// (or uses top_exp), then fills the tables
+void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
+                         int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
+                         cudaStream_t s);
 
 // hashed-space source of a set: DT-typed rows (l1) or the binary32 embedding (l2)
 struct HashSrc {
@@ -276,9 +281,9 @@ bool sort_group_supported(int64_t nA, int64_t nB, int L);
 void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L,
                        void* work, int64_t* bidx, uint8_t* level, cudaStream_t s);
 
-// D_a = canonical d(a, B[b(a)])
-void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D,
-                       cudaStream_t s);
+// D_a = canonical d(a, B[b(a)]); with maxD non-null also max_a D_a (ordered-encoded)
+void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, uint32_t* maxD,
+                       int sm_count, cudaStream_t s);
 
 // sampling
 struct SampleWork {
@@ -288,7 +293,9 @@ struct SampleWork {
   int32_t* S;            // [1]
 };
 size_t sample_blocks(int64_t nA);
-void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s);
+// weights and their prefix; max_ready: *sw.maxD already holds max_a D_a
+void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s,
+                    bool max_ready = false);
 void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed,
                   int64_t* idx, cudaStream_t s);
 

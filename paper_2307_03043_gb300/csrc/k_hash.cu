@@ -528,6 +528,8 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
     if (items > 0) issue(0);
     if (items > 1) issue(1);
   }
+  __shared__ uint32_t s_box[2 * KP];  // the block's box of y, ordered-encoded
+  if (threadIdx.x < 2 * KP) s_box[threadIdx.x] = threadIdx.x < KP ? 0xFFFFFFFFu : 0u;
   for (int t = threadIdx.x; t < d * KP; t += blockDim.x) sG[t] = gauss_entry(seed, k, t / KP, t % KP);
   __syncthreads();
 
@@ -637,22 +639,27 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
     // block's shared memory is released
     for (int64_t j = it; j < items && j < it + 2; ++j)
       mbar_wait_bounded(&bar[j & 1], static_cast<uint32_t>((j >> 1) & 1));
-    return;
   }
+  // box of y: lanes -> warp (shuffles) -> block (shared atomics) -> one partial
+  // box per block, written whole (no global atomics; the scale-table kernel
+  // takes the min / max over the blocks' partial boxes)
 #pragma unroll
   for (int i = 0; i < KP; ++i) {
-    if (i < k) {
-      float l = lo[i], h = hi[i];
+    float l = lo[i], h = hi[i];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        l = fminf(l, __shfl_xor_sync(0xFFFFFFFFu, l, o));
-        h = fmaxf(h, __shfl_xor_sync(0xFFFFFFFFu, h, o));
-      }
-      if (lane == 0 && l <= h) {
-        atomicMin(&box[i], ord_enc(l));
-        atomicMax(&box[k + i], ord_enc(h));
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      l = fminf(l, __shfl_xor_sync(0xFFFFFFFFu, l, o));
+      h = fmaxf(h, __shfl_xor_sync(0xFFFFFFFFu, h, o));
     }
+    if (lane == 0 && i < k && l <= h) {
+      atomicMin(&s_box[i], ord_enc(l));
+      atomicMax(&s_box[KP + i], ord_enc(h));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * k) {
+    const int i = threadIdx.x < k ? threadIdx.x : KP + threadIdx.x - k;
+    box[size_t(blockIdx.x) * 2 * k + threadIdx.x] = s_box[i];
   }
 }
 
@@ -667,7 +674,7 @@ static int project_tma_warps(const ch_set* X, int kp) {
   if (kp > 16) return 0;
   if ((int64_t(X->d) * int64_t(elem_size(DT))) % 16 != 0 || (reinterpret_cast<uintptr_t>(X->data) & 15) != 0) return 0;
   if (X->n >= (int64_t(1) << 31) - 32) return 0;
-  const size_t budget = 227 * 1024;
+  const size_t budget = 226 * 1024;  // leaves room for the kernel's static shared memory
   for (int w = pt_max_warps<DT>(); w >= 4; w -= 2)
     if (project_tma_smem<DT>(w, X->d, kp) <= budget) return w;
   return 0;
@@ -722,54 +729,62 @@ static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y,
 }
 
 template <int DT, int KP>
-static void launch_project_tma(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, float* norms,
-                               int warps, int sm_count, cudaStream_t s) {
+static int launch_project_tma(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, float* norms,
+                              int warps, int sm_count, cudaStream_t s) {
   static const bool attr = [] {
-    CHX_CUDA(cudaFuncSetAttribute(k_project_tma<DT, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    CHX_CUDA(cudaFuncSetAttribute(k_project_tma<DT, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
     return true;
   }();
   (void)attr;
   const CUtensorMap map = project_map<DT>(X);
   const int64_t ntiles = ceil_div(X->n, 32);
-  const int grid = static_cast<int>(std::min<int64_t>(sm_count, ceil_div(ntiles, warps)));
+  const int grid = static_cast<int>(std::min<int64_t>(std::min(sm_count, kMaxBoxParts), ceil_div(ntiles, warps)));
   k_project_tma<DT, KP><<<grid, warps * 32, project_tma_smem<DT>(warps, X->d, KP), s>>>(
       map, X->data, X->scales, X->n, X->d, seed, k, Y, box, norms, X->status);
+  return grid;
 }
 
 template <int DT>
-static void project_any(const ch_set* X, uint64_t seed, int k, int kp, float* Y, uint32_t* box, float* norms,
-                        int sm_count, cudaStream_t s) {
+static int project_any(const ch_set* X, uint64_t seed, int k, int kp, float* Y, uint32_t* box, float* norms,
+                       int sm_count, cudaStream_t s) {
   const int warps = project_tma_warps<DT>(X, kp);
   if (warps > 0) {
-    if (kp == 8) launch_project_tma<DT, 8>(X, seed, k, Y, box, norms, warps, sm_count, s);
-    else launch_project_tma<DT, 16>(X, seed, k, Y, box, norms, warps, sm_count, s);
-    return;
+    if (kp == 8) return launch_project_tma<DT, 8>(X, seed, k, Y, box, norms, warps, sm_count, s);
+    return launch_project_tma<DT, 16>(X, seed, k, Y, box, norms, warps, sm_count, s);
   }
+  // the other kernels merge into one box with global atomics
+  CHX_CUDA(cudaMemsetAsync(box, 0xFF, size_t(k) * 4, s));
+  CHX_CUDA(cudaMemsetAsync(box + k, 0, size_t(k) * 4, s));
   // the Gaussian matrix lives in the tail of Y's allocation
   float* G = Y + ((X->n * k + 3) & ~int64_t(3));  // 16-byte aligned
   const int64_t gn = int64_t(kp) * X->d;
   k_gauss<<<static_cast<int>(ceil_div(gn, 256)), 256, 0, s>>>(seed, k, kp, X->d, G);
   launch_check("gauss");
   project_dt<DT>(X, G, k, kp, Y, box, norms, s);
+  return 1;
 }
 
-void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, uint32_t* status, int sm_count,
-                    cudaStream_t s) {
+int launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, uint32_t* status, int sm_count,
+                   cudaStream_t s) {
   (void)status;
   const int kp = k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64;
   // the set's |x|^2 and finite check come for free with this pass
   ch_set* mut = const_cast<ch_set*>(X);
   float* norms = (X->ready & READY_NORMS) ? nullptr : X->norms;
   mut->ready |= READY_NORMS;
-  CHX_CUDA(cudaMemsetAsync(box, 0xFF, size_t(k) * 4, s));
-  CHX_CUDA(cudaMemsetAsync(box + k, 0, size_t(k) * 4, s));
-  if (X->n == 0) return;
+  if (X->n == 0) {  // an empty box
+    CHX_CUDA(cudaMemsetAsync(box, 0xFF, size_t(k) * 4, s));
+    CHX_CUDA(cudaMemsetAsync(box + k, 0, size_t(k) * 4, s));
+    return 1;
+  }
+  int parts;
   switch (X->dtype) {
-    case CH_F32: project_any<CH_F32>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
-    case CH_BF16: project_any<CH_BF16>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
-    default: project_any<CH_FP8E4M3>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
+    case CH_F32: parts = project_any<CH_F32>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
+    case CH_BF16: parts = project_any<CH_BF16>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
+    default: parts = project_any<CH_FP8E4M3>(X, seed, k, kp, Y, box, norms, sm_count, s); break;
   }
   launch_check("project");
+  return parts;
 }
 
 // ------------------------------------------------------------------ scales
@@ -777,9 +792,27 @@ void launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* b
 // e_top = ceil(log2 Delta) + 1 (0 if Delta = 0); scales 2^e, e = e_top-L+1..e_top.
 // Shift z_{e,j} = (w0 >> 8) 2^(e-24), w0 = Philox(j, e, 1, 0).x; multiplier
 // K_j = Philox(j, 0, 4, 0).(y:x) | 1; salt_e = mix64((uint32)e ^ seed).
-__global__ void k_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int dd, int L, int top_exp_in,
-                               uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status) {
+__global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
+                               int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status) {
   __shared__ int s_elo;
+  __shared__ uint32_t s_box[2 * kMaxProj];  // merged partial boxes (partial boxes only come with dd <= kMaxProj)
+  const bool merge = partsA > 1 || partsB > 1;
+  if (merge && top_exp_in == CH_TOP_EXP_AUTO) {
+    for (int c = threadIdx.x; c < 2 * dd; c += blockDim.x) {
+      const bool is_lo = c < dd;
+      uint32_t v = is_lo ? 0xFFFFFFFFu : 0u;
+      for (int p = 0; p < partsA; ++p) {
+        const uint32_t u = boxA[size_t(p) * 2 * dd + c];
+        v = is_lo ? min(v, u) : max(v, u);
+      }
+      for (int p = 0; p < partsB; ++p) {
+        const uint32_t u = boxB[size_t(p) * 2 * dd + c];
+        v = is_lo ? min(v, u) : max(v, u);
+      }
+      s_box[c] = v;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int e_top;
     if (top_exp_in != CH_TOP_EXP_AUTO) {
@@ -787,8 +820,8 @@ __global__ void k_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int d
     } else {
       double delta = 0.0;
       for (int j = 0; j < dd; ++j) {
-        const uint32_t lo = min(boxA[j], boxB[j]);
-        const uint32_t hi = max(boxA[dd + j], boxB[dd + j]);
+        const uint32_t lo = merge ? s_box[j] : min(boxA[j], boxB[j]);
+        const uint32_t hi = merge ? s_box[dd + j] : max(boxA[dd + j], boxB[dd + j]);
         delta += static_cast<double>(ord_dec(hi)) - static_cast<double>(ord_dec(lo));
       }
       if (delta == 0.0) {
@@ -828,70 +861,99 @@ __global__ void k_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int d
   }
 }
 
-void launch_scale_tables(const uint32_t* boxA, const uint32_t* boxB, int dd, int L, int top_exp_in, uint64_t seed,
-                         ScaleTables t, int32_t* e_top_out, uint32_t* status, cudaStream_t s) {
-  k_scale_tables<<<1, 256, 0, s>>>(boxA, boxB, dd, L, top_exp_in, seed, t, e_top_out, status);
+void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
+                         int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
+                         cudaStream_t s) {
+  CHX_CHECK((partsA <= 1 && partsB <= 1) || dd <= kMaxProj, CH_EINVAL, "partial boxes need dd <= 64");
+  k_scale_tables<<<1, 256, 0, s>>>(boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out, status);
   launch_check("scale_tables");
 }
 
 // ------------------------------------------------------------------ crude distance
 // D_a = canonical d(a, B[b(a)]): G lanes per a (G = min(32, next pow2 of d)),
 // lane q sums coordinates j = q, q+32, ... in increasing j; then p_q += p_{q+s}
-// for s = G/2 .. 1 via shuffles (steps s >= G would add +0).
+// for s = G/2 .. 1 via shuffles (steps s >= G would add +0).  Grid-stride; with
+// maxD set, each block also folds max_a D_a into *maxD (ordered-encoded) with a
+// single atomic, which saves the sampler its own pass over D.
 template <int DTA, int DTB, int METRIC>
 __global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* scA, int64_t nA, const void* B,
                                                     const float* scB, int d, int G, const int64_t* bidx,
-                                                    float* D) {
-  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t a = gt / G;
-  const int q = static_cast<int>(gt % G);
-  const bool live = a < nA;
-  float p = 0.0f;
-  if (live) {
-    const int64_t b = bidx[a];
-    for (int j = q; j < d; j += 32) {
-      const float t = __fsub_rn(load_elem<DTA>(A, a, d, j, scA), load_elem<DTB>(B, b, d, j, scB));
-      if (METRIC == CH_L1)
-        p = __fadd_rn(p, fabsf(t));
-      else
-        p = __fmaf_rn(t, t, p);
+                                                    float* D, uint32_t* maxD) {
+  __shared__ uint32_t s_max[8];
+  uint32_t mx = 0;
+  const int64_t total = nA * G;
+  const int64_t step = int64_t(gridDim.x) * blockDim.x;
+  // every lane runs the same number of rounds (the shuffles need the whole warp)
+  for (int64_t g0 = int64_t(blockIdx.x) * blockDim.x; g0 < total; g0 += step) {
+    const int64_t gt = g0 + threadIdx.x;
+    const int64_t a = gt / G;
+    const int q = static_cast<int>(gt % G);
+    const bool live = gt < total;
+    float p = 0.0f;
+    if (live) {
+      const int64_t b = bidx[a];
+      for (int j = q; j < d; j += 32) {
+        const float t = __fsub_rn(load_elem<DTA>(A, a, d, j, scA), load_elem<DTB>(B, b, d, j, scB));
+        if (METRIC == CH_L1)
+          p = __fadd_rn(p, fabsf(t));
+        else
+          p = __fmaf_rn(t, t, p);
+      }
+    }
+    for (int sh = G >> 1; sh >= 1; sh >>= 1) {
+      const float o = __shfl_down_sync(0xFFFFFFFFu, p, sh, G);
+      p = __fadd_rn(p, o);
+    }
+    if (live && q == 0) {
+      const float v = (METRIC == CH_L1) ? p : __fsqrt_rn(p);
+      D[a] = v;
+      mx = max(mx, ord_enc(v));
     }
   }
-  for (int s = G >> 1; s >= 1; s >>= 1) {
-    const float o = __shfl_down_sync(0xFFFFFFFFu, p, s, G);
-    p = __fadd_rn(p, o);
+  if (!maxD) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) mx = max(mx, s_max[w]);
+    if (mx) atomicMax(maxD, mx);
   }
-  if (live && q == 0) D[a] = (METRIC == CH_L1) ? p : __fsqrt_rn(p);
 }
 
 template <int DTA, int DTB>
-static void crude_dist_2(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, int G,
-                         int grid, cudaStream_t s) {
+static void crude_dist_2(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D,
+                         uint32_t* maxD, int G, int grid, cudaStream_t s) {
   if (metric == CH_L1)
-    k_crude_dist<DTA, DTB, CH_L1><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D);
+    k_crude_dist<DTA, DTB, CH_L1><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D,
+                                                        maxD);
   else
-    k_crude_dist<DTA, DTB, CH_L2><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D);
+    k_crude_dist<DTA, DTB, CH_L2><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D,
+                                                        maxD);
 }
 
 template <int DTA>
-static void crude_dist_1(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, int G,
-                         int grid, cudaStream_t s) {
+static void crude_dist_1(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, uint32_t* maxD,
+                         int G, int grid, cudaStream_t s) {
   switch (B->dtype) {
-    case CH_F32: crude_dist_2<DTA, CH_F32>(A, B, metric, bidx, D, G, grid, s); break;
-    case CH_BF16: crude_dist_2<DTA, CH_BF16>(A, B, metric, bidx, D, G, grid, s); break;
-    default: crude_dist_2<DTA, CH_FP8E4M3>(A, B, metric, bidx, D, G, grid, s); break;
+    case CH_F32: crude_dist_2<DTA, CH_F32>(A, B, metric, bidx, D, maxD, G, grid, s); break;
+    case CH_BF16: crude_dist_2<DTA, CH_BF16>(A, B, metric, bidx, D, maxD, G, grid, s); break;
+    default: crude_dist_2<DTA, CH_FP8E4M3>(A, B, metric, bidx, D, maxD, G, grid, s); break;
   }
 }
 
-void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, cudaStream_t s) {
+void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, uint32_t* maxD,
+                       int sm_count, cudaStream_t s) {
+  if (maxD) CHX_CUDA(cudaMemsetAsync(maxD, 0, sizeof(uint32_t), s));
   if (A->n == 0) return;
   int G = 1;
   while (G < A->d && G < 32) G <<= 1;
-  const int grid = static_cast<int>(ceil_div(A->n * G, 256));
+  // 8 resident blocks of 256 per SM; each block merges its maximum once
+  const int grid = static_cast<int>(std::min<int64_t>(ceil_div(A->n * G, 256), int64_t(sm_count) * 8));
   switch (A->dtype) {
-    case CH_F32: crude_dist_1<CH_F32>(A, B, metric, bidx, D, G, grid, s); break;
-    case CH_BF16: crude_dist_1<CH_BF16>(A, B, metric, bidx, D, G, grid, s); break;
-    default: crude_dist_1<CH_FP8E4M3>(A, B, metric, bidx, D, G, grid, s); break;
+    case CH_F32: crude_dist_1<CH_F32>(A, B, metric, bidx, D, maxD, G, grid, s); break;
+    case CH_BF16: crude_dist_1<CH_BF16>(A, B, metric, bidx, D, maxD, G, grid, s); break;
+    default: crude_dist_1<CH_FP8E4M3>(A, B, metric, bidx, D, maxD, G, grid, s); break;
   }
   launch_check("crude_dist");
 }

@@ -113,16 +113,19 @@ __global__ void k_add_offsets(uint64_t* prefix, int64_t nA, const uint64_t* bloc
   if (a < nA) prefix[a] += blockoff[a / kScanTile];
 }
 
-void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s) {
-  CHX_CUDA(cudaMemsetAsync(sw.maxD, 0, sizeof(uint32_t), s));
+void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s,
+                    bool max_ready) {
   if (nA == 0) {
     CHX_CUDA(cudaMemsetAsync(sw.W, 0, sizeof(uint64_t), s));
     CHX_CUDA(cudaMemsetAsync(sw.S, 0, sizeof(int32_t), s));
     return;
   }
-  const int gmax = static_cast<int>(std::min<int64_t>(ceil_div(nA, 256), 152 * 4));
-  k_max_d<<<gmax, 256, 0, s>>>(D, nA, sw.maxD);
-  launch_check("max_d");
+  if (!max_ready) {
+    CHX_CUDA(cudaMemsetAsync(sw.maxD, 0, sizeof(uint32_t), s));
+    const int gmax = static_cast<int>(std::min<int64_t>(ceil_div(nA, 256), 152 * 4));
+    k_max_d<<<gmax, 256, 0, s>>>(D, nA, sw.maxD);
+    launch_check("max_d");
+  }
   const int64_t nb = static_cast<int64_t>(sample_blocks(nA));
   k_weights<<<static_cast<int>(nb), kScanThreads, 0, s>>>(D, nA, sw.maxD, w, prefix, sw.blocksum, sw.S);
   launch_check("weights");
