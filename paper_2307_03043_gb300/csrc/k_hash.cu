@@ -798,18 +798,15 @@ __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t*
   __shared__ uint32_t s_box[2 * kMaxProj];  // merged partial boxes (partial boxes only come with dd <= kMaxProj)
   const bool merge = partsA > 1 || partsB > 1;
   if (merge && top_exp_in == CH_TOP_EXP_AUTO) {
-    for (int c = threadIdx.x; c < 2 * dd; c += blockDim.x) {
-      const bool is_lo = c < dd;
-      uint32_t v = is_lo ? 0xFFFFFFFFu : 0u;
-      for (int p = 0; p < partsA; ++p) {
-        const uint32_t u = boxA[size_t(p) * 2 * dd + c];
-        v = is_lo ? min(v, u) : max(v, u);
-      }
-      for (int p = 0; p < partsB; ++p) {
-        const uint32_t u = boxB[size_t(p) * 2 * dd + c];
-        v = is_lo ? min(v, u) : max(v, u);
-      }
-      s_box[c] = v;
+    for (int c = threadIdx.x; c < 2 * dd; c += blockDim.x) s_box[c] = c < dd ? 0xFFFFFFFFu : 0u;
+    __syncthreads();
+    // all threads over all (part, coordinate) entries: independent loads, shared atomics
+    const int na = partsA * 2 * dd, nb = partsB * 2 * dd;
+    for (int e = threadIdx.x; e < na + nb; e += blockDim.x) {
+      const uint32_t u = e < na ? boxA[e] : boxB[e - na];
+      const int c = (e < na ? e : e - na) % (2 * dd);
+      if (c < dd) atomicMin(&s_box[c], u);
+      else atomicMax(&s_box[c], u);
     }
   }
   __syncthreads();

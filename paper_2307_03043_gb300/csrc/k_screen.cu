@@ -28,9 +28,12 @@ namespace {
 constexpr int kBM = 128;          // samples per tile (TMEM lanes)
 constexpr int kBN = 256;          // B points per tile (accumulator columns)
 constexpr int kKB = 128;          // bytes of K per stage (one 128B swizzle row)
-constexpr int kThreads = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpiWarps = 16;     // epilogue warps: 4 per TMEM lane quadrant
+constexpr int kSlices = kEpiWarps / 4;     // column slices of an accumulator tile
+constexpr int kSliceCols = kBN / kSlices;  // 64 columns per epilogue thread and tile
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr int kMaxChunks = 32;
-constexpr int kClasses = 32;   // running minima per row and column partition (column mod 32)
+constexpr int kClasses = 16;   // running minima per row and column slice (column mod 16)
 constexpr int kMaxCand = 512;  // screened candidates per sample handed to the rerank
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -145,9 +148,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int S = args.stages;
   uint8_t* q_smem = smem;                                 // KB x (128 rows x 128 B)
   uint8_t* b_smem = q_smem + size_t(KB) * kBM * kKB;      // S x (256 rows x 128 B)
-  float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [8 warps][2][128] |b|^2
-  float* sb_s = nb_s + 8 * kBN;                                            // [8 warps][2][128] -2 x FP8 scale
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sb_s + 8 * kBN);
+  float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [warps][2][64] |b|^2
+  float* sb_s = nb_s + 2 * kEpiWarps * kSliceCols;                         // [warps][2][64] -2 x FP8 scale
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sb_s + 2 * kEpiWarps * kSliceCols);
   uint64_t* full = bars;            // [S]
   uint64_t* empty = bars + S;       // [S]
   uint64_t* q_full = bars + 2 * S;  // [1]
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(q_empty, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 256);
+      mbar_init(&acc_empty[i], 32 * kEpiWarps);
     }
     *abort_flag = 0;
     mbar_init_fence();
@@ -264,10 +267,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------ epilogue: one sample row per thread
-    // Eight warps: warp w reads TMEM lane quadrant w % 4 (the only one it may
-    // access) and one half (128 columns) of each accumulator tile.
+    // Sixteen warps: warp w reads TMEM lane quadrant w % 4 (the only one it may
+    // access) and one 64-column slice of each accumulator tile.
     const int ew = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int qs = (warp - 2) >> 2;  // column slice
     const int row = ew * 32 + lane;
     uint32_t acc = 0, accphase = 0;
     for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
@@ -277,24 +280,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t grow = int64_t(mt) * kBM + row;
       float sq = 1.0f;
       if constexpr (SCREEN == CH_SCREEN_FP8) sq = (grow < args.T) ? args.scaleQ[grow] : 1.0f;
-      // 32 running minima per row, one per residue class (column mod 32) of this
-      // warp's half-columns; best_c holds the 32-column group of each minimum.
-      float best_s[32];
-      int32_t best_c[32];
+      // 16 running minima per row, one per residue class (column mod 16) of this
+      // warp's slice; best_c holds the 16-column group of each minimum.
+      float best_s[kClasses];
+      int32_t best_c[kClasses];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < kClasses; ++i) {
         best_s[i] = __int_as_float(0x7F800000);
         best_c[i] = -1;
       }
-      int32_t group = 0;  // running 32-column group index within this half
-      // |b|^2 (and -2 x FP8 scale) of this lane's 4 columns of a tile half,
+      int32_t group = 0;  // running 16-column group index within this slice
+      // |b|^2 (and -2 x FP8 scale) of this lane's 2 columns of a tile slice,
       // fetched one tile ahead so the load latency hides behind a tile of work;
       // +inf past the end of the chunk
-      float pn[4], ps[4];
+      float pn[2], ps[2];
       auto prefetch_norms = [&](int64_t t0) {
-        const int64_t base = t0 + half * (kBN / 2);
+        const int64_t base = t0 + qs * kSliceCols;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
           const int64_t b = base + lane + 32 * k;
           pn[k] = (b < b_end) ? __ldg(&args.normB[b]) : __int_as_float(0x7F800000);
           ps[k] = 0.0f;
@@ -307,11 +310,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // stage |b|^2 (and -2 x FP8 scale) of this tile in this warp's own buffer;
         // +inf past the end of B.  Only __syncwarp is used inside the epilogue, so
         // a warp that gives up on a wait can never strand another one.
-        float* nb = nb_s + ((warp - 2) * 2 + acc) * (kBN / 2);
-        float* sb = sb_s + ((warp - 2) * 2 + acc) * (kBN / 2);
+        float* nb = nb_s + ((warp - 2) * 2 + acc) * kSliceCols;
+        float* sb = sb_s + ((warp - 2) * 2 + acc) * kSliceCols;
         // this tile's norms were fetched into registers during the previous tile
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
           nb[lane + 32 * k] = pn[k];
           if constexpr (SCREEN == CH_SCREEN_FP8) sb[lane + 32 * k] = ps[k];
         }
@@ -323,12 +326,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t taddr =
-            tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + half * (kBN / 2);
-        // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 32 columns, then
-        // the branch-free update of the residue-class minima
-        // chunk ch = columns ch*16 .. ch*16+15 of this warp's half: residue
-        // classes (ch%2)*16 + i, 32-column group (tile, ch/2)
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + qs * kSliceCols;
+        // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 16 columns, then
+        // the branch-free update of the residue-class minima; chunk ch = columns
+        // ch*16 .. ch*16+15 of this warp's slice = 16-column group (tile, ch)
         auto process = [&](uint32_t(&r)[16], int ch) {
           const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 16);
           const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 16);
@@ -348,13 +349,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
             r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
           }
-          const int cls = (ch & 1) * 16;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
+          for (int i = 0; i < kClasses; ++i) {
             const float v = __uint_as_float(r[i]);
-            const bool lt = v < best_s[cls + i];
-            best_s[cls + i] = lt ? v : best_s[cls + i];
-            best_c[cls + i] = lt ? group + (ch >> 1) : best_c[cls + i];
+            const bool lt = v < best_s[i];
+            best_s[i] = lt ? v : best_s[i];
+            best_c[i] = lt ? group + ch : best_c[i];
           }
         };
         // two 16-column register buffers: the next chunk loads while this one is processed
@@ -362,15 +362,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld16_async(taddr, ra);
         tmem_wait_ld();
 #pragma unroll
-        for (int ch = 0; ch < 8; ch += 2) {
+        for (int ch = 0; ch < kSliceCols / 16; ch += 2) {
           tmem_ld16_async(taddr + (ch + 1) * 16, rb);
           process(ra, ch);
           tmem_wait_ld();
-          if (ch + 2 < 8) tmem_ld16_async(taddr + (ch + 2) * 16, ra);
+          if (ch + 2 < kSliceCols / 16) tmem_ld16_async(taddr + (ch + 2) * 16, ra);
           process(rb, ch + 1);
           tmem_wait_ld();
         }
-        group += kBN / 64;
+        group += kSliceCols / 16;
         tc_fence_before();
         mbar_arrive(&acc_empty[acc]);
         acc ^= 1;
@@ -379,15 +379,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       if (grow < args.T) {
-        // group g of class i is column b_begin + (g/4)*256 + half*128 + (g%4)*32 + i
-        const size_t base = (size_t(ck * 2 + half) * args.T + grow) * kClasses;
+        // group g of class i is column b_begin + (g/4)*256 + slice*64 + (g%4)*16 + i
+        const size_t base = (size_t(ck * kSlices + qs) * args.T + grow) * kClasses;
 #pragma unroll
         for (int i = 0; i < kClasses; ++i) {
           const int32_t g = best_c[i];
           args.part_s[base + i] = best_s[i];
           args.part_i[base + i] =
               g < 0 ? -1
-                    : static_cast<int32_t>(b_begin + int64_t(g >> 2) * kBN + half * (kBN / 2) + (g & 3) * 32 + i);
+                    : static_cast<int32_t>(b_begin + int64_t(g >> 2) * kBN + qs * kSliceCols + (g & 3) * 16 + i);
         }
       }
     }
@@ -546,7 +546,7 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   int best_c = 1;
   double best_eff = 0.0;
   for (int c = 1; c <= kMaxChunks && c <= btiles; ++c) {
-    if (2 * c * kClasses > kMaxCand) break;  // two column halves per chunk
+    if (kSlices * c * kClasses > kMaxCand) break;  // kSlices column slices per chunk
     const int64_t items = int64_t(p.row_tiles) * c;
     const int64_t rounds = ceil_div(items, sm_count);
     const double eff = double(items) / double(rounds * sm_count);
@@ -592,7 +592,7 @@ size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int s
   const Plan p = make_plan(T, nB, d, R, sm_count, screen);
   const int es = static_cast<int>(elem_size(screen_dtype(screen)));
   const size_t q = ((size_t(T) * d * es + 255) & ~size_t(255)) + ((size_t(T) * 4 + 255) & ~size_t(255));
-  const size_t parts = size_t(2 * p.chunks) * T * kClasses * 8 + 512;
+  const size_t parts = size_t(kSlices * p.chunks) * T * kClasses * 8 + 512;
   return q + parts + 1024;
 }
 
@@ -609,7 +609,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   float* sQ = reinterpret_cast<float*>(w);
   w += (size_t(T) * 4 + 255) & ~size_t(255);
   float* part_s = reinterpret_cast<float*>(w);
-  w += (size_t(2 * p.chunks) * T * kClasses * 4 + 255) & ~size_t(255);
+  w += (size_t(kSlices * p.chunks) * T * kClasses * 4 + 255) & ~size_t(255);
   int32_t* part_i = reinterpret_cast<int32_t*>(w);
 
   const int64_t words = T * (row_bytes / 16);
@@ -652,13 +652,13 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   const int blocks = static_cast<int>(ceil_div(T, 8));
   if (A->dtype == CH_F32)
     k_rerank<CH_F32, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T, part_s,
-                                                   part_i, 2 * p.chunks, kClasses, p.R, min_d, argmin);
+                                                   part_i, kSlices * p.chunks, kClasses, p.R, min_d, argmin);
   else if (A->dtype == CH_BF16)
     k_rerank<CH_BF16, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
-                                                    part_s, part_i, 2 * p.chunks, kClasses, p.R, min_d, argmin);
+                                                    part_s, part_i, kSlices * p.chunks, kClasses, p.R, min_d, argmin);
   else
     k_rerank<CH_FP8E4M3, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
-                                                       part_s, part_i, 2 * p.chunks, kClasses, p.R, min_d, argmin);
+                                                       part_s, part_i, kSlices * p.chunks, kClasses, p.R, min_d, argmin);
   launch_check("rerank");
 }
 
