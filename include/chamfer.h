@@ -55,8 +55,10 @@ typedef enum { CH_F32 = 0, CH_BF16 = 1, CH_FP8E4M3 = 2 } ch_dtype;
 
 /* How the sampled l2 scan finds min_b d(q, b):
  *  EXACT  canonical binary32 distance to every b (CUDA cores);
- *  TF32/BF16/FP8  tensor-core screen of |b|^2 - 2 q.b keeping the rerank_k best
- *         candidates per sample, then the canonical distance on those;
+ *  TF32/BF16/FP8  tensor-core screen of |b|^2 - 2 q.b; per sample it keeps
+ *         screened entries (4 columns of B each, scored by their best column),
+ *         takes the rerank_k best entries and evaluates the canonical
+ *         distance on all their columns;
  *  AUTO   TF32 for F32 sets, BF16 for BF16 sets, FP8 for FP8 sets.
  * l1 always uses the exact CUDA-core scan. */
 typedef enum {
@@ -99,7 +101,7 @@ typedef struct {
     int64_t T;            /* samples; 0 = ceil(4 ln(max(|A|,|B|)) / eps^2) (Theorem 1) */
     uint64_t sample_seed; /* Philox key of the draws */
     int32_t screen;       /* ch_screen */
-    uint32_t rerank_k;    /* screen survivors per sample (1..32; default 8) */
+    uint32_t rerank_k;    /* screened entries reranked per sample, 4 columns each (1..32; default 8) */
 } ch_est_params;
 
 typedef struct {
@@ -210,7 +212,7 @@ ch_status ch_sample_static(const float* D, int64_t nA, int64_t T, uint64_t seed,
  * For each l < T: min_d[l] = min_b d_X(A[idx[l]], b) with the canonical
  * binary32 distance, argmin[l] its index (smallest on ties) -- exactly, for
  * screen EXACT; for tensor-core screens, exactly whenever the true nearest b
- * is among the rerank_k screen survivors.  idx: device int64 [T] (entries < 0
+ * is among the columns of the rerank_k best screened entries.  idx: device int64 [T] (entries < 0
  * give min_d 0, argmin -1).  min_d: device float [T]; argmin: device int64 [T]
  * or NULL. */
 ch_status ch_sampled_nn(ch_ctx* ctx, const ch_set* A, const int64_t* idx, int64_t T, const ch_set* B,

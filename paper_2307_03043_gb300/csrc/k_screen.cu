@@ -28,12 +28,19 @@ namespace {
 constexpr int kBM = 128;          // samples per tile (TMEM lanes)
 constexpr int kBN = 256;          // B points per tile (accumulator columns)
 constexpr int kKB = 128;          // bytes of K per stage (one 128B swizzle row)
-constexpr int kEpiWarps = 16;     // epilogue warps: 4 per TMEM lane quadrant
+constexpr int kEpiWarps = 8;      // epilogue warps: 2 per TMEM lane quadrant
 constexpr int kSlices = kEpiWarps / 4;     // column slices of an accumulator tile
-constexpr int kSliceCols = kBN / kSlices;  // 64 columns per epilogue thread and tile
+constexpr int kSliceCols = kBN / kSlices;  // 128 columns per epilogue thread and tile
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr int kMaxChunks = 32;
-constexpr int kClasses = 16;   // running minima per row and column slice (column mod 16)
+// Each epilogue thread keeps one running minimum per residue class (column mod
+// kClasses) of its slice; a class has kOcc columns in a tile slice, and the
+// thread first takes their minimum (kOcc - 1 min operations), then updates the
+// class's running (value, tile) pair once per tile.  A candidate is therefore a
+// (tile, class) entry standing for kOcc columns, all of which the rerank
+// evaluates exactly.
+constexpr int kOcc = 4;
+constexpr int kClasses = kSliceCols / kOcc;  // 32
 constexpr int kMaxCand = 512;  // screened candidates per sample handed to the rerank
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -280,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t grow = int64_t(mt) * kBM + row;
       float sq = 1.0f;
       if constexpr (SCREEN == CH_SCREEN_FP8) sq = (grow < args.T) ? args.scaleQ[grow] : 1.0f;
-      // 16 running minima per row, one per residue class (column mod 16) of this
-      // warp's slice; best_c holds the 16-column group of each minimum.
+      // running minima per residue class of this warp's slice; best_c holds the
+      // tile (within the chunk) of each minimum
       float best_s[kClasses];
       int32_t best_c[kClasses];
 #pragma unroll
@@ -289,15 +296,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         best_s[i] = __int_as_float(0x7F800000);
         best_c[i] = -1;
       }
-      int32_t group = 0;  // running 16-column group index within this slice
-      // |b|^2 (and -2 x FP8 scale) of this lane's 2 columns of a tile slice,
+      int32_t tile = 0;  // tile index within the chunk
+      // |b|^2 (and -2 x FP8 scale) of this lane's columns of a tile slice,
       // fetched one tile ahead so the load latency hides behind a tile of work;
       // +inf past the end of the chunk
-      float pn[2], ps[2];
+      constexpr int kPer = kSliceCols / 32;
+      float pn[kPer], ps[kPer];
       auto prefetch_norms = [&](int64_t t0) {
         const int64_t base = t0 + qs * kSliceCols;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kPer; ++k) {
           const int64_t b = base + lane + 32 * k;
           pn[k] = (b < b_end) ? __ldg(&args.normB[b]) : __int_as_float(0x7F800000);
           ps[k] = 0.0f;
@@ -314,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float* sb = sb_s + ((warp - 2) * 2 + acc) * kSliceCols;
         // this tile's norms were fetched into registers during the previous tile
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kPer; ++k) {
           nb[lane + 32 * k] = pn[k];
           if constexpr (SCREEN == CH_SCREEN_FP8) sb[lane + 32 * k] = ps[k];
         }
@@ -327,9 +335,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + qs * kSliceCols;
-        // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 16 columns, then
-        // the branch-free update of the residue-class minima; chunk ch = columns
-        // ch*16 .. ch*16+15 of this warp's slice = 16-column group (tile, ch)
+        // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 16 columns
+        // (chunk ch = slice columns ch*16 .. ch*16+15: classes (ch*16) mod
+        // kClasses + i, occurrence ch*16 / kClasses), folded into the tile minima tm
+        float tm[kClasses];
         auto process = [&](uint32_t(&r)[16], int ch) {
           const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 16);
           const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 16);
@@ -349,13 +358,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
             r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
           }
+          const int c0 = (ch * 16) % kClasses;
+          const bool first = ch * 16 < kClasses;
 #pragma unroll
-          for (int i = 0; i < kClasses; ++i) {
-            const float v = __uint_as_float(r[i]);
-            const bool lt = v < best_s[i];
-            best_s[i] = lt ? v : best_s[i];
-            best_c[i] = lt ? group + ch : best_c[i];
-          }
+          for (int i = 0; i < 16; ++i)
+            tm[c0 + i] = first ? __uint_as_float(r[i]) : fminf(tm[c0 + i], __uint_as_float(r[i]));
         };
         // two 16-column register buffers: the next chunk loads while this one is processed
         uint32_t ra[16], rb[16];
@@ -370,24 +377,31 @@ __global__ void __launch_bounds__(kThreads, 1)
           process(rb, ch + 1);
           tmem_wait_ld();
         }
-        group += kSliceCols / 16;
         tc_fence_before();
         mbar_arrive(&acc_empty[acc]);
+        // one running-minimum update per class and tile
+#pragma unroll
+        for (int i = 0; i < kClasses; ++i) {
+          const bool lt = tm[i] < best_s[i];
+          best_s[i] = lt ? tm[i] : best_s[i];
+          best_c[i] = lt ? tile : best_c[i];
+        }
+        ++tile;
         acc ^= 1;
         if (acc == 0) accphase ^= 1;
         __syncwarp();  // this warp's staging buffer is rewritten two tiles later
       }
       if (!ok) break;
       if (grow < args.T) {
-        // group g of class i is column b_begin + (g/4)*256 + slice*64 + (g%4)*16 + i
+        // entry (tile t, class i) stands for columns
+        // b_begin + t*256 + slice*kSliceCols + o*kClasses + i, o = 0 .. kOcc-1
         const size_t base = (size_t(ck * kSlices + qs) * args.T + grow) * kClasses;
 #pragma unroll
         for (int i = 0; i < kClasses; ++i) {
-          const int32_t g = best_c[i];
+          const int32_t t = best_c[i];
           args.part_s[base + i] = best_s[i];
           args.part_i[base + i] =
-              g < 0 ? -1
-                    : static_cast<int32_t>(b_begin + int64_t(g >> 2) * kBN + qs * kSliceCols + (g & 3) * 16 + i);
+              t < 0 ? -1 : static_cast<int32_t>(b_begin + int64_t(t) * kBN + qs * kSliceCols + i);
         }
       }
     }
@@ -426,13 +440,15 @@ __global__ void k_gather_rows(const uint8_t* A, const float* scA, int64_t nA, in
   if (sQ && w == 0) sQ[row] = (a >= 0 && a < nA) ? scA[a] : 1.0f;
 }
 
-// One warp per sample: the R best screened candidates over all chunks (by s,
-// then index), the canonical binary32 distance of each, and their minimum.
+// One warp per sample: the R best screened entries over all chunks (by s, then
+// index), the canonical binary32 distance of each of an entry's occ columns
+// (first column + o * stride, o < occ, columns < nB), and their minimum (ties:
+// smaller index).
 template <int DT, int METRIC>
 __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA, int64_t nA, const void* B,
-                                                const float* scB, int d, const int64_t* idx, int64_t T,
+                                                const float* scB, int64_t nB, int d, const int64_t* idx, int64_t T,
                                                 const float* part_s, const int32_t* part_i, int parts, int per,
-                                                int R, float* min_d, int64_t* argmin) {
+                                                int occ, int stride, int R, float* min_d, int64_t* argmin) {
   __shared__ float s_s[8][kMaxCand];
   __shared__ int32_t s_i[8][kMaxCand];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -480,21 +496,25 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
         mp = op;
       }
     }
-    if (mi == INT32_MAX || mi < 0) break;  // fewer than R candidates
+    if (mi == INT32_MAX || mi < 0) break;  // fewer than R entries
     if (lane == (mp & 31)) s_i[wib][mp] = -1;  // taken
     __syncwarp();
-    // canonical distance to candidate mi (lane r sums coordinates j = r mod 32)
-    float part = 0.0f;
-    for (int j = lane; j < d; j += 32) {
-      const float t = __fsub_rn(load_elem<DT>(A, a, d, j, scA), load_elem<DT>(B, mi, d, j, scB));
-      part = (METRIC == CH_L1) ? __fadd_rn(part, fabsf(t)) : __fmaf_rn(t, t, part);
-    }
+    // canonical distances to the entry's columns (lane r sums coordinates j = r mod 32)
+    for (int o = 0; o < occ; ++o) {
+      const int64_t b = int64_t(mi) + int64_t(o) * stride;
+      if (b >= nB) break;
+      float part = 0.0f;
+      for (int j = lane; j < d; j += 32) {
+        const float t = __fsub_rn(load_elem<DT>(A, a, d, j, scA), load_elem<DT>(B, b, d, j, scB));
+        part = (METRIC == CH_L1) ? __fadd_rn(part, fabsf(t)) : __fmaf_rn(t, t, part);
+      }
 #pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) part = __fadd_rn(part, __shfl_down_sync(0xFFFFFFFFu, part, s));
-    const float dist = __shfl_sync(0xFFFFFFFFu, (METRIC == CH_L1) ? part : __fsqrt_rn(part), 0);
-    if (dist < best || (dist == best && mi < bidx)) {
-      best = dist;
-      bidx = mi;
+      for (int sh = 16; sh >= 1; sh >>= 1) part = __fadd_rn(part, __shfl_down_sync(0xFFFFFFFFu, part, sh));
+      const float dist = __shfl_sync(0xFFFFFFFFu, (METRIC == CH_L1) ? part : __fsqrt_rn(part), 0);
+      if (dist < best || (dist == best && b < bidx)) {
+        best = dist;
+        bidx = b;
+      }
     }
   }
   if (lane == 0) {
@@ -651,14 +671,14 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
 
   const int blocks = static_cast<int>(ceil_div(T, 8));
   if (A->dtype == CH_F32)
-    k_rerank<CH_F32, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T, part_s,
-                                                   part_i, kSlices * p.chunks, kClasses, p.R, min_d, argmin);
+    k_rerank<CH_F32, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T, part_s,
+                                                   part_i, kSlices * p.chunks, kClasses, kOcc, kClasses, p.R, min_d, argmin);
   else if (A->dtype == CH_BF16)
-    k_rerank<CH_BF16, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
-                                                    part_s, part_i, kSlices * p.chunks, kClasses, p.R, min_d, argmin);
+    k_rerank<CH_BF16, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T,
+                                                    part_s, part_i, kSlices * p.chunks, kClasses, kOcc, kClasses, p.R, min_d, argmin);
   else
-    k_rerank<CH_FP8E4M3, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, qidx, T,
-                                                       part_s, part_i, kSlices * p.chunks, kClasses, p.R, min_d, argmin);
+    k_rerank<CH_FP8E4M3, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T,
+                                                       part_s, part_i, kSlices * p.chunks, kClasses, kOcc, kClasses, p.R, min_d, argmin);
   launch_check("rerank");
 }
 
