@@ -800,13 +800,25 @@ __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t*
   if (merge && top_exp_in == CH_TOP_EXP_AUTO) {
     for (int c = threadIdx.x; c < 2 * dd; c += blockDim.x) s_box[c] = c < dd ? 0xFFFFFFFFu : 0u;
     __syncthreads();
-    // all threads over all (part, coordinate) entries: independent loads, shared atomics
-    const int na = partsA * 2 * dd, nb = partsB * 2 * dd;
-    for (int e = threadIdx.x; e < na + nb; e += blockDim.x) {
-      const uint32_t u = e < na ? boxA[e] : boxB[e - na];
-      const int c = (e < na ? e : e - na) % (2 * dd);
-      if (c < dd) atomicMin(&s_box[c], u);
-      else atomicMax(&s_box[c], u);
+    // thread (group g, entry c): a register min / max over parts g, g + ng, ...
+    // (independent loads), then one shared atomic per thread
+    const int w = 2 * dd, ng = blockDim.x / w;
+    const int c = threadIdx.x % w, g = threadIdx.x / w;
+    if (g < ng) {
+      const bool is_lo = c < dd;
+      uint32_t v = is_lo ? 0xFFFFFFFFu : 0u;
+#pragma unroll 4
+      for (int p = g; p < partsA; p += ng) {
+        const uint32_t u = boxA[size_t(p) * w + c];
+        v = is_lo ? min(v, u) : max(v, u);
+      }
+#pragma unroll 4
+      for (int p = g; p < partsB; p += ng) {
+        const uint32_t u = boxB[size_t(p) * w + c];
+        v = is_lo ? min(v, u) : max(v, u);
+      }
+      if (is_lo) atomicMin(&s_box[c], v);
+      else atomicMax(&s_box[c], v);
     }
   }
   __syncthreads();

@@ -499,21 +499,38 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
     if (mi == INT32_MAX || mi < 0) break;  // fewer than R entries
     if (lane == (mp & 31)) s_i[wib][mp] = -1;  // taken
     __syncwarp();
-    // canonical distances to the entry's columns (lane r sums coordinates j = r mod 32)
-    for (int o = 0; o < occ; ++o) {
-      const int64_t b = int64_t(mi) + int64_t(o) * stride;
-      if (b >= nB) break;
-      float part = 0.0f;
-      for (int j = lane; j < d; j += 32) {
-        const float t = __fsub_rn(load_elem<DT>(A, a, d, j, scA), load_elem<DT>(B, b, d, j, scB));
-        part = (METRIC == CH_L1) ? __fadd_rn(part, fabsf(t)) : __fmaf_rn(t, t, part);
-      }
+    // canonical distances to the entry's columns, all at once (lane r sums
+    // coordinates j = r mod 32 of each; the reduction trees run side by side)
+    int64_t bo[kOcc];
+    bool vo[kOcc];
+    float part[kOcc];
 #pragma unroll
-      for (int sh = 16; sh >= 1; sh >>= 1) part = __fadd_rn(part, __shfl_down_sync(0xFFFFFFFFu, part, sh));
-      const float dist = __shfl_sync(0xFFFFFFFFu, (METRIC == CH_L1) ? part : __fsqrt_rn(part), 0);
-      if (dist < best || (dist == best && b < bidx)) {
+    for (int o = 0; o < kOcc; ++o) {
+      bo[o] = int64_t(mi) + int64_t(o) * stride;
+      vo[o] = o < occ && bo[o] < nB;
+      part[o] = 0.0f;
+    }
+    for (int j = lane; j < d; j += 32) {
+      const float x = load_elem<DT>(A, a, d, j, scA);
+#pragma unroll
+      for (int o = 0; o < kOcc; ++o) {
+        if (vo[o]) {
+          const float t = __fsub_rn(x, load_elem<DT>(B, bo[o], d, j, scB));
+          part[o] = (METRIC == CH_L1) ? __fadd_rn(part[o], fabsf(t)) : __fmaf_rn(t, t, part[o]);
+        }
+      }
+    }
+#pragma unroll
+    for (int sh = 16; sh >= 1; sh >>= 1) {
+#pragma unroll
+      for (int o = 0; o < kOcc; ++o) part[o] = __fadd_rn(part[o], __shfl_down_sync(0xFFFFFFFFu, part[o], sh));
+    }
+#pragma unroll
+    for (int o = 0; o < kOcc; ++o) {
+      const float dist = __shfl_sync(0xFFFFFFFFu, (METRIC == CH_L1) ? part[o] : __fsqrt_rn(part[o]), 0);
+      if (vo[o] && (dist < best || (dist == best && bo[o] < bidx))) {
         best = dist;
-        bidx = b;
+        bidx = bo[o];
       }
     }
   }
