@@ -53,7 +53,11 @@ WORKLOADS = {
     "precision_fp8": dict(n=1_000_000, d=384, dtype="fp8",
                           desc="precision: |A|=|B|=1000000, d=384, fp8 e4m3 + row scale, l2, eps=0.1, "
                                "1000-cluster unit-norm mixture"),
+    "batched": dict(n=0, d=3, dtype="f32",
+                    desc="batched: 4096 pairs, |A| and |B| log-uniform in [256, 50000], d=3 ellipsoid/box "
+                         "surfaces with 1% noise (B a resample of A's shape), fp32, l2 (l1 alongside), eps=0.1"),
 }
+BATCH_PAIRS = 4096
 
 
 def select_workload(name):
@@ -242,6 +246,162 @@ def serving_sample(ch, ctx, rank, n_req=200, seed=7):
             "pts_per_s": pts / wall, "peak_bytes": s.peak_bytes}
 
 
+def run_batched(args, ch, ctx, torch, rank, local, world):
+    """The batched workload: one step = ch_estimate_batch over all pairs (sets
+    resident on the device).  Each pair's estimate counts when it lies within
+    (1 +- 0.1) of its exact GPU brute force."""
+    from paper_2307_03043_gb300 import workloads
+    P = BATCH_PAIRS
+    sizes = workloads.log_uniform_sizes(2 * P, 256, 50_000, 1000 + rank)
+    host = [workloads.shape_surface(int(sizes[2 * i]), int(sizes[2 * i + 1]), 5000 + rank * P + i) for i in range(P)]
+    npts = [a.shape[0] + b.shape[0] for a, b in host]
+    sets = [(ch.ch_set_create(ctx, a, 0, a.shape[0], 3), ch.ch_set_create(ctx, b, 0, b.shape[0], 3)) for a, b in host]
+    A = [x[0] for x in sets]
+    B = [x[1] for x in sets]
+    stream = torch.cuda.current_stream()
+    out_metrics = {}
+    for metric, name in ((ch.CH_L2, "l2"), (ch.CH_L1, "l1")):
+        exact = [ch.ch_exact(ctx, a, b, metric, 0) for a, b in sets]
+        t_ex = time.perf_counter()
+        for a, b in sets[:256]:
+            ch.ch_exact(ctx, a, b, metric, 0)
+        ex_per_pair_s = (time.perf_counter() - t_ex) / 256
+
+        def params(seed):
+            return [ch.est_params(metric, LEVELS, PROJ, None, seed * P + i, eps=EPS, sample_seed=seed * P + i)
+                    for i in range(P)]
+
+        for w in range(args.warmup):
+            ch.ch_estimate_batch(ctx, A, B, params(10_000 + w))
+        torch.cuda.synchronize()
+        clocks = Clocks(local)
+        clocks.start()
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        step_ms, pts_ok, launches0 = [], 0.0, ch.ch_kernel_launches()
+        for k in range(args.steps):
+            prm = params(k)
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            eta, st = ch.ch_estimate_batch(ctx, A, B, prm)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            pts_ok += sum(n for n, e, x, s_ in zip(npts, eta, exact, st) if s_ == ch.CH_OK and abs(e / x - 1) <= 0.1)
+        launches = ch.ch_kernel_launches() - launches0
+        clk = clocks.stop()
+        total_ms = float(np.sum(step_ms))
+        within = pts_ok / (args.steps * sum(npts))
+        out_metrics[name] = {"value": pts_ok / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                             "points_within_10pct": within, "gpu_launches": launches, "clocks": clk,
+                             "exact_gpu_ms_per_pair": ex_per_pair_s * 1e3,
+                             "speedup_estimate_vs_exact": ex_per_pair_s * P / (total_ms / args.steps / 1e3)}
+    # end to end: sets from pinned host buffers, the batch, the results on the host
+    pinned = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in host]
+    e2e_s = []
+    for k in range(max(1, args.e2e_steps // 2) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ss = [(ch.ch_set_create(ctx, a, 0, a.shape[0], 3), ch.ch_set_create(ctx, b, 0, b.shape[0], 3))
+              for a, b in pinned]
+        prm = [ch.est_params(ch.CH_L2, LEVELS, PROJ, None, 77 + i, eps=EPS, sample_seed=77 + i) for i in range(P)]
+        ch.ch_estimate_batch(ctx, [x[0] for x in ss], [x[1] for x in ss], prm)
+        for a, b in ss:
+            ch.ch_set_destroy(a)
+            ch.ch_set_destroy(b)
+        ch.ch_ctx_sync(ctx)
+        if k > 0:
+            e2e_s.append(time.perf_counter() - t0)
+    e2e_value = sum(npts) / float(np.mean(e2e_s))
+    # roofline: the exact CUDA-core scan of the largest pair, timed on its own
+    big = int(np.argmax([a.shape[0] * b.shape[0] for a, b in host]))
+    kms = []
+    for k in range(3):
+        eta, rep = ch.ch_estimate(ctx, A[big], B[big], ch.est_params(ch.CH_L2, LEVELS, PROJ, None, k, eps=EPS,
+                                                                     sample_seed=k), report=True)
+        kms.append(rep.t_kernel_ms)
+    nB_big = host[big][1].shape[0]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    ops = 2.0 * rep.T * nB_big * 3
+    roof = {"bound": "alu", "achieved": ops / (np.median(kms) / 1e3) / 1e12, "peak": 152 * 128 * sm_max * 1e6 / 1e12,
+            "unit": "Tinst/s", "traffic": None,
+            "kernel": f"k_scan_exact (canonical fp32 l2 scan) of the largest pair ({host[big][0].shape[0]} x {nB_big}), "
+                      f"timed alone", "kernel_ms": float(np.median(kms)),
+            "peak_basis": "152 SMs x 128 FP32 lanes x sm_max_mhz (derived, not measured)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        sub = list(range(0, P, P // 16))[:16]
+        t0 = time.perf_counter()
+        for i in sub:
+            a, b = host[i]
+            oracle.estimate(a, b, oracle.L2, i, i, T=oracle.default_T(a.shape[0], b.shape[0], EPS))
+        sec = time.perf_counter() - t0
+        cpu = {"value": sum(npts[i] for i in sub) / sec, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"oracle Chamfer-Estimate (l2) of {len(sub)} of the {P} pairs, every "
+                                           f"{P // 16}th, in full"}
+    for a, b in sets:
+        ch.ch_set_destroy(a)
+        ch.ch_set_destroy(b)
+    if rank == 0:
+        main_m = out_metrics["l2"]
+        print(json.dumps({
+            "metric": METRIC, "value": main_m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main_m["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batched"]["desc"], "pairs": P, "points": int(sum(npts)), "d": 3,
+                       "metric": "l2", "eps": EPS, "levels": LEVELS, "proj_dim": PROJ,
+                       "l2_flush": "256 MiB write between timed steps, outside the timed events",
+                       "api": "ch_estimate_batch (4 streams)"},
+            "accuracy": {"points_within_10pct": main_m["points_within_10pct"]},
+            "exact_gpu": {"mode": "canonical fp32, all pairs, one ch_exact per pair",
+                          "ms_per_pair": main_m["exact_gpu_ms_per_pair"],
+                          "speedup_estimate_vs_exact": main_m["speedup_estimate_vs_exact"]},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(sum(npts)) * 3 * 4,
+                    "d2h_bytes_per_step": P * 48},
+            "gpu_launches": main_m["gpu_launches"], "roofline": roof, "cpu_baseline": cpu,
+            "clocks": main_m["clocks"], "l1": out_metrics["l1"],
+        }))
+
+
+def run_reference_batched(args):
+    """Oracle arm of the batched workload: each step runs the oracle on 16 of the
+    pairs (every 256th) in full; value in points per second."""
+    import oracle
+    from paper_2307_03043_gb300 import workloads
+    P = BATCH_PAIRS
+    sizes = workloads.log_uniform_sizes(2 * P, 256, 50_000, 1000)
+    sub = list(range(0, P, P // 16))[:16]
+    host = {i: workloads.shape_surface(int(sizes[2 * i]), int(sizes[2 * i + 1]), 5000 + i) for i in sub}
+    pts = sum(a.shape[0] + b.shape[0] for a, b in host.values())
+
+    def step(seed):
+        t0 = time.perf_counter()
+        for i in sub:
+            a, b = host[i]
+            oracle.estimate(a, b, oracle.L2, seed * P + i, seed * P + i, T=oracle.default_T(a.shape[0], b.shape[0], EPS))
+        return time.perf_counter() - t0
+
+    for w in range(args.warmup):
+        step(10_000 + w)
+    times = [step(k) for k in range(args.steps)]
+    sec = float(np.mean(times))
+    value = pts / sec
+    sample = f"each step: oracle Chamfer-Estimate (l2) of 16 of the {P} pairs (every {P // 16}th), in full"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["batched"]["desc"], "pairs": P, "d": 3, "metric": "l2", "eps": EPS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -249,6 +409,9 @@ def run_reference(args):
         return
     import oracle
     from paper_2307_03043_gb300 import workloads
+    if CONFIG == "batched":
+        run_reference_batched(args)
+        return
     A, B = workloads.gaussian_mixture(NA, NB, DIM, 0)
     T = oracle.default_T(NA, NB, EPS)
     frac = 8
@@ -295,6 +458,14 @@ def main():
         dist.barrier()
     from paper_2307_03043_gb300 import binding as ch
     from paper_2307_03043_gb300 import workloads
+
+    if CONFIG == "batched":
+        ctx = ch.ch_ctx_create(local, torch.cuda.current_stream())
+        run_batched(args, ch, ctx, torch, rank, local, world)
+        ch.ch_ctx_destroy(ctx)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     A_np, B_np, A_st, B_st, scA_np, scB_np = make_data(rank)
     A = torch.from_numpy(A_st).cuda()

@@ -224,6 +224,21 @@ ch_status ch_sampled_nn(ch_ctx* ctx, const ch_set* A, const int64_t* idx, int64_
 ch_status ch_estimate(ch_ctx* ctx, const ch_set* A, const ch_set* B, const ch_est_params* p, double* eta,
                       ch_est_report* report);
 
+/* ------------------------------------------------------------ many estimates
+ * Estimates of count independent pairs (A[i], B[i]) under params[i], as
+ * ch_estimate would return them (same values, bit for bit), in one call: the
+ * pairs are spread over a few internal streams of the context, so that the
+ * kernels of small pairs overlap, and the host waits once at the end.  Not in
+ * the paper (a throughput form of Fig. 1 for many small pairs).
+ * A, B: arrays of count sets of this context; params: count parameter blocks;
+ * eta: host double [count] (0 for failed pairs and for |A| = 0); status: host
+ * ch_status [count] or NULL.  Returns CH_OK, or the first failing pair's status
+ * (that pair's eta is 0; the other pairs are still computed).  Blocks until
+ * every eta is on the host.  The sets' lazy passes (|x|^2, box) run first on the
+ * context's stream, so one set may appear in many pairs. */
+ch_status ch_estimate_batch(ch_ctx* ctx, int64_t count, const ch_set* const* A, const ch_set* const* B,
+                            const ch_est_params* params, double* eta, ch_status* status);
+
 /* ------------------------------------------------------------ brute force (Section 1)
  * CH(A, B) = sum_a min_b d_X(a, b).  mode 0: canonical binary32 distance for
  * every pair (exact); mode 1: tensor-core screen + canonical rerank.

@@ -89,6 +89,7 @@ SIGNATURES = {
     "ch_sample_static": (_i32, [_vp, _i64, _i64, _u64, _vp, _vp, _vp, _vp]),
     "ch_sampled_nn": (_i32, [_vp, _vp, _vp, _i64, _vp, _i32, _i32, _u32, _vp, _vp]),
     "ch_estimate": (_i32, [_vp, _vp, _vp, _P(ch_est_params), _P(ctypes.c_double), _P(ch_est_report)]),
+    "ch_estimate_batch": (_i32, [_vp, _i64, _P(_vp), _P(_vp), _P(ch_est_params), _P(ctypes.c_double), _P(_i32)]),
     "ch_exact": (_i32, [_vp, _vp, _vp, _i32, _i32, _P(ctypes.c_double), _vp]),
     "ch_serve_create": (_i32, [_vp, _P(ch_serve_config), _P(_vp)]),
     "ch_serve_register": (_i32, [_vp, _vp, ctypes.c_int, _i64, _i32, _i32, _vp, _P(_u64)]),
@@ -254,6 +255,22 @@ def ch_estimate(ctx, A, B, p: ch_est_params, report: bool = False):
     _check(lib().ch_estimate(ctx, A, B, ctypes.byref(p), ctypes.byref(eta), ctypes.byref(rep) if report else None),
            "ch_estimate", ctx)
     return (eta.value, rep) if report else eta.value
+
+
+def ch_estimate_batch(ctx, A_sets, B_sets, params):
+    """Estimates of the pairs (A_sets[i], B_sets[i]) under params[i] in one call.
+    Returns (etas, statuses) as lists; never raises for a failing pair."""
+    n = len(A_sets)
+    assert len(B_sets) == n and len(params) == n
+    a = (_vp * n)(*A_sets)
+    b = (_vp * n)(*B_sets)
+    p = (ch_est_params * n)(*params)
+    eta = (ctypes.c_double * n)()
+    st = (_i32 * n)()
+    rc = lib().ch_estimate_batch(ctx, n, a, b, p, eta, st)
+    if rc not in (CH_OK,) and all(x == CH_OK for x in st):
+        _check(rc, "ch_estimate_batch", ctx)
+    return list(eta), list(st)
 
 
 def ch_exact(ctx, A, B, metric: int, mode: int = 0, per_a_min=None) -> float:

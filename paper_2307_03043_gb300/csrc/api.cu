@@ -104,15 +104,20 @@ __global__ void k_collect(ResBlock* r, const uint32_t* sa, const uint32_t* sb, c
   if (e_top) r->e_top = *e_top;
 }
 
-static void finish(ch_ctx* c, ResBlock* dres, ResBlock* hres) {
-  CHX_CUDA(cudaMemcpyAsync(hres, dres, sizeof(ResBlock), cudaMemcpyDeviceToHost, c->stream));
-  CHX_CUDA(cudaStreamSynchronize(c->stream));
+// raises the error a result block's status bits stand for
+static void check_result(const ResBlock* hres) {
   const uint32_t st = hres->status | hres->statusA | hres->statusB;
   if (st & ST_NONFINITE) throw Err{CH_EINVAL, "point set holds a non-finite value"};
   if (st & ST_RANGE) throw Err{CH_EINVAL, "scale exponents outside [-120, 120] (data range too large or too small)"};
   if (st & ST_BAD_INDEX) throw Err{CH_EINVAL, "sample index out of range"};
   if (st & ST_TABLE_FULL) throw Err{CH_ENOMEM, "bucket table overflow"};
   if (st & ST_TIMEOUT) throw Err{CH_ETIMEOUT, "a bounded device wait gave up"};
+}
+
+static void finish(ch_ctx* c, ResBlock* dres, ResBlock* hres) {
+  CHX_CUDA(cudaMemcpyAsync(hres, dres, sizeof(ResBlock), cudaMemcpyDeviceToHost, c->stream));
+  CHX_CUDA(cudaStreamSynchronize(c->stream));
+  check_result(hres);
 }
 
 static void check_hash(const ch_hash_params* hp) {
@@ -452,8 +457,11 @@ ch_status ch_ctx_create(int device, void* stream, ch_ctx** out) {
 
 void ch_ctx_destroy(ch_ctx* c) {
   if (!c) return;
+  for (ch_ctx* l : c->lanes) ch_ctx_destroy(l);
+  c->lanes.clear();
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->batch_pin) cudaFreeHost(c->batch_pin);
   c->ws.release();
   if (c->pool) cudaMemPoolDestroy(c->pool);
   for (auto& e : c->ev)
@@ -708,58 +716,93 @@ ch_status ch_sampled_nn(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t 
   CHX_GUARD_END
 }
 
-ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, double* eta,
-                      ch_est_report* rep) {
-  if (!c || !p || !eta) return CH_EINVAL;
-  CHX_GUARD_BEGIN(c)
+}  // extern "C"
+
+namespace chx {
+
+constexpr int kBatchLanes = 4;  // concurrent streams of a batched call
+
+// argument checks of one estimate; returns (T, R)
+static void check_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t* T,
+                           uint32_t* R) {
+  CHX_CHECK(p, CH_EINVAL, "params NULL");
   check_hash(&p->hash);
   check_pair(c, A, B);
   CHX_CHECK(p->screen >= CH_SCREEN_AUTO && p->screen <= CH_SCREEN_FP8, CH_EINVAL, "unknown screen");
-  const uint32_t R = p->rerank_k ? p->rerank_k : 8;
-  CHX_CHECK(R <= 32, CH_EINVAL, "rerank_k must be in 1..32");
+  *R = p->rerank_k ? p->rerank_k : 8;
+  CHX_CHECK(*R <= 32, CH_EINVAL, "rerank_k must be in 1..32");
   CHX_CHECK(p->T >= 0, CH_EINVAL, "T must be >= 0");
   CHX_CHECK(p->T > 0 || (p->eps > 0.0 && p->eps < 1.0), CH_EINVAL, "eps must be in (0, 1)");
-  CHX_CUDA(cudaSetDevice(c->device));
-  const int64_t nA = A->n, nB = B->n;
-  const int64_t T = p->T > 0 ? p->T : default_T(nA, nB, p->eps);
-  if (rep) {
-    std::memset(rep, 0, sizeof(*rep));
-    rep->T = T;
-  }
-  if (nA == 0) {
-    *eta = 0.0;
-    return CH_OK;
-  }
+  *T = p->T > 0 ? p->T : default_T(A->n, B->n, p->eps);
+}
+
+// Enqueues the whole estimate of (A, B) on c's stream, carving c's workspace; the
+// result block lands in res_out (or in the workspace when null).  With events,
+// records stage boundaries in c->ev.  Returns the result block and the screen used.
+static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t T,
+                                  uint32_t R, ResBlock* res_out, bool events, int* screen_used) {
+  const int64_t nA = A->n;
   EstBufs eb;
   carve(c, [&](auto& lay) { take_estimate(lay, c, A, B, p, T, R, &eb); });
+  if (res_out) eb.res = res_out;
   CrudeBufs& cb = eb.cb;
   SampleBufs& sb = eb.sb;
   ScanBufs& sc = eb.sc;
   ResBlock* res = eb.res;
-  int64_t *bidx = eb.bidx, *idx = eb.idx;
-  uint8_t* level = eb.level;
-  float *D = eb.D, *m = eb.m;
-  uint64_t* w = eb.w;
-  double* out2 = eb.out2;
   cudaStream_t s = c->stream;
-  if (rep) CHX_CUDA(cudaEventRecord(c->ev[0], s));
+  if (events) CHX_CUDA(cudaEventRecord(c->ev[0], s));
   CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
-  run_crude(c, A, B, &p->hash, &cb, bidx, level, D, &res->status, sb.sw.maxD);
-  if (rep) CHX_CUDA(cudaEventRecord(c->ev[1], s));
-  launch_weights(D, nA, w, sb.prefix, sb.sw, s, true);
-  launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, idx, s);
-  if (rep) CHX_CUDA(cudaEventRecord(c->ev[2], s));
+  run_crude(c, A, B, &p->hash, &cb, eb.bidx, eb.level, eb.D, &res->status, sb.sw.maxD);
+  if (events) CHX_CUDA(cudaEventRecord(c->ev[1], s));
+  launch_weights(eb.D, nA, eb.w, sb.prefix, sb.sw, s, true);
+  launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, eb.idx, s);
+  if (events) CHX_CUDA(cudaEventRecord(c->ev[2], s));
   KernelTimer kt;
-  if (rep) {
+  if (events) {
     kt.before = c->ev[5];
     kt.after = c->ev[6];
   }
-  run_scan(c, A, idx, T, B, p->hash.metric, R, &sc, m, nullptr, &res->status, kt);
-  if (rep) CHX_CUDA(cudaEventRecord(c->ev[3], s));
-  launch_combine(m, idx, w, sb.sw.W, T, D, nA, out2, s);
-  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, out2, sb.sw.W, sb.sw.S, cb.e_top);
+  run_scan(c, A, eb.idx, T, B, p->hash.metric, R, &sc, eb.m, nullptr, &res->status, kt);
+  if (events) CHX_CUDA(cudaEventRecord(c->ev[3], s));
+  launch_combine(eb.m, eb.idx, eb.w, sb.sw.W, T, eb.D, nA, eb.out2, s);
+  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, eb.out2, sb.sw.W, sb.sw.S, cb.e_top);
   launch_check("collect");
-  if (rep) CHX_CUDA(cudaEventRecord(c->ev[4], s));
+  if (events) CHX_CUDA(cudaEventRecord(c->ev[4], s));
+  if (screen_used) *screen_used = sc.screen;
+  return res;
+}
+
+// the workspace bytes estimate_enqueue carves for (A, B, p)
+static size_t estimate_need(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t T,
+                            uint32_t R) {
+  Layout m;
+  EstBufs eb;
+  take_estimate(m, c, A, B, p, T, R, &eb);
+  return m.need + 256;
+}
+
+}  // namespace chx
+
+extern "C" {
+
+ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, double* eta,
+                      ch_est_report* rep) {
+  if (!c || !p || !eta) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  int64_t T;
+  uint32_t R;
+  check_estimate(c, A, B, p, &T, &R);
+  CHX_CUDA(cudaSetDevice(c->device));
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->T = T;
+  }
+  if (A->n == 0) {
+    *eta = 0.0;
+    return CH_OK;
+  }
+  int screen = 0;
+  ResBlock* res = estimate_enqueue(c, A, B, p, T, R, nullptr, rep != nullptr, &screen);
   ResBlock* h = static_cast<ResBlock*>(c->host_pin);
   finish(c, res, h);
   *eta = h->eta;
@@ -775,9 +818,94 @@ ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_
     cudaEventElapsedTime(&rep->t_total_ms, c->ev[0], c->ev[4]);
     rep->t_kernel_ms = 0.0f;
     if (T > 0) cudaEventElapsedTime(&rep->t_kernel_ms, c->ev[5], c->ev[6]);
-    rep->screen = sc.screen;
+    rep->screen = screen;
   }
   return CH_OK;
+  CHX_GUARD_END
+}
+
+ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, const ch_set* const* B,
+                            const ch_est_params* params, double* eta, ch_status* status) {
+  if (!c || count < 0 || (count > 0 && (!A || !B || !params || !eta))) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  CHX_CUDA(cudaSetDevice(c->device));
+  if (count == 0) return CH_OK;
+  // per-pair checks; a failing pair gets its status and is skipped
+  std::vector<int64_t> Ts(count);
+  std::vector<uint32_t> Rs(count);
+  std::vector<ch_status> st(count, CH_OK);
+  for (int64_t i = 0; i < count; ++i) {
+    try {
+      check_estimate(c, A[i], B[i], &params[i], &Ts[i], &Rs[i]);
+      CHX_CHECK(A[i]->ctx == c && B[i]->ctx == c, CH_EINVAL, "batched sets must belong to the context");
+    } catch (const Err& e) {
+      st[i] = e.st;
+    }
+  }
+  // lanes: sub-contexts with their own streams and workspaces
+  const int K = static_cast<int>(std::min<int64_t>(kBatchLanes, count));
+  while (static_cast<int>(c->lanes.size()) < K) {
+    ch_ctx* l = nullptr;
+    const ch_status cs = ch_ctx_create(c->device, nullptr, &l);
+    CHX_CHECK(cs == CH_OK, cs, "batch lane creation failed");
+    c->lanes.push_back(l);
+  }
+  // the lazy set passes run here, on c's stream, so that no two lanes race on them
+  for (int64_t i = 0; i < count; ++i) {
+    if (st[i] != CH_OK) continue;
+    const ch_set* X[2] = {A[i], B[i]};
+    for (const ch_set* x : X) {
+      if (params[i].hash.metric == CH_L2) ensure_norms(const_cast<ch_set*>(x), c->stream);
+      else ensure_ingest(const_cast<ch_set*>(x), c->stream);
+    }
+  }
+  // workspaces sized once, for the largest pair of each lane
+  std::vector<size_t> need(K, 0);
+  for (int64_t i = 0; i < count; ++i)
+    if (st[i] == CH_OK && A[i]->n > 0)
+      need[i % K] = std::max(need[i % K], estimate_need(c->lanes[i % K], A[i], B[i], &params[i], Ts[i], Rs[i]));
+  for (int k = 0; k < K; ++k) c->lanes[k]->ws.reserve(need[k]);
+  ResBlock* dres = nullptr;
+  CHX_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dres), sizeof(ResBlock) * count, c->pool, c->stream));
+  CHX_CUDA(cudaMemsetAsync(dres, 0, sizeof(ResBlock) * count, c->stream));
+  CHX_CUDA(cudaEventRecord(c->ev[7], c->stream));
+  for (int k = 0; k < K; ++k) CHX_CUDA(cudaStreamWaitEvent(c->lanes[k]->stream, c->ev[7], 0));
+  for (int64_t i = 0; i < count; ++i) {
+    if (st[i] != CH_OK || A[i]->n == 0) continue;
+    estimate_enqueue(c->lanes[i % K], A[i], B[i], &params[i], Ts[i], Rs[i], dres + i, false, nullptr);
+  }
+  for (int k = 0; k < K; ++k) {
+    CHX_CUDA(cudaEventRecord(c->lanes[k]->ev[7], c->lanes[k]->stream));
+    CHX_CUDA(cudaStreamWaitEvent(c->stream, c->lanes[k]->ev[7], 0));
+  }
+  const size_t bytes = sizeof(ResBlock) * count;
+  if (c->batch_pin_cap < bytes) {
+    if (c->batch_pin) cudaFreeHost(c->batch_pin);
+    c->batch_pin = nullptr;
+    c->batch_pin_cap = 0;
+    CHX_CUDA(cudaMallocHost(&c->batch_pin, bytes));
+    c->batch_pin_cap = bytes;
+  }
+  ResBlock* h = static_cast<ResBlock*>(c->batch_pin);
+  CHX_CUDA(cudaMemcpyAsync(h, dres, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CHX_CUDA(cudaFreeAsync(dres, c->stream));
+  CHX_CUDA(cudaStreamSynchronize(c->stream));
+  ch_status first = CH_OK;
+  for (int64_t i = 0; i < count; ++i) {
+    eta[i] = 0.0;
+    if (st[i] == CH_OK && A[i]->n > 0) {
+      try {
+        check_result(&h[i]);
+        eta[i] = h[i].eta;
+      } catch (const Err& e) {
+        st[i] = e.st;
+      }
+    }
+    if (status) status[i] = st[i];
+    if (first == CH_OK && st[i] != CH_OK) first = st[i];
+  }
+  if (first != CH_OK) c->err = "one or more pairs failed (see the per-pair status)";
+  return first;
   CHX_GUARD_END
 }
 

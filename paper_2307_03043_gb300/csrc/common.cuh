@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include <string>
+#include <vector>
 
 #include "../../include/chamfer.h"
 
@@ -102,6 +103,9 @@ struct ch_ctx {
   void* host_pin = nullptr;   // pinned page for small readbacks
   std::string err;
   cudaEvent_t ev[8] = {};
+  std::vector<ch_ctx*> lanes;  // sub-contexts (own streams) of batched calls, made on first use
+  void* batch_pin = nullptr;   // pinned result blocks of batched calls
+  size_t batch_pin_cap = 0;
 };
 
 struct ch_set {

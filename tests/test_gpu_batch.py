@@ -1,0 +1,75 @@
+"""ch_estimate_batch: many pairs in one call, each equal bit for bit to its own
+ch_estimate; failing pairs report their status without stopping the others."""
+import numpy as np
+import pytest
+
+from paper_2307_03043_gb300 import binding as ch
+from paper_2307_03043_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_03043_gb300 import build
+    build.build()
+    c = ch.ch_ctx_create(0, torch.cuda.current_stream())
+    yield c
+    ch.ch_ctx_destroy(c)
+
+
+def _pairs(ctx, n_pairs, d, seed):
+    sizes = workloads.log_uniform_sizes(2 * n_pairs, 100, 20_000, seed)
+    sets = []
+    for i in range(2 * n_pairs):
+        if d == 3:
+            X, _ = workloads.shape_surface(int(sizes[i]), 1, seed * 100 + i)
+        else:
+            X, _ = workloads.gaussian_mixture(int(sizes[i]), 1, d, seed * 100 + i, clusters=10)
+        sets.append(ch.ch_set_create(ctx, X, 0, X.shape[0], d))
+    return sets
+
+
+@pytest.mark.parametrize("d", [3, 64])
+def test_batch_equals_single(ctx, d):
+    sets = _pairs(ctx, 12, d, d)
+    A, B, P = [], [], []
+    for i in range(12):
+        for metric in (ch.CH_L1, ch.CH_L2):
+            A.append(sets[2 * i])
+            B.append(sets[2 * i + 1])
+            P.append(ch.est_params(metric, 10, 16, None, 3 * i + metric, eps=0.1, sample_seed=7 * i + metric))
+    # one set in several pairs, on different lanes
+    A.append(sets[0]); B.append(sets[3]); P.append(ch.est_params(ch.CH_L2, hash_seed=1, sample_seed=2))
+    A.append(sets[3]); B.append(sets[0]); P.append(ch.est_params(ch.CH_L2, hash_seed=1, sample_seed=2))
+    eta, st = ch.ch_estimate_batch(ctx, A, B, P)
+    assert all(s == ch.CH_OK for s in st)
+    for i in range(len(A)):
+        assert eta[i] == ch.ch_estimate(ctx, A[i], B[i], P[i]), i
+        assert eta[i] > 0
+    for s in sets:
+        ch.ch_set_destroy(s)
+
+
+def test_batch_failures_and_empty(ctx):
+    X, Y = workloads.uniform(500, 700, 8, 4)
+    sX = ch.ch_set_create(ctx, X, 0, 500, 8)
+    sY = ch.ch_set_create(ctx, Y, 0, 700, 8)
+    sE = ch.ch_set_create(ctx, np.zeros((0, 8), np.float32), 0, 0, 8)
+    bad = X.copy()
+    bad[7, 3] = np.inf
+    sBad = ch.ch_set_create(ctx, bad, 0, 500, 8)
+    A = [sX, sE, sX, sBad, sY]
+    B = [sY, sY, sE, sY, sX]
+    P = [ch.est_params(ch.CH_L2, T=300, hash_seed=k, sample_seed=k) for k in range(5)]
+    P[4] = ch.est_params(ch.CH_L1, T=0, eps=1.5)  # eps outside (0, 1)
+    eta, st = ch.ch_estimate_batch(ctx, A, B, P)
+    assert st == [ch.CH_OK, ch.CH_OK, ch.CH_EINVAL, ch.CH_EINVAL, ch.CH_EINVAL]
+    assert eta[0] == ch.ch_estimate(ctx, sX, sY, P[0])
+    assert eta[1] == 0.0 and eta[2] == 0.0 and eta[3] == 0.0 and eta[4] == 0.0
+    assert ch.ch_estimate_batch(ctx, [], [], []) == ([], [])
+    for s in (sX, sY, sE, sBad):
+        ch.ch_set_destroy(s)
