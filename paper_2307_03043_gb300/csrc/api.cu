@@ -14,6 +14,7 @@
 using namespace chx;
 
 #include <atomic>
+#include <thread>
 
 namespace chx {
 
@@ -870,9 +871,25 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
   CHX_CUDA(cudaMemsetAsync(dres, 0, sizeof(ResBlock) * count, c->stream));
   CHX_CUDA(cudaEventRecord(c->ev[7], c->stream));
   for (int k = 0; k < K; ++k) CHX_CUDA(cudaStreamWaitEvent(c->lanes[k]->stream, c->ev[7], 0));
-  for (int64_t i = 0; i < count; ++i) {
-    if (st[i] != CH_OK || A[i]->n == 0) continue;
-    estimate_enqueue(c->lanes[i % K], A[i], B[i], &params[i], Ts[i], Rs[i], dres + i, false, nullptr);
+  // one host thread per lane enqueues that lane's pairs (kernel launches are
+  // the host-side cost of small pairs); the sets' lazy state is already final
+  {
+    std::vector<std::thread> th;
+    for (int k = 0; k < K; ++k)
+      th.emplace_back([&, k] {
+        cudaSetDevice(c->device);
+        for (int64_t i = k; i < count; i += K) {
+          if (st[i] != CH_OK || A[i]->n == 0) continue;
+          try {
+            estimate_enqueue(c->lanes[k], A[i], B[i], &params[i], Ts[i], Rs[i], dres + i, false, nullptr);
+          } catch (const Err& e) {
+            st[i] = e.st;
+          } catch (...) {
+            st[i] = CH_ECUDA;
+          }
+        }
+      });
+    for (auto& t : th) t.join();
   }
   for (int k = 0; k < K; ++k) {
     CHX_CUDA(cudaEventRecord(c->lanes[k]->ev[7], c->lanes[k]->stream));

@@ -771,7 +771,7 @@ int launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* bo
   // the set's |x|^2 and finite check come for free with this pass
   ch_set* mut = const_cast<ch_set*>(X);
   float* norms = (X->ready & READY_NORMS) ? nullptr : X->norms;
-  mut->ready |= READY_NORMS;
+  if (norms) mut->ready |= READY_NORMS;  // no write when ready (sets may be shared by host threads)
   if (X->n == 0) {  // an empty box
     CHX_CUDA(cudaMemsetAsync(box, 0xFF, size_t(k) * 4, s));
     CHX_CUDA(cudaMemsetAsync(box + k, 0, size_t(k) * 4, s));

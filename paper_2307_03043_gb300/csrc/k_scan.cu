@@ -181,6 +181,96 @@ __global__ void __launch_bounds__(256) k_scan_exact(const void* __restrict__ A, 
   }
 }
 
+// Small dimensions (d <= 4, known at compile time): every partial p_r of the
+// canonical distance holds the single term of coordinate r, so the halving tree
+// reduces to a fixed expression, folded here at compile time.  A thread keeps
+// kSmallPQ samples in registers and walks a shared-memory tile of B (broadcast
+// reads); about 3d + 3 instructions per (sample, point) pair.
+constexpr int kSmallMaxD = 4;
+constexpr int kSmallPQ = 4;
+constexpr int kSmallBT = 1024;
+constexpr int kSmallQ = 256 * kSmallPQ;  // samples per block
+
+// partial R after tree steps 16 .. S (S = 32: the leaf) for d = D <= 32 terms
+template <int D, int R, int S>
+__device__ __forceinline__ float small_node(const float (&leaf)[D]) {
+  if constexpr (S == 32) {
+    return leaf[R];
+  } else if constexpr (R + S < D) {
+    return __fadd_rn(small_node<D, R, 2 * S>(leaf), small_node<D, R + S, 2 * S>(leaf));
+  } else {
+    return small_node<D, R, 2 * S>(leaf);
+  }
+}
+
+template <int DT, int METRIC, int D>
+__global__ void __launch_bounds__(256) k_scan_small(const void* __restrict__ A, const float* __restrict__ scA,
+                                                    const int64_t* __restrict__ qidx, int64_t T, int64_t nA,
+                                                    const void* __restrict__ B, const float* __restrict__ scB,
+                                                    int64_t nB, int64_t chunk_len, float* part_val,
+                                                    int64_t* part_idx) {
+  __shared__ float Bs[kSmallBT * D];
+  const int64_t l0 = int64_t(blockIdx.x) * kSmallQ + threadIdx.x;  // samples l0 + 256 p
+  const int64_t b_begin = int64_t(blockIdx.y) * chunk_len;
+  const int64_t b_end = min(nB, b_begin + chunk_len);
+  float q[kSmallPQ][D];
+  float best_val[kSmallPQ], best_p0[kSmallPQ];
+  int64_t best_idx[kSmallPQ];
+#pragma unroll
+  for (int p = 0; p < kSmallPQ; ++p) {
+    const int64_t l = l0 + 256 * p;
+    int64_t a = -1;
+    if (l < T) a = qidx ? qidx[l] : l;
+#pragma unroll
+    for (int j = 0; j < D; ++j) q[p][j] = (a >= 0 && a < nA) ? load_elem<DT>(A, a, D, j, scA) : 0.0f;
+    best_val[p] = __int_as_float(0x7F800000);
+    best_p0[p] = __int_as_float(0x7F800000);
+    best_idx[p] = INT64_MAX;
+  }
+  for (int64_t b0 = b_begin; b0 < b_end; b0 += kSmallBT) {
+    const int rows = static_cast<int>(min(static_cast<int64_t>(kSmallBT), b_end - b0));
+    __syncthreads();
+    for (int f = threadIdx.x; f < rows * D; f += 256) Bs[f] = load_elem<DT>(B, b0 + f / D, D, f % D, scB);
+    __syncthreads();
+    for (int r = 0; r < rows; ++r) {
+      float bv[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) bv[j] = Bs[r * D + j];
+#pragma unroll
+      for (int p = 0; p < kSmallPQ; ++p) {
+        float leaf[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const float t = __fsub_rn(q[p][j], bv[j]);
+          leaf[j] = (METRIC == CH_L1) ? fabsf(t) : __fmul_rn(t, t);
+        }
+        const float v = small_node<D, 0, 1>(leaf);
+        if (METRIC == CH_L1) {
+          if (v < best_val[p]) {
+            best_val[p] = v;
+            best_idx[p] = b0 + r;
+          }
+        } else if (v < best_p0[p]) {
+          best_p0[p] = v;
+          const float sv = __fsqrt_rn(v);
+          if (sv < best_val[p]) {
+            best_val[p] = sv;
+            best_idx[p] = b0 + r;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < kSmallPQ; ++p) {
+    const int64_t l = l0 + 256 * p;
+    if (l < T) {
+      part_val[int64_t(blockIdx.y) * T + l] = best_val[p];
+      part_idx[int64_t(blockIdx.y) * T + l] = best_idx[p];
+    }
+  }
+}
+
 __global__ void k_scan_merge(const float* part_val, const int64_t* part_idx, int chunks, int64_t T,
                              const int64_t* qidx, float* min_d, int64_t* argmin) {
   const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -216,6 +306,12 @@ static size_t scan_smem(int d) {
 }
 
 int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
+  if (d <= kSmallMaxD) {  // k_scan_small: about 4 blocks per SM, chunks of >= 256 points
+    const int64_t qblocks = ceil_div(std::max<int64_t>(T, 1), kSmallQ);
+    int64_t chunks = ceil_div(int64_t(sm_count) * 4, qblocks);
+    chunks = std::min<int64_t>(chunks, ceil_div(nB, 256));
+    return static_cast<int>(std::max<int64_t>(chunks, 1));
+  }
   const TileShape t = tile_for(d);
   const int64_t qtiles = ceil_div(std::max<int64_t>(T, 1), t.QT);
   const int64_t target = int64_t(sm_count) * 4;
@@ -249,9 +345,36 @@ static void scan_shape(const ch_set* A, const int64_t* qidx, int64_t T, const ch
     scan_launch<DT, METRIC, 16, 16, 1, 1>(A, qidx, T, B, part, s);
 }
 
+template <int DT, int METRIC, int D>
+static void scan_small_launch(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, ScanPart part,
+                              cudaStream_t s) {
+  const int64_t chunk_len = ceil_div(B->n, part.chunks);
+  dim3 grid(static_cast<unsigned>(ceil_div(T, kSmallQ)), static_cast<unsigned>(part.chunks));
+  k_scan_small<DT, METRIC, D><<<grid, 256, 0, s>>>(A->data, A->scales, qidx, T, A->n, B->data, B->scales, B->n,
+                                                   chunk_len, part.val, part.idx);
+}
+
+template <int DT, int METRIC>
+static void scan_small(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, ScanPart part,
+                       cudaStream_t s) {
+  switch (A->d) {
+    case 1: scan_small_launch<DT, METRIC, 1>(A, qidx, T, B, part, s); break;
+    case 2: scan_small_launch<DT, METRIC, 2>(A, qidx, T, B, part, s); break;
+    case 3: scan_small_launch<DT, METRIC, 3>(A, qidx, T, B, part, s); break;
+    default: scan_small_launch<DT, METRIC, 4>(A, qidx, T, B, part, s); break;
+  }
+}
+
 template <int DT>
 static void scan_metric(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int metric, ScanPart part,
                         cudaStream_t s) {
+  if (A->d <= kSmallMaxD) {
+    if (metric == CH_L1)
+      scan_small<DT, CH_L1>(A, qidx, T, B, part, s);
+    else
+      scan_small<DT, CH_L2>(A, qidx, T, B, part, s);
+    return;
+  }
   if (metric == CH_L1)
     scan_shape<DT, CH_L1>(A, qidx, T, B, part, s);
   else

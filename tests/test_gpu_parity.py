@@ -281,6 +281,33 @@ def test_sampled_nn_exact_bit_exact(ctx, pair_factory, metric, nA, nB, d, T):
     assert np.all(m[~ok] == 0) and np.all(am[~ok] == -1)
 
 
+@pytest.mark.parametrize("dtype", [ch.CH_F32, ch.CH_BF16, ch.CH_FP8E4M3], ids=["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_small_d_scan_bit_exact(ctx, dtype, d):
+    """The compile-time-dimension scan (d <= 4): several sample blocks and B
+    chunks, duplicated points in B (ties resolved to the smallest index)."""
+    keep = []
+    A32, B32 = workloads.gaussian_mixture(3000, 5000, d, 40 + d, clusters=6)
+    B32[4000:4500] = B32[100:600]  # exact duplicates
+    sA, Ad = _typed_set(ctx, A32, dtype, keep)
+    sB, Bd = _typed_set(ctx, B32, dtype, keep)
+    T = 2600
+    idx = np.random.default_rng(d).integers(0, 3000, T).astype(np.int64)
+    idx[5::31] = -1
+    for metric in (L1, L2):
+        m = torch.zeros(T, dtype=torch.float32, device="cuda")
+        am = torch.zeros(T, dtype=torch.int64, device="cuda")
+        ch.ch_sampled_nn(ctx, sA, dev(idx), T, sB, metric, ch.CH_SCREEN_EXACT, 8, m, am)
+        m, am = m.cpu().numpy(), am.cpu().numpy()
+        ok = idx >= 0
+        mo, amo = oracle.scan(Ad, idx[ok], Bd, metric)
+        assert np.array_equal(m[ok].view(np.uint32), mo.view(np.uint32))
+        assert np.array_equal(am[ok], amo)
+        assert np.all(m[~ok] == 0) and np.all(am[~ok] == -1)
+    ch.ch_set_destroy(sA)
+    ch.ch_set_destroy(sB)
+
+
 @pytest.mark.parametrize("metric", [L1, L2])
 def test_exact_matches_oracle(ctx, pair_factory, metric):
     A, B = workloads.uniform(1500, 1300, 16, 21)
@@ -291,6 +318,12 @@ def test_exact_matches_oracle(ctx, pair_factory, metric):
     assert np.array_equal(mins.cpu().numpy(), mo)
     assert abs(v / vo - 1) < 1e-12
     assert abs(v / oracle.exact_fp64(A, B, metric) - 1) < 1e-5
+    A3, B3 = workloads.shape_surface(2100, 1900, 5)
+    p3 = pair_factory(A3, B3)
+    mins3 = torch.zeros(2100, dtype=torch.float32, device="cuda")
+    v3 = ch.ch_exact(ctx, p3.sA, p3.sB, metric, 0, mins3)
+    vo3, mo3 = oracle.exact_canonical(A3, B3, metric)
+    assert np.array_equal(mins3.cpu().numpy(), mo3) and abs(v3 / vo3 - 1) < 1e-12
 
 
 # ------------------------------------------------------------------ estimate
