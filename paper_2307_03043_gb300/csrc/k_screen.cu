@@ -41,7 +41,6 @@ constexpr int kMaxChunks = 32;
 // evaluates exactly.
 constexpr int kOcc = 4;
 constexpr int kClasses = kSliceCols / kOcc;  // 32
-constexpr int kMaxCand = 512;  // screened candidates per sample handed to the rerank
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -440,106 +439,6 @@ __global__ void k_gather_rows(const uint8_t* A, const float* scA, int64_t nA, in
   if (sQ && w == 0) sQ[row] = (a >= 0 && a < nA) ? scA[a] : 1.0f;
 }
 
-// One warp per sample: the R best screened entries over all chunks (by s, then
-// index), the canonical binary32 distance of each of an entry's occ columns
-// (first column + o * stride, o < occ, columns < nB), and their minimum (ties:
-// smaller index).
-template <int DT, int METRIC>
-__global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA, int64_t nA, const void* B,
-                                                const float* scB, int64_t nB, int d, const int64_t* idx, int64_t T,
-                                                const float* part_s, const int32_t* part_i, int parts, int per,
-                                                int occ, int stride, int R, float* min_d, int64_t* argmin) {
-  __shared__ float s_s[8][kMaxCand];
-  __shared__ int32_t s_i[8][kMaxCand];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t l = int64_t(blockIdx.x) * 8 + wib;
-  if (l >= T) return;
-  const int64_t a = idx ? idx[l] : l;
-  if (a < 0 || a >= nA) {
-    if (lane == 0) {
-      min_d[l] = 0.0f;
-      if (argmin) argmin[l] = -1;
-    }
-    return;
-  }
-  const int nc = parts * per;
-  for (int p = lane; p < nc; p += 32) {
-    const int c = p / per, k = p % per;
-    const size_t off = (size_t(c) * T + l) * per + k;
-    s_s[wib][p] = part_s[off];
-    s_i[wib][p] = part_i[off];
-  }
-  __syncwarp();
-  float best = __int_as_float(0x7F800000);
-  int64_t bidx = INT64_MAX;
-  for (int round = 0; round < R; ++round) {
-    float ms = __int_as_float(0x7F800000);
-    int32_t mi = INT32_MAX;
-    int mp = -1;
-    for (int p = lane; p < nc; p += 32) {
-      const float v = s_s[wib][p];
-      const int32_t i = s_i[wib][p];
-      if (i >= 0 && (v < ms || (v == ms && i < mi))) {
-        ms = v;
-        mi = i;
-        mp = p;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float os = __shfl_xor_sync(0xFFFFFFFFu, ms, o);
-      const int32_t oi = __shfl_xor_sync(0xFFFFFFFFu, mi, o);
-      const int op = __shfl_xor_sync(0xFFFFFFFFu, mp, o);
-      if (os < ms || (os == ms && oi < mi)) {
-        ms = os;
-        mi = oi;
-        mp = op;
-      }
-    }
-    if (mi == INT32_MAX || mi < 0) break;  // fewer than R entries
-    if (lane == (mp & 31)) s_i[wib][mp] = -1;  // taken
-    __syncwarp();
-    // canonical distances to the entry's columns, all at once (lane r sums
-    // coordinates j = r mod 32 of each; the reduction trees run side by side)
-    int64_t bo[kOcc];
-    bool vo[kOcc];
-    float part[kOcc];
-#pragma unroll
-    for (int o = 0; o < kOcc; ++o) {
-      bo[o] = int64_t(mi) + int64_t(o) * stride;
-      vo[o] = o < occ && bo[o] < nB;
-      part[o] = 0.0f;
-    }
-    for (int j = lane; j < d; j += 32) {
-      const float x = load_elem<DT>(A, a, d, j, scA);
-#pragma unroll
-      for (int o = 0; o < kOcc; ++o) {
-        if (vo[o]) {
-          const float t = __fsub_rn(x, load_elem<DT>(B, bo[o], d, j, scB));
-          part[o] = (METRIC == CH_L1) ? __fadd_rn(part[o], fabsf(t)) : __fmaf_rn(t, t, part[o]);
-        }
-      }
-    }
-#pragma unroll
-    for (int sh = 16; sh >= 1; sh >>= 1) {
-#pragma unroll
-      for (int o = 0; o < kOcc; ++o) part[o] = __fadd_rn(part[o], __shfl_down_sync(0xFFFFFFFFu, part[o], sh));
-    }
-#pragma unroll
-    for (int o = 0; o < kOcc; ++o) {
-      const float dist = __shfl_sync(0xFFFFFFFFu, (METRIC == CH_L1) ? part[o] : __fsqrt_rn(part[o]), 0);
-      if (vo[o] && (dist < best || (dist == best && bo[o] < bidx))) {
-        best = dist;
-        bidx = bo[o];
-      }
-    }
-  }
-  if (lane == 0) {
-    min_d[l] = best;
-    if (argmin) argmin[l] = bidx;
-  }
-}
-
 CUtensorMap make_map(const void* base, int dtype, int64_t rows, int d, int box_rows) {
   CUtensorMap m;
   const int es = static_cast<int>(elem_size(dtype));
@@ -583,7 +482,7 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   int best_c = 1;
   double best_eff = 0.0;
   for (int c = 1; c <= kMaxChunks && c <= btiles; ++c) {
-    if (kSlices * c * kClasses > kMaxCand) break;  // kSlices column slices per chunk
+    if (kSlices * c * kClasses > kRerankMaxCand) break;  // kSlices column slices per chunk
     const int64_t items = int64_t(p.row_tiles) * c;
     const int64_t rounds = ceil_div(items, sm_count);
     const double eff = double(items) / double(rounds * sm_count);
@@ -686,17 +585,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
 #undef CHX_SCREEN_LAUNCH
   launch_check("screen");
 
-  const int blocks = static_cast<int>(ceil_div(T, 8));
-  if (A->dtype == CH_F32)
-    k_rerank<CH_F32, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T, part_s,
-                                                   part_i, kSlices * p.chunks, kClasses, kOcc, kClasses, p.R, min_d, argmin);
-  else if (A->dtype == CH_BF16)
-    k_rerank<CH_BF16, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T,
-                                                    part_s, part_i, kSlices * p.chunks, kClasses, kOcc, kClasses, p.R, min_d, argmin);
-  else
-    k_rerank<CH_FP8E4M3, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T,
-                                                       part_s, part_i, kSlices * p.chunks, kClasses, kOcc, kClasses, p.R, min_d, argmin);
-  launch_check("rerank");
+  launch_rerank(A, qidx, T, B, part_s, part_i, kSlices * p.chunks, kClasses, kOcc, kClasses, p.R, min_d, argmin, s);
 }
 
 }  // namespace chx
