@@ -468,19 +468,44 @@ static size_t project_async_smem() {
 
 // TMA-streamed projection (rows whose byte length is a multiple of 16, KP <= 16).
 // A persistent grid of one block per SM; every warp is its own pipeline over
-// 32-row tiles: lane 0 streams 128-byte slices of the tile's rows (one TMA box
-// of 32 rows x 128 bytes, 128-byte swizzle) through two stages, each lane owns
-// one row.  The Gaussian matrix is generated into shared memory by each block
-// (same entries as k_gauss) while the first slices are in flight.  Per row:
-// y_i = fmaf chain over j in increasing order, |x|^2 likewise, so the results
-// are those of k_project bit for bit.  The box of y is kept per lane in
-// registers and merged once per warp at the end.
-// warps per block: 20 for binary32 rows (96 registers a thread), 16 for the
-// narrower types, whose unpacking needs more registers
+// 64-row tiles: lane 0 streams 128-byte slices of the tile's rows (one TMA box
+// of 64 rows x 128 bytes, 128-byte swizzle) through two stages; lane l owns rows
+// l and l + 32, so every Gaussian-matrix load from shared memory feeds two rows.
+// The matrix is generated into shared memory by each block (same entries as
+// k_gauss) while the first slices are in flight.  Per row: y_i = fmaf chain over
+// j in increasing order, |x|^2 likewise, so the results are those of k_project
+// bit for bit.  The box of y: after each tile a transposing butterfly leaves
+// lane l the tile's min and max of output l / (32 / KP), kept across tiles in
+// two registers; one partial box per block at the end.
 template <int DT>
-constexpr int pt_max_warps() { return DT == CH_F32 ? 20 : 16; }
+constexpr int pt_max_warps() { return 13; }
 constexpr int kPTBox = 128;            // bytes of a row per slice
-constexpr int kPTStage = 32 * kPTBox;  // one 32-row box
+constexpr int kPTRows = 64;            // rows per tile (two per lane)
+constexpr int kPTStage = kPTRows * kPTBox;
+
+// butterfly over the warp that reduces KP values per lane to one value per lane:
+// afterwards lane l holds the min (MIN) or max over all lanes of value l / (32 / KP)
+template <int KP, bool MIN>
+__device__ __forceinline__ float pt_xreduce(float (&v)[KP], int lane) {
+  int x = 16;
+#pragma unroll
+  for (int w = KP / 2; w >= 1; w >>= 1, x >>= 1) {
+    const bool up = (lane & x) != 0;
+#pragma unroll
+    for (int q = 0; q < w; ++q) {
+      const float keep = up ? v[q + w] : v[q];
+      const float send = up ? v[q] : v[q + w];
+      const float got = __shfl_xor_sync(0xFFFFFFFFu, send, x);
+      v[q] = MIN ? fminf(keep, got) : fmaxf(keep, got);
+    }
+  }
+  float r = v[0];
+  for (; x >= 1; x >>= 1) {
+    const float got = __shfl_xor_sync(0xFFFFFFFFu, r, x);
+    r = MIN ? fminf(r, got) : fmaxf(r, got);
+  }
+  return r;
+}
 
 template <int DT, int KP>
 __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
@@ -499,7 +524,7 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
   float* sG = reinterpret_cast<float*>(base + size_t(warps) * 2 * kPTStage);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sG + size_t(d) * KP) + 2 * warp;
 
-  const int64_t ntiles = (n + 31) >> 5;
+  const int64_t ntiles = (n + kPTRows - 1) / kPTRows;
   const int slices = (d + SLICE - 1) / SLICE;
   const int64_t gw = int64_t(blockIdx.x) * warps + warp, stride = int64_t(gridDim.x) * warps;
   const int64_t my_tiles = gw < ntiles ? (ntiles - gw + stride - 1) / stride : 0;
@@ -518,7 +543,7 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
   auto issue = [&](int64_t it) {  // lane 0: item it -> stage it & 1
     uint64_t* b = &bar[it & 1];
     mbar_expect_tx(b, kPTStage);
-    tma_load_2d(stage + (it & 1) * kPTStage, &map, psl * kPTBox, static_cast<int>(pt * 32), b);
+    tma_load_2d(stage + (it & 1) * kPTStage, &map, psl * kPTBox, static_cast<int>(pt * kPTRows), b);
     if (++psl == slices) {
       psl = 0;
       pt += stride;
@@ -533,57 +558,73 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
   for (int t = threadIdx.x; t < d * KP; t += blockDim.x) sG[t] = gauss_entry(seed, k, t / KP, t % KP);
   __syncthreads();
 
-  float lo[KP], hi[KP], acc[KP];
+  float acc[2][KP], sq[2];
 #pragma unroll
-  for (int i = 0; i < KP; ++i) {
-    lo[i] = __int_as_float(0x7F800000);
-    hi[i] = __int_as_float(0xFF800000);
-    acc[i] = 0.0f;
+  for (int r = 0; r < 2; ++r) {
+    sq[r] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < KP; ++i) acc[r][i] = 0.0f;
   }
-  float sq = 0.0f;
+  float run_lo = __int_as_float(0x7F800000), run_hi = __int_as_float(0xFF800000);
   bool ok = true;
   int64_t it = 0;
   int64_t t = gw;  // consumer's tile and slice
   int sl = 0;
   for (; it < items; ++it) {
-    const float scl = (DT == CH_FP8E4M3 && t * 32 + lane < n) ? scales[t * 32 + lane] : 1.0f;
+    float scl[2] = {1.0f, 1.0f};
+    if constexpr (DT == CH_FP8E4M3) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int64_t row = t * kPTRows + lane + 32 * r;
+        scl[r] = row < n ? scales[row] : 1.0f;
+      }
+    }
     ok = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(&bar[it & 1], static_cast<uint32_t>((it >> 1) & 1)));
     if (!ok) break;
-    const uint4* row = reinterpret_cast<const uint4*>(stage + (it & 1) * kPTStage + lane * kPTBox);
+    const uint4* rows[2] = {reinterpret_cast<const uint4*>(stage + (it & 1) * kPTStage + lane * kPTBox),
+                            reinterpret_cast<const uint4*>(stage + (it & 1) * kPTStage + (lane + 32) * kPTBox)};
     const int j0 = sl * SLICE;
     const int jn = min(SLICE, d - j0);
     auto chunk = [&](int c, int lim) {
-      const uint4 raw = row[c ^ (lane & 7)];
-      float xv[PER];
-      if constexpr (DT == CH_F32) {
-        xv[0] = __uint_as_float(raw.x);
-        xv[1] = __uint_as_float(raw.y);
-        xv[2] = __uint_as_float(raw.z);
-        xv[3] = __uint_as_float(raw.w);
-      } else if constexpr (DT == CH_BF16) {
-        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+      float xv[2][PER];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          xv[2 * e] = __uint_as_float(w4[e] << 16);
-          xv[2 * e + 1] = __uint_as_float(w4[e] & 0xFFFF0000u);
+      for (int r = 0; r < 2; ++r) {
+        const uint4 raw = rows[r][c ^ (lane & 7)];
+        if constexpr (DT == CH_F32) {
+          xv[r][0] = __uint_as_float(raw.x);
+          xv[r][1] = __uint_as_float(raw.y);
+          xv[r][2] = __uint_as_float(raw.z);
+          xv[r][3] = __uint_as_float(raw.w);
+        } else if constexpr (DT == CH_BF16) {
+          const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            xv[r][2 * e] = __uint_as_float(w4[e] << 16);
+            xv[r][2 * e + 1] = __uint_as_float(w4[e] & 0xFFFF0000u);
+          }
+        } else {
+          const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            xv[r][e] = __fmul_rn(e4m3_to_f32(static_cast<uint8_t>(w4[e / 4] >> (8 * (e % 4)))), scl[r]);
         }
-      } else {
-        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-        for (int e = 0; e < 16; ++e) xv[e] = __fmul_rn(e4m3_to_f32(static_cast<uint8_t>(w4[e / 4] >> (8 * (e % 4)))), scl);
       }
 #pragma unroll
       for (int e = 0; e < PER; ++e) {
         if (e < lim) {
-          sq = fmaf(xv[e], xv[e], sq);
+#pragma unroll
+          for (int r = 0; r < 2; ++r) sq[r] = fmaf(xv[r][e], xv[r][e], sq[r]);
           const float4* g4 = reinterpret_cast<const float4*>(sG + (j0 + c * PER + e) * KP);
 #pragma unroll
           for (int i4 = 0; i4 < KP / 4; ++i4) {
             const float4 gv = g4[i4];
-            acc[4 * i4 + 0] = __fmaf_rn(gv.x, xv[e], acc[4 * i4 + 0]);
-            acc[4 * i4 + 1] = __fmaf_rn(gv.y, xv[e], acc[4 * i4 + 1]);
-            acc[4 * i4 + 2] = __fmaf_rn(gv.z, xv[e], acc[4 * i4 + 2]);
-            acc[4 * i4 + 3] = __fmaf_rn(gv.w, xv[e], acc[4 * i4 + 3]);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              acc[r][4 * i4 + 0] = __fmaf_rn(gv.x, xv[r][e], acc[r][4 * i4 + 0]);
+              acc[r][4 * i4 + 1] = __fmaf_rn(gv.y, xv[r][e], acc[r][4 * i4 + 1]);
+              acc[r][4 * i4 + 2] = __fmaf_rn(gv.z, xv[r][e], acc[r][4 * i4 + 2]);
+              acc[r][4 * i4 + 3] = __fmaf_rn(gv.w, xv[r][e], acc[r][4 * i4 + 3]);
+            }
           }
         }
       }
@@ -600,33 +641,44 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
       issue(it + 2);
     }
     if (sl == slices - 1) {  // the tile's rows are complete
-      const int64_t r = t * 32 + lane;
-      if (r < n) {
-        if (KP == 16 && k == 16) {
-          float4* y4 = reinterpret_cast<float4*>(Y + r * 16);
+      float tlo[KP], thi[KP];
 #pragma unroll
-          for (int i4 = 0; i4 < 4; ++i4)
-            y4[i4] = make_float4(acc[4 * i4], acc[4 * i4 + 1], acc[4 * i4 + 2], acc[4 * i4 + 3]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < KP; ++i)
-            if (i < k) Y[r * k + i] = acc[i];
-        }
-        if (norms) norms[r] = sq;
-#pragma unroll
-        for (int i = 0; i < KP; ++i) {
-          lo[i] = fminf(lo[i], acc[i]);
-          hi[i] = fmaxf(hi[i], acc[i]);
-        }
-        if (!isfinite(sq)) {  // a non-finite coordinate, or only an overflowing square: look again
-          bool bad = false;
-          for (int j = 0; j < d; ++j) bad |= !isfinite(load_elem<DT>(X, r, d, j, scales));
-          if (bad) atomicOr(status, ST_NONFINITE);
-        }
+      for (int i = 0; i < KP; ++i) {
+        tlo[i] = __int_as_float(0x7F800000);
+        thi[i] = __int_as_float(0xFF800000);
       }
 #pragma unroll
-      for (int i = 0; i < KP; ++i) acc[i] = 0.0f;
-      sq = 0.0f;
+      for (int r = 0; r < 2; ++r) {
+        const int64_t row = t * kPTRows + lane + 32 * r;
+        if (row < n) {
+          if (KP == 16 && k == 16) {
+            float4* y4 = reinterpret_cast<float4*>(Y + row * 16);
+#pragma unroll
+            for (int i4 = 0; i4 < 4; ++i4)
+              y4[i4] = make_float4(acc[r][4 * i4], acc[r][4 * i4 + 1], acc[r][4 * i4 + 2], acc[r][4 * i4 + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < KP; ++i)
+              if (i < k) Y[row * k + i] = acc[r][i];
+          }
+          if (norms) norms[row] = sq[r];
+#pragma unroll
+          for (int i = 0; i < KP; ++i) {
+            tlo[i] = fminf(tlo[i], acc[r][i]);
+            thi[i] = fmaxf(thi[i], acc[r][i]);
+          }
+          if (!isfinite(sq[r])) {  // a non-finite coordinate, or only an overflowing square: look again
+            bool bad = false;
+            for (int j = 0; j < d; ++j) bad |= !isfinite(load_elem<DT>(X, row, d, j, scales));
+            if (bad) atomicOr(status, ST_NONFINITE);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < KP; ++i) acc[r][i] = 0.0f;
+        sq[r] = 0.0f;
+      }
+      run_lo = fminf(run_lo, pt_xreduce<KP, true>(tlo, lane));
+      run_hi = fmaxf(run_hi, pt_xreduce<KP, false>(thi, lane));
     }
     if (++sl == slices) {
       sl = 0;
@@ -640,21 +692,11 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
     for (int64_t j = it; j < items && j < it + 2; ++j)
       mbar_wait_bounded(&bar[j & 1], static_cast<uint32_t>((j >> 1) & 1));
   }
-  // box of y: lanes -> warp (shuffles) -> block (shared atomics) -> one partial
-  // box per block, written whole (no global atomics; the scale-table kernel
-  // takes the min / max over the blocks' partial boxes)
-#pragma unroll
-  for (int i = 0; i < KP; ++i) {
-    float l = lo[i], h = hi[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      l = fminf(l, __shfl_xor_sync(0xFFFFFFFFu, l, o));
-      h = fmaxf(h, __shfl_xor_sync(0xFFFFFFFFu, h, o));
-    }
-    if (lane == 0 && i < k && l <= h) {
-      atomicMin(&s_box[i], ord_enc(l));
-      atomicMax(&s_box[KP + i], ord_enc(h));
-    }
+  // lane l holds output o = l / (32 / KP); one lane per output merges into the block's box
+  const int o = lane / (32 / KP);
+  if (lane % (32 / KP) == 0 && o < k && run_lo <= run_hi) {
+    atomicMin(&s_box[o], ord_enc(run_lo));
+    atomicMax(&s_box[KP + o], ord_enc(run_hi));
   }
   __syncthreads();
   if (threadIdx.x < 2 * k) {
@@ -673,9 +715,9 @@ template <int DT>
 static int project_tma_warps(const ch_set* X, int kp) {
   if (kp > 16) return 0;
   if ((int64_t(X->d) * int64_t(elem_size(DT))) % 16 != 0 || (reinterpret_cast<uintptr_t>(X->data) & 15) != 0) return 0;
-  if (X->n >= (int64_t(1) << 31) - 32) return 0;
+  if (X->n >= (int64_t(1) << 31) - kPTRows) return 0;
   const size_t budget = 226 * 1024;  // leaves room for the kernel's static shared memory
-  for (int w = pt_max_warps<DT>(); w >= 4; w -= 2)
+  for (int w = pt_max_warps<DT>(); w >= 4; --w)
     if (project_tma_smem<DT>(w, X->d, kp) <= budget) return w;
   return 0;
 }
@@ -686,7 +728,7 @@ static CUtensorMap project_map(const ch_set* X) {
   const cuuint64_t rb = static_cast<cuuint64_t>(X->d) * elem_size(DT);
   cuuint64_t dims[2] = {rb, static_cast<cuuint64_t>(X->n)};
   cuuint64_t strides[1] = {rb};
-  cuuint32_t boxd[2] = {static_cast<cuuint32_t>(kPTBox), 32u};
+  cuuint32_t boxd[2] = {static_cast<cuuint32_t>(kPTBox), static_cast<cuuint32_t>(kPTRows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(X->data), dims, strides, boxd, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -737,7 +779,7 @@ static int launch_project_tma(const ch_set* X, uint64_t seed, int k, float* Y, u
   }();
   (void)attr;
   const CUtensorMap map = project_map<DT>(X);
-  const int64_t ntiles = ceil_div(X->n, 32);
+  const int64_t ntiles = ceil_div(X->n, kPTRows);
   const int grid = static_cast<int>(std::min<int64_t>(std::min(sm_count, kMaxBoxParts), ceil_div(ntiles, warps)));
   k_project_tma<DT, KP><<<grid, warps * 32, project_tma_smem<DT>(warps, X->d, KP), s>>>(
       map, X->data, X->scales, X->n, X->d, seed, k, Y, box, norms, X->status);
