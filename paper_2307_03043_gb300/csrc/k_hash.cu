@@ -526,7 +526,8 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
 
   const int64_t ntiles = (n + kPTRows - 1) / kPTRows;
   const int slices = (d + SLICE - 1) / SLICE;
-  const int64_t gw = int64_t(blockIdx.x) * warps + warp, stride = int64_t(gridDim.x) * warps;
+  // tiles go round-robin over the blocks first, so that the blocks' loads differ by one tile at most
+  const int64_t gw = int64_t(warp) * gridDim.x + blockIdx.x, stride = int64_t(gridDim.x) * warps;
   const int64_t my_tiles = gw < ntiles ? (ntiles - gw + stride - 1) / stride : 0;
   const int64_t items = my_tiles * slices;
 
@@ -780,7 +781,12 @@ static int launch_project_tma(const ch_set* X, uint64_t seed, int k, float* Y, u
   (void)attr;
   const CUtensorMap map = project_map<DT>(X);
   const int64_t ntiles = ceil_div(X->n, kPTRows);
-  const int grid = static_cast<int>(std::min<int64_t>(std::min(sm_count, kMaxBoxParts), ceil_div(ntiles, warps)));
+  const int sms = std::min(sm_count, kMaxBoxParts);
+  // as few warps per block as cover the tiles in the same number of rounds, so
+  // that every SM gets a block
+  const int64_t rounds = ceil_div(ntiles, int64_t(sms) * warps);
+  warps = static_cast<int>(std::min<int64_t>(warps, ceil_div(ntiles, int64_t(sms) * rounds)));
+  const int grid = static_cast<int>(std::min<int64_t>(sms, ntiles));
   k_project_tma<DT, KP><<<grid, warps * 32, project_tma_smem<DT>(warps, X->d, KP), s>>>(
       map, X->data, X->scales, X->n, X->d, seed, k, Y, box, norms, X->status);
   return grid;
