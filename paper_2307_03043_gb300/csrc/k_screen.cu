@@ -130,7 +130,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 struct ScreenArgs {
   int64_t T;          // samples (rows of Q)
   int64_t nB;
-  int kblocks;        // K blocks of 128 bytes: ceil(d * elem / 128), + 1 with the augmented block
+  int kblocks;        // ceil(d * elem / 128)
   int row_tiles;
   int chunks;
   int64_t chunk_len;  // B points per chunk (multiple of kBN)
@@ -143,19 +143,9 @@ struct ScreenArgs {
   uint32_t* status;
 };
 
-// TF32 / BF16: the contraction carries -|b|^2 / 2 in one extra 128-byte K block
-// (three exact pieces of it against ones in the sample's extra block), so the
-// accumulator holds q.b - |b|^2 / 2, whose maximum over b is the nearest b; the
-// epilogue is then one max per element.  FP8 keeps per-row scales outside the
-// contraction and forms the score in the epilogue.
-template <int SCREEN>
-__host__ __device__ constexpr bool screen_aug() { return SCREEN != CH_SCREEN_FP8; }
-
 template <int SCREEN>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_screen(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmB,
-             const __grid_constant__ CUtensorMap tmBa, ScreenArgs args) {
-  constexpr bool AUG = screen_aug<SCREEN>();
+    k_screen(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmB, ScreenArgs args) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned by an offset from the shared array itself, so that the
   // compiler keeps every access below in the shared state space
@@ -164,10 +154,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int S = args.stages;
   uint8_t* q_smem = smem;                                 // KB x (128 rows x 128 B)
   uint8_t* b_smem = q_smem + size_t(KB) * kBM * kKB;      // S x (256 rows x 128 B)
-  constexpr int kStaging = AUG ? 0 : 2 * kEpiWarps * kSliceCols;  // FP8 only
-  float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [warps][2][slice] |b|^2
-  float* sb_s = nb_s + kStaging;                                           // [warps][2][slice] -2 x FP8 scale
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sb_s + kStaging);
+  float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [warps][2][64] |b|^2
+  float* sb_s = nb_s + 2 * kEpiWarps * kSliceCols;                         // [warps][2][64] -2 x FP8 scale
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sb_s + 2 * kEpiWarps * kSliceCols);
   uint64_t* full = bars;            // [S]
   uint64_t* empty = bars + S;       // [S]
   uint64_t* q_full = bars + 2 * S;  // [1]
@@ -227,12 +216,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             mbar_expect_tx(&full[stage], uint32_t(kBN) * kKB);
-            if (AUG && kb == KB - 1)
-              tma_load_2d(b_smem + size_t(stage) * kBN * kKB, &tmBa, 0, static_cast<int>(b0), &full[stage]);
-            else
-              tma_load_2d(b_smem + size_t(stage) * kBN * kKB, &tmB,
-                          kb * kKB / (SCREEN == CH_SCREEN_TF32 ? 4 : SCREEN == CH_SCREEN_BF16 ? 2 : 1),
-                          static_cast<int>(b0), &full[stage]);
+            tma_load_2d(b_smem + size_t(stage) * kBN * kKB, &tmB,
+                        kb * kKB / (SCREEN == CH_SCREEN_TF32 ? 4 : SCREEN == CH_SCREEN_BF16 ? 2 : 1),
+                        static_cast<int>(b0), &full[stage]);
             if (++stage == S) {
               stage = 0;
               phase ^= 1;
@@ -267,9 +253,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t qa = su32(q_smem + size_t(kb) * kBM * kKB);
             const uint32_t ba = su32(b_smem + size_t(stage) * kBN * kKB);
-            // 32 bytes of K per instruction; the augmented block's pieces sit in its first 32 bytes
-            const int ksteps = (AUG && kb == KB - 1) ? 1 : kKB / 32;
-            for (int k = 0; k < ksteps; ++k)
+#pragma unroll
+            for (int k = 0; k < kKB / 32; ++k)  // 32 bytes of K per instruction
               tc_mma<SCREEN>(dtmem, sdesc(qa + k * 32), sdesc(ba + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
             tc_commit(&empty[stage]);
             if (++stage == S) {
@@ -301,20 +286,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t grow = int64_t(mt) * kBM + row;
       float sq = 1.0f;
       if constexpr (SCREEN == CH_SCREEN_FP8) sq = (grow < args.T) ? args.scaleQ[grow] : 1.0f;
-      // running best per residue class of this warp's slice (AUG: the largest
-      // q.b - |b|^2/2; otherwise the smallest score); best_c holds its tile
-      const float kWorst = AUG ? -INFINITY : INFINITY;
+      // running minima per residue class of this warp's slice; best_c holds the
+      // tile (within the chunk) of each minimum
       float best_s[kClasses];
       int32_t best_c[kClasses];
 #pragma unroll
       for (int i = 0; i < kClasses; ++i) {
-        best_s[i] = kWorst;
+        best_s[i] = __int_as_float(0x7F800000);
         best_c[i] = -1;
       }
       int32_t tile = 0;  // tile index within the chunk
-      // FP8: |b|^2 and -2 x scale of this lane's columns of a tile slice, fetched
-      // one tile ahead so the load latency hides behind a tile of work; +inf past
-      // the end of the chunk
+      // |b|^2 (and -2 x FP8 scale) of this lane's columns of a tile slice,
+      // fetched one tile ahead so the load latency hides behind a tile of work;
+      // +inf past the end of the chunk
       constexpr int kPer = kSliceCols / 32;
       float pn[kPer], ps[kPer];
       auto prefetch_norms = [&](int64_t t0) {
@@ -323,26 +307,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < kPer; ++k) {
           const int64_t b = base + lane + 32 * k;
           pn[k] = (b < b_end) ? __ldg(&args.normB[b]) : __int_as_float(0x7F800000);
-          ps[k] = (b < b_end) ? -2.0f * __ldg(&args.scaleB[b]) : 0.0f;
+          ps[k] = 0.0f;
+          if constexpr (SCREEN == CH_SCREEN_FP8) ps[k] = (b < b_end) ? -2.0f * __ldg(&args.scaleB[b]) : 0.0f;
         }
       };
-      if constexpr (!AUG) prefetch_norms(b_begin);
+      prefetch_norms(b_begin);
       bool ok = true;
       for (int64_t b0 = b_begin; b0 < b_end; b0 += kBN) {
-        // FP8: stage |b|^2 and -2 x scale of this tile in this warp's own buffer.
-        // Only __syncwarp is used inside the epilogue, so a warp that gives up on
-        // a wait can never strand another one.
+        // stage |b|^2 (and -2 x FP8 scale) of this tile in this warp's own buffer;
+        // +inf past the end of B.  Only __syncwarp is used inside the epilogue, so
+        // a warp that gives up on a wait can never strand another one.
         float* nb = nb_s + ((warp - 2) * 2 + acc) * kSliceCols;
         float* sb = sb_s + ((warp - 2) * 2 + acc) * kSliceCols;
-        if constexpr (!AUG) {
+        // this tile's norms were fetched into registers during the previous tile
 #pragma unroll
-          for (int k = 0; k < kPer; ++k) {
-            nb[lane + 32 * k] = pn[k];
-            sb[lane + 32 * k] = ps[k];
-          }
-          __syncwarp();
-          prefetch_norms(b0 + kBN);  // next tile's, consumed one tile from now
+        for (int k = 0; k < kPer; ++k) {
+          nb[lane + 32 * k] = pn[k];
+          if constexpr (SCREEN == CH_SCREEN_FP8) sb[lane + 32 * k] = ps[k];
         }
+        __syncwarp();
+        prefetch_norms(b0 + kBN);  // next tile's, consumed one tile from now
         const bool got = mbar_wait(&acc_full[acc], accphase, abort_flag);
         if (!__all_sync(0xFFFFFFFFu, got)) {
           ok = false;
@@ -350,43 +334,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + qs * kSliceCols;
-        const bool partial = b0 + kBN > b_end;  // columns past the end of B (AUG: masked here)
-        // chunk ch = slice columns ch*16 .. ch*16+15: classes (ch*16) mod kClasses + i,
-        // occurrence ch*16 / kClasses, folded into the tile's per-class best tm
+        // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 16 columns
+        // (chunk ch = slice columns ch*16 .. ch*16+15: classes (ch*16) mod
+        // kClasses + i, occurrence ch*16 / kClasses), folded into the tile minima tm
         float tm[kClasses];
         auto process = [&](uint32_t(&r)[16], int ch) {
-          const int c0 = (ch * 16) % kClasses;
-          const bool first = ch * 16 < kClasses;
-          if constexpr (AUG) {
-            if (partial) {
+          const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 16);
+          const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 16);
 #pragma unroll
-              for (int i = 0; i < 16; ++i)
-                if (b0 + qs * kSliceCols + ch * 16 + i >= b_end) r[i] = __float_as_uint(kWorst);
-            }
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-              tm[c0 + i] = first ? __uint_as_float(r[i]) : fmaxf(tm[c0 + i], __uint_as_float(r[i]));
-          } else {
-            // s = |b|^2 - 2 s_q s_b q8.b8
-            const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 16);
-            const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 16);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float4 n = nb4[q];
-              float4 m = sb4[q];  // -2 x column scale, times this row's sample scale
+          for (int q = 0; q < 4; ++q) {
+            const float4 n = nb4[q];
+            float4 m = make_float4(-2.0f, -2.0f, -2.0f, -2.0f);
+            if constexpr (SCREEN == CH_SCREEN_FP8) {
+              m = sb4[q];  // -2 x column scale, times this row's sample scale
               m.x *= sq;
               m.y *= sq;
               m.z *= sq;
               m.w *= sq;
-              r[4 * q + 0] = __float_as_uint(fmaf(m.x, __uint_as_float(r[4 * q + 0]), n.x));
-              r[4 * q + 1] = __float_as_uint(fmaf(m.y, __uint_as_float(r[4 * q + 1]), n.y));
-              r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
-              r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
             }
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-              tm[c0 + i] = first ? __uint_as_float(r[i]) : fminf(tm[c0 + i], __uint_as_float(r[i]));
+            r[4 * q + 0] = __float_as_uint(fmaf(m.x, __uint_as_float(r[4 * q + 0]), n.x));
+            r[4 * q + 1] = __float_as_uint(fmaf(m.y, __uint_as_float(r[4 * q + 1]), n.y));
+            r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
+            r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
           }
+          const int c0 = (ch * 16) % kClasses;
+          const bool first = ch * 16 < kClasses;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            tm[c0 + i] = first ? __uint_as_float(r[i]) : fminf(tm[c0 + i], __uint_as_float(r[i]));
         };
         // two 16-column register buffers: the next chunk loads while this one is processed
         uint32_t ra[16], rb[16];
@@ -403,12 +378,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_before();
         mbar_arrive(&acc_empty[acc]);
-        // one running-best update per class and tile
+        // one running-minimum update per class and tile
 #pragma unroll
         for (int i = 0; i < kClasses; ++i) {
-          const bool better = AUG ? tm[i] > best_s[i] : tm[i] < best_s[i];
-          best_s[i] = better ? tm[i] : best_s[i];
-          best_c[i] = better ? tile : best_c[i];
+          const bool lt = tm[i] < best_s[i];
+          best_s[i] = lt ? tm[i] : best_s[i];
+          best_c[i] = lt ? tile : best_c[i];
         }
         ++tile;
         acc ^= 1;
@@ -418,13 +393,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       if (grow < args.T) {
         // entry (tile t, class i) stands for columns
-        // b_begin + t*256 + slice*kSliceCols + o*kClasses + i, o = 0 .. kOcc-1;
-        // its score is reported as |b|^2 - 2 q.b (AUG: -2 x the best, exact scaling)
+        // b_begin + t*256 + slice*kSliceCols + o*kClasses + i, o = 0 .. kOcc-1
         const size_t base = (size_t(ck * kSlices + qs) * args.T + grow) * kClasses;
 #pragma unroll
         for (int i = 0; i < kClasses; ++i) {
           const int32_t t = best_c[i];
-          args.part_s[base + i] = AUG ? -2.0f * best_s[i] : best_s[i];
+          args.part_s[base + i] = best_s[i];
           args.part_i[base + i] =
               t < 0 ? -1 : static_cast<int32_t>(b_begin + int64_t(t) * kBN + qs * kSliceCols + i);
         }
@@ -449,51 +423,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Gathers the sampled rows A[idx] into a dense operand of qstride bytes per row
-// (raw storage type, zero-padded) and, for FP8, their scales; idx < 0 gives a zero
-// row.  With aug, the row's last 128 bytes are the augmented K block: ones in its
-// first three elements (binary32 or bf16), zeros elsewhere.
-__global__ void k_gather_rows(const uint8_t* A, const float* scA, int64_t nA, int row_bytes, int qstride, int aug,
-                              const int64_t* idx, int64_t T, uint8_t* Q, float* sQ) {
+// Gathers the sampled rows A[idx] into a dense [T][d] operand (raw storage type)
+// and, for FP8, their scales; idx < 0 gives a zero row.
+__global__ void k_gather_rows(const uint8_t* A, const float* scA, int64_t nA, int row_bytes, const int64_t* idx,
+                              int64_t T, uint8_t* Q, float* sQ) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int words = qstride / 16;
+  const int words = row_bytes / 16;
   const int64_t row = t / words;
   const int w = static_cast<int>(t % words);
   if (row >= T) return;
   const int64_t a = idx ? idx[row] : row;
   uint4 v = make_uint4(0, 0, 0, 0);
-  if (w < row_bytes / 16) {
-    if (a >= 0 && a < nA) v = reinterpret_cast<const uint4*>(A + a * row_bytes)[w];
-  } else if (aug && w == words - 8) {
-    v = aug == 1 ? make_uint4(0x3F800000u, 0x3F800000u, 0x3F800000u, 0u)   // binary32 ones
-                 : make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u);           // bf16 ones
-  }
-  reinterpret_cast<uint4*>(Q + row * qstride)[w] = v;
+  if (a >= 0 && a < nA) v = reinterpret_cast<const uint4*>(A + a * row_bytes)[w];
+  reinterpret_cast<uint4*>(Q + row * row_bytes)[w] = v;
   if (sQ && w == 0) sQ[row] = (a >= 0 && a < nA) ? scA[a] : 1.0f;
-}
-
-// The augmented K block of B: 128 bytes per point holding -|b|^2 / 2 as three
-// pieces exactly representable in the operand type (TF32: 10 stored mantissa bits,
-// bf16: 7), whose exact sum is -|b|^2 / 2, then zeros.
-__global__ void k_aug_rows(const float* norms, int64_t nB, int bf16, uint8_t* out) {
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t b = t >> 3;
-  const int w = static_cast<int>(t & 7);
-  if (b >= nB) return;
-  uint4 v = make_uint4(0, 0, 0, 0);
-  if (w == 0) {
-    const float x = -0.5f * norms[b];
-    const uint32_t mask = bf16 ? 0xFFFF0000u : 0xFFFFE000u;
-    const float h1 = __uint_as_float(__float_as_uint(x) & mask);
-    const float r1 = __fsub_rn(x, h1);
-    const float h2 = __uint_as_float(__float_as_uint(r1) & mask);
-    const float h3 = __uint_as_float(__float_as_uint(__fsub_rn(r1, h2)) & mask);
-    if (bf16)
-      v = make_uint4((__float_as_uint(h1) >> 16) | (__float_as_uint(h2) & 0xFFFF0000u), __float_as_uint(h3) >> 16, 0u, 0u);
-    else
-      v = make_uint4(__float_as_uint(h1), __float_as_uint(h2), __float_as_uint(h3), 0u);
-  }
-  reinterpret_cast<uint4*>(out + b * 128)[w] = v;
 }
 
 CUtensorMap make_map(const void* base, int dtype, int64_t rows, int d, int box_rows) {
@@ -527,11 +470,9 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   const int es = static_cast<int>(elem_size(screen_dtype(screen)));
   p.T = T;
   p.R = std::max(1, std::min(R, 32));  // candidates the rerank evaluates exactly
-  const bool aug = screen != CH_SCREEN_FP8;
-  p.kblocks = static_cast<int>(ceil_div(int64_t(d) * es, kKB)) + (aug ? 1 : 0);
+  p.kblocks = static_cast<int>(ceil_div(int64_t(d) * es, kKB));
   p.row_tiles = static_cast<int>(ceil_div(std::max<int64_t>(T, 1), kBM));
-  const size_t staging = aug ? 0 : size_t(4) * kEpiWarps * kSliceCols * sizeof(float);
-  const size_t fixed = 1024 + size_t(p.kblocks) * kBM * kKB + staging + 256;
+  const size_t fixed = 1024 + size_t(p.kblocks) * kBM * kKB + 16 * kBN * sizeof(float) + 256;
   const size_t per_stage = size_t(kBN) * kKB;
   const size_t limit = 227 * 1024;
   p.stages = static_cast<int>(std::min<size_t>(6, (limit - std::min(limit, fixed)) / per_stage));
@@ -586,10 +527,9 @@ bool screen_supported(int screen, const ch_set* A, const ch_set* B) {
 size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   const Plan p = make_plan(T, nB, d, R, sm_count, screen);
   const int es = static_cast<int>(elem_size(screen_dtype(screen)));
-  const size_t q = ((size_t(T) * p.kblocks * kKB + 255) & ~size_t(255)) + ((size_t(T) * 4 + 255) & ~size_t(255));
-  const size_t baug = screen != CH_SCREEN_FP8 ? ((size_t(nB) * kKB + 255) & ~size_t(255)) : 0;
+  const size_t q = ((size_t(T) * d * es + 255) & ~size_t(255)) + ((size_t(T) * 4 + 255) & ~size_t(255));
   const size_t parts = size_t(kSlices * p.chunks) * T * kClasses * 8 + 512;
-  return q + baug + parts + 1024;
+  return q + parts + 1024;
 }
 
 void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R, void* work,
@@ -599,36 +539,23 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   const Plan p = make_plan(T, B->n, A->d, R, sm_count, screen);
   const int es = static_cast<int>(elem_size(A->dtype));
   const int row_bytes = A->d * es;
-  const bool aug = screen != CH_SCREEN_FP8;
-  const int qstride = aug ? p.kblocks * kKB : row_bytes;  // the augmented block is the last K block
   uint8_t* w = static_cast<uint8_t*>(work);
   uint8_t* Q = w;
-  w += (size_t(T) * qstride + 255) & ~size_t(255);
+  w += (size_t(T) * row_bytes + 255) & ~size_t(255);
   float* sQ = reinterpret_cast<float*>(w);
   w += (size_t(T) * 4 + 255) & ~size_t(255);
-  uint8_t* Baug = nullptr;
-  if (aug) {
-    Baug = w;
-    w += (size_t(B->n) * kKB + 255) & ~size_t(255);
-  }
   float* part_s = reinterpret_cast<float*>(w);
   w += (size_t(kSlices * p.chunks) * T * kClasses * 4 + 255) & ~size_t(255);
   int32_t* part_i = reinterpret_cast<int32_t*>(w);
 
-  const int64_t words = T * (qstride / 16);
+  const int64_t words = T * (row_bytes / 16);
   k_gather_rows<<<static_cast<int>(ceil_div(words, 256)), 256, 0, s>>>(
-      static_cast<const uint8_t*>(A->data), A->scales, A->n, row_bytes, qstride,
-      aug ? (screen == CH_SCREEN_BF16 ? 2 : 1) : 0, qidx, T, Q, screen == CH_SCREEN_FP8 ? sQ : nullptr);
+      static_cast<const uint8_t*>(A->data), A->scales, A->n, row_bytes, qidx, T, Q,
+      screen == CH_SCREEN_FP8 ? sQ : nullptr);
   launch_check("gather_rows");
-  if (aug) {
-    k_aug_rows<<<static_cast<int>(ceil_div(B->n * 8, 256)), 256, 0, s>>>(B->norms, B->n,
-                                                                          screen == CH_SCREEN_BF16 ? 1 : 0, Baug);
-    launch_check("aug_rows");
-  }
 
-  const CUtensorMap tmQ = make_map(Q, A->dtype, T, qstride / es, kBM);
+  const CUtensorMap tmQ = make_map(Q, A->dtype, T, A->d, kBM);
   const CUtensorMap tmB = make_map(B->data, B->dtype, B->n, B->d, kBN);
-  const CUtensorMap tmBa = aug ? make_map(Baug, B->dtype, B->n, kKB / es, kBN) : tmB;
   ScreenArgs a;
   a.T = T;
   a.nB = B->n;
@@ -649,7 +576,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
     auto kern = k_screen<SCR>;                                                                              \
     CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)); /* constant */ \
     timer.start(s);                                                                                         \
-    kern<<<p.grid, kThreads, p.smem, s>>>(tmQ, tmB, tmBa, a);                                                     \
+    kern<<<p.grid, kThreads, p.smem, s>>>(tmQ, tmB, a);                                                     \
     timer.stop(s);                                                                                          \
   } while (0)
   if (screen == CH_SCREEN_TF32) CHX_SCREEN_LAUNCH(CH_SCREEN_TF32);
