@@ -103,6 +103,8 @@ def _bind(so):
         "or_default_T": (_i64, [_i64, _i64, ctypes.c_double]),
         "or_estimate": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _u64, _i32, _i32, _i32,
                                           _i64, _u64, _p, _p, _p, _p, _p, _p]),
+        "or_draws_uniform": (None, [_i64, _i64, _u64, _p]),
+        "or_estimate_uniform": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _i64, _u64, _p, _p]),
         "or_exact_fp64": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _p]),
         "or_exact_canonical": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _p]),
         "or_num_threads": (_i32, []),
@@ -279,6 +281,42 @@ def estimate(A, B, metric: int, hash_seed: int, sample_seed: int, T: int, L: int
         return float(eta)
     return float(eta), dict(bidx=bidx, D=D, level=level, idx=idx[:T], m=m[:T], W=int(rep.W),
                             D_total=rep.D_total, top_exp=rep.top_exp, S=rep.shift_S)
+
+
+def draws_uniform(nA: int, T: int, seed: int) -> np.ndarray:
+    """Uniform draws over A from the Philox counters of the importance draws."""
+    idx = np.zeros(max(T, 0), dtype=np.int64)
+    lib().or_draws_uniform(nA, T, seed, _ptr(idx))
+    return idx
+
+
+def estimate_uniform(A, B, metric: int, sample_seed: int, T: int, details: bool = False):
+    """The uniform-sampling baseline: (nA / T) sum_l min_b d(x_l, b), x_l uniform over A."""
+    A, B = _f32(A), _f32(B)
+    idx = np.zeros(max(T, 1), dtype=np.int64)
+    m = np.zeros(max(T, 1), dtype=np.float32)
+    eta = float(lib().or_estimate_uniform(_ptr(A), A.shape[0], _ptr(B), B.shape[0], A.shape[1], metric, T,
+                                          sample_seed, _ptr(idx), _ptr(m)))
+    return (eta, dict(idx=idx[:T], m=m[:T])) if details else eta
+
+
+# sample seed of the (B, A) direction of a symmetric estimate
+SYM_SEED_XOR = 0x9E3779B97F4A7C15
+
+
+def estimate_sym(A, B, metric: int, hash_seed: int, sample_seed: int, T: int, L: int = 10, proj_dim: int = 16,
+                 top_exp: int | None = None, uniform: bool = False):
+    """CH(A, B) + CH(B, A) estimated as two one-sided estimates (Section 1's symmetric
+    form): the same hash seed, the (B, A) draws keyed by sample_seed ^ SYM_SEED_XOR.
+    Returns (eta_AB + eta_BA, eta_AB, eta_BA)."""
+    s2 = sample_seed ^ SYM_SEED_XOR
+    if uniform:
+        ab = estimate_uniform(A, B, metric, sample_seed, T)
+        ba = estimate_uniform(B, A, metric, s2, T)
+    else:
+        ab = estimate(A, B, metric, hash_seed, sample_seed, T, L, proj_dim, top_exp)
+        ba = estimate(B, A, metric, hash_seed, s2, T, L, proj_dim, top_exp)
+    return ab + ba, ab, ba
 
 
 def exact_fp64(A, B, metric: int, per_a: bool = False):

@@ -470,6 +470,42 @@ typedef struct {
     int32_t shift_S;
 } or_report;
 
+/* The uniform-sampling baseline (Section 2, before Fig. 1; the estimator the   */
+/* paper compares importance sampling against): x_l uniform over A, drawn from */
+/* the same Philox counter (l_lo, l_hi, 3, 0) as or_draws: x_l = floor(u nA /   */
+/* 2^128), then eta = (1/T) sum_l nA m_l, summed in order in binary64.          */
+void or_draws_uniform(int64_t nA, int64_t T, uint64_t seed, int64_t* idx)
+{
+    uint32_t key[2];
+    seed_key(seed, key);
+    for (int64_t l = 0; l < T; l++) {
+        if (nA == 0) { idx[l] = -1; continue; }
+        uint32_t ctr[4] = {(uint32_t)l, (uint32_t)((uint64_t)l >> 32), 3u, 0u}, u[4];
+        or_philox4x32_10(ctr, key, u);
+        unsigned __int128 ulo = ((unsigned __int128)u[1] << 32) | u[0];
+        unsigned __int128 uhi = ((unsigned __int128)u[3] << 32) | u[2];
+        unsigned __int128 plo = ulo * (uint64_t)nA;
+        unsigned __int128 phi = uhi * (uint64_t)nA;
+        unsigned __int128 mid = (phi & 0xFFFFFFFFFFFFFFFFull) + (plo >> 64);
+        idx[l] = (int64_t)((phi >> 64) + (mid >> 64));
+    }
+}
+
+double or_estimate_uniform(const float* A, int64_t nA, const float* B, int64_t nB, int d, int metric, int64_t T,
+                           uint64_t sample_seed, int64_t* idx_out, float* m_out)
+{
+    if (nA == 0 || T == 0) return 0.0;
+    int64_t* idx = idx_out ? idx_out : (int64_t*)malloc(sizeof(int64_t) * T);
+    float* m = m_out ? m_out : (float*)malloc(sizeof(float) * T);
+    or_draws_uniform(nA, T, sample_seed, idx);
+    or_scan(A, idx, T, B, nB, d, metric, m, NULL);
+    double s = 0.0;
+    for (int64_t l = 0; l < T; l++) s += (double)m[l] * (double)nA;
+    if (!idx_out) free(idx);
+    if (!m_out) free(m);
+    return s / (double)T;
+}
+
 /* Chamfer-Estimate(A, B, T) (Fig. 1) end to end; optional outputs may be NULL. */
 double or_estimate(const float* A, int64_t nA, const float* B, int64_t nB, int d, int metric,
                    uint64_t hash_seed, int L, int proj_dim, int top_exp_in, int64_t T, uint64_t sample_seed,

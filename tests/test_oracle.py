@@ -435,7 +435,72 @@ def test_outlier_importance_beats_uniform():
     T = 400
     est, _ = _estimates_many(A, B, L1, range(20), T=T)
     assert np.mean(np.abs(est / ch - 1) < 0.2) >= 0.9
-    _, mins = oracle.exact_canonical(A, B, L1)
-    g = np.random.default_rng(0)
-    uni = [mins[g.integers(0, A.shape[0], T)].mean() * A.shape[0] for _ in range(20)]
-    assert np.mean(np.abs(np.array(uni) / ch - 1) < 0.2) < 0.5
+    uni = np.array([oracle.estimate_uniform(A, B, L1, s, T) for s in range(20)])
+    assert np.mean(np.abs(uni / ch - 1) < 0.2) < 0.5
+
+
+# ------------------------------------------------------------------ uniform baseline and symmetric form
+def test_uniform_draws_are_importance_draws_with_constant_weight():
+    """x_l = floor(u nA / 2^128) equals the importance draw with every D_a equal
+    (the weights route: w_a = 2^S, prefix (a+1) 2^S), for every l."""
+    for nA, seed in ((1, 0), (7, 3), (1000, 11), (123457, 5)):
+        w, prefix, W, _ = oracle.weights(np.ones(nA, np.float32))
+        assert np.array_equal(oracle.draws(prefix, W, 3000, seed), oracle.draws_uniform(nA, 3000, seed))
+
+
+def test_uniform_draw_frequencies():
+    """Chi-square of 200k uniform draws over 10 points (p > 1e-4)."""
+    from scipy import stats
+    idx = oracle.draws_uniform(10, 200_000, 42)
+    assert idx.min() == 0 and idx.max() == 9
+    counts = np.bincount(idx, minlength=10)
+    assert stats.chisquare(counts).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_uniform_estimator_unbiased(metric):
+    """E[eta_unif] = sum_a min_b dist_c(a, b) exactly for the implemented draws: the
+    mean over 4000 seeds lies within 5 standard errors."""
+    A, B = workloads.gaussian_mixture(60, 80, 5, 9, clusters=3)
+    ch_c, mins = oracle.exact_canonical(A, B, metric)
+    est = np.array([oracle.estimate_uniform(A, B, metric, s, 7) for s in range(4000)])
+    # the exact variance of the mean of 7 uniform draws of nA m_a
+    var1 = np.var(mins.astype(np.float64) * A.shape[0])
+    se = math.sqrt(var1 / 7 / est.size)
+    assert abs(est.mean() - ch_c) < 5 * se
+    assert abs(est.var(ddof=1) / (var1 / 7) - 1) < 0.15
+
+
+def test_uniform_estimator_whole_set_and_single_point():
+    A, B = workloads.uniform(50, 70, 3, 2)
+    for metric in (L1, L2):
+        eta, det = oracle.estimate_uniform(A, B, metric, 4, 333, details=True)
+        m, _ = oracle.scan(A, det["idx"], B, metric)
+        assert np.array_equal(m, det["m"])
+        assert eta == sum(float(v) * 50 for v in m) / 333
+        # |A| = 1: every draw is that point, eta = its nearest-neighbour distance
+        _, mins = oracle.exact_canonical(A[:1], B, metric)
+        assert oracle.estimate_uniform(A[:1], B, metric, 9, 17) == float(mins[0])
+
+
+def test_symmetric_estimate():
+    A, B = workloads.gaussian_mixture(400, 300, 6, 17, clusters=4)
+    for metric in (L1, L2):
+        tot, ab, ba = oracle.estimate_sym(A, B, metric, 3, 4, T=300)
+        assert ab == oracle.estimate(A, B, metric, 3, 4, T=300)
+        assert ba == oracle.estimate(B, A, metric, 3, 4 ^ oracle.SYM_SEED_XOR, T=300)
+        assert tot == ab + ba
+        # identical sets: every sample's nearest point is its copy
+        assert oracle.estimate_sym(A, A.copy(), metric, 3, 4, T=50)[0] == 0.0
+        assert oracle.estimate_sym(A, A.copy(), metric, 3, 4, T=50, uniform=True)[0] == 0.0
+
+
+@pytest.mark.slow
+def test_symmetric_estimate_unbiased():
+    """Mean over 600 seeds of the symmetric estimate within 5 standard errors of
+    CH(A, B) + CH(B, A) (canonical distances)."""
+    A, B = workloads.gaussian_mixture(120, 90, 4, 23, clusters=3)
+    for metric in (L1, L2):
+        target = oracle.exact_canonical(A, B, metric)[0] + oracle.exact_canonical(B, A, metric)[0]
+        est = np.array([oracle.estimate_sym(A, B, metric, s, s + 1, T=15)[0] for s in range(600)])
+        assert abs(est.mean() - target) < 5 * est.std(ddof=1) / math.sqrt(est.size)
