@@ -94,6 +94,13 @@ typedef struct {
     int32_t reserved;
 } ch_hash_params;
 
+/* How the samples x_l are drawn:
+ *  IMPORTANCE  Pr[x = a] = D_a / D from CrudeNN's upper bounds (Fig. 1);
+ *  UNIFORM     x uniform over A and eta = (|A| / T) sum_l min_b d(x_l, b): the
+ *              baseline the paper measures importance sampling against (Section 2),
+ *              with no CrudeNN pass.  Draws use the same Philox counters (l, 3). */
+typedef enum { CH_SAMPLING_IMPORTANCE = 0, CH_SAMPLING_UNIFORM = 1 } ch_sampling;
+
 /* Chamfer-Estimate parameters (Fig. 1). */
 typedef struct {
     ch_hash_params hash;
@@ -102,6 +109,7 @@ typedef struct {
     uint64_t sample_seed; /* Philox key of the draws */
     int32_t screen;       /* ch_screen */
     uint32_t rerank_k;    /* screened entries reranked per sample, 4 columns each (1..32; default 8) */
+    int32_t sampling;     /* ch_sampling (default IMPORTANCE) */
 } ch_est_params;
 
 typedef struct {
@@ -117,7 +125,7 @@ typedef struct {
 } ch_est_report;
 
 /* Fill defaults: L1, 10 levels, k = 16, auto scales, HASH grouping, seeds 0,
- * eps 0.1, T = 0 (default), AUTO screen, rerank_k 8. */
+ * eps 0.1, T = 0 (default), AUTO screen, rerank_k 8, importance sampling. */
 void ch_default_params(ch_est_params* p);
 
 /* ------------------------------------------------------------ context
@@ -238,6 +246,16 @@ ch_status ch_estimate(ch_ctx* ctx, const ch_set* A, const ch_set* B, const ch_es
  * context's stream, so one set may appear in many pairs. */
 ch_status ch_estimate_batch(ch_ctx* ctx, int64_t count, const ch_set* const* A, const ch_set* const* B,
                             const ch_est_params* params, double* eta, ch_status* status);
+
+/* ------------------------------------------------------------ symmetric estimate
+ * CH(A, B) + CH(B, A) (Section 1's symmetric Chamfer distance) as two one-sided
+ * estimates under the same parameters, except that the (B, A) draws use the key
+ * sample_seed ^ 0x9E3779B97F4A7C15; T = 0 gives both directions the default T of
+ * max(|A|, |B|).  The two directions run concurrently (as a batch of two).
+ * eta: host, the sum; eta_ab / eta_ba: host, each direction, or NULL.  Errors as
+ * ch_estimate (the first failing direction's status). */
+ch_status ch_estimate_sym(ch_ctx* ctx, const ch_set* A, const ch_set* B, const ch_est_params* p, double* eta,
+                          double* eta_ab, double* eta_ba);
 
 /* ------------------------------------------------------------ brute force (Section 1)
  * CH(A, B) = sum_a min_b d_X(a, b).  mode 0: canonical binary32 distance for

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libchamfer.so")
 
 CH_OK, CH_EINVAL, CH_ENOMEM, CH_ECUDA, CH_ENOTSUP, CH_ETIMEOUT, CH_EBUSY, CH_EAGAIN = range(8)
+CH_SAMPLING_IMPORTANCE, CH_SAMPLING_UNIFORM = 0, 1
 CH_L1, CH_L2 = 1, 2
 CH_F32, CH_BF16, CH_FP8E4M3 = 0, 1, 2
 CH_SCREEN_AUTO, CH_SCREEN_EXACT, CH_SCREEN_TF32, CH_SCREEN_BF16, CH_SCREEN_FP8 = range(5)
@@ -41,7 +42,8 @@ class ch_hash_params(ctypes.Structure):
 
 class ch_est_params(ctypes.Structure):
     _fields_ = [("hash", ch_hash_params), ("eps", ctypes.c_double), ("T", ctypes.c_int64),
-                ("sample_seed", ctypes.c_uint64), ("screen", ctypes.c_int32), ("rerank_k", ctypes.c_uint32)]
+                ("sample_seed", ctypes.c_uint64), ("screen", ctypes.c_int32), ("rerank_k", ctypes.c_uint32),
+                ("sampling", ctypes.c_int32)]
 
 
 class ch_est_report(ctypes.Structure):
@@ -90,6 +92,8 @@ SIGNATURES = {
     "ch_sampled_nn": (_i32, [_vp, _vp, _vp, _i64, _vp, _i32, _i32, _u32, _vp, _vp]),
     "ch_estimate": (_i32, [_vp, _vp, _vp, _P(ch_est_params), _P(ctypes.c_double), _P(ch_est_report)]),
     "ch_estimate_batch": (_i32, [_vp, _i64, _P(_vp), _P(_vp), _P(ch_est_params), _P(ctypes.c_double), _P(_i32)]),
+    "ch_estimate_sym": (_i32, [_vp, _vp, _vp, _P(ch_est_params), _P(ctypes.c_double), _P(ctypes.c_double),
+                               _P(ctypes.c_double)]),
     "ch_exact": (_i32, [_vp, _vp, _vp, _i32, _i32, _P(ctypes.c_double), _vp]),
     "ch_serve_create": (_i32, [_vp, _P(ch_serve_config), _P(_vp)]),
     "ch_serve_register": (_i32, [_vp, _vp, ctypes.c_int, _i64, _i32, _i32, _vp, _P(_u64)]),
@@ -146,11 +150,12 @@ def hash_params(metric=CH_L1, levels=10, proj_dim=16, top_exp=None, hash_seed=0,
 
 
 def est_params(metric=CH_L1, levels=10, proj_dim=16, top_exp=None, hash_seed=0, group=CH_GROUP_HASH,
-               eps=0.1, T=0, sample_seed=0, screen=CH_SCREEN_AUTO, rerank_k=8):
+               eps=0.1, T=0, sample_seed=0, screen=CH_SCREEN_AUTO, rerank_k=8, sampling=None):
     p = ch_est_params()
     lib().ch_default_params(ctypes.byref(p))
     p.hash = hash_params(metric, levels, proj_dim, top_exp, hash_seed, group)
     p.eps, p.T, p.sample_seed, p.screen, p.rerank_k = eps, T, sample_seed, screen, rerank_k
+    p.sampling = CH_SAMPLING_IMPORTANCE if sampling is None else sampling
     return p
 
 
@@ -271,6 +276,14 @@ def ch_estimate_batch(ctx, A_sets, B_sets, params):
     if rc not in (CH_OK,) and all(x == CH_OK for x in st):
         _check(rc, "ch_estimate_batch", ctx)
     return list(eta), list(st)
+
+
+def ch_estimate_sym(ctx, A, B, p: ch_est_params):
+    """CH(A, B) + CH(B, A); returns (sum, eta_AB, eta_BA)."""
+    e, ab, ba = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().ch_estimate_sym(ctx, A, B, ctypes.byref(p), ctypes.byref(e), ctypes.byref(ab), ctypes.byref(ba)),
+           "ch_estimate_sym", ctx)
+    return e.value, ab.value, ba.value
 
 
 def ch_exact(ctx, A, B, metric: int, mode: int = 0, per_a_min=None) -> float:

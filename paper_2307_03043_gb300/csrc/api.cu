@@ -734,6 +734,8 @@ static void check_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch
   CHX_CHECK(*R <= 32, CH_EINVAL, "rerank_k must be in 1..32");
   CHX_CHECK(p->T >= 0, CH_EINVAL, "T must be >= 0");
   CHX_CHECK(p->T > 0 || (p->eps > 0.0 && p->eps < 1.0), CH_EINVAL, "eps must be in (0, 1)");
+  CHX_CHECK(p->sampling == CH_SAMPLING_IMPORTANCE || p->sampling == CH_SAMPLING_UNIFORM, CH_EINVAL,
+            "unknown sampling");
   *T = p->T > 0 ? p->T : default_T(A->n, B->n, p->eps);
 }
 
@@ -753,9 +755,20 @@ static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, c
   cudaStream_t s = c->stream;
   if (events) CHX_CUDA(cudaEventRecord(c->ev[0], s));
   CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
-  run_crude(c, A, B, &p->hash, &cb, eb.bidx, eb.level, eb.D, &res->status, sb.sw.maxD);
+  const bool uniform = p->sampling == CH_SAMPLING_UNIFORM;
+  if (uniform) {
+    // the baseline: every D_a = 1, so the weights are equal and the draws uniform;
+    // the set passes still check both sets for non-finite values
+    for (const ch_set* x : {A, B}) {
+      if (p->hash.metric == CH_L2) ensure_norms(const_cast<ch_set*>(x), s);
+      else ensure_ingest(const_cast<ch_set*>(x), s);
+    }
+    launch_fill_ones(eb.D, nA, s);
+  } else {
+    run_crude(c, A, B, &p->hash, &cb, eb.bidx, eb.level, eb.D, &res->status, sb.sw.maxD);
+  }
   if (events) CHX_CUDA(cudaEventRecord(c->ev[1], s));
-  launch_weights(eb.D, nA, eb.w, sb.prefix, sb.sw, s, true);
+  launch_weights(eb.D, nA, eb.w, sb.prefix, sb.sw, s, !uniform);
   launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, eb.idx, s);
   if (events) CHX_CUDA(cudaEventRecord(c->ev[2], s));
   KernelTimer kt;
@@ -766,7 +779,7 @@ static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, c
   run_scan(c, A, eb.idx, T, B, p->hash.metric, R, &sc, eb.m, nullptr, &res->status, kt);
   if (events) CHX_CUDA(cudaEventRecord(c->ev[3], s));
   launch_combine(eb.m, eb.idx, eb.w, sb.sw.W, T, eb.D, nA, eb.out2, s);
-  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, eb.out2, sb.sw.W, sb.sw.S, cb.e_top);
+  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, eb.out2, sb.sw.W, sb.sw.S, uniform ? nullptr : cb.e_top);
   launch_check("collect");
   if (events) CHX_CUDA(cudaEventRecord(c->ev[4], s));
   if (screen_used) *screen_used = sc.screen;
@@ -923,6 +936,32 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
   }
   if (first != CH_OK) c->err = "one or more pairs failed (see the per-pair status)";
   return first;
+  CHX_GUARD_END
+}
+
+ch_status ch_estimate_sym(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, double* eta,
+                          double* eta_ab, double* eta_ba) {
+  if (!c || !p || !eta) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  CHX_CHECK(A && B, CH_EINVAL, "set NULL");
+  const ch_set* As[2] = {A, B};
+  const ch_set* Bs[2] = {B, A};
+  ch_est_params ps[2] = {*p, *p};
+  ps[1].sample_seed ^= 0x9E3779B97F4A7C15ull;
+  double e[2] = {0.0, 0.0};
+  ch_status st[2] = {CH_OK, CH_OK};
+  const ch_status r = ch_estimate_batch(c, 2, As, Bs, ps, e, st);
+  if (r != CH_OK) {
+    if (st[0] != CH_OK || st[1] != CH_OK) {
+      c->err = st[0] != CH_OK ? "direction (A, B) failed" : "direction (B, A) failed";
+      return st[0] != CH_OK ? st[0] : st[1];
+    }
+    return r;
+  }
+  *eta = e[0] + e[1];
+  if (eta_ab) *eta_ab = e[0];
+  if (eta_ba) *eta_ba = e[1];
+  return CH_OK;
   CHX_GUARD_END
 }
 

@@ -297,6 +297,9 @@ struct SampleWork {
   int32_t* S;            // [1]
 };
 size_t sample_blocks(int64_t nA);
+// D[0..n) = 1 (the uniform-sampling baseline's weights)
+void launch_fill_ones(float* D, int64_t n, cudaStream_t s);
+
 // weights and their prefix; max_ready: *sw.maxD already holds max_a D_a
 void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s,
                     bool max_ready = false);

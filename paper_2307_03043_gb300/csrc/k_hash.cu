@@ -161,8 +161,8 @@ void ensure_norms(ch_set* X, cudaStream_t s) {
 // summed exactly, centred, scaled by 2^-32 and rounded once to binary32
 // (the l2 -> l1 embedding theorem of App. A.2 with the 1/(beta k) factor left out).
 // entry (j, i) of the Gaussian matrix: Irwin-Hall sum of 12 Philox words
-// (counter (j, i, 2, m), m = 0..2), centred and scaled by 2^-32 in binary64,
-// rounded once to binary32; zero for i >= k
+// (counter (j, i, 2, m), m = 0..2), centred, times 2^-32, rounded once to
+// binary32; zero for i >= k
 __device__ inline float gauss_entry(uint64_t seed, int k, int j, int i) {
   if (i >= k) return 0.0f;
   uint64_t sum = 0;

@@ -113,6 +113,17 @@ __global__ void k_add_offsets(uint64_t* prefix, int64_t nA, const uint64_t* bloc
   if (a < nA) prefix[a] += blockoff[a / kScanTile];
 }
 
+__global__ void k_fill_ones(float* D, int64_t n) {
+  const int64_t a = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (a < n) D[a] = 1.0f;
+}
+
+void launch_fill_ones(float* D, int64_t n, cudaStream_t s) {
+  if (n == 0) return;
+  k_fill_ones<<<static_cast<int>(ceil_div(n, 256)), 256, 0, s>>>(D, n);
+  launch_check("fill_ones");
+}
+
 void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s,
                     bool max_ready) {
   if (nA == 0) {

@@ -343,6 +343,52 @@ def test_estimate_tiny_matches_oracle(ctx, pair_factory, metric, seed):
     assert abs(eta / ch_x - 1) < 0.2
 
 
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_uniform_estimate_matches_oracle(ctx, pair_factory, metric):
+    """The uniform-sampling baseline (no CrudeNN): same draws as the oracle, eta
+    within 1e-5; |A| = 1 gives that point's nearest distance."""
+    A, B = workloads.gaussian_mixture(3000, 2500, 12, 31, clusters=6)
+    p = pair_factory(A, B)
+    for seed, T in ((0, 2000), (5, 777)):
+        prm = ch.est_params(metric, T=T, sample_seed=seed, screen=ch.CH_SCREEN_EXACT,
+                            sampling=ch.CH_SAMPLING_UNIFORM)
+        eta, rep = ch.ch_estimate(ctx, p.sA, p.sB, prm, report=True)
+        eta_o = oracle.estimate_uniform(A, B, metric, seed, T)
+        assert abs(eta / eta_o - 1) < 1e-5
+        assert rep.D_total == 3000.0 and rep.T == T
+    s1 = ch.ch_set_create(ctx, A[:1].copy(), 0, 1, 12)
+    _, mins = oracle.exact_canonical(A[:1], B, metric)
+    assert ch.ch_estimate(ctx, s1, p.sB, ch.est_params(metric, T=9, sampling=ch.CH_SAMPLING_UNIFORM)) == float(mins[0])
+    ch.ch_set_destroy(s1)
+
+
+def test_uniform_estimate_screen_and_batch(ctx, pair_factory):
+    """Uniform sampling through the TF32 screen (within 1e-3 of the oracle) and
+    inside a batch (equal to the single call)."""
+    A, B = workloads.gaussian_mixture(20_000, 30_000, 128, 33)
+    p = pair_factory(A, B)
+    prm = ch.est_params(L2, T=3000, sample_seed=8, sampling=ch.CH_SAMPLING_UNIFORM)
+    eta = ch.ch_estimate(ctx, p.sA, p.sB, prm)
+    assert abs(eta / oracle.estimate_uniform(A, B, L2, 8, 3000) - 1) < 1e-3
+    etas, st = ch.ch_estimate_batch(ctx, [p.sA, p.sB], [p.sB, p.sA], [prm, prm])
+    assert st == [ch.CH_OK, ch.CH_OK] and etas[0] == eta
+
+
+@pytest.mark.parametrize("metric", [L1, L2])
+@pytest.mark.parametrize("uniform", [False, True])
+def test_symmetric_estimate_matches_oracle(ctx, pair_factory, metric, uniform):
+    A, B = workloads.gaussian_mixture(2500, 1800, 10, 41, clusters=7)
+    p = pair_factory(A, B)
+    T = 1500
+    prm = ch.est_params(metric, 10, 16, None, 3, T=T, sample_seed=4, screen=ch.CH_SCREEN_EXACT,
+                        sampling=ch.CH_SAMPLING_UNIFORM if uniform else ch.CH_SAMPLING_IMPORTANCE)
+    tot, ab, ba = ch.ch_estimate_sym(ctx, p.sA, p.sB, prm)
+    tot_o, ab_o, ba_o = oracle.estimate_sym(A, B, metric, 3, 4, T=T, uniform=uniform)
+    assert abs(ab / ab_o - 1) < 1e-5 and abs(ba / ba_o - 1) < 1e-5
+    assert tot == ab + ba
+    assert ab == ch.ch_estimate(ctx, p.sA, p.sB, prm)
+
+
 def test_estimate_edge_cases(ctx, pair_factory):
     A, B = workloads.uniform(10, 20, 4, 1)
     p = pair_factory(A, B)
