@@ -56,6 +56,10 @@ WORKLOADS = {
     "batched": dict(n=0, d=3, dtype="f32",
                     desc="batched: 4096 pairs, |A| and |B| log-uniform in [256, 50000], d=3 ellipsoid/box "
                          "surfaces with 1% noise (B a resample of A's shape), fp32, l2 (l1 alongside), eps=0.1"),
+    "curves": dict(n=0, d=16, dtype="f32",
+                   desc="sample complexity: relative error of importance vs uniform sampling over T, 32 seeds "
+                        "per T, on the 100k x 100k d=128 mixture and on two 100k d=16 Gaussian clouds with one "
+                        "far outlier in A (l2)"),
 }
 BATCH_PAIRS = 4096
 
@@ -367,6 +371,50 @@ def run_batched(args, ch, ctx, torch, rank, local, world):
         }))
 
 
+def run_curves(args, ch, ctx, torch):
+    """Sample-complexity curves: for each T, 32 seeds of the importance-sampling
+    estimate and of the uniform baseline (each seed an independent draw; hash and
+    sample seeds change together), relative error against ch_exact.  The seeds of
+    one T run as one ch_estimate_batch call."""
+    from paper_2307_03043_gb300 import workloads
+    seeds = 32
+    cases = {
+        "mixture_100k_d128": workloads.gaussian_mixture(100_000, 100_000, 128, 0),
+        "outlier_100k_d16": workloads.outlier_gaussian(100_000, 16, 1),
+    }
+    out = {}
+    for name, (A, B) in cases.items():
+        sA = ch.ch_set_create(ctx, A, 0, A.shape[0], A.shape[1])
+        sB = ch.ch_set_create(ctx, B, 0, B.shape[0], B.shape[1])
+        exact = ch.ch_exact(ctx, sA, sB, ch.CH_L2, 0)
+        rows = []
+        for T in (16, 64, 256, 1024, 4096):
+            rec = {"T": T}
+            for label, smp in (("importance", ch.CH_SAMPLING_IMPORTANCE), ("uniform", ch.CH_SAMPLING_UNIFORM)):
+                prm = [ch.est_params(ch.CH_L2, LEVELS, PROJ, None, 1000 * T + k, T=T, sample_seed=1000 * T + k,
+                                     sampling=smp) for k in range(seeds)]
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                eta, st = ch.ch_estimate_batch(ctx, [sA] * seeds, [sB] * seeds, prm)
+                sec = (time.perf_counter() - t0) / seeds
+                rel = np.abs(np.array(eta) / exact - 1.0)
+                rec[label] = {"median_rel_err": float(np.median(rel)), "p90_rel_err": float(np.quantile(rel, 0.9)),
+                              "max_rel_err": float(rel.max()), "within_10pct": float(np.mean(rel <= 0.1)),
+                              "ms_per_estimate": sec * 1e3}
+            rows.append(rec)
+        out[name] = {"exact": exact, "n": [int(A.shape[0]), int(B.shape[0])], "d": int(A.shape[1]), "rows": rows}
+        ch.ch_set_destroy(sA)
+        ch.ch_set_destroy(sB)
+    mid = out["mixture_100k_d128"]["rows"][-1]
+    print(json.dumps({
+        "metric": "median relative error of the estimate at T = 4096 (importance sampling)", "value":
+        mid["importance"]["median_rel_err"], "unit": "relative error", "n_gpus": 1, "steps": seeds,
+        "warmup": 0, "higher_is_better": False, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["curves"]["desc"], "seeds_per_T": seeds, "metric": "l2"},
+        "curves": out,
+    }))
+
+
 def run_reference_batched(args):
     """Oracle arm of the batched workload: each step runs the oracle on 16 of the
     pairs (every 256th) in full; value in points per second."""
@@ -412,6 +460,8 @@ def run_reference(args):
     if CONFIG == "batched":
         run_reference_batched(args)
         return
+    if CONFIG == "curves":  # an accuracy experiment, not a throughput one: time the mid workload
+        select_workload("mid")
     A, B = workloads.gaussian_mixture(NA, NB, DIM, 0)
     T = oracle.default_T(NA, NB, EPS)
     frac = 8
@@ -459,6 +509,14 @@ def main():
     from paper_2307_03043_gb300 import binding as ch
     from paper_2307_03043_gb300 import workloads
 
+    if CONFIG == "curves":
+        ctx = ch.ch_ctx_create(local, torch.cuda.current_stream())
+        if rank == 0:
+            run_curves(args, ch, ctx, torch)
+        ch.ch_ctx_destroy(ctx)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     if CONFIG == "batched":
         ctx = ch.ch_ctx_create(local, torch.cuda.current_stream())
         run_batched(args, ch, ctx, torch, rank, local, world)
