@@ -104,6 +104,7 @@ def _bind(so):
         "or_estimate": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _u64, _i32, _i32, _i32,
                                           _i64, _u64, _p, _p, _p, _p, _p, _p]),
         "or_draws_uniform": (None, [_i64, _i64, _u64, _p]),
+        "or_crude_nn_kw": (None, [_p, _i64, _p, _i64, _i32, _i32, _u64, _i32, _i32, _i32, _i32, _i32, _p, _p, _p]),
         "or_estimate_uniform": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _i64, _u64, _p, _p]),
         "or_exact_fp64": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _p]),
         "or_exact_canonical": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _p]),
@@ -281,6 +282,20 @@ def estimate(A, B, metric: int, hash_seed: int, sample_seed: int, T: int, L: int
         return float(eta)
     return float(eta), dict(bidx=bidx, D=D, level=level, idx=idx[:T], m=m[:T], W=int(rep.W),
                             D_total=rep.D_total, top_exp=rep.top_exp, S=rep.shift_S)
+
+
+def crude_nn_kw(A, B, metric: int, hash_seed: int = 0, L: int = 10, proj_dim: int = 16,
+                top_exp: int | None = None, k: int = 1, W: int = 1) -> dict:
+    """k x W CrudeNN (Section 3): k structures, the first W distinct points of B
+    from a's buckets in increasing scale order, D_a the closest of them."""
+    A, B = _f32(A), _f32(B)
+    nA = A.shape[0]
+    bidx = np.zeros(nA, dtype=np.int64)
+    D = np.zeros(nA, dtype=np.float32)
+    level = np.zeros(nA, dtype=np.uint8)
+    lib().or_crude_nn_kw(_ptr(A), nA, _ptr(B), B.shape[0], A.shape[1], metric, hash_seed, L, proj_dim,
+                         INT32_MIN if top_exp is None else int(top_exp), k, W, _ptr(bidx), _ptr(D), _ptr(level))
+    return {"bidx": bidx, "D": D, "level": level}
 
 
 def draws_uniform(nA: int, T: int, seed: int) -> np.ndarray:

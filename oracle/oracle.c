@@ -371,6 +371,70 @@ int or_crude_nn(const float* A, int64_t nA, const float* B, int64_t nB, int d, i
 }
 
 /* ------------------------------------------------------------------------ */
+/* k x W CrudeNN (Section 3, the large-scale variant): k independent hash    */
+/* structures; in each, a's buckets are visited in increasing scale order    */
+/* and the first W distinct points of B found there are retrieved; D_a is    */
+/* the distance to the closest of all retrieved points.  R12: structure r     */
+/* uses hash seed hash_seed + r * 0x9E3779B97F4A7C15 (r = 0 is Fig. 2's own   */
+/* structure), its own scales (e_top of its own hashed space, unless fixed), */
+/* and within a bucket the points in increasing index order; a structure     */
+/* that retrieves nothing contributes B[0].  b(a) = the retrieved point at   */
+/* the smallest canonical distance (smallest index on ties); level = the    */
+/* finest scale at which any structure found a point (L if none).  k = W = 1 */
+/* is or_crude_nn.  Brute force over B at every scale: small inputs only.    */
+/* ------------------------------------------------------------------------ */
+void or_crude_nn_kw(const float* A, int64_t nA, const float* B, int64_t nB, int d, int metric, uint64_t hash_seed,
+                    int L, int proj_dim, int top_exp_in, int k, int W, int64_t* bidx, float* D, uint8_t* level)
+{
+    for (int64_t a = 0; a < nA; a++) {
+        bidx[a] = -1;
+        D[a] = INFINITY;
+        level[a] = (uint8_t)L;
+    }
+    uint64_t* kA = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(nA > 0 ? nA : 1) * L);
+    uint64_t* kB = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(nB > 0 ? nB : 1) * L);
+    for (int r = 0; r < k; r++) {
+        const uint64_t seed = hash_seed + (uint64_t)r * 0x9E3779B97F4A7C15ull;
+        int dd;
+        float* YA = hashed_space(A, nA, d, metric, seed, proj_dim, &dd);
+        float* YB = hashed_space(B, nB, d, metric, seed, proj_dim, &dd);
+        const int e_top = top_exp_in != INT32_MIN ? top_exp_in : or_top_exp(YA, nA, YB, nB, dd);
+        or_keys(YA, nA, dd, e_top - L + 1, L, seed, kA);
+        or_keys(YB, nB, dd, e_top - L + 1, L, seed, kB);
+        #pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t a = 0; a < nA; a++) {
+            int64_t* taken = (int64_t*)malloc(sizeof(int64_t) * (size_t)W);
+            int cnt = 0, first_level = L;
+            for (int l = 0; l < L && cnt < W; l++) {
+                for (int64_t b = 0; b < nB && cnt < W; b++) {
+                    if (kB[(size_t)l * nB + b] != kA[(size_t)l * nA + a]) continue;
+                    int seen = 0;
+                    for (int t = 0; t < cnt; t++) seen |= taken[t] == b;
+                    if (!seen) {
+                        taken[cnt++] = b;
+                        if (l < first_level) first_level = l;
+                    }
+                }
+            }
+            if (cnt == 0) taken[cnt++] = 0;
+            for (int t = 0; t < cnt; t++) {
+                const float v = or_dist(A + (size_t)a * d, B + (size_t)taken[t] * d, d, metric);
+                if (v < D[a] || (v == D[a] && taken[t] < bidx[a])) {
+                    D[a] = v;
+                    bidx[a] = taken[t];
+                }
+            }
+            if (first_level < level[a]) level[a] = (uint8_t)first_level;
+            free(taken);
+        }
+        free(YA);
+        free(YB);
+    }
+    free(kA);
+    free(kB);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Importance distribution (Fig. 1, step 2): Pr[x = a] = D_a / D.           */
 /* R7: w_a = ceil(D_a 2^S) as a 64-bit integer, S = 62 - ceil(log2 nA) - e_M */
 /* with M = max D_a < 2^e_M; W = sum w_a < 2^63.  Returns S; W = 0 if M = 0.  */

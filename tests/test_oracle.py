@@ -504,3 +504,72 @@ def test_symmetric_estimate_unbiased():
         target = oracle.exact_canonical(A, B, metric)[0] + oracle.exact_canonical(B, A, metric)[0]
         est = np.array([oracle.estimate_sym(A, B, metric, s, s + 1, T=15)[0] for s in range(600)])
         assert abs(est.mean() - target) < 5 * est.std(ddof=1) / math.sqrt(est.size)
+
+
+# ------------------------------------------------------------------ k x W CrudeNN (Section 3)
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_kw_one_by_one_is_crude_nn(metric):
+    A, B = workloads.gaussian_mixture(700, 900, 7, 31, clusters=6)
+    for seed in (0, 5):
+        r = oracle.crude_nn(A, B, metric, hash_seed=seed)
+        q = oracle.crude_nn_kw(A, B, metric, hash_seed=seed, k=1, W=1)
+        assert np.array_equal(r["bidx"], q["bidx"]) and np.array_equal(r["level"], q["level"])
+        assert np.array_equal(r["D"].view(np.uint32), q["D"].view(np.uint32))
+
+
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_kw_monotone_and_bounded(metric):
+    """More structures or a wider window never raise D_a, and D_a never drops below
+    the canonical nearest-neighbour distance (it is a distance to a point of B)."""
+    A, B = workloads.gaussian_mixture(400, 500, 6, 8, clusters=4)
+    _, nn = oracle.exact_canonical(A, B, metric)
+    prev = None
+    for k, W in ((1, 1), (1, 4), (2, 4), (4, 4), (4, 16)):
+        q = oracle.crude_nn_kw(A, B, metric, hash_seed=2, k=k, W=W)
+        assert np.all(q["D"] >= nn)
+        for a in range(0, 400, 37):
+            assert q["D"][a] == oracle.dist(A[a], B[q["bidx"][a]], metric)
+        if prev is not None:
+            assert np.all(q["D"] <= prev)
+        prev = q["D"]
+
+
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_kw_whole_window_is_exact(metric):
+    """Scales so coarse that every point shares one bucket, and W = |B|: the window
+    holds all of B, so D_a is the exact canonical minimum and b(a) its smallest argmin."""
+    A, B = workloads.uniform(150, 120, 5, 6)
+    B[40] = B[7]  # a duplicate: ties go to the smaller index
+    q = oracle.crude_nn_kw(A, B, metric, hash_seed=1, top_exp=40, k=2, W=120)
+    m, am = oracle.scan(A, np.arange(150), B, metric)
+    assert np.array_equal(q["D"].view(np.uint32), m.view(np.uint32))
+    assert np.array_equal(q["bidx"], am)
+    assert np.all(q["level"] == 0)
+
+
+def test_kw_window_restated():
+    """The window rule restated in Python on tiny sets from the oracle's keys:
+    per structure, buckets in scale order, points by index, first W distinct."""
+    A, B = workloads.gaussian_mixture(40, 60, 3, 12, clusters=3)
+    L, k, W, seed = 6, 3, 5, 9
+    q = oracle.crude_nn_kw(A, B, L1, hash_seed=seed, L=L, k=k, W=W)
+    best = np.full(40, np.inf, np.float32)
+    arg = np.full(40, -1)
+    lev = np.full(40, L)
+    for r in range(k):
+        s = (seed + r * 0x9E3779B97F4A7C15) % (1 << 64)
+        e_lo = oracle.top_exp(A, B) - L + 1
+        kA, kB = oracle.keys(A, e_lo, L, s), oracle.keys(B, e_lo, L, s)
+        for a in range(40):
+            taken = []
+            for l in range(L):
+                for b in range(60):
+                    if len(taken) < W and kB[l, b] == kA[l, a] and b not in taken:
+                        taken.append(b)
+                        lev[a] = min(lev[a], l)
+            for b in taken or [0]:
+                v = oracle.dist(A[a], B[b], L1)
+                if v < best[a] or (v == best[a] and b < arg[a]):
+                    best[a], arg[a] = v, b
+    assert np.array_equal(q["bidx"], arg) and np.array_equal(q["level"], lev)
+    assert np.array_equal(q["D"], best)
