@@ -91,7 +91,13 @@ typedef struct {
     int32_t top_exp;    /* CH_TOP_EXP_AUTO: ceil(log2 Delta)+1 from the joint bounding box */
     uint64_t hash_seed; /* Philox key of the shifts, multipliers and Gaussian matrix */
     int32_t group;      /* ch_group */
-    int32_t reserved;
+    uint32_t window;    /* W of the k x W variant (Section 3): the first W distinct points of B in a's
+                           buckets, finest scale first, by index within a bucket (0 or 1: Fig. 2's first
+                           point; at most 64) */
+    uint32_t repeats;   /* k of the k x W variant: independent structures, structure r keyed by
+                           hash_seed + r * 0x9E3779B97F4A7C15 (0 or 1: one; at most 16); D_a is the
+                           distance to the closest of all retrieved points.  k x W > 1 uses the sort
+                           grouping whatever `group` says. */
 } ch_hash_params;
 
 /* How the samples x_l are drawn:

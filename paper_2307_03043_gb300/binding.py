@@ -37,7 +37,7 @@ class ChamferError(RuntimeError):
 class ch_hash_params(ctypes.Structure):
     _fields_ = [("metric", ctypes.c_int32), ("levels", ctypes.c_uint32), ("proj_dim", ctypes.c_uint32),
                 ("top_exp", ctypes.c_int32), ("hash_seed", ctypes.c_uint64), ("group", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("window", ctypes.c_uint32), ("repeats", ctypes.c_uint32)]
 
 
 class ch_est_params(ctypes.Structure):
@@ -144,16 +144,17 @@ def _check(st, where, ctx=None):
         raise ChamferError(st, where, msg)
 
 
-def hash_params(metric=CH_L1, levels=10, proj_dim=16, top_exp=None, hash_seed=0, group=CH_GROUP_HASH):
+def hash_params(metric=CH_L1, levels=10, proj_dim=16, top_exp=None, hash_seed=0, group=CH_GROUP_HASH, window=1,
+                repeats=1):
     return ch_hash_params(metric, levels, proj_dim, CH_TOP_EXP_AUTO if top_exp is None else top_exp,
-                          hash_seed, group, 0)
+                          hash_seed, group, window, repeats)
 
 
 def est_params(metric=CH_L1, levels=10, proj_dim=16, top_exp=None, hash_seed=0, group=CH_GROUP_HASH,
-               eps=0.1, T=0, sample_seed=0, screen=CH_SCREEN_AUTO, rerank_k=8, sampling=None):
+               eps=0.1, T=0, sample_seed=0, screen=CH_SCREEN_AUTO, rerank_k=8, sampling=None, window=1, repeats=1):
     p = ch_est_params()
     lib().ch_default_params(ctypes.byref(p))
-    p.hash = hash_params(metric, levels, proj_dim, top_exp, hash_seed, group)
+    p.hash = hash_params(metric, levels, proj_dim, top_exp, hash_seed, group, window, repeats)
     p.eps, p.T, p.sample_seed, p.screen, p.rerank_k = eps, T, sample_seed, screen, rerank_k
     p.sampling = CH_SAMPLING_IMPORTANCE if sampling is None else sampling
     return p

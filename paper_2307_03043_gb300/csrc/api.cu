@@ -128,6 +128,8 @@ static void check_hash(const ch_hash_params* hp) {
   if (hp->metric == CH_L2)
     CHX_CHECK(hp->proj_dim >= 1 && hp->proj_dim <= uint32_t(kMaxProj), CH_EINVAL, "proj_dim must be in 1..64");
   CHX_CHECK(hp->group == CH_GROUP_HASH || hp->group == CH_GROUP_SORT, CH_EINVAL, "group must be HASH or SORT");
+  CHX_CHECK(hp->window <= uint32_t(kWindowMax), CH_EINVAL, "window must be in 0..64 (0 = 1)");
+  CHX_CHECK(hp->repeats <= 16u, CH_EINVAL, "repeats must be in 0..16 (0 = 1)");
 }
 
 static void check_pair(ch_ctx* c, const ch_set* A, const ch_set* B) {
@@ -210,9 +212,17 @@ struct CrudeBufs {
   int32_t* e_top;
   ulonglong2* slots;   // CH_GROUP_HASH: bucket tables of one scale group
   TablePlan plan;
-  uint64_t *keysA, *keysB;  // CH_GROUP_SORT: keys [L][n] and the sort's scratch
+  uint64_t *keysA, *keysB;  // CH_GROUP_SORT and k x W: keys [L][n] and the sort's scratch
   void* sort_work;
+  int32_t* cand;  // k x W: [nA][k W] candidate indices
 };
+
+// k x W CrudeNN (Section 3's large-scale variant) is asked for
+static bool crude_kw(const ch_hash_params* hp) { return hp->window > 1 || hp->repeats > 1; }
+static int kw_k(const ch_hash_params* hp) { return hp->repeats ? static_cast<int>(hp->repeats) : 1; }
+static int kw_w(const ch_hash_params* hp) { return hp->window ? static_cast<int>(hp->window) : 1; }
+// hash seed of structure r (r = 0: the base structure)
+static uint64_t kw_seed(uint64_t seed, int r) { return seed + uint64_t(r) * 0x9E3779B97F4A7C15ull; }
 
 template <class L>
 static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_params* hp, CrudeBufs* cb) {
@@ -222,6 +232,17 @@ static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_p
   cb->tab = take_tables(lay, dd, static_cast<int>(hp->levels));
   cb->e_top = lay.template take<int32_t>(1);
   const int nl = static_cast<int>(hp->levels);
+  cb->cand = nullptr;
+  if (crude_kw(hp)) {
+    CHX_CHECK(sort_group_supported(A->n, B->n, nl), CH_EINVAL, "k x W CrudeNN: (nA + nB) * levels must be below 2^31");
+    cb->plan = TablePlan{0, 0};
+    cb->slots = nullptr;
+    cb->keysA = lay.template take<uint64_t>(std::max<size_t>(size_t(nl) * A->n, 1));
+    cb->keysB = lay.template take<uint64_t>(size_t(nl) * B->n);
+    cb->sort_work = lay.template take<char>(sort_window_workspace(A->n, B->n, nl));
+    cb->cand = lay.template take<int32_t>(std::max<size_t>(size_t(A->n) * kw_k(hp) * kw_w(hp), 1));
+    return;
+  }
   if (hp->group == CH_GROUP_SORT) {
     CHX_CHECK(sort_group_supported(A->n, B->n, nl), CH_EINVAL, "sort grouping: (nA + nB) * levels must be below 2^31");
     cb->plan = TablePlan{0, 0};
@@ -244,6 +265,24 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
   const int L = static_cast<int>(hp->levels);
   const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
   cudaStream_t s = c->stream;
+  if (crude_kw(hp)) {
+    // k structures in turn (own embedding seed, scales, keys), each adding its
+    // window to the candidate lists; then D_a over all candidates
+    const int k = kw_k(hp), W = kw_w(hp);
+    for (int r = 0; r < k; ++r) {
+      ch_hash_params hr = *hp;
+      hr.hash_seed = kw_seed(hp->hash_seed, r);
+      run_hashed(c, A, &hr, &cb->hA, status);
+      run_hashed(c, B, &hr, &cb->hB, status);
+      launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp,
+                          hr.hash_seed, cb->tab, r == 0 ? cb->e_top : nullptr, status, s);
+      launch_keys_write(cb->hB.src, L, cb->tab, cb->keysB, s);
+      launch_keys_write(cb->hA.src, L, cb->tab, cb->keysA, s);
+      launch_sort_window(cb->keysA, A->n, cb->keysB, B->n, L, W, r, cb->sort_work, cb->cand, k * W, level, s);
+    }
+    launch_cand_dist(A, B, hp->metric, cb->cand, k * W, bidx, D, maxD, s);
+    return;
+  }
   run_hashed(c, A, hp, &cb->hA, status);
   run_hashed(c, B, hp, &cb->hB, status);
   launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp, hp->hash_seed,

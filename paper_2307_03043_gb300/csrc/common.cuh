@@ -282,6 +282,18 @@ void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStre
 // radix-sort grouping (CH_GROUP_SORT): keys [L][nA] and [L][nB] -> bidx, level
 size_t sort_group_workspace(int64_t nA, int64_t nB, int L);
 bool sort_group_supported(int64_t nA, int64_t nB, int L);
+
+// k x W CrudeNN (Section 3): structure r's window of W points per a, by the same
+// sort, into cand[a * stride + r * W + q] (-1 past the retrieved points); level[a]
+// = the finest scale any structure so far found a point at (set by r = 0)
+constexpr int kWindowMax = 64;
+size_t sort_window_workspace(int64_t nA, int64_t nB, int L);
+void launch_sort_window(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L, int W, int r,
+                        void* work, int32_t* cand, int stride, uint8_t* level, cudaStream_t s);
+// D_a = min over a's candidates of the canonical distance, b(a) its argmin
+// (smallest index on ties); with maxD, max_a D_a (ordered-encoded)
+void launch_cand_dist(const ch_set* A, const ch_set* B, int metric, const int32_t* cand, int stride, int64_t* bidx,
+                      float* D, uint32_t* maxD, cudaStream_t s);
 void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L,
                        void* work, int64_t* bidx, uint8_t* level, cudaStream_t s);
 

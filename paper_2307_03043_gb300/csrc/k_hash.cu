@@ -2,6 +2,7 @@
 // l2 -> l1 Gaussian embedding, the shifted grids at every scale, bucket
 // tables of B probed by A in increasing scale order, and D_a = d(a, b(a)).
 #include <cstring>
+#include <type_traits>
 
 #include "tma.cuh"
 
@@ -1013,6 +1014,68 @@ void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64
     default: crude_dist_1<CH_FP8E4M3>(A, B, metric, bidx, D, maxD, G, grid, s); break;
   }
   launch_check("crude_dist");
+}
+
+// ------------------------------------------------------------------ k x W candidates
+// One warp per a: the canonical distance to each candidate (lane r sums
+// coordinates j = r mod 32, then the halving tree by shuffles), the minimum with
+// the smallest index on ties; one atomic per warp folds max D into *maxD.
+template <int DTA, int DTB, int METRIC>
+__global__ void __launch_bounds__(256) k_cand_dist(const void* A, const float* scA, int64_t nA, const void* B,
+                                                   const float* scB, int d, const int32_t* cand, int stride,
+                                                   int64_t* bidx, float* D, uint32_t* maxD) {
+  const int64_t a = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (a >= nA) return;
+  float best = __int_as_float(0x7F800000);
+  int64_t arg = INT64_MAX;
+  for (int c = 0; c < stride; ++c) {
+    const int32_t b = cand[a * stride + c];
+    if (b < 0) continue;
+    float p = 0.0f;
+    for (int j = lane; j < d; j += 32) {
+      const float t = __fsub_rn(load_elem<DTA>(A, a, d, j, scA), load_elem<DTB>(B, b, d, j, scB));
+      p = (METRIC == CH_L1) ? __fadd_rn(p, fabsf(t)) : __fmaf_rn(t, t, p);
+    }
+#pragma unroll
+    for (int sh = 16; sh >= 1; sh >>= 1) p = __fadd_rn(p, __shfl_down_sync(0xFFFFFFFFu, p, sh));
+    const float v = __shfl_sync(0xFFFFFFFFu, (METRIC == CH_L1) ? p : __fsqrt_rn(p), 0);
+    if (v < best || (v == best && b < arg)) {
+      best = v;
+      arg = b;
+    }
+  }
+  if (lane == 0) {
+    D[a] = best;
+    bidx[a] = arg;
+    if (maxD) atomicMax(maxD, ord_enc(best));
+  }
+}
+
+void launch_cand_dist(const ch_set* A, const ch_set* B, int metric, const int32_t* cand, int stride, int64_t* bidx,
+                      float* D, uint32_t* maxD, cudaStream_t s) {
+  if (maxD) CHX_CUDA(cudaMemsetAsync(maxD, 0, sizeof(uint32_t), s));
+  if (A->n == 0) return;
+  const int grid = static_cast<int>(ceil_div(A->n * 32, 256));
+  auto go = [&](auto dta, auto dtb) {
+    constexpr int DTA = decltype(dta)::value, DTB = decltype(dtb)::value;
+    if (metric == CH_L1)
+      k_cand_dist<DTA, DTB, CH_L1><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, cand,
+                                                          stride, bidx, D, maxD);
+    else
+      k_cand_dist<DTA, DTB, CH_L2><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, cand,
+                                                          stride, bidx, D, maxD);
+  };
+  using F = std::integral_constant<int, CH_F32>;
+  using H = std::integral_constant<int, CH_BF16>;
+  using E = std::integral_constant<int, CH_FP8E4M3>;
+  // both sets have one storage type (checked by the caller)
+  switch (A->dtype) {
+    case CH_F32: go(F{}, F{}); break;
+    case CH_BF16: go(H{}, H{}); break;
+    default: go(E{}, E{}); break;
+  }
+  launch_check("cand_dist");
 }
 
 }  // namespace chx

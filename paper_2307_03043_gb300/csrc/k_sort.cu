@@ -263,11 +263,10 @@ bool sort_group_supported(int64_t nA, int64_t nB, int L) {
          (nA + nB) * L < (int64_t(1) << 31);
 }
 
-void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L, void* work,
-                       int64_t* bidx, uint8_t* level, cudaStream_t s) {
-  if (nA == 0) return;
+// the stable sort and the run heads; returns the sorted tags
+static const uint32_t* sort_core(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L,
+                                 const SortWork& w, cudaStream_t s) {
   const int64_t n = (nA + nB) * L;
-  SortWork w = carve_sort(work, nA, nB, L);
   const int gb = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 152 * 16));
   k_sort_build<<<gb, 256, 0, s>>>(keysA, nA, keysB, nB, L, w.k0, w.t0);
   launch_check("sort_build");
@@ -287,11 +286,87 @@ void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB,
   launch_check("sort_heads");
   k_sort_carry<<<1, 1024, 0, s>>>(w.blast, w.nhb);
   launch_check("sort_carry");
+  return tin;
+}
+
+void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L, void* work,
+                       int64_t* bidx, uint8_t* level, cudaStream_t s) {
+  if (nA == 0) return;
+  const int64_t n = (nA + nB) * L;
+  SortWork w = carve_sort(work, nA, nB, L);
+  const uint32_t* tin = sort_core(keysA, nA, keysB, nB, L, w, s);
+  const int gb = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 152 * 16));
   CHX_CUDA(cudaMemsetAsync(w.packed, 0xFF, size_t(nA) * 8, s));
   k_sort_assign<<<gb, 256, 0, s>>>(tin, w.hp, w.blast, n, w.packed);
   launch_check("sort_assign");
   k_sort_finish<<<static_cast<int>(ceil_div(nA, 256)), 256, 0, s>>>(w.packed, nA, L, bidx, level);
   launch_check("sort_finish");
+}
+
+// ------------------------------------------------------------------ k x W window
+namespace {
+
+// pos[scale * nA + a] = sorted position of a's entry at that scale
+__global__ void k_sort_pos(const uint32_t* tag, int64_t n, int64_t nA, int32_t* pos) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t t = tag[i];
+    if (t & 0x80000000u) pos[int64_t(tag_scale(t)) * nA + (t & kIdxMask)] = static_cast<int32_t>(i);
+  }
+}
+
+// Structure r's window for each a: scales in increasing order; in a's run the B
+// entries come first, in increasing index (initial order + stable sort), so the
+// first W distinct of them, over the scales, are read off directly.  A structure
+// that finds nothing contributes B[0].
+__global__ void k_window(const uint32_t* tag, const int32_t* hp, const int32_t* carry, const int32_t* pos,
+                         int64_t n, int64_t nA, int L, int W, int r, int stride, int32_t* cand, uint8_t* level) {
+  const int64_t a = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (a >= nA) return;
+  int32_t taken[kWindowMax];
+  int cnt = 0, first = L;
+  for (int l = 0; l < L && cnt < W; ++l) {
+    const int64_t i = pos[int64_t(l) * nA + a];
+    int64_t j = hp[i];
+    if (j < 0) j = carry[i / kHeadBlock];
+    for (; j < n && cnt < W; ++j) {
+      const uint32_t t = tag[j];
+      if (t & 0x80000000u) break;  // the run's B entries are over
+      const int32_t b = static_cast<int32_t>(t & kIdxMask);
+      bool seen = false;
+      for (int q = 0; q < cnt; ++q) seen |= taken[q] == b;
+      if (!seen) {
+        taken[cnt++] = b;
+        first = min(first, l);
+      }
+    }
+  }
+  if (cnt == 0) taken[cnt++] = 0;
+  int32_t* out = cand + a * stride + int64_t(r) * W;
+  for (int q = 0; q < W; ++q) out[q] = q < cnt ? taken[q] : -1;
+  if (r == 0 || first < level[a]) level[a] = static_cast<uint8_t>(first);
+}
+
+}  // namespace
+
+size_t sort_window_workspace(int64_t nA, int64_t nB, int L) {
+  return sort_group_workspace(nA, nB, L) + size_t(nA) * L * 4 + 256;
+}
+
+void launch_sort_window(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L, int W, int r,
+                        void* work, int32_t* cand, int stride, uint8_t* level, cudaStream_t s) {
+  if (nA == 0) return;
+  CHX_CHECK(W >= 1 && W <= kWindowMax, CH_EINVAL, "window must be in 1..64");
+  const int64_t n = (nA + nB) * L;
+  SortWork w = carve_sort(work, nA, nB, L);
+  int32_t* pos = reinterpret_cast<int32_t*>(static_cast<char*>(work) +
+                                            ((sort_group_workspace(nA, nB, L) + 255) & ~size_t(255)));
+  const uint32_t* tin = sort_core(keysA, nA, keysB, nB, L, w, s);
+  const int gb = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 152 * 16));
+  k_sort_pos<<<gb, 256, 0, s>>>(tin, n, nA, pos);
+  launch_check("sort_pos");
+  k_window<<<static_cast<int>(ceil_div(nA, 128)), 128, 0, s>>>(tin, w.hp, w.blast, pos, n, nA, L, W, r, stride, cand,
+                                                               level);
+  launch_check("window");
 }
 
 }  // namespace chx

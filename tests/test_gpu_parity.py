@@ -187,6 +187,44 @@ def test_crude_nn_few_levels_and_fallback(ctx, pair_factory, group):
         assert np.array_equal(D, r["D"])
 
 
+@pytest.mark.parametrize("metric", [L1, L2])
+@pytest.mark.parametrize("k,W", [(1, 4), (3, 1), (2, 8), (4, 16), (1, 64)])
+def test_kw_crude_nn_bit_exact(ctx, pair_factory, metric, k, W):
+    """k x W CrudeNN (Section 3): b(a), level and D_a bit-exact against the oracle."""
+    A, B = workloads.gaussian_mixture(2100, 2600, 12, 5 + k + W, clusters=8)
+    B[2000:2300] = B[10:310]  # duplicates: ties by index
+    p = pair_factory(A, B)
+    nA = A.shape[0]
+    bidx = torch.full((nA,), -5, dtype=torch.int64, device="cuda")
+    D = torch.full((nA,), -1.0, dtype=torch.float32, device="cuda")
+    lv = torch.full((nA,), 255, dtype=torch.uint8, device="cuda")
+    hp = ch.hash_params(metric, 10, 16, None, 7, ch.CH_GROUP_HASH, W, k)
+    ch.ch_crude_nn(ctx, p.sA, p.sB, hp, bidx, D, lv)
+    r = oracle.crude_nn_kw(A, B, metric, hash_seed=7, k=k, W=W)
+    assert np.array_equal(bidx.cpu().numpy(), r["bidx"])
+    assert np.array_equal(lv.cpu().numpy(), r["level"])
+    assert np.array_equal(D.cpu().numpy().view(np.uint32), r["D"].view(np.uint32))
+
+
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_kw_estimate_matches_oracle(ctx, pair_factory, metric):
+    A, B = workloads.gaussian_mixture(3000, 2000, 16, 77, clusters=5)
+    p = pair_factory(A, B)
+    T = 1500
+    prm = ch.est_params(metric, 10, 16, None, 3, T=T, sample_seed=9, screen=ch.CH_SCREEN_EXACT, window=8, repeats=2)
+    eta, rep = ch.ch_estimate(ctx, p.sA, p.sB, prm, report=True)
+    r = oracle.crude_nn_kw(A, B, metric, hash_seed=3, k=2, W=8)
+    w, prefix, W, _ = oracle.weights(r["D"])
+    idx = oracle.draws(prefix, W, T, 9)
+    m, _ = oracle.scan(A, idx, B, metric)
+    eta_o = oracle.combine(m, idx, w, W)
+    assert rep.W == W and abs(eta / eta_o - 1) < 1e-5
+    # a wider window never raises D, so D_total does not grow
+    _, rep1 = ch.ch_estimate(ctx, p.sA, p.sB, ch.est_params(metric, 10, 16, None, 3, T=T, sample_seed=9,
+                                                            screen=ch.CH_SCREEN_EXACT), report=True)
+    assert rep.D_total <= rep1.D_total
+
+
 def test_sort_grouping_long_runs(ctx, pair_factory):
     """Radix-sort grouping over many tiles: runs of equal keys that cross sort
     tiles and head-scan blocks (B holds few distinct points, A many copies)."""
