@@ -57,7 +57,8 @@ WORKLOADS = {
                     desc="batched: 4096 pairs, |A| and |B| log-uniform in [256, 50000], d=3 ellipsoid/box "
                          "surfaces with 1% noise (B a resample of A's shape), fp32, l2 (l1 alongside), eps=0.1"),
     "curves": dict(n=0, d=16, dtype="f32",
-                   desc="sample complexity: relative error of importance vs uniform sampling over T, 32 seeds "
+                   desc="sample complexity: relative error of importance (CrudeNN 1x1 and 4x16) vs uniform "
+                        "sampling over T, 32 seeds "
                         "per T, on the 100k x 100k d=128 mixture and on two 100k d=16 Gaussian clouds with one "
                         "far outlier in A (l2)"),
 }
@@ -390,9 +391,11 @@ def run_curves(args, ch, ctx, torch):
         rows = []
         for T in (16, 64, 256, 1024, 4096):
             rec = {"T": T}
-            for label, smp in (("importance", ch.CH_SAMPLING_IMPORTANCE), ("uniform", ch.CH_SAMPLING_UNIFORM)):
+            for label, smp, kk, ww in (("importance", ch.CH_SAMPLING_IMPORTANCE, 1, 1),
+                                       ("importance_4x16", ch.CH_SAMPLING_IMPORTANCE, 4, 16),
+                                       ("uniform", ch.CH_SAMPLING_UNIFORM, 1, 1)):
                 prm = [ch.est_params(ch.CH_L2, LEVELS, PROJ, None, 1000 * T + k, T=T, sample_seed=1000 * T + k,
-                                     sampling=smp) for k in range(seeds)]
+                                     sampling=smp, repeats=kk, window=ww) for k in range(seeds)]
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 eta, st = ch.ch_estimate_batch(ctx, [sA] * seeds, [sB] * seeds, prm)
