@@ -104,6 +104,8 @@ def _bind(so):
         "or_estimate": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _u64, _i32, _i32, _i32,
                                           _i64, _u64, _p, _p, _p, _p, _p, _p]),
         "or_draws_uniform": (None, [_i64, _i64, _u64, _p]),
+        "or_keys_simhash": (None, [_p, _i64, _i32, _i32, _u64, _p]),
+        "or_crude_nn_simhash": (None, [_p, _i64, _p, _i64, _i32, _i32, _u64, _i32, _i32, _p, _p, _p]),
         "or_crude_nn_kw": (None, [_p, _i64, _p, _i64, _i32, _i32, _u64, _i32, _i32, _i32, _i32, _i32, _p, _p, _p]),
         "or_estimate_uniform": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _i64, _u64, _p, _p]),
         "or_exact_fp64": (ctypes.c_double, [_p, _i64, _p, _i64, _i32, _i32, _p]),
@@ -295,6 +297,26 @@ def crude_nn_kw(A, B, metric: int, hash_seed: int = 0, L: int = 10, proj_dim: in
     level = np.zeros(nA, dtype=np.uint8)
     lib().or_crude_nn_kw(_ptr(A), nA, _ptr(B), B.shape[0], A.shape[1], metric, hash_seed, L, proj_dim,
                          INT32_MIN if top_exp is None else int(top_exp), k, W, _ptr(bidx), _ptr(D), _ptr(level))
+    return {"bidx": bidx, "D": D, "level": level}
+
+
+def keys_simhash(Y, L: int, seed: int) -> np.ndarray:
+    """SimHash keys [L][n] of embedded points Y [n][K] (first K >> l sign bits at level l)."""
+    Y = _f32(Y)
+    out = np.zeros((L, Y.shape[0]), dtype=np.uint64)
+    lib().or_keys_simhash(_ptr(Y), Y.shape[0], Y.shape[1], L, seed, _ptr(out))
+    return out
+
+
+def crude_nn_simhash(A, B, metric: int, hash_seed: int = 0, L: int = 10, K: int = 16) -> dict:
+    """CrudeNN (Fig. 2) with SimHash buckets on the K-wide Gaussian embedding."""
+    A, B = _f32(A), _f32(B)
+    nA = A.shape[0]
+    bidx = np.zeros(nA, dtype=np.int64)
+    D = np.zeros(nA, dtype=np.float32)
+    level = np.zeros(nA, dtype=np.uint8)
+    lib().or_crude_nn_simhash(_ptr(A), nA, _ptr(B), B.shape[0], A.shape[1], metric, hash_seed, L, K,
+                              _ptr(bidx), _ptr(D), _ptr(level))
     return {"bidx": bidx, "D": D, "level": level}
 
 

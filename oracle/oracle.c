@@ -371,6 +371,53 @@ int or_crude_nn(const float* A, int64_t nA, const float* B, int64_t nB, int d, i
 }
 
 /* ------------------------------------------------------------------------ */
+/* SimHash at every scale (the family Section 3 ran at scale on unit-norm    */
+/* data: random hyperplanes, Charikar 2002).  R14: the hyperplanes are the   */
+/* rows of the l2 embedding's Gaussian matrix (K = proj_dim <= 64 of them);  */
+/* bit i of a point is 1 unless y_i < 0; level l (finest first) keeps the    */
+/* first t_l = max(1, K >> l) bits, and its key is                           */
+/* mix64(bits + mix64(((u64)l << 32) ^ seed)), 0 replaced by 1.  For a fixed */
+/* level the key is a bijection of the kept bits, so keys collide exactly    */
+/* when the sign prefixes agree, and a collision at one level implies one    */
+/* at every coarser level.                                                  */
+/* ------------------------------------------------------------------------ */
+void or_keys_simhash(const float* Y, int64_t n, int K, int L, uint64_t seed, uint64_t* keys)
+{
+    for (int64_t p = 0; p < n; p++) {
+        uint64_t word = 0;
+        for (int i = 0; i < K; i++)
+            if (!(Y[(size_t)p * K + i] < 0.0f)) word |= 1ull << i;
+        for (int l = 0; l < L; l++) {
+            int t = K >> l;
+            if (t < 1) t = 1;
+            const uint64_t bits = t >= 64 ? word : (word & ((1ull << t) - 1));
+            uint64_t k = or_mix64(bits + or_mix64(((uint64_t)(uint32_t)l << 32) ^ seed));
+            keys[(size_t)l * n + p] = k == 0 ? 1 : k;
+        }
+    }
+}
+
+/* CrudeNN (Fig. 2) with the SimHash family: buckets from or_keys_simhash on */
+/* the embedding y = G x, then the same first-colliding-level rule (R6).     */
+void or_crude_nn_simhash(const float* A, int64_t nA, const float* B, int64_t nB, int d, int metric,
+                         uint64_t hash_seed, int L, int K, int64_t* bidx, float* D, uint8_t* level)
+{
+    int dd;
+    float* YA = hashed_space(A, nA, d, OR_L2, hash_seed, K, &dd);
+    float* YB = hashed_space(B, nB, d, OR_L2, hash_seed, K, &dd);
+    uint64_t* kA = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(nA > 0 ? nA : 1) * L);
+    uint64_t* kB = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(nB > 0 ? nB : 1) * L);
+    or_keys_simhash(YA, nA, K, L, hash_seed, kA);
+    or_keys_simhash(YB, nB, K, L, hash_seed, kB);
+    crude_from_keys(kA, nA, kB, nB, L, bidx, level);
+    for (int64_t a = 0; a < nA; a++) D[a] = or_dist(A + (size_t)a * d, B + (size_t)bidx[a] * d, d, metric);
+    free(kA);
+    free(kB);
+    free(YA);
+    free(YB);
+}
+
+/* ------------------------------------------------------------------------ */
 /* k x W CrudeNN (Section 3, the large-scale variant): k independent hash    */
 /* structures; in each, a's buckets are visited in increasing scale order    */
 /* and the first W distinct points of B found there are retrieved; D_a is    */

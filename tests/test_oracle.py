@@ -573,3 +573,65 @@ def test_kw_window_restated():
                     best[a], arg[a] = v, b
     assert np.array_equal(q["bidx"], arg) and np.array_equal(q["level"], lev)
     assert np.array_equal(q["D"], best)
+
+
+# ------------------------------------------------------------------ SimHash family (Section 3)
+def test_simhash_keys_are_sign_prefixes():
+    """Keys agree exactly when the kept sign prefixes agree; a collision at a level
+    implies one at every coarser level."""
+    g = np.random.default_rng(3)
+    Y = g.standard_normal((300, 16)).astype(np.float32)
+    Y[100:150] = Y[:50]
+    Y[150:200, :4] = Y[:50, :4]  # the same 4-bit prefix, different tails
+    Y[7, 3] = 0.0                # +0 and -0 both give bit 1
+    Y[8] = Y[7]
+    Y[8, 3] = -0.0
+    L = 6
+    keys = oracle.keys_simhash(Y, L, 11)
+    bits = (~(Y < 0)).astype(np.uint64)
+    for l in range(L):
+        t = max(1, 16 >> l)
+        pref = (bits[:, :t] << np.arange(t, dtype=np.uint64)).sum(axis=1)
+        same_key = keys[l][:, None] == keys[l][None, :]
+        same_pref = pref[:, None] == pref[None, :]
+        assert np.array_equal(same_key, same_pref)
+        if l + 1 < L:
+            assert np.all(~same_key | (keys[l + 1][:, None] == keys[l + 1][None, :]))
+    assert np.all(keys != 0)
+
+
+def test_simhash_bit_collision_probability():
+    """Per hyperplane, Pr[same bit] = 1 - theta / pi for two vectors at angle theta
+    (the SimHash property; the Irwin-Hall rows are nearly Gaussian): 4000 hyperplane
+    draws, within 0.02."""
+    d = 24
+    for theta in (0.3, 1.0, 2.2):
+        x = np.zeros(d, np.float32)
+        x[0] = 1.0
+        y = np.zeros(d, np.float32)
+        y[0], y[1] = math.cos(theta), math.sin(theta)
+        same = 0
+        for seed in range(250):
+            Y = oracle.hashed(np.stack([x, y]), L2, seed, 16)
+            same += int(np.sum((Y[0] < 0) == (Y[1] < 0)))
+        assert abs(same / 4000 - (1 - theta / math.pi)) < 0.02
+
+
+def test_simhash_crude_nn():
+    """SimHash CrudeNN: b(a) is the smallest index in the first level whose sign
+    prefix matches (restated from the keys), D_a = d(a, b(a)) >= the nearest distance."""
+    A, B = workloads.unit_mixture(500, 700, 12, 4)
+    L, K, seed = 8, 32, 5
+    r = oracle.crude_nn_simhash(A, B, L2, hash_seed=seed, L=L, K=K)
+    kA = oracle.keys_simhash(oracle.hashed(A, L2, seed, K), L, seed)
+    kB = oracle.keys_simhash(oracle.hashed(B, L2, seed, K), L, seed)
+    _, nn = oracle.exact_canonical(A, B, L2)
+    for a in range(500):
+        lv, b = L, 0
+        for l in range(L):
+            hit = np.flatnonzero(kB[l] == kA[l, a])
+            if hit.size:
+                lv, b = l, int(hit[0])
+                break
+        assert r["level"][a] == lv and r["bidx"][a] == b
+        assert r["D"][a] == oracle.dist(A[a], B[b], L2) >= nn[a]
