@@ -76,6 +76,13 @@ typedef enum {
  * Both give bit-identical b(a). */
 typedef enum { CH_GROUP_HASH = 0, CH_GROUP_SORT = 1 } ch_group;
 
+/* LSH family at every scale:
+ *  GRID     shifted grids of side 2^e on x (l1) or on the Gaussian embedding (l2), App. A.2;
+ *  SIMHASH  random hyperplanes (the family Section 3 ran at scale on unit-norm data): the
+ *           signs of the proj_dim-wide Gaussian embedding, the first max(1, proj_dim >> l)
+ *           of them at level l (finest first); l2 only; top_exp is ignored. */
+typedef enum { CH_FAMILY_GRID = 0, CH_FAMILY_SIMHASH = 1 } ch_family;
+
 typedef struct ch_ctx ch_ctx;
 typedef struct ch_set ch_set;
 typedef struct ch_server ch_server;
@@ -98,6 +105,7 @@ typedef struct {
                            hash_seed + r * 0x9E3779B97F4A7C15 (0 or 1: one; at most 16); D_a is the
                            distance to the closest of all retrieved points.  k x W > 1 uses the sort
                            grouping whatever `group` says. */
+    int32_t family;     /* ch_family (default GRID) */
 } ch_hash_params;
 
 /* How the samples x_l are drawn:
@@ -183,7 +191,8 @@ ch_status ch_top_exp(ch_ctx* ctx, const ch_set* A, const ch_set* B, const ch_has
  * keys = device uint64 [L][n] (scale-major).  A key is the 64-bit fingerprint
  * of the integer grid cell ceil((y_j + z_{e,j}) / 2^e) of the point's hashed
  * coordinates y (x for l1, the Gaussian embedding for l2); two points share a
- * bucket at scale e iff their keys at e are equal (Lemma on the l1 family). */
+ * bucket at scale e iff their keys at e are equal (Lemma on the l1 family).
+ * With the SimHash family, the keys of its L sign-prefix levels (e_lo unused). */
 ch_status ch_hash_keys(ch_ctx* ctx, const ch_set* X, const ch_hash_params* hp, int32_t e_lo, uint64_t* keys);
 
 /* For each a in A: the smallest scale at which some b in B shares a's bucket,

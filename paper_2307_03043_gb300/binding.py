@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libchamfer.so")
 
 CH_OK, CH_EINVAL, CH_ENOMEM, CH_ECUDA, CH_ENOTSUP, CH_ETIMEOUT, CH_EBUSY, CH_EAGAIN = range(8)
 CH_SAMPLING_IMPORTANCE, CH_SAMPLING_UNIFORM = 0, 1
+CH_FAMILY_GRID, CH_FAMILY_SIMHASH = 0, 1
 CH_L1, CH_L2 = 1, 2
 CH_F32, CH_BF16, CH_FP8E4M3 = 0, 1, 2
 CH_SCREEN_AUTO, CH_SCREEN_EXACT, CH_SCREEN_TF32, CH_SCREEN_BF16, CH_SCREEN_FP8 = range(5)
@@ -37,7 +38,7 @@ class ChamferError(RuntimeError):
 class ch_hash_params(ctypes.Structure):
     _fields_ = [("metric", ctypes.c_int32), ("levels", ctypes.c_uint32), ("proj_dim", ctypes.c_uint32),
                 ("top_exp", ctypes.c_int32), ("hash_seed", ctypes.c_uint64), ("group", ctypes.c_int32),
-                ("window", ctypes.c_uint32), ("repeats", ctypes.c_uint32)]
+                ("window", ctypes.c_uint32), ("repeats", ctypes.c_uint32), ("family", ctypes.c_int32)]
 
 
 class ch_est_params(ctypes.Structure):
@@ -145,16 +146,17 @@ def _check(st, where, ctx=None):
 
 
 def hash_params(metric=CH_L1, levels=10, proj_dim=16, top_exp=None, hash_seed=0, group=CH_GROUP_HASH, window=1,
-                repeats=1):
+                repeats=1, family=0):
     return ch_hash_params(metric, levels, proj_dim, CH_TOP_EXP_AUTO if top_exp is None else top_exp,
-                          hash_seed, group, window, repeats)
+                          hash_seed, group, window, repeats, family)
 
 
 def est_params(metric=CH_L1, levels=10, proj_dim=16, top_exp=None, hash_seed=0, group=CH_GROUP_HASH,
-               eps=0.1, T=0, sample_seed=0, screen=CH_SCREEN_AUTO, rerank_k=8, sampling=None, window=1, repeats=1):
+               eps=0.1, T=0, sample_seed=0, screen=CH_SCREEN_AUTO, rerank_k=8, sampling=None, window=1, repeats=1,
+               family=0):
     p = ch_est_params()
     lib().ch_default_params(ctypes.byref(p))
-    p.hash = hash_params(metric, levels, proj_dim, top_exp, hash_seed, group, window, repeats)
+    p.hash = hash_params(metric, levels, proj_dim, top_exp, hash_seed, group, window, repeats, family)
     p.eps, p.T, p.sample_seed, p.screen, p.rerank_k = eps, T, sample_seed, screen, rerank_k
     p.sampling = CH_SAMPLING_IMPORTANCE if sampling is None else sampling
     return p

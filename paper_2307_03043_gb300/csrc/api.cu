@@ -130,6 +130,8 @@ static void check_hash(const ch_hash_params* hp) {
   CHX_CHECK(hp->group == CH_GROUP_HASH || hp->group == CH_GROUP_SORT, CH_EINVAL, "group must be HASH or SORT");
   CHX_CHECK(hp->window <= uint32_t(kWindowMax), CH_EINVAL, "window must be in 0..64 (0 = 1)");
   CHX_CHECK(hp->repeats <= 16u, CH_EINVAL, "repeats must be in 0..16 (0 = 1)");
+  CHX_CHECK(hp->family == CH_FAMILY_GRID || hp->family == CH_FAMILY_SIMHASH, CH_EINVAL, "unknown family");
+  CHX_CHECK(hp->family != CH_FAMILY_SIMHASH || hp->metric == CH_L2, CH_EINVAL, "SimHash hashes the l2 embedding");
 }
 
 static void check_pair(ch_ctx* c, const ch_set* A, const ch_set* B) {
@@ -243,7 +245,7 @@ static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_p
     cb->cand = lay.template take<int32_t>(std::max<size_t>(size_t(A->n) * kw_k(hp) * kw_w(hp), 1));
     return;
   }
-  if (hp->group == CH_GROUP_SORT) {
+  if (hp->group == CH_GROUP_SORT || hp->family == CH_FAMILY_SIMHASH) {
     CHX_CHECK(sort_group_supported(A->n, B->n, nl), CH_EINVAL, "sort grouping: (nA + nB) * levels must be below 2^31");
     cb->plan = TablePlan{0, 0};
     cb->slots = nullptr;
@@ -256,6 +258,26 @@ static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_p
   cb->slots = lay.template take<ulonglong2>(size_t(cb->plan.per_group) << cb->plan.log_cap);
   cb->keysA = cb->keysB = nullptr;
   cb->sort_work = nullptr;
+}
+
+// keys [L][n] of both sets into cb->keysA / keysB after their hashed passes: the
+// grid family's scales and cells, or SimHash's sign prefixes (no scales)
+static void bucket_keys(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash_params* hp, CrudeBufs* cb,
+                        bool report_top, uint32_t* status) {
+  const int L = static_cast<int>(hp->levels);
+  cudaStream_t s = c->stream;
+  if (hp->family == CH_FAMILY_SIMHASH) {
+    const int K = static_cast<int>(hp->proj_dim);
+    if (report_top) CHX_CUDA(cudaMemsetAsync(cb->e_top, 0, sizeof(int32_t), s));  // no scales: reported as 0
+    launch_simhash_keys(cb->hB.Y, B->n, K, L, hp->hash_seed, cb->keysB, s);
+    launch_simhash_keys(cb->hA.Y, A->n, K, L, hp->hash_seed, cb->keysA, s);
+    return;
+  }
+  const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
+  launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp, hp->hash_seed,
+                      cb->tab, report_top ? cb->e_top : nullptr, status, s);
+  launch_keys_write(cb->hB.src, L, cb->tab, cb->keysB, s);
+  launch_keys_write(cb->hA.src, L, cb->tab, cb->keysA, s);
 }
 
 // CrudeNN (Fig. 2): embedding, scales, per-scale bucket tables of B, probes of A,
@@ -274,10 +296,7 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
       hr.hash_seed = kw_seed(hp->hash_seed, r);
       run_hashed(c, A, &hr, &cb->hA, status);
       run_hashed(c, B, &hr, &cb->hB, status);
-      launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp,
-                          hr.hash_seed, cb->tab, r == 0 ? cb->e_top : nullptr, status, s);
-      launch_keys_write(cb->hB.src, L, cb->tab, cb->keysB, s);
-      launch_keys_write(cb->hA.src, L, cb->tab, cb->keysA, s);
+      bucket_keys(c, A, B, &hr, cb, r == 0, status);
       launch_sort_window(cb->keysA, A->n, cb->keysB, B->n, L, W, r, cb->sort_work, cb->cand, k * W, level, s);
     }
     launch_cand_dist(A, B, hp->metric, cb->cand, k * W, bidx, D, maxD, s);
@@ -285,15 +304,14 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
   }
   run_hashed(c, A, hp, &cb->hA, status);
   run_hashed(c, B, hp, &cb->hB, status);
-  launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp, hp->hash_seed,
-                      cb->tab, cb->e_top, status, s);
-  if (hp->group == CH_GROUP_SORT) {
-    launch_keys_write(cb->hB.src, L, cb->tab, cb->keysB, s);
-    launch_keys_write(cb->hA.src, L, cb->tab, cb->keysA, s);
+  if (hp->group == CH_GROUP_SORT || hp->family == CH_FAMILY_SIMHASH) {
+    bucket_keys(c, A, B, hp, cb, true, status);
     launch_sort_group(cb->keysA, A->n, cb->keysB, B->n, L, cb->sort_work, bidx, level, s);
     launch_crude_dist(A, B, hp->metric, bidx, D, maxD, c->sm_count, s);
     return;
   }
+  launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp, hp->hash_seed,
+                      cb->tab, cb->e_top, status, s);
   const size_t cap = size_t(1) << cb->plan.log_cap;
   for (int L0 = 0; L0 < L; L0 += cb->plan.per_group) {
     const int nl = std::min(cb->plan.per_group, L - L0);
@@ -665,6 +683,10 @@ ch_status ch_hash_keys(ch_ctx* c, const ch_set* X, const ch_hash_params* hp, int
   cudaStream_t s = c->stream;
   CHX_CUDA(cudaMemsetAsync(st, 0, 4, s));
   run_hashed(c, X, hp, &h, st);
+  if (hp->family == CH_FAMILY_SIMHASH) {  // sign prefixes; e_lo does not apply
+    launch_simhash_keys(h.Y, X->n, static_cast<int>(hp->proj_dim), L, hp->hash_seed, keys, s);
+    return CH_OK;
+  }
   launch_scale_tables(h.box, h.box_parts, h.box, h.box_parts, dd, L, e_lo + L - 1, hp->hash_seed, tab, nullptr, st,
                       s);
   launch_keys_write(h.src, L, tab, keys, s);

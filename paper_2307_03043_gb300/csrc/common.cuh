@@ -278,6 +278,8 @@ void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTa
 void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
                         uint8_t* level, cudaStream_t s);
 void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStream_t s);
+// SimHash keys [L][n] of embedded rows Y [n][K] (K <= 64)
+void launch_simhash_keys(const float* Y, int64_t n, int K, int L, uint64_t seed, uint64_t* keys, cudaStream_t s);
 
 // radix-sort grouping (CH_GROUP_SORT): keys [L][nA] and [L][nB] -> bidx, level
 size_t sort_group_workspace(int64_t nA, int64_t nB, int L);

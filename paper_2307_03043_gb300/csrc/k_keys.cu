@@ -248,6 +248,29 @@ void dispatch_dt_w(int dtype, int dd, F&& f) {
 
 }  // namespace
 
+// SimHash keys (random hyperplanes at every scale): bit i of a point is 1 unless
+// y_i < 0; level l keeps the first max(1, K >> l) bits; key = mix64(bits +
+// mix64((l << 32) ^ seed)), 0 replaced by 1.  One thread per point, all levels.
+__global__ void k_simhash_keys(const float* Y, int64_t n, int K, int L, uint64_t seed, uint64_t* keys) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint64_t word = 0;
+  for (int i = 0; i < K; ++i)
+    if (!(Y[p * K + i] < 0.0f)) word |= 1ull << i;
+  for (int l = 0; l < L; ++l) {
+    const int t = max(1, K >> l);
+    const uint64_t bits = t >= 64 ? word : (word & ((1ull << t) - 1));
+    const uint64_t k = mix64(bits + mix64((static_cast<uint64_t>(static_cast<uint32_t>(l)) << 32) ^ seed));
+    keys[int64_t(l) * n + p] = k == 0 ? 1 : k;
+  }
+}
+
+void launch_simhash_keys(const float* Y, int64_t n, int K, int L, uint64_t seed, uint64_t* keys, cudaStream_t s) {
+  if (n == 0) return;
+  k_simhash_keys<<<static_cast<int>(ceil_div(n, 128)), 128, 0, s>>>(Y, n, K, L, seed, keys);
+  launch_check("simhash_keys");
+}
+
 void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStream_t s) {
   if (X.n == 0) return;
   const int grid = static_cast<int>(ceil_div(X.n, 128));

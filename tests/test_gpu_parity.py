@@ -225,6 +225,35 @@ def test_kw_estimate_matches_oracle(ctx, pair_factory, metric):
     assert rep.D_total <= rep1.D_total
 
 
+@pytest.mark.parametrize("K", [16, 33, 64])
+def test_simhash_keys_and_crude_nn(ctx, pair_factory, K):
+    """SimHash family (Section 3): keys and CrudeNN bit-exact against the oracle, on
+    unit-norm data; with k x W the window rule runs on SimHash buckets."""
+    A, B = workloads.unit_mixture(2500, 3000, 48, 6, clusters=40)
+    p = pair_factory(A, B)
+    L = 7
+    hp = ch.hash_params(L2, L, K, None, 12, family=ch.CH_FAMILY_SIMHASH)
+    keys = torch.zeros((L, 2500), dtype=torch.int64, device="cuda")
+    ch.ch_hash_keys(ctx, p.sA, hp, 0, keys)
+    want = oracle.keys_simhash(oracle.hashed(A, L2, 12, K), L, 12)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), want)
+    bidx = torch.full((2500,), -5, dtype=torch.int64, device="cuda")
+    D = torch.full((2500,), -1.0, dtype=torch.float32, device="cuda")
+    lv = torch.full((2500,), 255, dtype=torch.uint8, device="cuda")
+    ch.ch_crude_nn(ctx, p.sA, p.sB, hp, bidx, D, lv)
+    r = oracle.crude_nn_simhash(A, B, L2, hash_seed=12, L=L, K=K)
+    assert np.array_equal(bidx.cpu().numpy(), r["bidx"]) and np.array_equal(lv.cpu().numpy(), r["level"])
+    assert np.array_equal(D.cpu().numpy().view(np.uint32), r["D"].view(np.uint32))
+    eta = ch.ch_estimate(ctx, p.sA, p.sB, ch.est_params(L2, L, K, None, 12, T=2000, sample_seed=3,
+                                                        screen=ch.CH_SCREEN_EXACT, family=ch.CH_FAMILY_SIMHASH))
+    w, prefix, W, _ = oracle.weights(r["D"])
+    idx = oracle.draws(prefix, W, 2000, 3)
+    m, _ = oracle.scan(A, idx, B, L2)
+    assert abs(eta / oracle.combine(m, idx, w, W) - 1) < 1e-5
+    with pytest.raises(ch.ChamferError):
+        ch.ch_crude_nn(ctx, p.sA, p.sB, ch.hash_params(L1, L, K, None, 12, family=ch.CH_FAMILY_SIMHASH), bidx, D, lv)
+
+
 def test_sort_grouping_long_runs(ctx, pair_factory):
     """Radix-sort grouping over many tiles: runs of equal keys that cross sort
     tiles and head-scan blocks (B holds few distinct points, A many copies)."""
