@@ -829,8 +829,8 @@ static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, c
     run_crude(c, A, B, &p->hash, &cb, eb.bidx, eb.level, eb.D, &res->status, sb.sw.maxD);
   }
   if (events) CHX_CUDA(cudaEventRecord(c->ev[1], s));
-  launch_weights(eb.D, nA, eb.w, sb.prefix, sb.sw, s, !uniform);
-  launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, eb.idx, s);
+  launch_weights(eb.D, nA, eb.w, sb.prefix, sb.sw, s, !uniform, true);
+  launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, eb.idx, s, sb.sw.blocksum);
   if (events) CHX_CUDA(cudaEventRecord(c->ev[2], s));
   KernelTimer kt;
   if (events) {

@@ -314,11 +314,13 @@ size_t sample_blocks(int64_t nA);
 // D[0..n) = 1 (the uniform-sampling baseline's weights)
 void launch_fill_ones(float* D, int64_t n, cudaStream_t s);
 
-// weights and their prefix; max_ready: *sw.maxD already holds max_a D_a
+// weights and their prefix; max_ready: *sw.maxD already holds max_a D_a;
+// local_prefix: leave prefix block-local (sw.blocksum then holds the blocks'
+// exclusive offsets, which launch_draws takes as blockoff)
 void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s,
-                    bool max_ready = false);
+                    bool max_ready = false, bool local_prefix = false);
 void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed,
-                  int64_t* idx, cudaStream_t s);
+                  int64_t* idx, cudaStream_t s, const uint64_t* blockoff = nullptr);
 
 // optional CUDA events recorded around a stage's main kernel
 struct KernelTimer {

@@ -856,14 +856,14 @@ __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t*
     if (g < ng) {
       const bool is_lo = c < dd;
       uint32_t v = is_lo ? 0xFFFFFFFFu : 0u;
-#pragma unroll 4
+#pragma unroll 8
       for (int p = g; p < partsA; p += ng) {
-        const uint32_t u = boxA[size_t(p) * w + c];
+        const uint32_t u = __ldg(&boxA[size_t(p) * w + c]);
         v = is_lo ? min(v, u) : max(v, u);
       }
-#pragma unroll 4
+#pragma unroll 8
       for (int p = g; p < partsB; p += ng) {
-        const uint32_t u = boxB[size_t(p) * w + c];
+        const uint32_t u = __ldg(&boxB[size_t(p) * w + c]);
         v = is_lo ? min(v, u) : max(v, u);
       }
       if (is_lo) atomicMin(&s_box[c], v);
@@ -923,7 +923,8 @@ void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB,
                          int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
                          cudaStream_t s) {
   CHX_CHECK((partsA <= 1 && partsB <= 1) || dd <= kMaxProj, CH_EINVAL, "partial boxes need dd <= 64");
-  k_scale_tables<<<1, 256, 0, s>>>(boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out, status);
+  // 1024 threads: the partial-box loads of all blocks are in flight at once
+  k_scale_tables<<<1, 1024, 0, s>>>(boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out, status);
   launch_check("scale_tables");
 }
 

@@ -125,7 +125,7 @@ void launch_fill_ones(float* D, int64_t n, cudaStream_t s) {
 }
 
 void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s,
-                    bool max_ready) {
+                    bool max_ready, bool local_prefix) {
   if (nA == 0) {
     CHX_CUDA(cudaMemsetAsync(sw.W, 0, sizeof(uint64_t), s));
     CHX_CUDA(cudaMemsetAsync(sw.S, 0, sizeof(int32_t), s));
@@ -142,15 +142,18 @@ void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, S
   launch_check("weights");
   k_scan_blocksums<<<1, 1024, 0, s>>>(sw.blocksum, nb, sw.W);
   launch_check("scan_blocksums");
-  if (nb > 1) {
+  if (nb > 1 && !local_prefix) {
     k_add_offsets<<<static_cast<int>(ceil_div(nA, 256)), 256, 0, s>>>(prefix, nA, sw.blocksum);
     launch_check("add_offsets");
   }
 }
 
-// x_l = first a with prefix_a > floor(u W / 2^128), u = Philox(l_lo, l_hi, 3, 0)
+// x_l = first a with prefix_a > floor(u W / 2^128), u = Philox(l_lo, l_hi, 3, 0).
+// With blockoff, prefix holds the block-local inclusive sums of kScanTile-point
+// blocks and blockoff their exclusive offsets: the search first finds the block
+// whose inclusive end exceeds t, then the point inside it -- the same a.
 __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, int64_t T, uint64_t seed,
-                        int64_t* idx) {
+                        int64_t* idx, const uint64_t* blockoff) {
   const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (l >= T) return;
   const uint64_t W = *Wp;
@@ -166,6 +169,29 @@ __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, 
   const uint64_t phi_hi = __umul64hi(uhi, W);
   const uint64_t mid = phi_lo + plo_hi;
   const uint64_t t = phi_hi + (mid < phi_lo ? 1 : 0);
+  if (blockoff) {
+    const int64_t nb = ceil_div_dev(nA, kScanTile);
+    int64_t lo = 0, hi = nb;  // first block whose inclusive end (next block's offset, or W) exceeds t
+    while (lo < hi) {
+      const int64_t m = lo + ((hi - lo) >> 1);
+      const uint64_t end = m + 1 < nb ? blockoff[m + 1] : W;
+      if (end > t)
+        hi = m;
+      else
+        lo = m + 1;
+    }
+    const uint64_t off = blockoff[lo];
+    int64_t a0 = lo * kScanTile, a1 = min(nA, a0 + kScanTile);
+    while (a0 < a1) {  // first a in the block with off + local prefix > t
+      const int64_t m = a0 + ((a1 - a0) >> 1);
+      if (off + prefix[m] > t)
+        a1 = m;
+      else
+        a0 = m + 1;
+    }
+    idx[l] = a0;
+    return;
+  }
   int64_t lo = 0, hi = nA;  // first a with prefix[a] > t
   while (lo < hi) {
     const int64_t m = lo + ((hi - lo) >> 1);
@@ -178,9 +204,9 @@ __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, 
 }
 
 void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed, int64_t* idx,
-                  cudaStream_t s) {
+                  cudaStream_t s, const uint64_t* blockoff) {
   if (T == 0) return;
-  k_draws<<<static_cast<int>(ceil_div(T, 256)), 256, 0, s>>>(prefix, nA, W, T, seed, idx);
+  k_draws<<<static_cast<int>(ceil_div(T, 256)), 256, 0, s>>>(prefix, nA, W, T, seed, idx, blockoff);
   launch_check("draws");
 }
 
