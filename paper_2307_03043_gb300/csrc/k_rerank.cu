@@ -7,13 +7,10 @@ namespace chx {
 
 namespace {
 
-// One warp per sample.  First the R best screened entries over all chunks (by s,
-// then index); an entry stands for occ columns (first + o * stride, o < occ,
-// columns < nB).  Then their canonical binary32 distances, 32 columns at a time:
-// lane r sums coordinates j = r mod 32 of all 32 columns (loads of every column
-// in flight together), and a transposing butterfly finishes the 32 halving trees
-// at once -- at step s lane pairs (q, q + s) add the same partials the tree adds,
-// so lane q ends with column q's canonical sum.  Minimum, smallest index on ties.
+// One warp per sample: the R best screened entries over all chunks (by s, then
+// index), the canonical binary32 distance of each of an entry's occ columns
+// (first column + o * stride, o < occ, columns < nB), and their minimum (ties:
+// smaller index).
 template <int DT, int METRIC>
 __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA, int64_t nA, const void* B,
                                                 const float* scB, int64_t nB, int d, const int64_t* idx, int64_t T,
@@ -21,7 +18,6 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
                                                 int occ, int stride, int R, float* min_d, int64_t* argmin) {
   __shared__ float s_s[8][kRerankMaxCand];
   __shared__ int32_t s_i[8][kRerankMaxCand];
-  __shared__ int32_t s_sel[8][32];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t l = int64_t(blockIdx.x) * 8 + wib;
   if (l >= T) return;
@@ -41,8 +37,8 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
     s_i[wib][p] = part_i[off];
   }
   __syncwarp();
-  // the R best entries (selection only; no distance yet)
-  int nsel = 0;
+  float best = __int_as_float(0x7F800000);
+  int64_t bidx = INT64_MAX;
   for (int round = 0; round < R; ++round) {
     float ms = __int_as_float(0x7F800000);
     int32_t mi = INT32_MAX;
@@ -69,71 +65,40 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
     }
     if (mi == INT32_MAX || mi < 0) break;  // fewer than R entries
     if (lane == (mp & 31)) s_i[wib][mp] = -1;  // taken
-    if (lane == 0) s_sel[wib][round] = mi;
-    ++nsel;
     __syncwarp();
-  }
-  __syncwarp();
-  float best = __int_as_float(0x7F800000);
-  int64_t bidx = INT64_MAX;
-  const int ncol = nsel * occ;
-  for (int c0 = 0; c0 < ncol; c0 += 32) {
-    // column c0 + q: entry (c0 + q) / occ, occurrence (c0 + q) % occ
-    int32_t col[32];  // B has fewer than 2^31 points (the screen's own limit)
+    // canonical distances to the entry's columns, all at once (lane r sums
+    // coordinates j = r mod 32 of each; the reduction trees run side by side)
+    int64_t bo[kRerankMaxOcc];
+    bool vo[kRerankMaxOcc];
+    float part[kRerankMaxOcc];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int c = c0 + q;
-      col[q] = -1;
-      if (c < ncol) {
-        const int64_t b = int64_t(s_sel[wib][c / occ]) + int64_t(c % occ) * stride;
-        if (b < nB) col[q] = static_cast<int32_t>(b);
-      }
+    for (int o = 0; o < kRerankMaxOcc; ++o) {
+      bo[o] = int64_t(mi) + int64_t(o) * stride;
+      vo[o] = o < occ && bo[o] < nB;
+      part[o] = 0.0f;
     }
-    float v[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = 0.0f;
     for (int j = lane; j < d; j += 32) {
       const float x = load_elem<DT>(A, a, d, j, scA);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        if (col[q] >= 0) {
-          const float t = __fsub_rn(x, load_elem<DT>(B, col[q], d, j, scB));
-          v[q] = (METRIC == CH_L1) ? __fadd_rn(v[q], fabsf(t)) : __fmaf_rn(t, t, v[q]);
+      for (int o = 0; o < kRerankMaxOcc; ++o) {
+        if (vo[o]) {
+          const float t = __fsub_rn(x, load_elem<DT>(B, bo[o], d, j, scB));
+          part[o] = (METRIC == CH_L1) ? __fadd_rn(part[o], fabsf(t)) : __fmaf_rn(t, t, part[o]);
         }
       }
     }
-    // transposing butterfly: at the step with xor distance w the lane keeps the
-    // columns whose bit w agrees with its own lane bit w
 #pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-      const bool up = (lane & w) != 0;
+    for (int sh = 16; sh >= 1; sh >>= 1) {
 #pragma unroll
-      for (int k = 0; k < w; ++k) {
-        const float keep = up ? v[k + w] : v[k];
-        const float send = up ? v[k] : v[k + w];
-        v[k] = __fadd_rn(keep, __shfl_xor_sync(0xFFFFFFFFu, send, w));
-      }
+      for (int o = 0; o < kRerankMaxOcc; ++o) part[o] = __fadd_rn(part[o], __shfl_down_sync(0xFFFFFFFFu, part[o], sh));
     }
-    // lane q now holds column c0 + q
-    int64_t mine = -1;
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
-      if (q == lane) mine = col[q];  // -1 stays -1
-    float dist = (METRIC == CH_L1) ? v[0] : __fsqrt_rn(v[0]);
-    if (mine < 0) dist = __int_as_float(0x7F800000);
-    int64_t bi = mine < 0 ? INT64_MAX : mine;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float od = __shfl_xor_sync(0xFFFFFFFFu, dist, o);
-      const int64_t oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
-      if (od < dist || (od == dist && oi < bi)) {
-        dist = od;
-        bi = oi;
+    for (int o = 0; o < kRerankMaxOcc; ++o) {
+      const float dist = __shfl_sync(0xFFFFFFFFu, (METRIC == CH_L1) ? part[o] : __fsqrt_rn(part[o]), 0);
+      if (vo[o] && (dist < best || (dist == best && bo[o] < bidx))) {
+        best = dist;
+        bidx = bo[o];
       }
-    }
-    if (dist < best || (dist == best && bi < bidx)) {
-      best = dist;
-      bidx = bi;
     }
   }
   if (lane == 0) {
