@@ -78,18 +78,6 @@ static void carve(ch_ctx* c, F&& f) {
   f(t);
 }
 
-// result block copied to the host at the end of a synchronising call
-struct ResBlock {
-  double eta;
-  double D_total;
-  uint64_t W;
-  int32_t e_top;
-  int32_t S;
-  uint32_t status;   // call status bits
-  uint32_t statusA;  // set A status bits
-  uint32_t statusB;  // set B status bits
-  uint32_t pad;
-};
 
 __global__ void k_collect(ResBlock* r, const uint32_t* sa, const uint32_t* sb, const double* out2,
                           const uint64_t* W, const int32_t* S, const int32_t* e_top) {
@@ -839,9 +827,9 @@ static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, c
   }
   run_scan(c, A, eb.idx, T, B, p->hash.metric, R, &sc, eb.m, nullptr, &res->status, kt);
   if (events) CHX_CUDA(cudaEventRecord(c->ev[3], s));
-  launch_combine(eb.m, eb.idx, eb.w, sb.sw.W, T, eb.D, nA, eb.out2, s);
-  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, eb.out2, sb.sw.W, sb.sw.S, uniform ? nullptr : cb.e_top);
-  launch_check("collect");
+  // the combine's last pass also fills the result block
+  launch_combine(eb.m, eb.idx, eb.w, sb.sw.W, T, eb.D, nA, eb.out2, s,
+                 CollectArgs{res, A->status, B->status, sb.sw.S, uniform ? nullptr : cb.e_top});
   if (events) CHX_CUDA(cudaEventRecord(c->ev[4], s));
   if (screen_used) *screen_used = sc.screen;
   return res;

@@ -360,6 +360,28 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
                       void* work, float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s,
                       const KernelTimer& timer);
 
+// result block copied to the host at the end of a synchronising call
+struct ResBlock {
+  double eta;
+  double D_total;
+  uint64_t W;
+  int32_t e_top;
+  int32_t S;
+  uint32_t status;   // call status bits
+  uint32_t statusA;  // set A status bits
+  uint32_t statusB;  // set B status bits
+  uint32_t pad;
+};
+
+// what the combine's final pass copies into a result block (null fields skipped)
+struct CollectArgs {
+  ResBlock* res = nullptr;
+  const uint32_t* statusA = nullptr;
+  const uint32_t* statusB = nullptr;
+  const int32_t* S = nullptr;
+  const int32_t* e_top = nullptr;
+};
+
 // combine: eta = (1/T) sum m_l W / w_{x_l} (binary64) and sum D (binary64).
 // out must hold kCombineDoubles doubles: out[0] = eta, out[1] = sum D, then
 // per-block partials.  The block count is fixed, so the summation order (and
@@ -367,7 +389,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
 constexpr int kCombineBlocks = 128;
 constexpr int kCombineDoubles = 2 + 2 * kCombineBlocks;
 void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
-                    const float* D, int64_t nA, double* out, cudaStream_t s);
+                    const float* D, int64_t nA, double* out, cudaStream_t s, CollectArgs collect = CollectArgs());
 // sum of per-a minima (binary64): out[1] = sum (same layout as launch_combine)
 void launch_sum_f32(const float* v, int64_t n, double* out, cudaStream_t s);
 

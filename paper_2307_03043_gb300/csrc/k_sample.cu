@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(256) k_combine_part(const float* m, const int6
   }
 }
 
-__global__ void __launch_bounds__(kCombineBlocks) k_combine_final(const uint64_t* Wp, int64_t T, double* out) {
+__global__ void __launch_bounds__(kCombineBlocks) k_combine_final(const uint64_t* Wp, int64_t T, double* out,
+                                                                  CollectArgs c) {
   __shared__ double s_a[kCombineBlocks], s_b[kCombineBlocks];
   double a = out[2 + 2 * threadIdx.x], b = out[3 + 2 * threadIdx.x];
   block_sum2(a, b, s_a, s_b);
@@ -262,14 +263,23 @@ __global__ void __launch_bounds__(kCombineBlocks) k_combine_final(const uint64_t
     const uint64_t W = Wp ? *Wp : 0;
     out[0] = (W != 0 && T > 0) ? a / static_cast<double>(T) : 0.0;
     out[1] = b;
+    if (c.res) {
+      c.res->eta = out[0];
+      c.res->D_total = b;
+      c.res->W = W;
+      if (c.statusA) c.res->statusA = *c.statusA;
+      if (c.statusB) c.res->statusB = *c.statusB;
+      if (c.S) c.res->S = *c.S;
+      if (c.e_top) c.res->e_top = *c.e_top;
+    }
   }
 }
 
 void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
-                    const float* D, int64_t nA, double* out, cudaStream_t s) {
+                    const float* D, int64_t nA, double* out, cudaStream_t s, CollectArgs collect) {
   k_combine_part<<<kCombineBlocks, 256, 0, s>>>(m, idx, w, W, T, D, nA, out);
   launch_check("combine_part");
-  k_combine_final<<<1, kCombineBlocks, 0, s>>>(W, T, out);
+  k_combine_final<<<1, kCombineBlocks, 0, s>>>(W, T, out, collect);
   launch_check("combine_final");
 }
 

@@ -135,6 +135,7 @@ struct ScreenArgs {
   int chunks;
   int64_t chunk_len;  // B points per chunk (multiple of kBN)
   int stages;
+  int stream_q;       // 1: the sample tile's K blocks stream through the stages with B's (rows too wide to keep)
   const float* normB;   // |b|^2 [nB]
   const float* scaleB;  // FP8 row scales [nB] or null
   const float* scaleQ;  // FP8 sample scales [T] or null
@@ -152,8 +153,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int KB = args.kblocks;
   const int S = args.stages;
-  uint8_t* q_smem = smem;                                 // KB x (128 rows x 128 B)
-  uint8_t* b_smem = q_smem + size_t(KB) * kBM * kKB;      // S x (256 rows x 128 B)
+  const bool streamq = args.stream_q != 0;
+  uint8_t* q_smem = smem;  // KB x (128 rows x 128 B) resident, or S x (128 rows x 128 B) streamed
+  uint8_t* b_smem = q_smem + size_t(streamq ? S : KB) * kBM * kKB;  // S x (256 rows x 128 B)
   float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [warps][2][64] |b|^2
   float* sb_s = nb_s + 2 * kEpiWarps * kSliceCols;                         // [warps][2][64] -2 x FP8 scale
   uint64_t* bars = reinterpret_cast<uint64_t*>(sb_s + 2 * kEpiWarps * kSliceCols);
@@ -202,12 +204,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int mt = item % args.row_tiles, ck = item / args.row_tiles;
         const int64_t b_begin = int64_t(ck) * args.chunk_len;
         const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
-        if (!mbar_wait(q_empty, qphase ^ 1, abort_flag)) break;
-        qphase ^= 1;
-        mbar_expect_tx(q_full, uint32_t(KB) * kBM * kKB);
-        for (int kb = 0; kb < KB; ++kb)
-          tma_load_2d(q_smem + size_t(kb) * kBM * kKB, &tmQ, kb * kKB / (SCREEN == CH_SCREEN_TF32 ? 4 : SCREEN == CH_SCREEN_BF16 ? 2 : 1),
-                      mt * kBM, q_full);
+        constexpr int kEs = SCREEN == CH_SCREEN_TF32 ? 4 : SCREEN == CH_SCREEN_BF16 ? 2 : 1;
+        if (!streamq) {
+          if (!mbar_wait(q_empty, qphase ^ 1, abort_flag)) break;
+          qphase ^= 1;
+          mbar_expect_tx(q_full, uint32_t(KB) * kBM * kKB);
+          for (int kb = 0; kb < KB; ++kb)
+            tma_load_2d(q_smem + size_t(kb) * kBM * kKB, &tmQ, kb * kKB / kEs, mt * kBM, q_full);
+        }
         bool ok = true;
         for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += kBN) {
           for (int kb = 0; kb < KB; ++kb) {
@@ -215,10 +219,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               ok = false;
               break;
             }
-            mbar_expect_tx(&full[stage], uint32_t(kBN) * kKB);
-            tma_load_2d(b_smem + size_t(stage) * kBN * kKB, &tmB,
-                        kb * kKB / (SCREEN == CH_SCREEN_TF32 ? 4 : SCREEN == CH_SCREEN_BF16 ? 2 : 1),
-                        static_cast<int>(b0), &full[stage]);
+            mbar_expect_tx(&full[stage], uint32_t(kBN) * kKB + (streamq ? uint32_t(kBM) * kKB : 0u));
+            if (streamq)  // this K block of the sample tile rides along with B's
+              tma_load_2d(q_smem + size_t(stage) * kBM * kKB, &tmQ, kb * kKB / kEs, mt * kBM, &full[stage]);
+            tma_load_2d(b_smem + size_t(stage) * kBN * kKB, &tmB, kb * kKB / kEs, static_cast<int>(b0),
+                        &full[stage]);
             if (++stage == S) {
               stage = 0;
               phase ^= 1;
@@ -237,9 +242,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ck = item / args.row_tiles;
         const int64_t b_begin = int64_t(ck) * args.chunk_len;
         const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
-        if (!mbar_wait(q_full, qphase, abort_flag)) break;
-        qphase ^= 1;
-        tc_fence_after();
+        if (!streamq) {
+          if (!mbar_wait(q_full, qphase, abort_flag)) break;
+          qphase ^= 1;
+          tc_fence_after();
+        }
         bool ok = true;
         for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += kBN) {
           if (!mbar_wait(&acc_empty[acc], accphase ^ 1, abort_flag)) break;
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t qa = su32(q_smem + size_t(kb) * kBM * kKB);
+            const uint32_t qa = su32(q_smem + size_t(streamq ? stage : kb) * kBM * kKB);
             const uint32_t ba = su32(b_smem + size_t(stage) * kBN * kKB);
 #pragma unroll
             for (int k = 0; k < kKB / 32; ++k)  // 32 bytes of K per instruction
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           acc ^= 1;
           if (acc == 0) accphase ^= 1;
         }
-        tc_commit(q_empty);
+        if (!streamq) tc_commit(q_empty);
         if (!ok) break;
       }
     }
@@ -458,6 +465,7 @@ CUtensorMap make_map(const void* base, int dtype, int64_t rows, int d, int box_r
 
 struct Plan {
   int kblocks, row_tiles, chunks, stages, R;
+  bool stream_q;
   int64_t chunk_len, T;
   size_t smem;
   int grid;
@@ -472,8 +480,10 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   p.R = std::max(1, std::min(R, 32));  // candidates the rerank evaluates exactly
   p.kblocks = static_cast<int>(ceil_div(int64_t(d) * es, kKB));
   p.row_tiles = static_cast<int>(ceil_div(std::max<int64_t>(T, 1), kBM));
-  const size_t fixed = 1024 + size_t(p.kblocks) * kBM * kKB + 16 * kBN * sizeof(float) + 256;
-  const size_t per_stage = size_t(kBN) * kKB;
+  // the sample tile stays resident up to 96 KB (d * elem <= 768 bytes); wider rows stream
+  p.stream_q = int64_t(p.kblocks) * kBM * kKB > 96 * 1024;
+  const size_t fixed = 1024 + (p.stream_q ? 0 : size_t(p.kblocks) * kBM * kKB) + 16 * kBN * sizeof(float) + 256;
+  const size_t per_stage = size_t(kBN) * kKB + (p.stream_q ? size_t(kBM) * kKB : 0);
   const size_t limit = 227 * 1024;
   p.stages = static_cast<int>(std::min<size_t>(6, (limit - std::min(limit, fixed)) / per_stage));
   p.smem = fixed + size_t(p.stages) * per_stage;
@@ -519,7 +529,7 @@ bool screen_supported(int screen, const ch_set* A, const ch_set* B) {
   const int es = static_cast<int>(elem_size(A->dtype));
   if ((int64_t(A->d) * es) % 16 != 0) return false;     // TMA row stride
   if (int64_t(A->d) * es < kKB) return false;            // at least one full 128-byte swizzle row
-  if (int64_t(A->d) * es > 96 * 1024 / kBM) return false; // resident sample tile <= 96 KB
+  if (int64_t(A->d) * es > 16384) return false;          // rows up to 16 KB (wider than 768 B stream)
   if (B->n >= (int64_t(1) << 31)) return false;
   return true;
 }
@@ -564,6 +574,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   a.chunks = p.chunks;
   a.chunk_len = p.chunk_len;
   a.stages = p.stages;
+  a.stream_q = p.stream_q ? 1 : 0;
   a.normB = B->norms;
   a.scaleB = B->scales;
   a.scaleQ = sQ;

@@ -140,3 +140,35 @@ def test_exact_tc_mode_matches_direct(ctx):
     assert abs(v1 / v0 - 1) < 1e-4
     ch.ch_set_destroy(sA)
     ch.ch_set_destroy(sB)
+
+
+@pytest.mark.parametrize("dtype,d", [(ch.CH_F32, 768), (ch.CH_F32, 1000), (ch.CH_BF16, 768), (ch.CH_BF16, 1536),
+                                     (ch.CH_FP8E4M3, 1024)])
+def test_wide_rows_stream_the_sample_tile(ctx, dtype, d):
+    """Rows wider than 768 bytes: the sample tile's K blocks stream through the
+    stages with B's instead of staying resident (the serving mix has d = 768)."""
+    A, B = workloads.unit_mixture(900, 2600, d, 7 + d, clusters=30)
+    if dtype == ch.CH_F32:
+        A32, B32, sa, sb = A, B, None, None
+        sA, tA, _ = _set(ctx, A, dtype)
+        sB, tB, _ = _set(ctx, B, dtype)
+        screen = ch.CH_SCREEN_TF32
+    elif dtype == ch.CH_BF16:
+        Ah, Bh = workloads.to_bf16_bits(A), workloads.to_bf16_bits(B)
+        A32, B32 = workloads.bf16_bits_to_f32(Ah), workloads.bf16_bits_to_f32(Bh)
+        sA, tA, _ = _set(ctx, Ah, dtype)
+        sB, tB, _ = _set(ctx, Bh, dtype)
+        screen = ch.CH_SCREEN_BF16
+    else:
+        ca, sa = workloads.to_fp8_e4m3(A)
+        cb, sb = workloads.to_fp8_e4m3(B)
+        A32, B32 = workloads.fp8_dequant(ca, sa), workloads.fp8_dequant(cb, sb)
+        sA, tA, _ = _set(ctx, ca, dtype, sa)
+        sB, tB, _ = _set(ctx, cb, dtype, sb)
+        screen = ch.CH_SCREEN_FP8
+    idx = np.random.default_rng(d).integers(0, 900, 333).astype(np.int64)
+    idx[::41] = -1
+    m, am = _run(ctx, sA, sB, idx, screen)
+    _check(A32, B32, idx, m, am, 0.01)
+    ch.ch_set_destroy(sA)
+    ch.ch_set_destroy(sB)
