@@ -61,6 +61,10 @@ WORKLOADS = {
                         "sampling over T, 32 seeds "
                         "per T, on the 100k x 100k d=128 mixture and on two 100k d=16 Gaussian clouds with one "
                         "far outlier in A (l2)"),
+    "serving": dict(n=0, d=768, dtype="f32",
+                    desc="serving: resident sets of log-uniform 1k-500k points, d uniform in {3,128,768}, fp32 or "
+                         "bf16 uniform, l2, eps=0.1; requests pick a (d, type) pool and two of its sets; a closed "
+                         "burst measures saturation, then Poisson arrivals at 0.5/0.8/0.95x of it"),
 }
 BATCH_PAIRS = 4096
 
@@ -418,6 +422,83 @@ def run_curves(args, ch, ctx, torch):
     }))
 
 
+def run_serving(args, ch, ctx, torch):
+    """The serving workload of the measurement plan: 8 resident sets per (d, type)
+    pool, 20 000 requests in total over the three load levels (fewer with
+    --serve-requests), p50/p99 submit-to-result latency per level."""
+    from paper_2307_03043_gb300 import workloads
+    rng = np.random.default_rng(11)
+    total_req = args.serve_requests if args.serve_requests > 0 else 20_000
+    srv = ch.ch_serve_create(ctx, 48 << 30, 8, 8192)
+    pools = {}
+    k = 0
+    for d in (3, 128, 768):
+        for dt in ("f32", "bf16"):
+            sizes = workloads.log_uniform_sizes(8, 1000, 500_000, 100 + k)
+            ids = []
+            for i, n in enumerate(sizes):
+                X, _ = workloads.gaussian_mixture(int(n), 1, d, 1000 * k + i, clusters=20)
+                if dt == "bf16":
+                    X = workloads.to_bf16_bits(X)
+                ids.append((ch.ch_serve_register(srv, X, 0, X.shape[0], d, ch.CH_F32 if dt == "f32" else ch.CH_BF16),
+                            int(n)))
+            pools[(d, dt)] = ids
+            k += 1
+    keys = list(pools)
+
+    def req(seed):
+        pool = pools[keys[rng.integers(len(keys))]]
+        a, b = pool[rng.integers(len(pool))], pool[rng.integers(len(pool))]
+        p = ch.est_params(ch.CH_L2, LEVELS, PROJ, None, seed, eps=EPS, sample_seed=seed)
+        st, t = ch.ch_serve_submit(srv, a[0], b[0], p)
+        return st, t, a[1] + b[1]
+
+    burst = 300
+    t0 = time.perf_counter()
+    tickets = [req(s_) for s_ in range(burst)]
+    for st, t, _ in tickets:
+        ch.ch_serve_wait(srv, t, 600_000)
+    sat = burst / (time.perf_counter() - t0)
+    levels = []
+    seed = 10_000
+    for frac in (0.5, 0.8, 0.95):
+        n_req = total_req // 3
+        ch.ch_serve_stats_reset(srv)
+        arrivals = np.cumsum(rng.exponential(1.0 / (frac * sat), n_req))
+        tk, pts = [], 0
+        lat = []
+        t0 = time.perf_counter()
+        for at in arrivals:
+            while time.perf_counter() - t0 < at:
+                time.sleep(0.0001)
+            st, t, n = req(seed)
+            seed += 1
+            if st == ch.CH_OK:
+                tk.append((t, time.perf_counter()))
+                pts += n
+        ok = 0
+        for t, ts in tk:
+            st, eta, rs = ch.ch_serve_wait(srv, t, 600_000)
+            ok += int(st == ch.CH_OK and rs == ch.CH_OK)
+        wall = time.perf_counter() - t0
+        after = ch.ch_serve_stats_get(srv)
+        levels.append({"load": frac, "offered_rps": frac * sat, "requests": n_req, "completed": ok,
+                       "throughput_rps": ok / wall, "pts_per_s": pts / wall,
+                       "p50_us": after.p50_us, "p99_us": after.p99_us, "mean_us": after.mean_us,
+                       "rejected": int(after.rejected)})
+    stats = ch.ch_serve_stats_get(srv)
+    ch.ch_serve_destroy(srv)
+    mid = levels[1]
+    print(json.dumps({
+        "metric": "requests/s at 0.8x saturation, with p50/p99 submit-to-result latency", "value":
+        mid["throughput_rps"], "unit": "requests/s", "n_gpus": 1, "steps": total_req, "warmup": burst,
+        "higher_is_better": True, "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+        "config": {"workload": WORKLOADS["serving"]["desc"], "slots": 8, "sets": 48},
+        "saturation_rps": sat, "levels": levels, "p50_us": mid["p50_us"], "p99_us": mid["p99_us"],
+        "peak_bytes": stats.peak_bytes,
+    }))
+
+
 def run_reference_batched(args):
     """Oracle arm of the batched workload: each step runs the oracle on 16 of the
     pairs (every 256th) in full; value in points per second."""
@@ -463,7 +544,7 @@ def run_reference(args):
     if CONFIG == "batched":
         run_reference_batched(args)
         return
-    if CONFIG == "curves":  # an accuracy experiment, not a throughput one: time the mid workload
+    if CONFIG in ("curves", "serving"):  # not a points/s workload: the reference arm times the mid one
         select_workload("mid")
     A, B = workloads.gaussian_mixture(NA, NB, DIM, 0)
     T = oracle.default_T(NA, NB, EPS)
@@ -512,10 +593,10 @@ def main():
     from paper_2307_03043_gb300 import binding as ch
     from paper_2307_03043_gb300 import workloads
 
-    if CONFIG == "curves":
+    if CONFIG in ("curves", "serving"):
         ctx = ch.ch_ctx_create(local, torch.cuda.current_stream())
         if rank == 0:
-            run_curves(args, ch, ctx, torch)
+            (run_curves if CONFIG == "curves" else run_serving)(args, ch, ctx, torch)
         ch.ch_ctx_destroy(ctx)
         if world > 1:
             dist.destroy_process_group()

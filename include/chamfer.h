@@ -309,6 +309,9 @@ ch_status ch_serve_poll(ch_server* s, uint64_t ticket, double* eta, int32_t* req
 /* Waits at most timeout_ms; CH_ETIMEOUT if still pending. */
 ch_status ch_serve_wait(ch_server* s, uint64_t ticket, uint32_t timeout_ms, double* eta, int32_t* req_status);
 ch_status ch_serve_stats_get(ch_server* s, ch_serve_stats* out);
+/* Starts a new measurement window: clears the latency record and the completed /
+ * failed / rejected counts, and restarts the throughput clock (peak_bytes kept). */
+ch_status ch_serve_stats_reset(ch_server* s);
 void ch_serve_destroy(ch_server* s);
 
 #ifdef __cplusplus

@@ -102,6 +102,7 @@ SIGNATURES = {
     "ch_serve_poll": (_i32, [_vp, _u64, _P(ctypes.c_double), _P(_i32)]),
     "ch_serve_wait": (_i32, [_vp, _u64, _u32, _P(ctypes.c_double), _P(_i32)]),
     "ch_serve_stats_get": (_i32, [_vp, _P(ch_serve_stats)]),
+    "ch_serve_stats_reset": (_i32, [_vp]),
     "ch_serve_destroy": (None, [_vp]),
 }
 
@@ -336,6 +337,10 @@ def ch_serve_wait(srv, ticket: int, timeout_ms: int = 60000):
     if st not in (CH_OK, CH_ETIMEOUT):
         _check(st, "ch_serve_wait")
     return st, eta.value, int(rs.value)
+
+
+def ch_serve_stats_reset(srv):
+    _check(lib().ch_serve_stats_reset(srv), "ch_serve_stats_reset")
 
 
 def ch_serve_stats_get(srv) -> ch_serve_stats:

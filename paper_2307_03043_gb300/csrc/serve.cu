@@ -320,6 +320,15 @@ ch_status ch_serve_stats_get(ch_server* s, ch_serve_stats* out) {
   return CH_OK;
 }
 
+ch_status ch_serve_stats_reset(ch_server* s) {
+  if (!s) return CH_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->lat_us.clear();
+  s->completed = s->failed = s->rejected = 0;
+  s->t_create = Clock::now();
+  return CH_OK;
+}
+
 void ch_serve_destroy(ch_server* s) {
   if (s) destroy_server(s);
 }

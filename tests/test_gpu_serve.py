@@ -66,6 +66,12 @@ def test_results_identical_alone_and_mixed(ctx):
     stats = ch.ch_serve_stats_get(srv)
     assert stats.completed == 24 and stats.failed == 0
     assert stats.p50_us > 0 and stats.p99_us >= stats.p50_us
+    ch.ch_serve_stats_reset(srv)  # a new measurement window
+    stats = ch.ch_serve_stats_get(srv)
+    assert stats.completed == 0 and stats.p50_us == 0 and stats.peak_bytes > 0
+    st, t = ch.ch_serve_submit(srv, ids[0], ids[1], jobs[0][3])
+    ch.ch_serve_wait(srv, t, 60000)
+    assert ch.ch_serve_stats_get(srv).completed == 1
     ch.ch_serve_destroy(srv)
     # each request alone, on a fresh context and fresh sets
     c2 = ch.ch_ctx_create(0, None)
