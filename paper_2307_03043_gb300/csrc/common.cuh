@@ -7,6 +7,8 @@
 // (the library is built with -ftz=false -prec-div=true -prec-sqrt=true).
 #pragma once
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -187,17 +189,12 @@ __host__ __device__ inline float ord_dec(uint32_t u) {
 // exact 2^e as binary32 for -126 <= e <= 127
 __device__ inline float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 
-// E4M3 (OCP FP8, no infinities) code -> binary32, exact
+// E4M3 (OCP FP8, no infinities) code -> binary32, exact: the hardware conversion
+// to binary16 (every E4M3 value, subnormals included, is a binary16 value; the two
+// NaN codes give NaN), then binary16 -> binary32, also exact
 __device__ inline float e4m3_to_f32(uint8_t b) {
-  const uint32_t s = (b & 0x80u) << 24;
-  const uint32_t e = (b >> 3) & 0xFu;
-  const uint32_t m = b & 7u;
-  if (e == 0xFu && m == 7u) return __int_as_float(0x7FC00000u);
-  if (e == 0) {
-    float v = __fmul_rn(static_cast<float>(m), 1.0f / 512.0f);
-    return s ? -v : v;
-  }
-  return __int_as_float(s | ((e + 120u) << 23) | (m << 20));
+  const __half_raw h = __nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(b), __NV_E4M3);
+  return __half2float(__half(h));
 }
 
 __device__ inline float bf16_to_f32(uint16_t h) { return __int_as_float(static_cast<uint32_t>(h) << 16); }

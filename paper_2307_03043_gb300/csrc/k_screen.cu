@@ -144,7 +144,7 @@ struct ScreenArgs {
   uint32_t* status;
 };
 
-template <int SCREEN>
+template <int SCREEN, bool STREAMQ>
 __global__ void __launch_bounds__(kThreads, 1)
     k_screen(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmB, ScreenArgs args) {
   extern __shared__ uint8_t smem_raw[];
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int KB = args.kblocks;
   const int S = args.stages;
-  const bool streamq = args.stream_q != 0;
+  constexpr bool streamq = STREAMQ;  // the sample tile streams with B (rows wider than 768 bytes)
   uint8_t* q_smem = smem;  // KB x (128 rows x 128 B) resident, or S x (128 rows x 128 B) streamed
   uint8_t* b_smem = q_smem + size_t(streamq ? S : KB) * kBM * kKB;  // S x (256 rows x 128 B)
   float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [warps][2][64] |b|^2
@@ -584,7 +584,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
 
 #define CHX_SCREEN_LAUNCH(SCR)                                                                              \
   do {                                                                                                      \
-    auto kern = k_screen<SCR>;                                                                              \
+    auto kern = p.stream_q ? k_screen<SCR, true> : k_screen<SCR, false>;                                    \
     CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)); /* constant */ \
     timer.start(s);                                                                                         \
     kern<<<p.grid, kThreads, p.smem, s>>>(tmQ, tmB, a);                                                     \
