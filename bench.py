@@ -499,6 +499,20 @@ def run_serving(args, ch, ctx, torch):
     }))
 
 
+def aggregate_replicas(total_ms, pts_ok, world, device):
+    """Whole-job numbers of N independent replicas: the slowest rank's time and
+    every rank's points (each rank ran its own pair; no data-path collective)."""
+    if world <= 1:
+        return total_ms, pts_ok
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    pts = torch.tensor([pts_ok], device=device, dtype=torch.float64)
+    dist.all_reduce(pts, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(pts.item())
+
+
 def run_reference_batched(args):
     """Oracle arm of the batched workload: each step runs the oracle on 16 of the
     pairs (every 256th) in full; value in points per second."""
@@ -686,12 +700,7 @@ def main():
 
     total_ms = float(np.sum(step_ms))
     pts_ok = float(sum((NA + NB) for o in ok if o))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        pts = torch.tensor([pts_ok], device="cuda", dtype=torch.float64)
-        dist.all_reduce(pts, op=dist.ReduceOp.SUM)
-        total_ms, pts_ok = float(t.item()), float(pts.item())
+    total_ms, pts_ok = aggregate_replicas(total_ms, pts_ok, world, "cuda")
     value = pts_ok / (total_ms / 1e3)
 
     # end to end through the public API from pinned host buffers
