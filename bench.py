@@ -364,7 +364,7 @@ def run_batched(args, ch, ctx, torch, rank, local, world):
             "config": {"workload": WORKLOADS["batched"]["desc"], "pairs": P, "points": int(sum(npts)), "d": 3,
                        "metric": "l2", "eps": EPS, "levels": LEVELS, "proj_dim": PROJ,
                        "l2_flush": "256 MiB write between timed steps, outside the timed events",
-                       "api": "ch_estimate_batch (4 streams)"},
+                       "api": "ch_estimate_batch (8 streams)"},
             "accuracy": {"points_within_10pct": main_m["points_within_10pct"]},
             "exact_gpu": {"mode": "canonical fp32, all pairs, one ch_exact per pair",
                           "ms_per_pair": main_m["exact_gpu_ms_per_pair"],

@@ -774,7 +774,7 @@ ch_status ch_sampled_nn(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t 
 
 namespace chx {
 
-constexpr int kBatchLanes = 4;  // concurrent streams of a batched call
+constexpr int kBatchLanes = 8;  // concurrent streams (and host threads) of a batched call
 
 // argument checks of one estimate; returns (T, R)
 static void check_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t* T,
