@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int KB = args.kblocks;
   const int S = args.stages;
-  constexpr bool streamq = STREAMQ;  // the sample tile streams with B (rows wider than 768 bytes)
+  constexpr bool streamq = STREAMQ;  // the sample tile streams with B (rows of 768 bytes or more)
   uint8_t* q_smem = smem;  // KB x (128 rows x 128 B) resident, or S x (128 rows x 128 B) streamed
   uint8_t* b_smem = q_smem + size_t(streamq ? S : KB) * kBM * kKB;  // S x (256 rows x 128 B)
   float* nb_s = reinterpret_cast<float*>(b_smem + size_t(S) * kBN * kKB);  // [warps][2][64] |b|^2
@@ -480,8 +480,11 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   p.R = std::max(1, std::min(R, 32));  // candidates the rerank evaluates exactly
   p.kblocks = static_cast<int>(ceil_div(int64_t(d) * es, kKB));
   p.row_tiles = static_cast<int>(ceil_div(std::max<int64_t>(T, 1), kBM));
-  // the sample tile stays resident up to 96 KB (d * elem <= 768 bytes); wider rows stream
-  p.stream_q = int64_t(p.kblocks) * kBM * kKB > 96 * 1024;
+  // the sample tile stays resident below 96 KB (d * elem < 768 bytes); wider rows
+  // stream, which leaves room for four or more B stages (at 768-byte rows a
+  // resident tile leaves three, and the bf16 d = 384 screen ran 3.01 ms resident
+  // against 2.81 ms streamed on 1M x 1M)
+  p.stream_q = int64_t(p.kblocks) * kBM * kKB >= 96 * 1024;
   const size_t fixed = 1024 + (p.stream_q ? 0 : size_t(p.kblocks) * kBM * kKB) + 16 * kBN * sizeof(float) + 256;
   const size_t per_stage = size_t(kBN) * kKB + (p.stream_q ? size_t(kBM) * kKB : 0);
   const size_t limit = 227 * 1024;
@@ -529,7 +532,7 @@ bool screen_supported(int screen, const ch_set* A, const ch_set* B) {
   const int es = static_cast<int>(elem_size(A->dtype));
   if ((int64_t(A->d) * es) % 16 != 0) return false;     // TMA row stride
   if (int64_t(A->d) * es < kKB) return false;            // at least one full 128-byte swizzle row
-  if (int64_t(A->d) * es > 16384) return false;          // rows up to 16 KB (wider than 768 B stream)
+  if (int64_t(A->d) * es > 16384) return false;          // rows up to 16 KB (768 B or more stream)
   if (B->n >= (int64_t(1) << 31)) return false;
   return true;
 }

@@ -145,7 +145,7 @@ def test_exact_tc_mode_matches_direct(ctx):
 @pytest.mark.parametrize("dtype,d", [(ch.CH_F32, 768), (ch.CH_F32, 1000), (ch.CH_BF16, 768), (ch.CH_BF16, 1536),
                                      (ch.CH_FP8E4M3, 1024)])
 def test_wide_rows_stream_the_sample_tile(ctx, dtype, d):
-    """Rows wider than 768 bytes: the sample tile's K blocks stream through the
+    """Rows of 768 bytes or more: the sample tile's K blocks stream through the
     stages with B's instead of staying resident (the serving mix has d = 768)."""
     A, B = workloads.unit_mixture(900, 2600, d, 7 + d, clusters=30)
     if dtype == ch.CH_F32:
