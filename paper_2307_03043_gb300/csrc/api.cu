@@ -81,6 +81,7 @@ static void carve(ch_ctx* c, F&& f) {
 
 __global__ void k_collect(ResBlock* r, const uint32_t* sa, const uint32_t* sb, const double* out2,
                           const uint64_t* W, const int32_t* S, const int32_t* e_top) {
+  pdl_entry();
   if (threadIdx.x != 0) return;
   r->statusA = sa ? *sa : 0u;
   r->statusB = sb ? *sb : 0u;
@@ -611,7 +612,7 @@ ch_status ch_set_prepare(ch_ctx* c, ch_set* X) {
   CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
   ensure_ingest(X, s);
   ensure_norms(X, s);
-  k_collect<<<1, 32, 0, s>>>(res, X->status, nullptr, nullptr, nullptr, nullptr, nullptr);
+  launch_k(k_collect, 1, 32, 0, s, res, X->status, nullptr, nullptr, nullptr, nullptr, nullptr);
   launch_check("collect");
   finish(c, res, static_cast<ResBlock*>(c->host_pin));
   return CH_OK;
@@ -646,7 +647,7 @@ ch_status ch_top_exp(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash_
   launch_scale_tables(hA.box, hA.box_parts, hB.box, hB.box_parts, dd, static_cast<int>(hp->levels), hp->top_exp,
                       hp->hash_seed, tab, et,
                       &res->status, s);
-  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, nullptr, nullptr, nullptr, et);
+  launch_k(k_collect, 1, 32, 0, s, res, A->status, B->status, nullptr, nullptr, nullptr, et);
   launch_check("collect");
   ResBlock* h = static_cast<ResBlock*>(c->host_pin);
   finish(c, res, h);
@@ -736,7 +737,7 @@ ch_status ch_sample(ch_ctx* c, const float* D, int64_t nA, int64_t T, uint64_t s
   }
   if (W_total) {
     CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
-    k_collect<<<1, 32, 0, s>>>(res, nullptr, nullptr, nullptr, sb.sw.W, sb.sw.S, nullptr);
+    launch_k(k_collect, 1, 32, 0, s, res, nullptr, nullptr, nullptr, sb.sw.W, sb.sw.S, nullptr);
     launch_check("collect");
     ResBlock* h = static_cast<ResBlock*>(c->host_pin);
     finish(c, res, h);
@@ -1047,7 +1048,7 @@ ch_status ch_exact(ch_ctx* c, const ch_set* A, const ch_set* B, int32_t metric, 
     run_scan(c, A, nullptr, nA, B, metric, 8, &sc, mins, nullptr, &res->status);
     launch_sum_f32(mins, nA, out2, s);
   }
-  k_collect<<<1, 32, 0, s>>>(res, A->status, B->status, out2, nullptr, nullptr, nullptr);
+  launch_k(k_collect, 1, 32, 0, s, res, A->status, B->status, out2, nullptr, nullptr, nullptr);
   launch_check("collect");
   ResBlock* h = static_cast<ResBlock*>(c->host_pin);
   finish(c, res, h);

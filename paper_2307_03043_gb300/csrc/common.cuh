@@ -54,6 +54,33 @@ inline void launch_check(const char* what) {
   if (e != cudaSuccess) throw Err{CH_ECUDA, std::string("launch ") + what + ": " + cudaGetErrorString(e)};
 }
 
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_entry(): it waits until the kernel launched before it on the stream has
+// completed and its writes are visible (a no-op when there is no such
+// dependency), then lets the next kernel be scheduled.  Launched through
+// launch_k, a kernel's launch and block scheduling thus overlap the tail of its
+// predecessor while its own work still starts after the predecessor's ends.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... P, class... A>
+inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+  if (e != cudaSuccess) throw Err{CH_ECUDA, std::string("launch: ") + cudaGetErrorString(e)};
+}
+
 // device status bits (written by kernels, read back by synchronising calls)
 enum : uint32_t {
   ST_NONFINITE = 1u << 0,   // a set holds NaN or Inf

@@ -17,6 +17,7 @@ size_t elem_size(int dtype) { return dtype == CH_F32 ? 4 : dtype == CH_BF16 ? 2 
 template <int DT, int CB>
 __global__ void __launch_bounds__(256) k_ingest(const void* X, const float* scales, int64_t n, int d,
                                                 float* norms, uint32_t* box, uint32_t* status) {
+  pdl_entry();
   extern __shared__ uint32_t s_box[];  // [2][d]
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
     s_box[c] = 0xFFFFFFFFu;
@@ -96,7 +97,7 @@ static void ingest_dt(const ch_set* X, cudaStream_t s, int grid) {
   const size_t smem = size_t(2) * d * sizeof(uint32_t);
   const int cb = (d + 31) / 32;
 #define CHX_INGEST(CBV) \
-  k_ingest<DT, CBV><<<grid, 256, smem, s>>>(X->data, X->scales, X->n, d, X->norms, X->box_x, X->status)
+  launch_k(k_ingest<DT, CBV>, grid, 256, smem, s, X->data, X->scales, X->n, d, X->norms, X->box_x, X->status)
   if (cb <= 1) CHX_INGEST(1);
   else if (cb <= 2) CHX_INGEST(2);
   else if (cb <= 4) CHX_INGEST(4);
@@ -130,6 +131,7 @@ void ensure_ingest(ch_set* X, cudaStream_t s) {
 template <int DT>
 __global__ void __launch_bounds__(256) k_norms(const void* X, const float* scales, int64_t n, int d, float* norms,
                                                uint32_t* status) {
+  pdl_entry();
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   bool bad = false;
   if (r < n) {
@@ -150,9 +152,9 @@ void ensure_norms(ch_set* X, cudaStream_t s) {
   if (X->n == 0) return;
   const int grid = static_cast<int>(ceil_div(X->n, 256));
   switch (X->dtype) {
-    case CH_F32: k_norms<CH_F32><<<grid, 256, 0, s>>>(X->data, X->scales, X->n, X->d, X->norms, X->status); break;
-    case CH_BF16: k_norms<CH_BF16><<<grid, 256, 0, s>>>(X->data, X->scales, X->n, X->d, X->norms, X->status); break;
-    default: k_norms<CH_FP8E4M3><<<grid, 256, 0, s>>>(X->data, X->scales, X->n, X->d, X->norms, X->status); break;
+    case CH_F32: launch_k(k_norms<CH_F32>, grid, 256, 0, s, X->data, X->scales, X->n, X->d, X->norms, X->status); break;
+    case CH_BF16: launch_k(k_norms<CH_BF16>, grid, 256, 0, s, X->data, X->scales, X->n, X->d, X->norms, X->status); break;
+    default: launch_k(k_norms<CH_FP8E4M3>, grid, 256, 0, s, X->data, X->scales, X->n, X->d, X->norms, X->status); break;
   }
   launch_check("norms");
 }
@@ -179,6 +181,7 @@ __device__ inline float gauss_entry(uint64_t seed, int k, int j, int i) {
 }
 
 __global__ void k_gauss(uint64_t seed, int k, int kp, int d, float* G /* [d][kp], zero rows i >= k */) {
+  pdl_entry();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(kp) * d) return;
   G[t] = gauss_entry(seed, k, static_cast<int>(t / kp), static_cast<int>(t % kp));
@@ -192,6 +195,7 @@ template <int DT, int KP>
 __global__ void __launch_bounds__(128) k_project(const void* X, const float* scales, int64_t n, int d,
                                                  const float* G, int k, float* Y, uint32_t* box, float* norms,
                                                  uint32_t* status) {
+  pdl_entry();
   // RPT rows per thread (rows tid and tid + 128) so that each G value read from
   // shared memory feeds RPT fused multiply-adds
   constexpr int RPT = KP <= 16 ? 2 : 1;
@@ -311,6 +315,7 @@ template <int DT, int KP>
 __global__ void __launch_bounds__(kProjThreads) k_project_async(const void* X, const float* scales, int64_t n, int d,
                                                        const float* G, int k, float* Y, uint32_t* box, float* norms,
                                                        uint32_t* status) {
+  pdl_entry();
   constexpr int RPT = KP <= 16 ? 2 : 1;
   constexpr int ROWS = kProjThreads * RPT;
   constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
@@ -512,6 +517,7 @@ template <int DT, int KP>
 __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
     k_project_tma(const __grid_constant__ CUtensorMap map, const void* X, const float* scales, int64_t n, int d,
                   uint64_t seed, int k, float* Y, uint32_t* box, float* norms, uint32_t* status) {
+  pdl_entry();
   constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
   constexpr int PER = 16 / ES;          // coordinates per 16-byte chunk
   constexpr int SLICE = kPTBox / ES;    // coordinates per slice
@@ -755,7 +761,7 @@ static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y,
     const size_t sm = project_async_smem<DT, KPV>();                                                         \
     CHX_CUDA(cudaFuncSetAttribute(k_project_async<DT, KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                   static_cast<int>(project_async_smem<DT, KPV>())));                         \
-    k_project_async<DT, KPV><<<grid_a, kProjThreads, sm, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box, norms,      \
+    launch_k(k_project_async<DT, KPV>, grid_a, kProjThreads, sm, s, X->data, X->scales, X->n, X->d, G, k, Y, box, norms,      \
                                                    X->status);                                               \
   } while (0)
     if (kp == 8) CHX_PROJA(8);
@@ -766,7 +772,7 @@ static void project_dt(const ch_set* X, const float* G, int k, int kp, float* Y,
     return;
   }
 #define CHX_PROJ(KPV) \
-  k_project<DT, KPV><<<grid, 128, 0, s>>>(X->data, X->scales, X->n, X->d, G, k, Y, box, norms, X->status)
+  launch_k(k_project<DT, KPV>, grid, 128, 0, s, X->data, X->scales, X->n, X->d, G, k, Y, box, norms, X->status)
   if (kp == 8) CHX_PROJ(8);
   else if (kp == 16) CHX_PROJ(16);
   else if (kp == 32) CHX_PROJ(32);
@@ -790,7 +796,7 @@ static int launch_project_tma(const ch_set* X, uint64_t seed, int k, float* Y, u
   const int64_t rounds = ceil_div(ntiles, int64_t(sms) * warps);
   warps = static_cast<int>(std::min<int64_t>(warps, ceil_div(ntiles, int64_t(sms) * rounds)));
   const int grid = static_cast<int>(std::min<int64_t>(sms, ntiles));
-  k_project_tma<DT, KP><<<grid, warps * 32, project_tma_smem<DT>(warps, X->d, KP), s>>>(
+  launch_k(k_project_tma<DT, KP>, grid, warps * 32, project_tma_smem<DT>(warps, X->d, KP), s, 
       map, X->data, X->scales, X->n, X->d, seed, k, Y, box, norms, X->status);
   return grid;
 }
@@ -809,7 +815,7 @@ static int project_any(const ch_set* X, uint64_t seed, int k, int kp, float* Y, 
   // the Gaussian matrix lives in the tail of Y's allocation
   float* G = Y + ((X->n * k + 3) & ~int64_t(3));  // 16-byte aligned
   const int64_t gn = int64_t(kp) * X->d;
-  k_gauss<<<static_cast<int>(ceil_div(gn, 256)), 256, 0, s>>>(seed, k, kp, X->d, G);
+  launch_k(k_gauss, static_cast<int>(ceil_div(gn, 256)), 256, 0, s, seed, k, kp, X->d, G);
   launch_check("gauss");
   project_dt<DT>(X, G, k, kp, Y, box, norms, s);
   return 1;
@@ -845,6 +851,7 @@ int launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* bo
 // K_j = Philox(j, 0, 4, 0).(y:x) | 1; salt_e = mix64((uint32)e ^ seed).
 __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
                                int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status) {
+  pdl_entry();
   __shared__ int s_elo;
   __shared__ uint32_t s_box[2 * kMaxProj];  // merged partial boxes (partial boxes only come with dd <= kMaxProj)
   const bool merge = partsA > 1 || partsB > 1;
@@ -926,7 +933,7 @@ void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB,
                          cudaStream_t s) {
   CHX_CHECK((partsA <= 1 && partsB <= 1) || dd <= kMaxProj, CH_EINVAL, "partial boxes need dd <= 64");
   // 1024 threads: the partial-box loads of all blocks are in flight at once
-  k_scale_tables<<<1, 1024, 0, s>>>(boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out, status);
+  launch_k(k_scale_tables, 1, 1024, 0, s, boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out, status);
   launch_check("scale_tables");
 }
 
@@ -940,6 +947,7 @@ template <int DTA, int DTB, int METRIC>
 __global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* scA, int64_t nA, const void* B,
                                                     const float* scB, int d, int G, const int64_t* bidx,
                                                     float* D, uint32_t* maxD) {
+  pdl_entry();
   __shared__ uint32_t s_max[8];
   uint32_t mx = 0;
   const int64_t total = nA * G;
@@ -986,10 +994,10 @@ template <int DTA, int DTB>
 static void crude_dist_2(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D,
                          uint32_t* maxD, int G, int grid, cudaStream_t s) {
   if (metric == CH_L1)
-    k_crude_dist<DTA, DTB, CH_L1><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D,
+    launch_k(k_crude_dist<DTA, DTB, CH_L1>, grid, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D,
                                                         maxD);
   else
-    k_crude_dist<DTA, DTB, CH_L2><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D,
+    launch_k(k_crude_dist<DTA, DTB, CH_L2>, grid, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, A->d, G, bidx, D,
                                                         maxD);
 }
 
@@ -1027,6 +1035,7 @@ template <int DTA, int DTB, int METRIC>
 __global__ void __launch_bounds__(256) k_cand_dist(const void* A, const float* scA, int64_t nA, const void* B,
                                                    const float* scB, int d, const int32_t* cand, int stride,
                                                    int64_t* bidx, float* D, uint32_t* maxD) {
+  pdl_entry();
   const int64_t a = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (a >= nA) return;
@@ -1063,10 +1072,10 @@ void launch_cand_dist(const ch_set* A, const ch_set* B, int metric, const int32_
   auto go = [&](auto dta, auto dtb) {
     constexpr int DTA = decltype(dta)::value, DTB = decltype(dtb)::value;
     if (metric == CH_L1)
-      k_cand_dist<DTA, DTB, CH_L1><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, cand,
+      launch_k(k_cand_dist<DTA, DTB, CH_L1>, grid, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, A->d, cand,
                                                           stride, bidx, D, maxD);
     else
-      k_cand_dist<DTA, DTB, CH_L2><<<grid, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, A->d, cand,
+      launch_k(k_cand_dist<DTA, DTB, CH_L2>, grid, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, A->d, cand,
                                                           stride, bidx, D, maxD);
   };
   using F = std::integral_constant<int, CH_F32>;

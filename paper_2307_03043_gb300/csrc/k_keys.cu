@@ -138,6 +138,7 @@ __device__ inline int64_t table_find(const ulonglong2* tab, uint32_t log_cap, ui
 template <int DT, int W>
 __global__ void __launch_bounds__(128) k_table_insert_ps(HashSrc src, int L, int L0, int nl, ScaleTables t,
                                                          HashTable h, uint32_t* status) {
+  pdl_entry();
   const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (g >= src.n * nl) return;
   const int l = static_cast<int>(g / src.n);
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(128) k_table_insert_ps(HashSrc src, int L, int
 template <int DT>
 __global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
                                                       uint32_t* status) {
+  pdl_entry();
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= src.n) return;
   const size_t cap = size_t(1) << h.log_cap;
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0
 template <int DT, int W>
 __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
                                                      int64_t* bidx, uint8_t* level) {
+  pdl_entry();
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= src.n) return;
   if (L0 > 0 && level[r] < L) return;  // resolved at a finer scale group
@@ -212,6 +215,7 @@ __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0,
 
 template <int DT, int W>
 __global__ void __launch_bounds__(128) k_keys_write(HashSrc src, int L, ScaleTables t, uint64_t* keys) {
+  pdl_entry();
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= src.n) return;
   if (src.dd <= W) {
@@ -252,6 +256,7 @@ void dispatch_dt_w(int dtype, int dd, F&& f) {
 // y_i < 0; level l keeps the first max(1, K >> l) bits; key = mix64(bits +
 // mix64((l << 32) ^ seed)), 0 replaced by 1.  One thread per point, all levels.
 __global__ void k_simhash_keys(const float* Y, int64_t n, int K, int L, uint64_t seed, uint64_t* keys) {
+  pdl_entry();
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= n) return;
   uint64_t word = 0;
@@ -267,7 +272,7 @@ __global__ void k_simhash_keys(const float* Y, int64_t n, int K, int L, uint64_t
 
 void launch_simhash_keys(const float* Y, int64_t n, int K, int L, uint64_t seed, uint64_t* keys, cudaStream_t s) {
   if (n == 0) return;
-  k_simhash_keys<<<static_cast<int>(ceil_div(n, 128)), 128, 0, s>>>(Y, n, K, L, seed, keys);
+  launch_k(k_simhash_keys, static_cast<int>(ceil_div(n, 128)), 128, 0, s, Y, n, K, L, seed, keys);
   launch_check("simhash_keys");
 }
 
@@ -275,7 +280,7 @@ void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStre
   if (X.n == 0) return;
   const int grid = static_cast<int>(ceil_div(X.n, 128));
   dispatch_dt_w(X.dtype, X.dd, [&](auto dtc, auto wc) {
-    k_keys_write<decltype(dtc)::value, decltype(wc)::value><<<grid, 128, 0, s>>>(X, L, t, keys);
+    launch_k(k_keys_write<decltype(dtc)::value, decltype(wc)::value>, grid, 128, 0, s, X, L, t, keys);
   });
   launch_check("keys_write");
 }
@@ -286,7 +291,7 @@ void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTa
   if (B.dd <= kRegRow) {
     const int grid_ps = static_cast<int>(ceil_div(B.n * nl, 128));
     dispatch_dt_w(B.dtype, B.dd, [&](auto dtc, auto wc) {
-      k_table_insert_ps<decltype(dtc)::value, decltype(wc)::value><<<grid_ps, 128, 0, s>>>(B, L, L0, nl, t, h,
+      launch_k(k_table_insert_ps<decltype(dtc)::value, decltype(wc)::value>, grid_ps, 128, 0, s, B, L, L0, nl, t, h,
                                                                                             status);
     });
     launch_check("table_insert");
@@ -294,9 +299,9 @@ void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTa
   }
   const int grid = static_cast<int>(ceil_div(B.n, 128));
   switch (B.dtype) {
-    case CH_F32: k_table_insert<CH_F32><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
-    case CH_BF16: k_table_insert<CH_BF16><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
-    default: k_table_insert<CH_FP8E4M3><<<grid, 128, 0, s>>>(B, L, L0, nl, t, h, status); break;
+    case CH_F32: launch_k(k_table_insert<CH_F32>, grid, 128, 0, s, B, L, L0, nl, t, h, status); break;
+    case CH_BF16: launch_k(k_table_insert<CH_BF16>, grid, 128, 0, s, B, L, L0, nl, t, h, status); break;
+    default: launch_k(k_table_insert<CH_FP8E4M3>, grid, 128, 0, s, B, L, L0, nl, t, h, status); break;
   }
   launch_check("table_insert");
 }
@@ -306,7 +311,7 @@ void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTab
   if (A.n == 0) return;
   const int grid = static_cast<int>(ceil_div(A.n, 128));
   dispatch_dt_w(A.dtype, A.dd, [&](auto dtc, auto wc) {
-    k_table_probe<decltype(dtc)::value, decltype(wc)::value><<<grid, 128, 0, s>>>(A, L, L0, nl, t, h, bidx, level);
+    launch_k(k_table_probe<decltype(dtc)::value, decltype(wc)::value>, grid, 128, 0, s, A, L, L0, nl, t, h, bidx, level);
   });
   launch_check("table_probe");
 }

@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
                                                 const float* scB, int64_t nB, int d, const int64_t* idx, int64_t T,
                                                 const float* part_s, const int32_t* part_i, int parts, int per,
                                                 int occ, int stride, int R, float* min_d, int64_t* argmin) {
+  pdl_entry();
   __shared__ float s_s[8][kRerankMaxCand];
   __shared__ int32_t s_i[8][kRerankMaxCand];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -115,7 +116,7 @@ void launch_rerank(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set
   CHX_CHECK(parts * per <= kRerankMaxCand && occ <= kRerankMaxOcc, CH_EINVAL, "rerank candidate list too long");
   const int blocks = static_cast<int>(ceil_div(T, 8));
 #define CHX_RERANK(DT)                                                                                              \
-  k_rerank<DT, CH_L2><<<blocks, 256, 0, s>>>(A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T,  \
+  launch_k(k_rerank<DT, CH_L2>, blocks, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T,  \
                                              part_s, part_i, parts, per, occ, stride, R, min_d, argmin)
   if (A->dtype == CH_F32) CHX_RERANK(CH_F32);
   else if (A->dtype == CH_BF16) CHX_RERANK(CH_BF16);

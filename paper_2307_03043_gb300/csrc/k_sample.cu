@@ -15,6 +15,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;  // elements per block
 size_t sample_blocks(int64_t nA) { return static_cast<size_t>(ceil_div(nA, kScanTile)); }
 
 __global__ void k_max_d(const float* D, int64_t n, uint32_t* maxD) {
+  pdl_entry();
   uint32_t m = 0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     m = max(m, ord_enc(D[i]));
@@ -39,6 +40,7 @@ __device__ inline int weight_shift(const uint32_t* maxD, int64_t nA, bool* zero)
 __global__ void __launch_bounds__(kScanThreads) k_weights(const float* D, int64_t nA, const uint32_t* maxD,
                                                           uint64_t* w, uint64_t* prefix, uint64_t* blocksum,
                                                           int32_t* S_out) {
+  pdl_entry();
   __shared__ uint64_t s_warp[kScanThreads / 32];
   bool zero;
   const int S = weight_shift(maxD, nA, &zero);
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(kScanThreads) k_weights(const float* D, int64_
 
 // exclusive scan of the block sums (one block, sequential chunks of 1024)
 __global__ void k_scan_blocksums(uint64_t* blocksum, int64_t nb, uint64_t* W) {
+  pdl_entry();
   __shared__ uint64_t s_warp[32];
   __shared__ uint64_t s_carry;
   if (threadIdx.x == 0) s_carry = 0;
@@ -109,18 +112,20 @@ __global__ void k_scan_blocksums(uint64_t* blocksum, int64_t nb, uint64_t* W) {
 }
 
 __global__ void k_add_offsets(uint64_t* prefix, int64_t nA, const uint64_t* blockoff) {
+  pdl_entry();
   const int64_t a = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (a < nA) prefix[a] += blockoff[a / kScanTile];
 }
 
 __global__ void k_fill_ones(float* D, int64_t n) {
+  pdl_entry();
   const int64_t a = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (a < n) D[a] = 1.0f;
 }
 
 void launch_fill_ones(float* D, int64_t n, cudaStream_t s) {
   if (n == 0) return;
-  k_fill_ones<<<static_cast<int>(ceil_div(n, 256)), 256, 0, s>>>(D, n);
+  launch_k(k_fill_ones, static_cast<int>(ceil_div(n, 256)), 256, 0, s, D, n);
   launch_check("fill_ones");
 }
 
@@ -134,16 +139,16 @@ void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, S
   if (!max_ready) {
     CHX_CUDA(cudaMemsetAsync(sw.maxD, 0, sizeof(uint32_t), s));
     const int gmax = static_cast<int>(std::min<int64_t>(ceil_div(nA, 256), 152 * 4));
-    k_max_d<<<gmax, 256, 0, s>>>(D, nA, sw.maxD);
+    launch_k(k_max_d, gmax, 256, 0, s, D, nA, sw.maxD);
     launch_check("max_d");
   }
   const int64_t nb = static_cast<int64_t>(sample_blocks(nA));
-  k_weights<<<static_cast<int>(nb), kScanThreads, 0, s>>>(D, nA, sw.maxD, w, prefix, sw.blocksum, sw.S);
+  launch_k(k_weights, static_cast<int>(nb), kScanThreads, 0, s, D, nA, sw.maxD, w, prefix, sw.blocksum, sw.S);
   launch_check("weights");
-  k_scan_blocksums<<<1, 1024, 0, s>>>(sw.blocksum, nb, sw.W);
+  launch_k(k_scan_blocksums, 1, 1024, 0, s, sw.blocksum, nb, sw.W);
   launch_check("scan_blocksums");
   if (nb > 1 && !local_prefix) {
-    k_add_offsets<<<static_cast<int>(ceil_div(nA, 256)), 256, 0, s>>>(prefix, nA, sw.blocksum);
+    launch_k(k_add_offsets, static_cast<int>(ceil_div(nA, 256)), 256, 0, s, prefix, nA, sw.blocksum);
     launch_check("add_offsets");
   }
 }
@@ -154,6 +159,7 @@ void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, S
 // whose inclusive end exceeds t, then the point inside it -- the same a.
 __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, int64_t T, uint64_t seed,
                         int64_t* idx, const uint64_t* blockoff) {
+  pdl_entry();
   const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (l >= T) return;
   const uint64_t W = *Wp;
@@ -206,7 +212,7 @@ __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, 
 void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed, int64_t* idx,
                   cudaStream_t s, const uint64_t* blockoff) {
   if (T == 0) return;
-  k_draws<<<static_cast<int>(ceil_div(T, 256)), 256, 0, s>>>(prefix, nA, W, T, seed, idx, blockoff);
+  launch_k(k_draws, static_cast<int>(ceil_div(T, 256)), 256, 0, s, prefix, nA, W, T, seed, idx, blockoff);
   launch_check("draws");
 }
 
@@ -233,6 +239,7 @@ __device__ inline void block_sum2(double& a, double& b, double* sa, double* sb) 
 __global__ void __launch_bounds__(256) k_combine_part(const float* m, const int64_t* idx, const uint64_t* w,
                                                       const uint64_t* Wp, int64_t T, const float* D, int64_t nA,
                                                       double* out) {
+  pdl_entry();
   __shared__ double s_a[256], s_b[256];
   const uint64_t W = Wp ? *Wp : 0;
   const int64_t lt = ceil_div_dev(T, kCombineBlocks), la = ceil_div_dev(nA, kCombineBlocks);
@@ -256,6 +263,7 @@ __global__ void __launch_bounds__(256) k_combine_part(const float* m, const int6
 
 __global__ void __launch_bounds__(kCombineBlocks) k_combine_final(const uint64_t* Wp, int64_t T, double* out,
                                                                   CollectArgs c) {
+  pdl_entry();
   __shared__ double s_a[kCombineBlocks], s_b[kCombineBlocks];
   double a = out[2 + 2 * threadIdx.x], b = out[3 + 2 * threadIdx.x];
   block_sum2(a, b, s_a, s_b);
@@ -277,9 +285,9 @@ __global__ void __launch_bounds__(kCombineBlocks) k_combine_final(const uint64_t
 
 void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
                     const float* D, int64_t nA, double* out, cudaStream_t s, CollectArgs collect) {
-  k_combine_part<<<kCombineBlocks, 256, 0, s>>>(m, idx, w, W, T, D, nA, out);
+  launch_k(k_combine_part, kCombineBlocks, 256, 0, s, m, idx, w, W, T, D, nA, out);
   launch_check("combine_part");
-  k_combine_final<<<1, kCombineBlocks, 0, s>>>(W, T, out, collect);
+  launch_k(k_combine_final, 1, kCombineBlocks, 0, s, W, T, out, collect);
   launch_check("combine_final");
 }
 

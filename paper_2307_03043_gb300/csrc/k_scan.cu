@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(256) k_scan_exact(const void* __restrict__ A, 
                                                     const void* __restrict__ B, const float* __restrict__ scB,
                                                     int64_t nB, int d, int64_t chunk_len, float* part_val,
                                                     int64_t* part_idx) {
+  pdl_entry();
   constexpr int NTQ = QT / PQ, NTB = BT / PB;
   static_assert(NTQ * NTB == 256, "256 threads");
   constexpr int QS = QT + 4, BS = BT + 4;
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(256) k_scan_small(const void* __restrict__ A, 
                                                     const void* __restrict__ B, const float* __restrict__ scB,
                                                     int64_t nB, int64_t chunk_len, float* part_val,
                                                     int64_t* part_idx) {
+  pdl_entry();
   __shared__ float Bs[kSmallBT * D];
   const int64_t l0 = int64_t(blockIdx.x) * kSmallQ + threadIdx.x;  // samples l0 + 256 p
   const int64_t b_begin = int64_t(blockIdx.y) * chunk_len;
@@ -273,6 +275,7 @@ __global__ void __launch_bounds__(256) k_scan_small(const void* __restrict__ A, 
 
 __global__ void k_scan_merge(const float* part_val, const int64_t* part_idx, int chunks, int64_t T,
                              const int64_t* qidx, float* min_d, int64_t* argmin) {
+  pdl_entry();
   const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (l >= T) return;
   float bv = part_val[l];
@@ -329,7 +332,7 @@ static void scan_launch(const ch_set* A, const int64_t* qidx, int64_t T, const c
   CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
   const int64_t chunk_len = ceil_div(ceil_div(B->n, part.chunks), BT) * BT;
   dim3 grid(static_cast<unsigned>(ceil_div(T, QT)), static_cast<unsigned>(part.chunks));
-  kern<<<grid, 256, smem, s>>>(A->data, A->scales, qidx, T, A->n, B->data, B->scales, B->n, A->d, chunk_len,
+  launch_k(kern, grid, 256, smem, s, A->data, A->scales, qidx, T, A->n, B->data, B->scales, B->n, A->d, chunk_len,
                                part.val, part.idx);
 }
 
@@ -350,7 +353,7 @@ static void scan_small_launch(const ch_set* A, const int64_t* qidx, int64_t T, c
                               cudaStream_t s) {
   const int64_t chunk_len = ceil_div(B->n, part.chunks);
   dim3 grid(static_cast<unsigned>(ceil_div(T, kSmallQ)), static_cast<unsigned>(part.chunks));
-  k_scan_small<DT, METRIC, D><<<grid, 256, 0, s>>>(A->data, A->scales, qidx, T, A->n, B->data, B->scales, B->n,
+  launch_k(k_scan_small<DT, METRIC, D>, grid, 256, 0, s, A->data, A->scales, qidx, T, A->n, B->data, B->scales, B->n,
                                                    chunk_len, part.val, part.idx);
 }
 
@@ -396,7 +399,7 @@ void launch_scan_exact(const ch_set* A, const int64_t* qidx, int64_t T, const ch
 
 void launch_scan_merge(ScanPart part, int64_t T, const int64_t* qidx, float* min_d, int64_t* argmin, cudaStream_t s) {
   if (T == 0) return;
-  k_scan_merge<<<static_cast<int>(ceil_div(T, 256)), 256, 0, s>>>(part.val, part.idx, part.chunks, T, qidx, min_d,
+  launch_k(k_scan_merge, static_cast<int>(ceil_div(T, 256)), 256, 0, s, part.val, part.idx, part.chunks, T, qidx, min_d,
                                                                   argmin);
   launch_check("scan_merge");
 }

@@ -147,6 +147,7 @@ struct ScreenArgs {
 template <int SCREEN, bool STREAMQ>
 __global__ void __launch_bounds__(kThreads, 1)
     k_screen(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmB, ScreenArgs args) {
+  pdl_entry();
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned by an offset from the shared array itself, so that the
   // compiler keeps every access below in the shared state space
@@ -434,6 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // and, for FP8, their scales; idx < 0 gives a zero row.
 __global__ void k_gather_rows(const uint8_t* A, const float* scA, int64_t nA, int row_bytes, const int64_t* idx,
                               int64_t T, uint8_t* Q, float* sQ) {
+  pdl_entry();
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int words = row_bytes / 16;
   const int64_t row = t / words;
@@ -562,7 +564,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   int32_t* part_i = reinterpret_cast<int32_t*>(w);
 
   const int64_t words = T * (row_bytes / 16);
-  k_gather_rows<<<static_cast<int>(ceil_div(words, 256)), 256, 0, s>>>(
+  launch_k(k_gather_rows, static_cast<int>(ceil_div(words, 256)), 256, 0, s, 
       static_cast<const uint8_t*>(A->data), A->scales, A->n, row_bytes, qidx, T, Q,
       screen == CH_SCREEN_FP8 ? sQ : nullptr);
   launch_check("gather_rows");
@@ -590,7 +592,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
     auto kern = p.stream_q ? k_screen<SCR, true> : k_screen<SCR, false>;                                    \
     CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)); /* constant */ \
     timer.start(s);                                                                                         \
-    kern<<<p.grid, kThreads, p.smem, s>>>(tmQ, tmB, a);                                                     \
+    launch_k(kern, p.grid, kThreads, p.smem, s, tmQ, tmB, a);                                                     \
     timer.stop(s);                                                                                          \
   } while (0)
   if (screen == CH_SCREEN_TF32) CHX_SCREEN_LAUNCH(CH_SCREEN_TF32);

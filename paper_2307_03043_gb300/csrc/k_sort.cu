@@ -28,6 +28,7 @@ __device__ inline uint32_t tag_scale(uint32_t t) { return (t >> kIdxBits) & 31u;
 
 __global__ void k_sort_build(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L,
                              uint64_t* key, uint32_t* tag) {
+  pdl_entry();
   const int64_t N = nA + nB, total = N * L;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t l = i / N, p = i - l * N;
@@ -49,6 +50,7 @@ __device__ inline uint32_t sort_digit(uint64_t k, uint32_t t, int pass) {
 // per-tile digit histogram, stored digit-major: hist[digit * ntiles + tile]
 __global__ void __launch_bounds__(kST) k_sort_hist(const uint64_t* key, const uint32_t* tag, int64_t n, int pass,
                                                    uint32_t* hist, int ntiles) {
+  pdl_entry();
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -66,6 +68,7 @@ __global__ void __launch_bounds__(kST) k_sort_hist(const uint64_t* key, const ui
 
 // exclusive scan of the digit-major histogram (one block of 1024 threads)
 __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int64_t M) {
+  pdl_entry();
   __shared__ uint32_t s[1024];
   const int64_t per = (M + 1023) / 1024;
   const int64_t b = threadIdx.x * per, e = min(M, b + per);
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int64_t M) {
 __global__ void __launch_bounds__(kST) k_sort_scatter(const uint64_t* kin, const uint32_t* tin, uint64_t* kout,
                                                       uint32_t* tout, int64_t n, int pass, const uint32_t* hist,
                                                       int ntiles) {
+  pdl_entry();
   __shared__ uint32_t off[256], run[256];
   __shared__ uint32_t wc[kSWarps][256];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -135,6 +139,7 @@ __global__ void __launch_bounds__(kST) k_sort_scatter(const uint64_t* kin, const
 // this block (-1 if the block's prefix holds none); block_last = the block's last head
 __global__ void __launch_bounds__(kST) k_sort_heads(const uint64_t* key, const uint32_t* tag, int64_t n, int32_t* hp,
                                                     int32_t* block_last) {
+  pdl_entry();
   __shared__ int32_t s[kST];
   const int64_t b = int64_t(blockIdx.x) * kHeadBlock + int64_t(threadIdx.x) * kHeadPer;
   int32_t cur = -1;
@@ -167,6 +172,7 @@ __global__ void __launch_bounds__(kST) k_sort_heads(const uint64_t* key, const u
 
 // exclusive max-scan of the blocks' last heads (one block)
 __global__ void __launch_bounds__(1024) k_sort_carry(int32_t* block_last, int64_t nb) {
+  pdl_entry();
   __shared__ int32_t s[1024];
   __shared__ int32_t carry;
   if (threadIdx.x == 0) carry = -1;
@@ -193,6 +199,7 @@ __global__ void __launch_bounds__(1024) k_sort_carry(int32_t* block_last, int64_
 // each A entry whose run starts with a B proposes (scale, b)
 __global__ void k_sort_assign(const uint32_t* tag, const int32_t* hp, const int32_t* carry, int64_t n,
                               unsigned long long* packed) {
+  pdl_entry();
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t t = tag[i];
     if (!(t & 0x80000000u)) continue;
@@ -206,6 +213,7 @@ __global__ void k_sort_assign(const uint32_t* tag, const int32_t* hp, const int3
 }
 
 __global__ void k_sort_finish(const unsigned long long* packed, int64_t nA, int L, int64_t* bidx, uint8_t* level) {
+  pdl_entry();
   const int64_t a = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (a >= nA) return;
   const unsigned long long p = packed[a];
@@ -268,23 +276,23 @@ static const uint32_t* sort_core(const uint64_t* keysA, int64_t nA, const uint64
                                  const SortWork& w, cudaStream_t s) {
   const int64_t n = (nA + nB) * L;
   const int gb = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 152 * 16));
-  k_sort_build<<<gb, 256, 0, s>>>(keysA, nA, keysB, nB, L, w.k0, w.t0);
+  launch_k(k_sort_build, gb, 256, 0, s, keysA, nA, keysB, nB, L, w.k0, w.t0);
   launch_check("sort_build");
   uint64_t *kin = w.k0, *kout = w.k1;
   uint32_t *tin = w.t0, *tout = w.t1;
   for (int pass = 0; pass < 9; ++pass) {
-    k_sort_hist<<<w.ntiles, kST, 0, s>>>(kin, tin, n, pass, w.hist, w.ntiles);
+    launch_k(k_sort_hist, w.ntiles, kST, 0, s, kin, tin, n, pass, w.hist, w.ntiles);
     launch_check("sort_hist");
-    k_sort_scan<<<1, 1024, 0, s>>>(w.hist, int64_t(256) * w.ntiles);
+    launch_k(k_sort_scan, 1, 1024, 0, s, w.hist, int64_t(256) * w.ntiles);
     launch_check("sort_scan");
-    k_sort_scatter<<<w.ntiles, kST, 0, s>>>(kin, tin, kout, tout, n, pass, w.hist, w.ntiles);
+    launch_k(k_sort_scatter, w.ntiles, kST, 0, s, kin, tin, kout, tout, n, pass, w.hist, w.ntiles);
     launch_check("sort_scatter");
     std::swap(kin, kout);
     std::swap(tin, tout);
   }
-  k_sort_heads<<<static_cast<int>(w.nhb), kST, 0, s>>>(kin, tin, n, w.hp, w.blast);
+  launch_k(k_sort_heads, static_cast<int>(w.nhb), kST, 0, s, kin, tin, n, w.hp, w.blast);
   launch_check("sort_heads");
-  k_sort_carry<<<1, 1024, 0, s>>>(w.blast, w.nhb);
+  launch_k(k_sort_carry, 1, 1024, 0, s, w.blast, w.nhb);
   launch_check("sort_carry");
   return tin;
 }
@@ -297,9 +305,9 @@ void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB,
   const uint32_t* tin = sort_core(keysA, nA, keysB, nB, L, w, s);
   const int gb = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 152 * 16));
   CHX_CUDA(cudaMemsetAsync(w.packed, 0xFF, size_t(nA) * 8, s));
-  k_sort_assign<<<gb, 256, 0, s>>>(tin, w.hp, w.blast, n, w.packed);
+  launch_k(k_sort_assign, gb, 256, 0, s, tin, w.hp, w.blast, n, w.packed);
   launch_check("sort_assign");
-  k_sort_finish<<<static_cast<int>(ceil_div(nA, 256)), 256, 0, s>>>(w.packed, nA, L, bidx, level);
+  launch_k(k_sort_finish, static_cast<int>(ceil_div(nA, 256)), 256, 0, s, w.packed, nA, L, bidx, level);
   launch_check("sort_finish");
 }
 
@@ -308,6 +316,7 @@ namespace {
 
 // pos[scale * nA + a] = sorted position of a's entry at that scale
 __global__ void k_sort_pos(const uint32_t* tag, int64_t n, int64_t nA, int32_t* pos) {
+  pdl_entry();
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t t = tag[i];
     if (t & 0x80000000u) pos[int64_t(tag_scale(t)) * nA + (t & kIdxMask)] = static_cast<int32_t>(i);
@@ -320,6 +329,7 @@ __global__ void k_sort_pos(const uint32_t* tag, int64_t n, int64_t nA, int32_t* 
 // that finds nothing contributes B[0].
 __global__ void k_window(const uint32_t* tag, const int32_t* hp, const int32_t* carry, const int32_t* pos,
                          int64_t n, int64_t nA, int L, int W, int r, int stride, int32_t* cand, uint8_t* level) {
+  pdl_entry();
   const int64_t a = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (a >= nA) return;
   int32_t taken[kWindowMax];
@@ -362,9 +372,9 @@ void launch_sort_window(const uint64_t* keysA, int64_t nA, const uint64_t* keysB
                                             ((sort_group_workspace(nA, nB, L) + 255) & ~size_t(255)));
   const uint32_t* tin = sort_core(keysA, nA, keysB, nB, L, w, s);
   const int gb = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 152 * 16));
-  k_sort_pos<<<gb, 256, 0, s>>>(tin, n, nA, pos);
+  launch_k(k_sort_pos, gb, 256, 0, s, tin, n, nA, pos);
   launch_check("sort_pos");
-  k_window<<<static_cast<int>(ceil_div(nA, 128)), 128, 0, s>>>(tin, w.hp, w.blast, pos, n, nA, L, W, r, stride, cand,
+  launch_k(k_window, static_cast<int>(ceil_div(nA, 128)), 128, 0, s, tin, w.hp, w.blast, pos, n, nA, L, W, r, stride, cand,
                                                                level);
   launch_check("window");
 }
