@@ -108,12 +108,24 @@ __device__ inline void table_insert(ulonglong2* tab, uint32_t log_cap, uint64_t 
   const unsigned long long want = ~static_cast<unsigned long long>(b);
   uint32_t pos = slot_home(key, log_cap);
   for (uint32_t it = 0; it < cap; ++it) {
-    // one round trip: claim the slot or learn its owner; the min-update is a
-    // fire-and-forget reduction
-    const unsigned long long cur = atomicCAS(&tab[pos].x, 0ull, static_cast<unsigned long long>(key));
-    if (cur == 0ull || cur == key) {
-      atomicMax(&tab[pos].y, want);
+    // A read first: a slot's key only ever goes from 0 to its final value and
+    // its y only grows, so a stale read is safe.  A present key costs no atomic
+    // round trip (points of one cluster share buckets at the coarse scales,
+    // and their CAS would queue on one address), and the min-update is skipped
+    // when it cannot raise y.
+    const ulonglong2 seen = __ldcg(&tab[pos]);
+    if (seen.x == key) {
+      if (seen.y < want) atomicMax(&tab[pos].y, want);
       return;
+    }
+    if (seen.x == 0ull) {
+      // one round trip: claim the slot or learn its owner; the min-update is a
+      // fire-and-forget reduction
+      const unsigned long long cur = atomicCAS(&tab[pos].x, 0ull, static_cast<unsigned long long>(key));
+      if (cur == 0ull || cur == key) {
+        atomicMax(&tab[pos].y, want);
+        return;
+      }
     }
     pos = (pos + 1) & (cap - 1);
   }
