@@ -359,7 +359,7 @@ struct KernelTimer {
 
 // canonical rerank of screened entries: part_s / part_i [parts][T][per] (score,
 // first column or -1); an entry stands for columns first + o * stride, o < occ
-constexpr int kRerankMaxCand = 512;  // parts * per
+constexpr int kRerankMaxCand = 1024;  // parts * per
 constexpr int kRerankMaxOcc = 4;
 void launch_rerank(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, const float* part_s,
                    const int32_t* part_i, int parts, int per, int occ, int stride, int R, float* min_d,

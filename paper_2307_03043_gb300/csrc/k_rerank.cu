@@ -7,20 +7,24 @@ namespace chx {
 
 namespace {
 
+constexpr int kRerankWarps = 8;  // samples per block; each warp's candidate list in dynamic shared memory
+
 // One warp per sample: the R best screened entries over all chunks (by s, then
 // index), the canonical binary32 distance of each of an entry's occ columns
 // (first column + o * stride, o < occ, columns < nB), and their minimum (ties:
 // smaller index).
 template <int DT, int METRIC>
-__global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA, int64_t nA, const void* B,
+__global__ void __launch_bounds__(32 * kRerankWarps) k_rerank(const void* A, const float* scA, int64_t nA, const void* B,
                                                 const float* scB, int64_t nB, int d, const int64_t* idx, int64_t T,
                                                 const float* part_s, const int32_t* part_i, int parts, int per,
                                                 int occ, int stride, int R, float* min_d, int64_t* argmin) {
   pdl_entry();
-  __shared__ float s_s[8][kRerankMaxCand];
-  __shared__ int32_t s_i[8][kRerankMaxCand];
+  extern __shared__ float s_dyn[];  // [kRerankWarps][parts * per] scores, then as many indices
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t l = int64_t(blockIdx.x) * 8 + wib;
+  const int nc = parts * per;
+  float* s_s = s_dyn + wib * nc;
+  int32_t* s_i = reinterpret_cast<int32_t*>(s_dyn + kRerankWarps * nc) + wib * nc;
+  const int64_t l = int64_t(blockIdx.x) * kRerankWarps + wib;
   if (l >= T) return;
   const int64_t a = idx ? idx[l] : l;
   if (a < 0 || a >= nA) {
@@ -30,12 +34,11 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
     }
     return;
   }
-  const int nc = parts * per;
   for (int p = lane; p < nc; p += 32) {
     const int c = p / per, k = p % per;
     const size_t off = (size_t(c) * T + l) * per + k;
-    s_s[wib][p] = part_s[off];
-    s_i[wib][p] = part_i[off];
+    s_s[p] = part_s[off];
+    s_i[p] = part_i[off];
   }
   __syncwarp();
   float best = __int_as_float(0x7F800000);
@@ -45,8 +48,8 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
     int32_t mi = INT32_MAX;
     int mp = -1;
     for (int p = lane; p < nc; p += 32) {
-      const float v = s_s[wib][p];
-      const int32_t i = s_i[wib][p];
+      const float v = s_s[p];
+      const int32_t i = s_i[p];
       if (i >= 0 && (v < ms || (v == ms && i < mi))) {
         ms = v;
         mi = i;
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(256) k_rerank(const void* A, const float* scA,
       }
     }
     if (mi == INT32_MAX || mi < 0) break;  // fewer than R entries
-    if (lane == (mp & 31)) s_i[wib][mp] = -1;  // taken
+    if (lane == (mp & 31)) s_i[mp] = -1;  // taken
     __syncwarp();
     // canonical distances to the entry's columns, all at once (lane r sums
     // coordinates j = r mod 32 of each; the reduction trees run side by side)
@@ -114,10 +117,15 @@ void launch_rerank(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set
                    const int32_t* part_i, int parts, int per, int occ, int stride, int R, float* min_d,
                    int64_t* argmin, cudaStream_t s) {
   CHX_CHECK(parts * per <= kRerankMaxCand && occ <= kRerankMaxOcc, CH_EINVAL, "rerank candidate list too long");
-  const int blocks = static_cast<int>(ceil_div(T, 8));
-#define CHX_RERANK(DT)                                                                                              \
-  launch_k(k_rerank<DT, CH_L2>, blocks, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, B->n, A->d, qidx, T,  \
-                                             part_s, part_i, parts, per, occ, stride, R, min_d, argmin)
+  const int blocks = static_cast<int>(ceil_div(T, kRerankWarps));
+  const size_t smem = size_t(kRerankWarps) * parts * per * 8;
+#define CHX_RERANK(DT)                                                                                        \
+  do {                                                                                                        \
+    CHX_CUDA(cudaFuncSetAttribute(k_rerank<DT, CH_L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                  static_cast<int>(size_t(kRerankWarps) * kRerankMaxCand * 8)));               \
+    launch_k(k_rerank<DT, CH_L2>, blocks, 32 * kRerankWarps, smem, s, A->data, A->scales, A->n, B->data,        \
+             B->scales, B->n, A->d, qidx, T, part_s, part_i, parts, per, occ, stride, R, min_d, argmin);       \
+  } while (0)
   if (A->dtype == CH_F32) CHX_RERANK(CH_F32);
   else if (A->dtype == CH_BF16) CHX_RERANK(CH_BF16);
   else CHX_RERANK(CH_FP8E4M3);

@@ -32,7 +32,7 @@ constexpr int kEpiWarps = 8;      // epilogue warps: 2 per TMEM lane quadrant
 constexpr int kSlices = kEpiWarps / 4;     // column slices of an accumulator tile
 constexpr int kSliceCols = kBN / kSlices;  // 128 columns per epilogue thread and tile
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
-constexpr int kMaxChunks = 32;
+constexpr int kMaxChunks = 16;  // kSlices x 16 x kClasses = the rerank's 1024 candidates
 // Each epilogue thread keeps one running minimum per residue class (column mod
 // kClasses) of its slice; a class has kOcc columns in a tile slice, and the
 // thread first takes their minimum (kOcc - 1 min operations), then updates the
