@@ -133,6 +133,8 @@ struct ch_ctx {
   std::string err;
   cudaEvent_t ev[8] = {};
   std::vector<ch_ctx*> lanes;  // sub-contexts (own streams) of batched calls, made on first use
+  cudaStream_t side = nullptr;  // second stream for work that runs beside the main one, made on first use
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   void* batch_pin = nullptr;   // pinned result blocks of batched calls
   size_t batch_pin_cap = 0;
 };
