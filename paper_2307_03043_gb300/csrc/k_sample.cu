@@ -157,14 +157,39 @@ void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, S
 // With blockoff, prefix holds the block-local inclusive sums of kScanTile-point
 // blocks and blockoff their exclusive offsets: the search first finds the block
 // whose inclusive end exceeds t, then the point inside it -- the same a.
+// First index in [lo, hi) whose predicate holds (monotone: false ... false
+// true ... true), or hi: a 32-ary search by one warp.  Each round the lanes
+// test the last element of 32 equal segments and the first true segment is
+// kept, so a range of n takes about log32(n) dependent loads instead of
+// log2(n).  The whole warp calls it with the same range.
+template <class Pred>
+__device__ __forceinline__ int64_t warp_first_true(int64_t lo, int64_t hi, int lane, Pred pred) {
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t probe = min(hi - 1, lo + (lane + 1) * step - 1);
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred(probe));
+    if (bal == 0) return hi;
+    const int j = __ffs(bal) - 1;
+    const int64_t nlo = lo + int64_t(j) * step;
+    hi = min(hi, nlo + step);
+    lo = nlo;
+  }
+  const int64_t e = lo + lane;
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, e < hi && pred(e));
+  return bal == 0 ? hi : lo + (__ffs(bal) - 1);
+}
+
+// Draw l (one warp): u = Philox(l, 3) as a 128-bit fraction, t = floor(u W),
+// x_l = the first a whose inclusive prefix exceeds t.
 __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, int64_t T, uint64_t seed,
                         int64_t* idx, const uint64_t* blockoff) {
   pdl_entry();
-  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (l >= T) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t l = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (l >= T) return;  // whole warps
   const uint64_t W = *Wp;
   if (W == 0) {
-    idx[l] = -1;
+    if (lane == 0) idx[l] = -1;
     return;
   }
   const P4 u = philox10(P4{uint32_t(l), uint32_t(uint64_t(l) >> 32), 3u, 0u}, uint32_t(seed), uint32_t(seed >> 32));
@@ -175,44 +200,28 @@ __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, 
   const uint64_t phi_hi = __umul64hi(uhi, W);
   const uint64_t mid = phi_lo + plo_hi;
   const uint64_t t = phi_hi + (mid < phi_lo ? 1 : 0);
+  int64_t a;
   if (blockoff) {
+    // the first block whose inclusive end (the next block's offset, or W) exceeds
+    // t, then the first a in it with offset + local prefix > t
     const int64_t nb = ceil_div_dev(nA, kScanTile);
-    int64_t lo = 0, hi = nb;  // first block whose inclusive end (next block's offset, or W) exceeds t
-    while (lo < hi) {
-      const int64_t m = lo + ((hi - lo) >> 1);
+    const int64_t blk = warp_first_true(0, nb, lane, [&](int64_t m) {
       const uint64_t end = m + 1 < nb ? blockoff[m + 1] : W;
-      if (end > t)
-        hi = m;
-      else
-        lo = m + 1;
-    }
-    const uint64_t off = blockoff[lo];
-    int64_t a0 = lo * kScanTile, a1 = min(nA, a0 + kScanTile);
-    while (a0 < a1) {  // first a in the block with off + local prefix > t
-      const int64_t m = a0 + ((a1 - a0) >> 1);
-      if (off + prefix[m] > t)
-        a1 = m;
-      else
-        a0 = m + 1;
-    }
-    idx[l] = a0;
-    return;
+      return end > t;
+    });
+    const uint64_t off = blockoff[blk];
+    const int64_t a0 = blk * kScanTile, a1 = min(nA, a0 + kScanTile);
+    a = warp_first_true(a0, a1, lane, [&](int64_t m) { return off + prefix[m] > t; });
+  } else {
+    a = warp_first_true(0, nA, lane, [&](int64_t m) { return prefix[m] > t; });
   }
-  int64_t lo = 0, hi = nA;  // first a with prefix[a] > t
-  while (lo < hi) {
-    const int64_t m = lo + ((hi - lo) >> 1);
-    if (prefix[m] > t)
-      hi = m;
-    else
-      lo = m + 1;
-  }
-  idx[l] = lo;
+  if (lane == 0) idx[l] = a;
 }
 
 void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed, int64_t* idx,
                   cudaStream_t s, const uint64_t* blockoff) {
   if (T == 0) return;
-  launch_k(k_draws, static_cast<int>(ceil_div(T, 256)), 256, 0, s, prefix, nA, W, T, seed, idx, blockoff);
+  launch_k(k_draws, static_cast<int>(ceil_div(T, 8)), 256, 0, s, prefix, nA, W, T, seed, idx, blockoff);  // a warp per draw
   launch_check("draws");
 }
 
@@ -236,11 +245,32 @@ __device__ inline void block_sum2(double& a, double& b, double* sa, double* sb) 
   b = sb[0];
 }
 
+// the result block from the summed partials (thread 0)
+__device__ inline void combine_write(double a, double b, const uint64_t* Wp, int64_t T, double* out,
+                                     const CollectArgs& c) {
+  const uint64_t W = Wp ? *Wp : 0;
+  out[0] = (W != 0 && T > 0) ? a / static_cast<double>(T) : 0.0;
+  out[1] = b;
+  if (c.res) {
+    c.res->eta = out[0];
+    c.res->D_total = b;
+    c.res->W = W;
+    if (c.statusA) c.res->statusA = *c.statusA;
+    if (c.statusB) c.res->statusB = *c.statusB;
+    if (c.S) c.res->S = *c.S;
+    if (c.e_top) c.res->e_top = *c.e_top;
+  }
+}
+
+// With ticket (a zeroed counter): the block that finishes last also sums the
+// kCombineBlocks partials, with the same tree as k_combine_final (256 threads,
+// the upper half adding exact zeros), so one launch does both passes.
 __global__ void __launch_bounds__(256) k_combine_part(const float* m, const int64_t* idx, const uint64_t* w,
                                                       const uint64_t* Wp, int64_t T, const float* D, int64_t nA,
-                                                      double* out) {
+                                                      double* out, uint32_t* ticket, CollectArgs collect) {
   pdl_entry();
   __shared__ double s_a[256], s_b[256];
+  __shared__ bool s_last;
   const uint64_t W = Wp ? *Wp : 0;
   const int64_t lt = ceil_div_dev(T, kCombineBlocks), la = ceil_div_dev(nA, kCombineBlocks);
   double acc = 0.0, accD = 0.0;
@@ -259,6 +289,21 @@ __global__ void __launch_bounds__(256) k_combine_part(const float* m, const int6
     out[2 + 2 * blockIdx.x] = acc;
     out[3 + 2 * blockIdx.x] = accD;
   }
+  if (!ticket) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == kCombineBlocks - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  if (threadIdx.x < kCombineBlocks) {
+    a = __ldcg(&out[2 + 2 * threadIdx.x]);
+    b = __ldcg(&out[3 + 2 * threadIdx.x]);
+  }
+  __syncthreads();  // s_a / s_b are reused
+  block_sum2(a, b, s_a, s_b);
+  if (threadIdx.x == 0) combine_write(a, b, Wp, T, out, collect);
 }
 
 __global__ void __launch_bounds__(kCombineBlocks) k_combine_final(const uint64_t* Wp, int64_t T, double* out,
@@ -267,25 +312,18 @@ __global__ void __launch_bounds__(kCombineBlocks) k_combine_final(const uint64_t
   __shared__ double s_a[kCombineBlocks], s_b[kCombineBlocks];
   double a = out[2 + 2 * threadIdx.x], b = out[3 + 2 * threadIdx.x];
   block_sum2(a, b, s_a, s_b);
-  if (threadIdx.x == 0) {
-    const uint64_t W = Wp ? *Wp : 0;
-    out[0] = (W != 0 && T > 0) ? a / static_cast<double>(T) : 0.0;
-    out[1] = b;
-    if (c.res) {
-      c.res->eta = out[0];
-      c.res->D_total = b;
-      c.res->W = W;
-      if (c.statusA) c.res->statusA = *c.statusA;
-      if (c.statusB) c.res->statusB = *c.statusB;
-      if (c.S) c.res->S = *c.S;
-      if (c.e_top) c.res->e_top = *c.e_top;
-    }
-  }
+  if (threadIdx.x == 0) combine_write(a, b, Wp, T, out, c);
 }
 
 void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
                     const float* D, int64_t nA, double* out, cudaStream_t s, CollectArgs collect) {
-  launch_k(k_combine_part, kCombineBlocks, 256, 0, s, m, idx, w, W, T, D, nA, out);
+  if (collect.res) {  // the result block's spare word, zeroed with the block, counts the finished blocks
+    launch_k(k_combine_part, kCombineBlocks, 256, 0, s, m, idx, w, W, T, D, nA, out, &collect.res->pad, collect);
+    launch_check("combine");
+    return;
+  }
+  launch_k(k_combine_part, kCombineBlocks, 256, 0, s, m, idx, w, W, T, D, nA, out, static_cast<uint32_t*>(nullptr),
+           collect);
   launch_check("combine_part");
   launch_k(k_combine_final, 1, kCombineBlocks, 0, s, W, T, out, collect);
   launch_check("combine_final");
