@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(32 * kRerankWarps) k_rerank(const void* A, con
       vo[o] = o < occ && bo[o] < nB;
       part[o] = 0.0f;
     }
+#pragma unroll 4
     for (int j = lane; j < d; j += 32) {
       const float x = load_elem<DT>(A, a, d, j, scA);
 #pragma unroll
