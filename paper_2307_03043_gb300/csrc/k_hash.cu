@@ -638,10 +638,17 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
       }
     };
     if (jn == SLICE) {
-      // two chunks per loop body: the fully unrolled slice overflowed the
-      // instruction cache (no_instruction stalls; fp8 d = 384 ran 21 % slower)
+      // two chunks per loop body (one for fp8, whose chunk decodes 16 codes): the
+      // fully unrolled slice overflowed the instruction cache (no_instruction
+      // stalls); two projections, fp8 300k x 384: 368 us fully unrolled, 289 us
+      // at two chunks, 274 us at one; bf16 1M x 384: 611 / 602 / 624 us at 1 / 2 / 4
+      if constexpr (DT == CH_FP8E4M3) {
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) chunk(c, PER);
+      } else {
 #pragma unroll 2
-      for (int c = 0; c < 8; ++c) chunk(c, PER);
+        for (int c = 0; c < 8; ++c) chunk(c, PER);
+      }
     } else {
       for (int c = 0; c * PER < jn; ++c) chunk(c, min(PER, jn - c * PER));
     }
