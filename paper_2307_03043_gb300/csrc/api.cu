@@ -830,7 +830,8 @@ static void check_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch
 // result block lands in res_out (or in the workspace when null).  With events,
 // records stage boundaries in c->ev.  Returns the result block and the screen used.
 static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t T,
-                                  uint32_t R, ResBlock* res_out, bool events, int* screen_used) {
+                                  uint32_t R, ResBlock* res_out, bool events, int* screen_used,
+                                  ResBlock* host_out = nullptr) {
   const int64_t nA = A->n;
   EstBufs eb;
   carve(c, [&](auto& lay) { take_estimate(lay, c, A, B, p, T, R, &eb); });
@@ -867,7 +868,7 @@ static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, c
   if (events) CHX_CUDA(cudaEventRecord(c->ev[3], s));
   // the combine's last pass also fills the result block
   launch_combine(eb.m, eb.idx, eb.w, sb.sw.W, T, eb.D, nA, eb.out2, s,
-                 CollectArgs{res, A->status, B->status, sb.sw.S, uniform ? nullptr : cb.e_top});
+                 CollectArgs{res, A->status, B->status, sb.sw.S, uniform ? nullptr : cb.e_top, host_out});
   if (events) CHX_CUDA(cudaEventRecord(c->ev[4], s));
   if (screen_used) *screen_used = sc.screen;
   return res;
@@ -903,9 +904,11 @@ ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_
     return CH_OK;
   }
   int screen = 0;
-  ResBlock* res = estimate_enqueue(c, A, B, p, T, R, nullptr, rep != nullptr, &screen);
+  // the combine's last block writes the finished result block into the pinned page
   ResBlock* h = static_cast<ResBlock*>(c->host_pin);
-  finish(c, res, h);
+  estimate_enqueue(c, A, B, p, T, R, nullptr, rep != nullptr, &screen, h);
+  CHX_CUDA(cudaStreamSynchronize(c->stream));
+  check_result(h);
   *eta = h->eta;
   if (rep) {
     rep->eta = h->eta;

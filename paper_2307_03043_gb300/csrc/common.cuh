@@ -406,6 +406,7 @@ struct CollectArgs {
   const uint32_t* statusB = nullptr;
   const int32_t* S = nullptr;
   const int32_t* e_top = nullptr;
+  ResBlock* host = nullptr;  // pinned host page that also receives the finished block (no copy afterwards)
 };
 
 // combine: eta = (1/T) sum m_l W / w_{x_l} (binary64) and sum D (binary64).

@@ -259,6 +259,10 @@ __device__ inline void combine_write(double a, double b, const uint64_t* Wp, int
     if (c.statusB) c.res->statusB = *c.statusB;
     if (c.S) c.res->S = *c.S;
     if (c.e_top) c.res->e_top = *c.e_top;
+    if (c.host) {  // the whole block, status words included, straight into host memory
+      *c.host = *c.res;
+      __threadfence_system();
+    }
   }
 }
 
