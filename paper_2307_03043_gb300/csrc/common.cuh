@@ -279,10 +279,11 @@ struct ScaleTables {
 };
 
 // computes e_top from the two boxes, each given as partial boxes [parts][2][dd]
-// (or uses top_exp), then fills the tables
+// (or uses top_exp), then fills the tables; with zero (16-byte aligned), further
+// blocks of the same launch set zero_bytes (a multiple of 16) there to zero
 void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
                          int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
-                         cudaStream_t s);
+                         cudaStream_t s, void* zero = nullptr, size_t zero_bytes = 0, int sm_count = 1);
 
 // hashed-space source of a set: DT-typed rows (l1) or the binary32 embedding (l2)
 struct HashSrc {

@@ -857,8 +857,16 @@ int launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* bo
 // Shift z_{e,j} = (w0 >> 8) 2^(e-24), w0 = Philox(j, e, 1, 0).x; multiplier
 // K_j = Philox(j, 0, 4, 0).(y:x) | 1; salt_e = mix64((uint32)e ^ seed).
 __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
-                               int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status) {
+                               int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
+                               uint4* zero, int64_t zero16) {
   pdl_entry();
+  if (blockIdx.x > 0) {  // the other blocks clear the bucket tables meanwhile
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int64_t i = int64_t(blockIdx.x - 1) * blockDim.x + threadIdx.x; i < zero16;
+         i += int64_t(gridDim.x - 1) * blockDim.x)
+      zero[i] = z;
+    return;
+  }
   __shared__ int s_elo;
   __shared__ uint32_t s_box[2 * kMaxProj];  // merged partial boxes (partial boxes only come with dd <= kMaxProj)
   const bool merge = partsA > 1 || partsB > 1;
@@ -937,12 +945,16 @@ __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t*
 
 void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
                          int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
-                         cudaStream_t s) {
+                         cudaStream_t s, void* zero, size_t zero_bytes, int sm_count) {
   CHX_CHECK((partsA <= 1 && partsB <= 1) || dd <= kMaxProj, CH_EINVAL, "partial boxes need dd <= 64");
   // 1024 threads: the partial-box loads of all blocks are in flight at once
-  launch_k(k_scale_tables, 1, 1024, 0, s, boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out, status);
+  const int64_t zero16 = zero ? static_cast<int64_t>(zero_bytes / 16) : 0;
+  const int zblocks = zero16 ? static_cast<int>(std::min<int64_t>(ceil_div(zero16, 1024 * 4), 2 * sm_count)) : 0;
+  launch_k(k_scale_tables, 1 + zblocks, 1024, 0, s, boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out,
+           status, static_cast<uint4*>(zero), zero16);
   launch_check("scale_tables");
 }
+
 
 // ------------------------------------------------------------------ crude distance
 // D_a = canonical d(a, B[b(a)]): G lanes per a (G = min(32, next pow2 of d)),
