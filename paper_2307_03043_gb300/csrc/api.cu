@@ -838,7 +838,7 @@ static void check_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch
 // records stage boundaries in c->ev.  Returns the result block and the screen used.
 static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t T,
                                   uint32_t R, ResBlock* res_out, bool events, int* screen_used,
-                                  ResBlock* host_out = nullptr) {
+                                  ResBlock* host_out = nullptr, bool lone = false) {
   const int64_t nA = A->n;
   EstBufs eb;
   carve(c, [&](auto& lay) { take_estimate(lay, c, A, B, p, T, R, &eb); });
@@ -864,7 +864,7 @@ static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, c
   }
   if (events) CHX_CUDA(cudaEventRecord(c->ev[1], s));
   launch_weights(eb.D, nA, eb.w, sb.prefix, sb.sw, s, !uniform, true);
-  launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, eb.idx, s, sb.sw.blocksum);
+  launch_draws(sb.prefix, nA, sb.sw.W, T, p->sample_seed, eb.idx, s, sb.sw.blocksum, lone);
   if (events) CHX_CUDA(cudaEventRecord(c->ev[2], s));
   KernelTimer kt;
   if (events) {
@@ -913,7 +913,7 @@ ch_status ch_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_
   int screen = 0;
   // the combine's last block writes the finished result block into the pinned page
   ResBlock* h = static_cast<ResBlock*>(c->host_pin);
-  estimate_enqueue(c, A, B, p, T, R, nullptr, rep != nullptr, &screen, h);
+  estimate_enqueue(c, A, B, p, T, R, nullptr, rep != nullptr, &screen, h, true);
   CHX_CUDA(cudaStreamSynchronize(c->stream));
   check_result(h);
   *eta = h->eta;

@@ -346,8 +346,10 @@ void launch_fill_ones(float* D, int64_t n, cudaStream_t s);
 // exclusive offsets, which launch_draws takes as blockoff)
 void launch_weights(const float* D, int64_t nA, uint64_t* w, uint64_t* prefix, SampleWork sw, cudaStream_t s,
                     bool max_ready = false, bool local_prefix = false);
+// warp_search: a warp per draw (for a lone estimate, whose few draws are
+// latency-bound) instead of a thread per draw (for many concurrent estimates)
 void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed,
-                  int64_t* idx, cudaStream_t s, const uint64_t* blockoff = nullptr);
+                  int64_t* idx, cudaStream_t s, const uint64_t* blockoff = nullptr, bool warp_search = false);
 
 // optional CUDA events recorded around a stage's main kernel
 struct KernelTimer {

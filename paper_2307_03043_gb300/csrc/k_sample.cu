@@ -179,10 +179,70 @@ __device__ __forceinline__ int64_t warp_first_true(int64_t lo, int64_t hi, int l
   return bal == 0 ? hi : lo + (__ffs(bal) - 1);
 }
 
-// Draw l (one warp): u = Philox(l, 3) as a 128-bit fraction, t = floor(u W),
-// x_l = the first a whose inclusive prefix exceeds t.
+// t = floor(u W) for draw l, u = Philox(l, 3) read as a 128-bit fraction
+__device__ __forceinline__ uint64_t draw_point(int64_t l, uint64_t seed, uint64_t W) {
+  const P4 u = philox10(P4{uint32_t(l), uint32_t(uint64_t(l) >> 32), 3u, 0u}, uint32_t(seed), uint32_t(seed >> 32));
+  const uint64_t ulo = (uint64_t(u.y) << 32) | u.x;
+  const uint64_t uhi = (uint64_t(u.w) << 32) | u.z;
+  const uint64_t plo_hi = __umul64hi(ulo, W);
+  const uint64_t phi_lo = uhi * W;
+  const uint64_t phi_hi = __umul64hi(uhi, W);
+  const uint64_t mid = phi_lo + plo_hi;
+  return phi_hi + (mid < phi_lo ? 1 : 0);
+}
+
+// Draw l by one thread: x_l = the first a whose inclusive prefix exceeds t,
+// by binary search (the form for many draws, where loads in flight, not their
+// latency, set the pace)
 __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, int64_t T, uint64_t seed,
                         int64_t* idx, const uint64_t* blockoff) {
+  pdl_entry();
+  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= T) return;
+  const uint64_t W = *Wp;
+  if (W == 0) {
+    idx[l] = -1;
+    return;
+  }
+  const uint64_t t = draw_point(l, seed, W);
+  if (blockoff) {
+    const int64_t nb = ceil_div_dev(nA, kScanTile);
+    int64_t lo = 0, hi = nb;  // first block whose inclusive end (next block's offset, or W) exceeds t
+    while (lo < hi) {
+      const int64_t m = lo + ((hi - lo) >> 1);
+      const uint64_t end = m + 1 < nb ? blockoff[m + 1] : W;
+      if (end > t)
+        hi = m;
+      else
+        lo = m + 1;
+    }
+    const uint64_t off = blockoff[lo];
+    int64_t a0 = lo * kScanTile, a1 = min(nA, a0 + kScanTile);
+    while (a0 < a1) {  // first a in the block with off + local prefix > t
+      const int64_t m = a0 + ((a1 - a0) >> 1);
+      if (off + prefix[m] > t)
+        a1 = m;
+      else
+        a0 = m + 1;
+    }
+    idx[l] = a0;
+    return;
+  }
+  int64_t lo = 0, hi = nA;  // first a with prefix[a] > t
+  while (lo < hi) {
+    const int64_t m = lo + ((hi - lo) >> 1);
+    if (prefix[m] > t)
+      hi = m;
+    else
+      lo = m + 1;
+  }
+  idx[l] = lo;
+}
+
+// Draw l by one warp with the 32-ary search: about 4 dependent loads instead of
+// 17, for few draws, where their latency sets the pace
+__global__ void k_draws_warp(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, int64_t T, uint64_t seed,
+                             int64_t* idx, const uint64_t* blockoff) {
   pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t l = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -192,14 +252,7 @@ __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, 
     if (lane == 0) idx[l] = -1;
     return;
   }
-  const P4 u = philox10(P4{uint32_t(l), uint32_t(uint64_t(l) >> 32), 3u, 0u}, uint32_t(seed), uint32_t(seed >> 32));
-  const uint64_t ulo = (uint64_t(u.y) << 32) | u.x;
-  const uint64_t uhi = (uint64_t(u.w) << 32) | u.z;
-  const uint64_t plo_hi = __umul64hi(ulo, W);
-  const uint64_t phi_lo = uhi * W;
-  const uint64_t phi_hi = __umul64hi(uhi, W);
-  const uint64_t mid = phi_lo + plo_hi;
-  const uint64_t t = phi_hi + (mid < phi_lo ? 1 : 0);
+  const uint64_t t = draw_point(l, seed, W);
   int64_t a;
   if (blockoff) {
     // the first block whose inclusive end (the next block's offset, or W) exceeds
@@ -219,9 +272,15 @@ __global__ void k_draws(const uint64_t* prefix, int64_t nA, const uint64_t* Wp, 
 }
 
 void launch_draws(const uint64_t* prefix, int64_t nA, const uint64_t* W, int64_t T, uint64_t seed, int64_t* idx,
-                  cudaStream_t s, const uint64_t* blockoff) {
+                  cudaStream_t s, const uint64_t* blockoff, bool warp_search) {
   if (T == 0) return;
-  launch_k(k_draws, static_cast<int>(ceil_div(T, 8)), 256, 0, s, prefix, nA, W, T, seed, idx, blockoff);  // a warp per draw
+  // a warp per draw for a lone estimate of up to 16384 draws (100k x 128: 2 us
+  // less); a thread per draw otherwise, where the warp form's extra loads cost
+  // throughput (4096 concurrent pairs of d = 3, l1: 114 vs 128 ms per batch)
+  if (warp_search && T <= 16384)
+    launch_k(k_draws_warp, static_cast<int>(ceil_div(T, 8)), 256, 0, s, prefix, nA, W, T, seed, idx, blockoff);
+  else
+    launch_k(k_draws, static_cast<int>(ceil_div(T, 256)), 256, 0, s, prefix, nA, W, T, seed, idx, blockoff);
   launch_check("draws");
 }
 
