@@ -176,6 +176,23 @@ def test_crude_nn_bit_exact(ctx, pair_factory, metric, shape, group):
         assert np.array_equal(D.view(np.uint32), r["D"].view(np.uint32))
 
 
+@pytest.mark.parametrize("metric", [L1, L2])
+def test_crude_nn_bit_exact_two_table_groups(ctx, pair_factory, metric):
+    """|B| = 300k: a scale's bucket table takes 2^20 slots (16 MB), so the ten
+    scales run as two groups of five under the table budget; the second group
+    only probes the points the first left unresolved.  Also the size where the
+    two l2 projections run side by side."""
+    A, B = workloads.gaussian_mixture(40_000, 300_000, 16, 21, clusters=60)
+    A[:2000] += np.float32(25.0)  # far from every cluster: resolved only at the coarse scales
+    p = pair_factory(A, B)
+    bidx, D, lv = gpu_crude(ctx, p, metric, 5)
+    r = oracle.crude_nn(A, B, metric, hash_seed=5)
+    assert np.array_equal(bidx, r["bidx"])
+    assert np.array_equal(lv, r["level"])
+    assert np.array_equal(D.view(np.uint32), r["D"].view(np.uint32))
+    assert lv.max() >= 5  # some points resolve in the second group
+
+
 @pytest.mark.parametrize("group", GROUPS, ids=["hash", "sort"])
 def test_crude_nn_few_levels_and_fallback(ctx, pair_factory, group):
     A, B = workloads.uniform(400, 600, 6, 5)
