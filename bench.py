@@ -753,6 +753,16 @@ def main():
                 "peak_basis": f"of measured: bf16_tflops (burst) x {ratio:.3f} nominal {kind.lower()}:bf16"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel_ms"] = kern_avg
+    # CrudeNN as a whole against HBM: algorithmic bytes = each set read once by the
+    # embedding pass, A and the rows b(a) of B read once by the crude distances,
+    # the k-wide binary32 embedding of both sets written once and read once, D written
+    crude_ms = float(np.mean([s[0] for s in stages]))
+    crude_bytes = (NA + NB + 2 * NA) * DIM * elem_bytes() + (NA + NB) * PROJ * 4 * 2 + NA * 4
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    crude_roof = {"bound": "hbm", "bytes": crude_bytes, "achieved": crude_bytes / (crude_ms / 1e3) / 1e9,
+                  "peak": hbm, "unit": "GB/s", "frac": crude_bytes / (crude_ms / 1e3) / 1e9 / hbm,
+                  "stage_ms": crude_ms,
+                  "basis": "of measured hbm_gbs; stage time from CUDA events around the CrudeNN kernels"}
 
     serving = serving_sample(ch, ctx, rank, args.serve_requests) if args.serve_requests > 0 else None
     cpu = None
@@ -786,6 +796,7 @@ def main():
                     "d2h_bytes_per_step": 48},
             "gpu_launches": launches,
             "roofline": roof,
+            "crude_nn_roofline": crude_roof,
             "cpu_baseline": cpu,
             "clocks": clk,
             "serving": serving,
