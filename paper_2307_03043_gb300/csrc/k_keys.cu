@@ -101,9 +101,12 @@ __device__ inline uint32_t slot_home(uint64_t key, uint32_t log_cap) {
 // first: only the lowest lane (the smallest b, since b grows with the lane)
 // touches the table, which keeps the coarse scales -- where most points share
 // a handful of buckets -- from serialising on one L2 line.
+template <bool MERGE = true>
 __device__ inline void table_insert(ulonglong2* tab, uint32_t log_cap, uint64_t key, int64_t b, uint32_t* status) {
-  const unsigned peers = __match_any_sync(__activemask(), static_cast<unsigned long long>(key));
-  if ((threadIdx.x & 31) != __ffs(peers) - 1) return;
+  if (MERGE) {  // equal keys of a warp: only the lowest lane (the smallest b) inserts
+    const unsigned peers = __match_any_sync(__activemask(), static_cast<unsigned long long>(key));
+    if ((threadIdx.x & 31) != __ffs(peers) - 1) return;
+  }
   const uint32_t cap = 1u << log_cap;
   const unsigned long long want = ~static_cast<unsigned long long>(b);
   uint32_t pos = slot_home(key, log_cap);
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0
 
 // Each unresolved a walks the scales of the group in increasing order and
 // stops at the first bucket that holds a b (Fig. 2, step 3).
-template <int DT, int W>
+template <int DT, int W, bool WIDE>
 __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
                                                      int64_t* bidx, uint8_t* level) {
   pdl_entry();
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0,
     level[r] = static_cast<uint8_t>(L);
   }
   const size_t cap = size_t(1) << h.log_cap;
-  if (src.dd <= W) {
+  if (!WIDE) {  // rows in registers (dd <= W); the wide form is compiled only where needed
     float y[W];
     load_row<DT, W>(src, r, y);
     for (int l = 0; l < nl; ++l) {
@@ -323,7 +326,11 @@ void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTab
   if (A.n == 0) return;
   const int grid = static_cast<int>(ceil_div(A.n, 128));
   dispatch_dt_w(A.dtype, A.dd, [&](auto dtc, auto wc) {
-    launch_k(k_table_probe<decltype(dtc)::value, decltype(wc)::value>, grid, 128, 0, s, A, L, L0, nl, t, h, bidx, level);
+    constexpr int DT = decltype(dtc)::value, W = decltype(wc)::value;
+    if (A.dd <= W)  // the register form alone: 32-odd registers instead of 115, so 4x the resident warps
+      launch_k(k_table_probe<DT, W, false>, grid, 128, 0, s, A, L, L0, nl, t, h, bidx, level);
+    else
+      launch_k(k_table_probe<DT, W, true>, grid, 128, 0, s, A, L, L0, nl, t, h, bidx, level);
   });
   launch_check("table_probe");
 }
