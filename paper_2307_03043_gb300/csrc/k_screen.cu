@@ -4,17 +4,20 @@
 // |q - b|^2 (|q|^2 is constant per sample).  The dot products are a dense
 // contraction S = Q B^T run on the 5th-generation tensor cores:
 //   * TMA (cp.async.bulk.tensor, 128-byte swizzle) stages Q (128 samples x d,
-//     resident per work item) and B tiles (256 points x one 128-byte K block)
-//     through a ring of shared-memory stages;
+//     resident per work item below 768-byte rows, else streamed beside B) and B
+//     tiles (256 points x one 128-byte K block) through a ring of shared-memory
+//     stages;
 //   * one elected thread issues tcgen05.mma (kind::tf32 for binary32 data,
 //     kind::f16 with bf16 operands, kind::f8f6f4 with e4m3 operands) into a
 //     double-buffered 128 x 256 binary32 accumulator in tensor memory;
-//   * eight epilogue warps read the accumulator with tcgen05.ld (one row per
-//     thread), form s and keep each row's R smallest (s, b) in registers.
+//   * eight epilogue warps read the accumulator with tcgen05.ld (one row and a
+//     128-column slice per thread), form s and keep, per residue class of
+//     columns, the running minimum and the tile it came from.
 // Work items are (128-sample tile, chunk of B) pairs spread over a persistent
-// grid; a rerank kernel then takes each sample's R best screened candidates
-// over all chunks and evaluates the canonical binary32 distance on them, so the
-// reported minimum is exact whenever the true nearest point survives the screen.
+// grid (up to 16 chunks, so that the items fill the SMs); a rerank kernel then
+// takes each sample's R best screened entries over all chunks and evaluates the
+// canonical binary32 distance on the columns each stands for, so the reported
+// minimum is exact whenever the true nearest point survives the screen.
 //
 // Every mbarrier wait is bounded (about 2 s of SM clock); on expiry the CTA
 // raises ST_TIMEOUT, stops issuing work, lets in-flight copies and MMAs drain
@@ -281,8 +284,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------ epilogue: one sample row per thread
-    // Sixteen warps: warp w reads TMEM lane quadrant w % 4 (the only one it may
-    // access) and one 64-column slice of each accumulator tile.
+    // Eight warps: warp w reads TMEM lane quadrant w % 4 (the only one it may
+    // access) and one 128-column slice of each accumulator tile.
     const int ew = warp & 3;
     const int qs = (warp - 2) >> 2;  // column slice
     const int row = ew * 32 + lane;
