@@ -967,6 +967,7 @@ __global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* 
                                                     const float* scB, int d, int G, const int64_t* bidx,
                                                     float* D, uint32_t* maxD) {
   pdl_entry();
+  const int gshift = __ffs(G) - 1;
   __shared__ uint32_t s_max[8];
   uint32_t mx = 0;
   const int64_t total = nA * G;
@@ -974,8 +975,8 @@ __global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* 
   // every lane runs the same number of rounds (the shuffles need the whole warp)
   for (int64_t g0 = int64_t(blockIdx.x) * blockDim.x; g0 < total; g0 += step) {
     const int64_t gt = g0 + threadIdx.x;
-    const int64_t a = gt / G;
-    const int q = static_cast<int>(gt % G);
+    const int64_t a = gt >> gshift;  // G is a power of two: no 64-bit division
+    const int q = static_cast<int>(gt & (G - 1));
     const bool live = gt < total;
     float p = 0.0f;
     if (live) {

@@ -148,16 +148,15 @@ __device__ inline int64_t table_find(const ulonglong2* tab, uint32_t log_cap, ui
   return -1;
 }
 
-// Narrow rows: one thread per (point, scale), thread t = l * n + r, so the
+// Narrow rows: one thread per (point, scale) (blockIdx.y = scale), so the
 // scales' insert round trips overlap instead of forming one chain per point.
 template <int DT, int W>
 __global__ void __launch_bounds__(128) k_table_insert_ps(HashSrc src, int L, int L0, int nl, ScaleTables t,
                                                          HashTable h, uint32_t* status) {
   pdl_entry();
-  const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (g >= src.n * nl) return;
-  const int l = static_cast<int>(g / src.n);
-  const int64_t r = g - int64_t(l) * src.n;
+  const int l = blockIdx.y;  // scale; blocks run scale by scale, as the flat order t = l * n + r did
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= src.n) return;
   float y[W];
   load_row<DT, W>(src, r, y);
   const size_t cap = size_t(1) << h.log_cap;
@@ -304,7 +303,7 @@ void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTa
                          cudaStream_t s) {
   if (B.n == 0) return;
   if (B.dd <= kRegRow) {
-    const int grid_ps = static_cast<int>(ceil_div(B.n * nl, 128));
+    const dim3 grid_ps(static_cast<unsigned>(ceil_div(B.n, 128)), static_cast<unsigned>(nl));
     dispatch_dt_w(B.dtype, B.dd, [&](auto dtc, auto wc) {
       launch_k(k_table_insert_ps<decltype(dtc)::value, decltype(wc)::value>, grid_ps, 128, 0, s, B, L, L0, nl, t, h,
                                                                                             status);
