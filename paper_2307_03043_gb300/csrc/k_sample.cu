@@ -36,6 +36,25 @@ __device__ inline int weight_shift(const uint32_t* maxD, int64_t nA, bool* zero)
   return 62 - ceil_log2_i64(nA) - eM;
 }
 
+// ceil(Da 2^S) for a finite Da > 0, exactly, from the bits of Da (the same
+// integer as ceil(ldexp(double(Da), S)), without the FP64 pipe): Da = m 2^(e-150)
+// with a 24-bit m, so the scaled value is m shifted by e - 150 + S, rounded up.
+// S keeps every weight below 2^63, so a left shift never overflows.
+__device__ __forceinline__ uint64_t ceil_scaled(float Da, int S) {
+  const uint32_t bits = __float_as_uint(Da);
+  int e = static_cast<int>((bits >> 23) & 0xFFu);
+  uint64_t m = bits & 0x7FFFFFu;
+  if (e == 0)
+    e = 1;  // subnormal
+  else
+    m |= 0x800000u;
+  const int sh = e - 150 + S;
+  if (sh >= 0) return m << sh;
+  const int k = -sh;
+  if (k >= 32) return 1;  // 0 < m 2^-k < 1
+  return (m + (uint64_t(1) << k) - 1) >> k;
+}
+
 // block-local inclusive scan of u64 weights; writes w, the local prefix and the block sum
 __global__ void __launch_bounds__(kScanThreads) k_weights(const float* D, int64_t nA, const uint32_t* maxD,
                                                           uint64_t* w, uint64_t* prefix, uint64_t* blocksum,
@@ -54,7 +73,7 @@ __global__ void __launch_bounds__(kScanThreads) k_weights(const float* D, int64_
     uint64_t wa = 0;
     if (a < nA && !zero) {
       const float Da = D[a];
-      if (Da > 0.0f) wa = static_cast<uint64_t>(ceil(ldexp(static_cast<double>(Da), S)));
+      if (Da > 0.0f) wa = ceil_scaled(Da, S);
     }
     if (a < nA) w[a] = wa;
     run += wa;
