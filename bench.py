@@ -53,9 +53,12 @@ WORKLOADS = {
     "precision_fp8": dict(n=1_000_000, d=384, dtype="fp8",
                           desc="precision: |A|=|B|=1000000, d=384, fp8 e4m3 + row scale, l2, eps=0.1, "
                                "1000-cluster unit-norm mixture"),
-    "batched": dict(n=0, d=3, dtype="f32",
+    "batched": dict(n=0, d=3, dtype="f32", pairs=4096,
                     desc="batched: 4096 pairs, |A| and |B| log-uniform in [256, 50000], d=3 ellipsoid/box "
                          "surfaces with 1% noise (B a resample of A's shape), fp32, l2 (l1 alongside), eps=0.1"),
+    "batched_d64": dict(n=0, d=64, dtype="f32", pairs=1024,
+                        desc="batched d=64: 1024 pairs, |A| and |B| log-uniform in [256, 50000], d=64 10-cluster "
+                             "Gaussian mixtures, fp32, l2 (l1 alongside), eps=0.1"),
     "curves": dict(n=0, d=16, dtype="f32",
                    desc="sample complexity: relative error of importance (CrudeNN 1x1 and 4x16) vs uniform "
                         "sampling over T, 32 seeds "
@@ -66,7 +69,16 @@ WORKLOADS = {
                          "bf16 uniform, l2, eps=0.1; requests pick a (d, type) pool and two of its sets; a closed "
                          "burst measures saturation, then Poisson arrivals at 0.5/0.8/0.95x of it"),
 }
-BATCH_PAIRS = 4096
+BATCHED = ("batched", "batched_d64")
+
+
+def batched_pair(na, nb, seed):
+    """One pair of the batched workloads: d=3 surface samples, else a 10-cluster
+    Gaussian mixture in DIM dimensions."""
+    from paper_2307_03043_gb300 import workloads
+    if DIM == 3:
+        return workloads.shape_surface(na, nb, seed)
+    return workloads.gaussian_mixture(na, nb, DIM, seed, clusters=10)
 
 
 def select_workload(name):
@@ -260,11 +272,12 @@ def run_batched(args, ch, ctx, torch, rank, local, world):
     resident on the device).  Each pair's estimate counts when it lies within
     (1 +- 0.1) of its exact GPU brute force."""
     from paper_2307_03043_gb300 import workloads
-    P = BATCH_PAIRS
+    P = WORKLOADS[CONFIG]["pairs"]
     sizes = workloads.log_uniform_sizes(2 * P, 256, 50_000, 1000 + rank)
-    host = [workloads.shape_surface(int(sizes[2 * i]), int(sizes[2 * i + 1]), 5000 + rank * P + i) for i in range(P)]
+    host = [batched_pair(int(sizes[2 * i]), int(sizes[2 * i + 1]), 5000 + rank * P + i) for i in range(P)]
     npts = [a.shape[0] + b.shape[0] for a, b in host]
-    sets = [(ch.ch_set_create(ctx, a, 0, a.shape[0], 3), ch.ch_set_create(ctx, b, 0, b.shape[0], 3)) for a, b in host]
+    sets = [(ch.ch_set_create(ctx, a, 0, a.shape[0], DIM), ch.ch_set_create(ctx, b, 0, b.shape[0], DIM))
+            for a, b in host]
     A = [x[0] for x in sets]
     B = [x[1] for x in sets]
     stream = torch.cuda.current_stream()
@@ -311,7 +324,7 @@ def run_batched(args, ch, ctx, torch, rank, local, world):
     for k in range(max(1, args.e2e_steps // 2) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ss = [(ch.ch_set_create(ctx, a, 0, a.shape[0], 3), ch.ch_set_create(ctx, b, 0, b.shape[0], 3))
+        ss = [(ch.ch_set_create(ctx, a, 0, a.shape[0], DIM), ch.ch_set_create(ctx, b, 0, b.shape[0], DIM))
               for a, b in pinned]
         prm = [ch.est_params(ch.CH_L2, LEVELS, PROJ, None, 77 + i, eps=EPS, sample_seed=77 + i) for i in range(P)]
         ch.ch_estimate_batch(ctx, [x[0] for x in ss], [x[1] for x in ss], prm)
@@ -322,7 +335,7 @@ def run_batched(args, ch, ctx, torch, rank, local, world):
         if k > 0:
             e2e_s.append(time.perf_counter() - t0)
     e2e_value = sum(npts) / float(np.mean(e2e_s))
-    # roofline: the exact CUDA-core scan of the largest pair, timed on its own
+    # roofline: the sampled scan's main kernel on the largest pair, timed on its own
     big = int(np.argmax([a.shape[0] * b.shape[0] for a, b in host]))
     kms = []
     for k in range(3):
@@ -330,15 +343,24 @@ def run_batched(args, ch, ctx, torch, rank, local, world):
                                                                      sample_seed=k), report=True)
         kms.append(rep.t_kernel_ms)
     nB_big = host[big][1].shape[0]
+    pair = f"of the largest pair ({host[big][0].shape[0]} x {nB_big}), timed alone"
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    ops = 2.0 * rep.T * nB_big * 3
-    roof = {"bound": "alu", "achieved": ops / (np.median(kms) / 1e3) / 1e12, "peak": 152 * 128 * sm_max * 1e6 / 1e12,
-            "unit": "Tinst/s", "traffic": None,
-            "kernel": f"k_scan_exact (canonical fp32 l2 scan) of the largest pair ({host[big][0].shape[0]} x {nB_big}), "
-                      f"timed alone", "kernel_ms": float(np.median(kms)),
-            "peak_basis": "152 SMs x 128 FP32 lanes x sm_max_mhz (derived, not measured)"}
+    ops = 2.0 * rep.T * nB_big * DIM
+    if rep.screen == ch.CH_SCREEN_EXACT:
+        kname = "k_scan_small" if DIM <= 4 else "k_scan_exact"
+        roof = {"bound": "alu", "achieved": ops / (np.median(kms) / 1e3) / 1e12,
+                "peak": 152 * 128 * sm_max * 1e6 / 1e12, "unit": "Tinst/s", "traffic": None,
+                "kernel": f"{kname} (canonical fp32 l2 scan) {pair}",
+                "peak_basis": "152 SMs x 128 FP32 lanes x sm_max_mhz (derived, not measured)"}
+    else:
+        ratio = 1.1 / 2.25
+        roof = {"bound": "tensor", "achieved": ops / (np.median(kms) / 1e3) / 1e12,
+                "peak": peaks.get("bf16_tflops", 1910.1) * ratio, "unit": "TFLOP/s", "traffic": None,
+                "kernel": f"k_screen<TF32> (tcgen05 screen, 2*T*nB*d flops) {pair}",
+                "peak_basis": f"of measured: bf16_tflops (burst) x {ratio:.3f} nominal tf32:bf16"}
+    roof["kernel_ms"] = float(np.median(kms))
     roof["frac"] = roof["achieved"] / roof["peak"]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -361,7 +383,7 @@ def run_batched(args, ch, ctx, torch, rank, local, world):
             "metric": METRIC, "value": main_m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_m["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batched"]["desc"], "pairs": P, "points": int(sum(npts)), "d": 3,
+            "config": {"workload": WORKLOADS[CONFIG]["desc"], "pairs": P, "points": int(sum(npts)), "d": DIM,
                        "metric": "l2", "eps": EPS, "levels": LEVELS, "proj_dim": PROJ,
                        "l2_flush": "256 MiB write between timed steps, outside the timed events",
                        "api": "ch_estimate_batch (8 streams)"},
@@ -369,7 +391,7 @@ def run_batched(args, ch, ctx, torch, rank, local, world):
             "exact_gpu": {"mode": "canonical fp32, all pairs, one ch_exact per pair",
                           "ms_per_pair": main_m["exact_gpu_ms_per_pair"],
                           "speedup_estimate_vs_exact": main_m["speedup_estimate_vs_exact"]},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(sum(npts)) * 3 * 4,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(sum(npts)) * DIM * 4,
                     "d2h_bytes_per_step": P * 48},
             "gpu_launches": main_m["gpu_launches"], "roofline": roof, "cpu_baseline": cpu,
             "clocks": main_m["clocks"], "l1": out_metrics["l1"],
@@ -518,10 +540,10 @@ def run_reference_batched(args):
     pairs (every 256th) in full; value in points per second."""
     import oracle
     from paper_2307_03043_gb300 import workloads
-    P = BATCH_PAIRS
+    P = WORKLOADS[CONFIG]["pairs"]
     sizes = workloads.log_uniform_sizes(2 * P, 256, 50_000, 1000)
     sub = list(range(0, P, P // 16))[:16]
-    host = {i: workloads.shape_surface(int(sizes[2 * i]), int(sizes[2 * i + 1]), 5000 + i) for i in sub}
+    host = {i: batched_pair(int(sizes[2 * i]), int(sizes[2 * i + 1]), 5000 + i) for i in sub}
     pts = sum(a.shape[0] + b.shape[0] for a, b in host.values())
 
     def step(seed):
@@ -541,7 +563,7 @@ def run_reference_batched(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS["batched"]["desc"], "pairs": P, "d": 3, "metric": "l2", "eps": EPS},
+        "config": {"workload": WORKLOADS[CONFIG]["desc"], "pairs": P, "d": DIM, "metric": "l2", "eps": EPS},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -555,7 +577,7 @@ def run_reference(args):
         return
     import oracle
     from paper_2307_03043_gb300 import workloads
-    if CONFIG == "batched":
+    if CONFIG in BATCHED:
         run_reference_batched(args)
         return
     if CONFIG in ("curves", "serving"):  # not a points/s workload: the reference arm times the mid one
@@ -620,7 +642,7 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    if CONFIG == "batched":
+    if CONFIG in BATCHED:
         ctx = ch.ch_ctx_create(local, torch.cuda.current_stream())
         run_batched(args, ch, ctx, torch, rank, local, world)
         ch.ch_ctx_destroy(ctx)

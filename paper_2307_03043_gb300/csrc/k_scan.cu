@@ -13,50 +13,66 @@
 
 namespace chx {
 
-template <int METRIC, int PQ, int PB, int QS, int BS>
+// Resident blocks per SM of k_scan_exact: the register cap (80 per thread,
+// no spills) lets three 256-thread blocks share an SM, so one block's tile
+// copy overlaps the others' arithmetic.
+constexpr int kScanBlocksPerSM = 3;
+
+// NJ > 0: d lies in (32 (NJ - 1), 32 NJ], so every partial holds NJ - 1 or NJ
+// terms and the loops unroll; NJ = 0: any d, runtime loops.
+template <int METRIC, int PQ, int PB, int QS, int BS, int NJ>
 struct Tree {
-  // leaf r: sum over j = r, r+32, ... of |q_j - b_j| or (q_j - b_j)^2
-  template <int R>
-  static __device__ __forceinline__ void leaf(float (&acc)[PQ][PB], const float* __restrict__ Qt,
-                                              const float* __restrict__ Bt, int d) {
+  // the term of coordinate j for every pair; FIRST starts the partial with it
+  // (|t| or t*t alone, bit-identical to adding it to +0)
+  template <bool FIRST>
+  static __device__ __forceinline__ void term(float (&acc)[PQ][PB], const float* __restrict__ Qt,
+                                              const float* __restrict__ Bt, int j) {
+    float qv[PQ], bv[PB];
+    if constexpr (PQ == 2) {
+      const float2 t = *reinterpret_cast<const float2*>(Qt + j * QS);
+      qv[0] = t.x;
+      qv[1] = t.y;
+    } else {
+#pragma unroll
+      for (int p = 0; p < PQ; ++p) qv[p] = Qt[j * QS + p];
+    }
+    if constexpr (PB == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(Bt + j * BS);
+      bv[0] = t.x;
+      bv[1] = t.y;
+      bv[2] = t.z;
+      bv[3] = t.w;
+    } else if constexpr (PB == 2) {
+      const float2 t = *reinterpret_cast<const float2*>(Bt + j * BS);
+      bv[0] = t.x;
+      bv[1] = t.y;
+    } else {
+#pragma unroll
+      for (int b = 0; b < PB; ++b) bv[b] = Bt[j * BS + b];
+    }
 #pragma unroll
     for (int p = 0; p < PQ; ++p)
 #pragma unroll
-      for (int b = 0; b < PB; ++b) acc[p][b] = 0.0f;
-    for (int j = R; j < d; j += 32) {
-      float qv[PQ], bv[PB];
-      if constexpr (PQ == 2) {
-        const float2 t = *reinterpret_cast<const float2*>(Qt + j * QS);
-        qv[0] = t.x;
-        qv[1] = t.y;
-      } else {
-#pragma unroll
-        for (int p = 0; p < PQ; ++p) qv[p] = Qt[j * QS + p];
+      for (int b = 0; b < PB; ++b) {
+        const float t = __fsub_rn(qv[p], bv[b]);
+        if constexpr (METRIC == CH_L1)
+          acc[p][b] = FIRST ? fabsf(t) : __fadd_rn(acc[p][b], fabsf(t));
+        else
+          acc[p][b] = FIRST ? __fmul_rn(t, t) : __fmaf_rn(t, t, acc[p][b]);
       }
-      if constexpr (PB == 4) {
-        const float4 t = *reinterpret_cast<const float4*>(Bt + j * BS);
-        bv[0] = t.x;
-        bv[1] = t.y;
-        bv[2] = t.z;
-        bv[3] = t.w;
-      } else if constexpr (PB == 2) {
-        const float2 t = *reinterpret_cast<const float2*>(Bt + j * BS);
-        bv[0] = t.x;
-        bv[1] = t.y;
-      } else {
+  }
+
+  // leaf R (R < d): sum over j = R, R+32, ... of |q_j - b_j| or (q_j - b_j)^2
+  template <int R>
+  static __device__ __forceinline__ void leaf(float (&acc)[PQ][PB], const float* __restrict__ Qt,
+                                              const float* __restrict__ Bt, int d) {
+    term<true>(acc, Qt, Bt, R);
+    if constexpr (NJ > 0) {
 #pragma unroll
-        for (int b = 0; b < PB; ++b) bv[b] = Bt[j * BS + b];
-      }
-#pragma unroll
-      for (int p = 0; p < PQ; ++p)
-#pragma unroll
-        for (int b = 0; b < PB; ++b) {
-          const float t = __fsub_rn(qv[p], bv[b]);
-          if constexpr (METRIC == CH_L1)
-            acc[p][b] = __fadd_rn(acc[p][b], fabsf(t));
-          else
-            acc[p][b] = __fmaf_rn(t, t, acc[p][b]);
-        }
+      for (int t = 1; t < NJ; ++t)
+        if (t < NJ - 1 || R + 32 * t < d) term<false>(acc, Qt, Bt, R + 32 * t);
+    } else {
+      for (int j = R + 32; j < d; j += 32) term<false>(acc, Qt, Bt, j);
     }
   }
 
@@ -68,7 +84,7 @@ struct Tree {
       leaf<R>(out, Qt, Bt, d);
     } else {
       node<R, 2 * S>(out, Qt, Bt, d);
-      if (R + S < d) {
+      if (NJ >= 2 || R + S < d) {  // d > 32: no partial is empty
         float tmp[PQ][PB];
         node<R + S, 2 * S>(tmp, Qt, Bt, d);
 #pragma unroll
@@ -80,8 +96,8 @@ struct Tree {
   }
 };
 
-template <int DT, int METRIC, int QT, int BT, int PQ, int PB>
-__global__ void __launch_bounds__(256) k_scan_exact(const void* __restrict__ A, const float* __restrict__ scA,
+template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ>
+__global__ void __launch_bounds__(256, kScanBlocksPerSM) k_scan_exact(const void* __restrict__ A, const float* __restrict__ scA,
                                                     const int64_t* __restrict__ qidx, int64_t T, int64_t nA,
                                                     const void* __restrict__ B, const float* __restrict__ scB,
                                                     int64_t nB, int d, int64_t chunk_len, float* part_val,
@@ -89,6 +105,7 @@ __global__ void __launch_bounds__(256) k_scan_exact(const void* __restrict__ A, 
   pdl_entry();
   constexpr int NTQ = QT / PQ, NTB = BT / PB;
   static_assert(NTQ * NTB == 256, "256 threads");
+  static_assert(NTB == 16, "16 thread rows (the occupancy estimate assumes it)");
   constexpr int QS = QT + 4, BS = BT + 4;
   extern __shared__ __align__(16) float smem[];
   float* Qs = smem;
@@ -102,15 +119,14 @@ __global__ void __launch_bounds__(256) k_scan_exact(const void* __restrict__ A, 
   const int64_t b_begin = int64_t(blockIdx.y) * chunk_len;
   const int64_t b_end = min(nB, b_begin + chunk_len);
 
-  for (int f = tid; f < QT * d; f += 256) {
-    const int q = f / d, j = f - q * d;
+  // tiles are staged transposed (coordinate-major); a warp copies whole rows,
+  // its lanes striding over the coordinates
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int q = warp; q < QT; q += 8) {
     const int64_t l = q0 + q;
-    float v = 0.0f;
-    if (l < T) {
-      const int64_t a = qidx ? qidx[l] : l;
-      if (a >= 0 && a < nA) v = load_elem<DT>(A, a, d, j, scA);
-    }
-    Qs[j * QS + q] = v;
+    const int64_t a = l < T ? (qidx ? qidx[l] : l) : -1;
+    const bool ok = a >= 0 && a < nA;
+    for (int j = lane; j < d; j += 32) Qs[j * QS + q] = ok ? load_elem<DT>(A, a, d, j, scA) : 0.0f;
   }
 
   float best_val[PQ], best_p0[PQ];
@@ -127,13 +143,13 @@ __global__ void __launch_bounds__(256) k_scan_exact(const void* __restrict__ A, 
   for (int64_t b0 = b_begin; b0 < b_end; b0 += BT) {
     __syncthreads();
     const int64_t rows = min(static_cast<int64_t>(BT), b_end - b0);
-    for (int f = tid; f < BT * d; f += 256) {
-      const int r = f / d, j = f - r * d;
-      Bs[j * BS + r] = (r < rows) ? load_elem<DT>(B, b0 + r, d, j, scB) : 0.0f;
+    for (int r = warp; r < BT; r += 8) {
+      const bool ok = r < rows;
+      for (int j = lane; j < d; j += 32) Bs[j * BS + r] = ok ? load_elem<DT>(B, b0 + r, d, j, scB) : 0.0f;
     }
     __syncthreads();
     float out[PQ][PB];
-    Tree<METRIC, PQ, PB, QS, BS>::template node<0, 1>(out, Qt, Bt, d);
+    Tree<METRIC, PQ, PB, QS, BS, NJ>::template node<0, 1>(out, Qt, Bt, d);
 #pragma unroll
     for (int p = 0; p < PQ; ++p)
 #pragma unroll
@@ -308,6 +324,15 @@ static size_t scan_smem(int d) {
   return size_t(d) * ((t.QT + 4) + (t.BT + 4)) * sizeof(float);
 }
 
+// Blocks of k_scan_exact one SM holds at once for dimension d: the dynamic
+// tiles, the static per-row minima (16 thread rows x QT x (4 + 8) bytes) and
+// the 1 KB reserved per block, out of 228 KB of shared memory per SM.
+static int scan_blocks_per_sm(int d) {
+  const TileShape t = tile_for(d);
+  const size_t per_block = scan_smem(d) + size_t(16) * t.QT * 12 + 1024;
+  return static_cast<int>(std::max<size_t>(1, std::min<size_t>(kScanBlocksPerSM, (228u * 1024u) / per_block)));
+}
+
 int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
   if (d <= kSmallMaxD) {  // k_scan_small: about 4 blocks per SM, chunks of >= 256 points
     const int64_t qblocks = ceil_div(std::max<int64_t>(T, 1), kSmallQ);
@@ -315,18 +340,30 @@ int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
     chunks = std::min<int64_t>(chunks, ceil_div(nB, 256));
     return static_cast<int>(std::max<int64_t>(chunks, 1));
   }
+  // B is cut into equal chunks, one block per (sample tile, chunk).  The count
+  // minimises (waves of resident blocks) x (B tiles per block), the kernel's time
+  // when every wave runs at the same rate; ties go to fewer chunks (less merging).
   const TileShape t = tile_for(d);
   const int64_t qtiles = ceil_div(std::max<int64_t>(T, 1), t.QT);
-  const int64_t target = int64_t(sm_count) * 4;
-  int64_t chunks = ceil_div(target, qtiles);
-  chunks = std::min<int64_t>(chunks, ceil_div(nB, int64_t(t.BT) * 4));
-  return static_cast<int>(std::max<int64_t>(chunks, 1));
+  const int64_t resident = int64_t(sm_count) * scan_blocks_per_sm(d);
+  const int64_t btiles = ceil_div(std::max<int64_t>(nB, 1), t.BT);
+  const int64_t max_chunks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(btiles, 4), 4 * resident));
+  int64_t best = 1, best_cost = INT64_MAX;
+  for (int64_t c = 1; c <= max_chunks; ++c) {
+    const int64_t cost = ceil_div(qtiles * c, resident) * ceil_div(btiles, c);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+    if (qtiles * c >= 8 * resident) break;  // past eight waves the cost only flattens
+  }
+  return static_cast<int>(best);
 }
 
-template <int DT, int METRIC, int QT, int BT, int PQ, int PB>
+template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ = 0>
 static void scan_launch(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, ScanPart part,
                         cudaStream_t s) {
-  auto kern = k_scan_exact<DT, METRIC, QT, BT, PQ, PB>;
+  auto kern = k_scan_exact<DT, METRIC, QT, BT, PQ, PB, NJ>;
   const size_t smem = scan_smem(A->d);
   // a constant value, so concurrent callers on other threads never race on it
   CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
@@ -340,7 +377,14 @@ template <int DT, int METRIC>
 static void scan_shape(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, ScanPart part,
                        cudaStream_t s) {
   const TileShape t = tile_for(A->d);
-  if (t.BT == 64)
+  if (A->d <= 128) {  // terms per partial fixed at compile time
+    switch ((A->d + 31) / 32) {
+      case 1: scan_launch<DT, METRIC, 32, 64, 2, 4, 1>(A, qidx, T, B, part, s); break;
+      case 2: scan_launch<DT, METRIC, 32, 64, 2, 4, 2>(A, qidx, T, B, part, s); break;
+      case 3: scan_launch<DT, METRIC, 32, 64, 2, 4, 3>(A, qidx, T, B, part, s); break;
+      default: scan_launch<DT, METRIC, 32, 64, 2, 4, 4>(A, qidx, T, B, part, s); break;
+    }
+  } else if (t.BT == 64)
     scan_launch<DT, METRIC, 32, 64, 2, 4>(A, qidx, T, B, part, s);
   else if (t.BT == 32)
     scan_launch<DT, METRIC, 32, 32, 2, 2>(A, qidx, T, B, part, s);
