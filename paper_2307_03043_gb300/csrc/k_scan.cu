@@ -96,6 +96,26 @@ struct Tree {
   }
 };
 
+// Copies coordinates jl, jl + 8, ... of source row `row` (-1: zeros) into column
+// r of a coordinate-major tile (Ts[j * S + r]).  Lane (rl, jl) = (lane & 3,
+// lane >> 2) of a warp takes row 4g + rl of row group g: one warp instruction
+// reads 8 consecutive coordinates of 4 rows and, with S = 4 mod 8, stores to
+// 32 distinct banks.
+template <int DT, int S, int NJ>
+__device__ __forceinline__ void stage_row(float* __restrict__ Ts, int r, const void* __restrict__ base,
+                                          const float* __restrict__ scales, int64_t row, int d, int jl) {
+  static_assert(S % 8 == 4, "conflict-free staging needs S = 4 mod 8");
+  if constexpr (NJ > 0) {
+#pragma unroll
+    for (int k = 0; k < 4 * NJ; ++k) {
+      const int j = jl + 8 * k;
+      if (k < 4 * (NJ - 1) || j < d) Ts[j * S + r] = row >= 0 ? load_elem<DT>(base, row, d, j, scales) : 0.0f;
+    }
+  } else {
+    for (int j = jl; j < d; j += 8) Ts[j * S + r] = row >= 0 ? load_elem<DT>(base, row, d, j, scales) : 0.0f;
+  }
+}
+
 template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ>
 __global__ void __launch_bounds__(256, kScanBlocksPerSM) k_scan_exact(const void* __restrict__ A, const float* __restrict__ scA,
                                                     const int64_t* __restrict__ qidx, int64_t T, int64_t nA,
@@ -119,14 +139,14 @@ __global__ void __launch_bounds__(256, kScanBlocksPerSM) k_scan_exact(const void
   const int64_t b_begin = int64_t(blockIdx.y) * chunk_len;
   const int64_t b_end = min(nB, b_begin + chunk_len);
 
-  // tiles are staged transposed (coordinate-major); a warp copies whole rows,
-  // its lanes striding over the coordinates
-  const int warp = tid >> 5, lane = tid & 31;
-  for (int q = warp; q < QT; q += 8) {
+  // tiles are staged transposed (coordinate-major), four rows per warp instruction
+  const int warp = tid >> 5, rl = (tid & 31) & 3, jl = (tid & 31) >> 2;
+  for (int g = warp; g < QT / 4; g += 8) {
+    const int q = 4 * g + rl;
     const int64_t l = q0 + q;
-    const int64_t a = l < T ? (qidx ? qidx[l] : l) : -1;
-    const bool ok = a >= 0 && a < nA;
-    for (int j = lane; j < d; j += 32) Qs[j * QS + q] = ok ? load_elem<DT>(A, a, d, j, scA) : 0.0f;
+    int64_t a = l < T ? (qidx ? qidx[l] : l) : -1;
+    if (a >= nA) a = -1;
+    stage_row<DT, QS, NJ>(Qs, q, A, scA, a, d, jl);
   }
 
   float best_val[PQ], best_p0[PQ];
@@ -143,9 +163,9 @@ __global__ void __launch_bounds__(256, kScanBlocksPerSM) k_scan_exact(const void
   for (int64_t b0 = b_begin; b0 < b_end; b0 += BT) {
     __syncthreads();
     const int64_t rows = min(static_cast<int64_t>(BT), b_end - b0);
-    for (int r = warp; r < BT; r += 8) {
-      const bool ok = r < rows;
-      for (int j = lane; j < d; j += 32) Bs[j * BS + r] = ok ? load_elem<DT>(B, b0 + r, d, j, scB) : 0.0f;
+    for (int g = warp; g < BT / 4; g += 8) {
+      const int r = 4 * g + rl;
+      stage_row<DT, BS, NJ>(Bs, r, B, scB, r < rows ? b0 + r : int64_t(-1), d, jl);
     }
     __syncthreads();
     float out[PQ][PB];
