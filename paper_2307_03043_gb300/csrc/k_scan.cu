@@ -116,7 +116,10 @@ __device__ __forceinline__ void stage_row(float* __restrict__ Ts, int r, const v
   }
 }
 
-template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ>
+// One block: QT samples against a chunk of B, staged SUB x BT rows at a time
+// (one pair of barriers per stage); each thread owns PQ samples x PB rows of
+// every BT-row sub-tile.
+template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ, int SUB>
 __global__ void __launch_bounds__(256, kScanBlocksPerSM) k_scan_exact(const void* __restrict__ A, const float* __restrict__ scA,
                                                     const int64_t* __restrict__ qidx, int64_t T, int64_t nA,
                                                     const void* __restrict__ B, const float* __restrict__ scB,
@@ -126,7 +129,8 @@ __global__ void __launch_bounds__(256, kScanBlocksPerSM) k_scan_exact(const void
   constexpr int NTQ = QT / PQ, NTB = BT / PB;
   static_assert(NTQ * NTB == 256, "256 threads");
   static_assert(NTB == 16, "16 thread rows (the occupancy estimate assumes it)");
-  constexpr int QS = QT + 4, BS = BT + 4;
+  constexpr int ST = BT * SUB;  // rows per stage
+  constexpr int QS = QT + 4, BS = ST + 4;
   extern __shared__ __align__(16) float smem[];
   float* Qs = smem;
   float* Bs = smem + size_t(d) * QS;
@@ -160,38 +164,47 @@ __global__ void __launch_bounds__(256, kScanBlocksPerSM) k_scan_exact(const void
   const float* Qt = Qs + tq * PQ;
   const float* Bt = Bs + tb * PB;
 
-  for (int64_t b0 = b_begin; b0 < b_end; b0 += BT) {
+  for (int64_t b0 = b_begin; b0 < b_end; b0 += ST) {
     __syncthreads();
-    const int64_t rows = min(static_cast<int64_t>(BT), b_end - b0);
-    for (int g = warp; g < BT / 4; g += 8) {
+    const int64_t rows = min(static_cast<int64_t>(ST), b_end - b0);
+    for (int g = warp; g < ST / 4; g += 8) {
       const int r = 4 * g + rl;
       stage_row<DT, BS, NJ>(Bs, r, B, scB, r < rows ? b0 + r : int64_t(-1), d, jl);
     }
     __syncthreads();
-    float out[PQ][PB];
-    Tree<METRIC, PQ, PB, QS, BS, NJ>::template node<0, 1>(out, Qt, Bt, d);
+    // distances of this thread's pairs in sub-tile `sub`, folded into its minima
+    auto scan_sub = [&](int sub) {
+      float out[PQ][PB];
+      Tree<METRIC, PQ, PB, QS, BS, NJ>::template node<0, 1>(out, Qt, Bt + sub * BT, d);
 #pragma unroll
-    for (int p = 0; p < PQ; ++p)
+      for (int p = 0; p < PQ; ++p)
 #pragma unroll
-      for (int b = 0; b < PB; ++b) {
-        const int r = tb * PB + b;
-        if (r < rows) {
-          const float v = out[p][b];
-          if constexpr (METRIC == CH_L1) {
-            if (v < best_val[p]) {
-              best_val[p] = v;
-              best_idx[p] = b0 + r;
-            }
-          } else if (v < best_p0[p]) {
-            best_p0[p] = v;
-            const float sv = __fsqrt_rn(v);
-            if (sv < best_val[p]) {
-              best_val[p] = sv;
-              best_idx[p] = b0 + r;
+        for (int b = 0; b < PB; ++b) {
+          const int r = sub * BT + tb * PB + b;
+          if (r < rows) {
+            const float v = out[p][b];
+            if constexpr (METRIC == CH_L1) {
+              if (v < best_val[p]) {
+                best_val[p] = v;
+                best_idx[p] = b0 + r;
+              }
+            } else if (v < best_p0[p]) {
+              best_p0[p] = v;
+              const float sv = __fsqrt_rn(v);
+              if (sv < best_val[p]) {
+                best_val[p] = sv;
+                best_idx[p] = b0 + r;
+              }
             }
           }
         }
-      }
+    };
+    if constexpr (SUB == 1) {
+      scan_sub(0);
+    } else {
+#pragma unroll 1
+      for (int sub = 0; sub < SUB && sub * BT < rows; ++sub) scan_sub(sub);
+    }
   }
 #pragma unroll
   for (int p = 0; p < PQ; ++p) {
@@ -330,18 +343,21 @@ __global__ void k_scan_merge(const float* part_val, const int64_t* part_idx, int
 }
 
 struct TileShape {
-  int QT, BT;
+  int QT, BT, SUB;  // samples, rows per sub-tile, sub-tiles per stage
 };
 
+// small d stages more rows per barrier pair, so the copy of a stage is not
+// short next to its latency
 static TileShape tile_for(int d) {
-  if (d <= 192) return {32, 64};
-  if (d <= 768) return {32, 32};
-  return {16, 16};
+  if (d <= 32) return {32, 64, 4};
+  if (d <= 192) return {32, 64, 1};
+  if (d <= 768) return {32, 32, 1};
+  return {16, 16, 1};
 }
 
 static size_t scan_smem(int d) {
   const TileShape t = tile_for(d);
-  return size_t(d) * ((t.QT + 4) + (t.BT + 4)) * sizeof(float);
+  return size_t(d) * ((t.QT + 4) + (t.BT * t.SUB + 4)) * sizeof(float);
 }
 
 // Blocks of k_scan_exact one SM holds at once for dimension d: the dynamic
@@ -366,7 +382,7 @@ int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
   const TileShape t = tile_for(d);
   const int64_t qtiles = ceil_div(std::max<int64_t>(T, 1), t.QT);
   const int64_t resident = int64_t(sm_count) * scan_blocks_per_sm(d);
-  const int64_t btiles = ceil_div(std::max<int64_t>(nB, 1), t.BT);
+  const int64_t btiles = ceil_div(std::max<int64_t>(nB, 1), int64_t(t.BT) * t.SUB);  // stages
   const int64_t max_chunks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(btiles, 4), 4 * resident));
   int64_t best = 1, best_cost = INT64_MAX;
   for (int64_t c = 1; c <= max_chunks; ++c) {
@@ -380,14 +396,15 @@ int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
   return static_cast<int>(best);
 }
 
-template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ = 0>
+template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ = 0, int SUB = 1>
 static void scan_launch(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, ScanPart part,
                         cudaStream_t s) {
-  auto kern = k_scan_exact<DT, METRIC, QT, BT, PQ, PB, NJ>;
+  auto kern = k_scan_exact<DT, METRIC, QT, BT, PQ, PB, NJ, SUB>;
+  CHX_CHECK(tile_for(A->d).BT == BT && tile_for(A->d).SUB == SUB, CH_ENOTSUP, "scan tile mismatch");
   const size_t smem = scan_smem(A->d);
   // a constant value, so concurrent callers on other threads never race on it
   CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-  const int64_t chunk_len = ceil_div(ceil_div(B->n, part.chunks), BT) * BT;
+  const int64_t chunk_len = ceil_div(ceil_div(B->n, part.chunks), BT * SUB) * (BT * SUB);
   dim3 grid(static_cast<unsigned>(ceil_div(T, QT)), static_cast<unsigned>(part.chunks));
   launch_k(kern, grid, 256, smem, s, A->data, A->scales, qidx, T, A->n, B->data, B->scales, B->n, A->d, chunk_len,
                                part.val, part.idx);
@@ -399,7 +416,7 @@ static void scan_shape(const ch_set* A, const int64_t* qidx, int64_t T, const ch
   const TileShape t = tile_for(A->d);
   if (A->d <= 128) {  // terms per partial fixed at compile time
     switch ((A->d + 31) / 32) {
-      case 1: scan_launch<DT, METRIC, 32, 64, 2, 4, 1>(A, qidx, T, B, part, s); break;
+      case 1: scan_launch<DT, METRIC, 32, 64, 2, 4, 1, 4>(A, qidx, T, B, part, s); break;
       case 2: scan_launch<DT, METRIC, 32, 64, 2, 4, 2>(A, qidx, T, B, part, s); break;
       case 3: scan_launch<DT, METRIC, 32, 64, 2, 4, 3>(A, qidx, T, B, part, s); break;
       default: scan_launch<DT, METRIC, 32, 64, 2, 4, 4>(A, qidx, T, B, part, s); break;

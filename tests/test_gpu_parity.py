@@ -349,7 +349,8 @@ def test_sample_all_zero(ctx):
 @pytest.mark.parametrize("nA,nB,d,T", [(500, 2000, 16, 777), (300, 4099, 3, 301), (200, 1500, 128, 97),
                                        (120, 700, 200, 65), (64, 333, 768, 33), (50, 123, 1, 40),
                                        (400, 3000, 40, 513), (300, 2100, 96, 257), (150, 1000, 160, 70),
-                                       (40, 200, 1000, 20), (900, 5000, 64, 4100)])
+                                       (40, 200, 1000, 20), (900, 5000, 64, 4100), (256, 1333, 32, 300),
+                                       (333, 2500, 5, 1000)])
 def test_sampled_nn_exact_bit_exact(ctx, pair_factory, metric, nA, nB, d, T):
     A, B = workloads.gaussian_mixture(nA, nB, d, nA + d, clusters=9)
     p = pair_factory(A, B)
