@@ -248,11 +248,15 @@ ch_status ch_estimate(ch_ctx* ctx, const ch_set* A, const ch_set* B, const ch_es
                       ch_est_report* report);
 
 /* ------------------------------------------------------------ many estimates
- * Estimates of count independent pairs (A[i], B[i]) under params[i], as
- * ch_estimate would return them (same values, bit for bit), in one call: the
- * pairs are spread over a few internal streams of the context, so that the
- * kernels of small pairs overlap, and the host waits once at the end.  Not in
- * the paper (a throughput form of Fig. 1 for many small pairs).
+ * Estimates of count independent pairs (A[i], B[i]) under params[i], in one
+ * call: the pairs are spread over a few internal streams of the context, so that
+ * the kernels of small pairs overlap, and the host waits once at the end.  Not in
+ * the paper (a throughput form of Fig. 1 for many small pairs).  With the exact
+ * scans (l1, CH_SCREEN_EXACT) each value equals ch_estimate's bit for bit.  With
+ * a tensor-core screen, B is split into chunks for one stream's share of the SMs,
+ * and ch_estimate splits it for all of them.  The two can then differ only where
+ * a sample's nearest point misses the R reranked entries under one split but not
+ * under the other.
  * A, B: arrays of count sets of this context; params: count parameter blocks;
  * eta: host double [count] (0 for failed pairs and for |A| = 0); status: host
  * ch_status [count] or NULL.  Returns CH_OK, or the first failing pair's status

@@ -393,7 +393,8 @@ static void take_scan(L& lay, ch_ctx* c, const ch_set* A, const ch_set* B, int64
   } else {
     sb->part = ScanPart{nullptr, nullptr, 0};
     sb->screen_work =
-        lay.template take<char>(screen_workspace(T, B->n, A->d, static_cast<int>(R), c->sm_count, sb->screen));
+        lay.template take<char>(screen_workspace(T, B->n, A->d, static_cast<int>(R), c->sm_count,
+                                                 c->screen_chunk_sms, sb->screen));
   }
 }
 
@@ -409,7 +410,7 @@ static void run_scan(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t T, 
   } else {
     ensure_norms(const_cast<ch_set*>(B), c->stream);
     launch_screen_l2(A, idx, T, B, sb->screen, static_cast<int>(R), sb->screen_work, m, argmin, status, c->sm_count,
-                     c->stream, timer);
+                     c->screen_chunk_sms, c->stream, timer);
   }
 }
 
@@ -961,6 +962,9 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
     CHX_CHECK(cs == CH_OK, cs, "batch lane creation failed");
     c->lanes.push_back(l);
   }
+  // K lanes run at once, so each screen splits B for its share of the SMs only
+  // (fewer chunks, fewer rerank candidates per sample)
+  for (int k = 0; k < K; ++k) c->lanes[k]->screen_chunk_sms = std::max(1, c->sm_count / K);
   // the lazy set passes run here, on c's stream, so that no two lanes race on them
   for (int64_t i = 0; i < count; ++i) {
     if (st[i] != CH_OK) continue;

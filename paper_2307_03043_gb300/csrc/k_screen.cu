@@ -478,7 +478,7 @@ struct Plan {
 
 int screen_dtype(int screen) { return screen == CH_SCREEN_TF32 ? CH_F32 : screen == CH_SCREEN_BF16 ? CH_BF16 : CH_FP8E4M3; }
 
-Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
+Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int chunk_sms, int screen) {
   Plan p;
   const int es = static_cast<int>(elem_size(screen_dtype(screen)));
   p.T = T;
@@ -495,15 +495,17 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
   const size_t limit = 227 * 1024;
   p.stages = static_cast<int>(std::min<size_t>(6, (limit - std::min(limit, fixed)) / per_stage));
   p.smem = fixed + size_t(p.stages) * per_stage;
-  // chunks: smallest count whose items fill the SMs to >= 90 % (at most kMaxChunks)
+  // chunks: smallest count whose items fill chunk_sms SMs to >= 90 % (at most
+  // kMaxChunks); more chunks also mean more rerank candidates per sample
+  const int fill = chunk_sms > 0 ? std::min(chunk_sms, sm_count) : sm_count;
   const int64_t btiles = ceil_div(nB, kBN);
   int best_c = 1;
   double best_eff = 0.0;
   for (int c = 1; c <= kMaxChunks && c <= btiles; ++c) {
     if (kSlices * c * kClasses > kRerankMaxCand) break;  // kSlices column slices per chunk
     const int64_t items = int64_t(p.row_tiles) * c;
-    const int64_t rounds = ceil_div(items, sm_count);
-    const double eff = double(items) / double(rounds * sm_count);
+    const int64_t rounds = ceil_div(items, fill);
+    const double eff = double(items) / double(rounds * fill);
     if (eff > best_eff + 1e-9) {
       best_eff = eff;
       best_c = c;
@@ -542,8 +544,8 @@ bool screen_supported(int screen, const ch_set* A, const ch_set* B) {
   return true;
 }
 
-size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int screen) {
-  const Plan p = make_plan(T, nB, d, R, sm_count, screen);
+size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int chunk_sms, int screen) {
+  const Plan p = make_plan(T, nB, d, R, sm_count, chunk_sms, screen);
   const int es = static_cast<int>(elem_size(screen_dtype(screen)));
   const size_t q = ((size_t(T) * d * es + 255) & ~size_t(255)) + ((size_t(T) * 4 + 255) & ~size_t(255));
   const size_t parts = size_t(kSlices * p.chunks) * T * kClasses * 8 + 512;
@@ -551,10 +553,10 @@ size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int s
 }
 
 void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R, void* work,
-                      float* min_d, int64_t* argmin, uint32_t* status, int sm_count, cudaStream_t s,
-                      const KernelTimer& timer) {
+                      float* min_d, int64_t* argmin, uint32_t* status, int sm_count, int chunk_sms,
+                      cudaStream_t s, const KernelTimer& timer) {
   if (T == 0) return;
-  const Plan p = make_plan(T, B->n, A->d, R, sm_count, screen);
+  const Plan p = make_plan(T, B->n, A->d, R, sm_count, chunk_sms, screen);
   const int es = static_cast<int>(elem_size(A->dtype));
   const int row_bytes = A->d * es;
   uint8_t* w = static_cast<uint8_t*>(work);
