@@ -120,11 +120,10 @@ __device__ __forceinline__ void stage_row(float* __restrict__ Ts, int r, const v
 // (one pair of barriers per stage); each thread owns PQ samples x PB rows of
 // every BT-row sub-tile.
 template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ, int SUB>
-__global__ void __launch_bounds__(256, kScanBlocksPerSM) k_scan_exact(const void* __restrict__ A, const float* __restrict__ scA,
-                                                    const int64_t* __restrict__ qidx, int64_t T, int64_t nA,
-                                                    const void* __restrict__ B, const float* __restrict__ scB,
-                                                    int64_t nB, int d, int64_t chunk_len, float* part_val,
-                                                    int64_t* part_idx) {
+__global__ void __launch_bounds__(256, kScanBlocksPerSM)
+    k_scan_exact(const void* __restrict__ A, const float* __restrict__ scA, const int64_t* __restrict__ qidx, int64_t T,
+                 int64_t nA, const void* __restrict__ B, const float* __restrict__ scB, int64_t nB, int d,
+                 int64_t chunk_len, float* part_val, int64_t* part_idx) {
   pdl_entry();
   constexpr int NTQ = QT / PQ, NTB = BT / PB;
   static_assert(NTQ * NTB == 256, "256 threads");
