@@ -68,3 +68,19 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(binding.ChamferError):
         binding.lib()
+
+
+def test_default_params_match_the_header(built):
+    """ch_default_params fills the defaults include/chamfer.h documents (a host
+    call: no device is touched)."""
+    import ctypes
+    from paper_2307_03043_gb300 import binding as ch
+    p = ch.ch_est_params()
+    ctypes.memset(ctypes.byref(p), 0xAB, ctypes.sizeof(p))
+    ch.lib().ch_default_params(ctypes.byref(p))
+    h = p.hash
+    assert (h.metric, h.levels, h.proj_dim, h.top_exp, h.hash_seed, h.group) == \
+        (ch.CH_L1, 10, 16, ch.CH_TOP_EXP_AUTO, 0, ch.CH_GROUP_HASH)
+    assert h.window in (0, 1) and h.repeats in (0, 1) and h.family == 0  # Fig. 2's single structure, grids
+    assert (p.eps, p.T, p.sample_seed, p.screen, p.rerank_k, p.sampling) == \
+        (0.1, 0, 0, ch.CH_SCREEN_AUTO, 8, ch.CH_SAMPLING_IMPORTANCE)
