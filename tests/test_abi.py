@@ -84,3 +84,33 @@ def test_default_params_match_the_header(built):
     assert h.window in (0, 1) and h.repeats in (0, 1) and h.family == 0  # Fig. 2's single structure, grids
     assert (p.eps, p.T, p.sample_seed, p.screen, p.rerank_k, p.sampling) == \
         (0.1, 0, 0, ch.CH_SCREEN_AUTO, 8, ch.CH_SAMPLING_IMPORTANCE)
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets that a C
+    compiler gives the header's declaration (gcc on this host)."""
+    import ctypes
+    import shutil
+    from paper_2307_03043_gb300 import binding as ch
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [ch.ch_hash_params, ch.ch_est_params, ch.ch_est_report, ch.ch_serve_config, ch.ch_serve_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "chamfer.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'  printf("{s.__name__} size %zu\\n", sizeof({s.__name__}));')
+        for f in s._fields_:
+            lines.append(f'  printf("{s.__name__} {f[0]} %zu\\n", offsetof({s.__name__}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, value = ln.split()
+        got[(name, field)] = int(value)
+    for s in structs:
+        assert got[(s.__name__, "size")] == ctypes.sizeof(s), s.__name__
+        for f in s._fields_:
+            assert got[(s.__name__, f[0])] == getattr(s, f[0]).offset, (s.__name__, f[0])
