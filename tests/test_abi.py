@@ -114,3 +114,25 @@ def test_binding_structs_match_the_c_layout(tmp_path):
         assert got[(s.__name__, "size")] == ctypes.sizeof(s), s.__name__
         for f in s._fields_:
             assert got[(s.__name__, f[0])] == getattr(s, f[0]).offset, (s.__name__, f[0])
+
+
+NULL_CTX_CALLS = ["ch_ctx_sync", "ch_set_create", "ch_set_prepare", "ch_top_exp", "ch_hash_keys", "ch_crude_nn",
+                  "ch_sample", "ch_sampled_nn", "ch_estimate", "ch_estimate_batch", "ch_estimate_sym", "ch_exact"]
+
+
+@pytest.mark.parametrize("name", NULL_CTX_CALLS)
+def test_null_context_is_an_argument_error(built, name):
+    """Every call that takes a context answers CH_EINVAL to a NULL one, before
+    any device work (the header's error contract; runs without a GPU)."""
+    import ctypes
+    from paper_2307_03043_gb300 import binding as ch
+    fn = getattr(ch.lib(), name)
+    args = []
+    for t in fn.argtypes:
+        if t in (ctypes.c_double, ctypes.c_float):
+            args.append(0.0)
+        elif issubclass(t, ctypes._SimpleCData) and t is not ctypes.c_void_p and t._type_ not in "zPO":
+            args.append(0)
+        else:
+            args.append(None)
+    assert fn(*args) == ch.CH_EINVAL
