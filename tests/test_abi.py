@@ -136,3 +136,17 @@ def test_null_context_is_an_argument_error(built, name):
         else:
             args.append(None)
     assert fn(*args) == ch.CH_EINVAL
+
+
+def test_context_without_a_device_is_a_cuda_error(built):
+    """With no CUDA device, ch_ctx_create reports CH_ECUDA, frees what it made
+    and leaves *out as it was (set on success only)."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2307_03043_gb300 import binding as ch
+    out = ctypes.c_void_p(1234)
+    assert ch.lib().ch_ctx_create(0, None, ctypes.byref(out)) == ch.CH_ECUDA
+    assert out.value == 1234
+    assert ch.lib().ch_ctx_create(0, None, None) == ch.CH_EINVAL
