@@ -40,3 +40,23 @@ def test_reference_arm_prints_the_contract_line():
 
 def test_reference_arm_runs_on_rank_zero_only():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_screen_traffic_is_dropped_once_the_kernel_source_changes(tmp_path, monkeypatch):
+    """bench.py reports the committed DRAM bytes of the screen only while
+    k_screen.cu is the source those counters were taken from."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = b"// a kernel source\n"
+    (tmp_path / "paper_2307_03043_gb300" / "csrc").mkdir(parents=True)
+    (tmp_path / "paper_2307_03043_gb300" / "csrc" / "k_screen.cu").write_bytes(src)
+    (tmp_path / "profiles").mkdir()
+    rec = {"mid/TF32": {"k_screen_sha256": hashlib.sha256(src).hexdigest(), "dram_bytes_per_launch": 123}}
+    (tmp_path / "profiles" / "screen_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "CONFIG", "mid")
+    assert bench.screen_traffic("TF32") == 123
+    assert bench.screen_traffic("BF16") is None
+    (tmp_path / "paper_2307_03043_gb300" / "csrc" / "k_screen.cu").write_bytes(src + b"// changed\n")
+    assert bench.screen_traffic("TF32") is None
