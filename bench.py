@@ -1,10 +1,11 @@
 #!/usr/bin/env python3
 """Benchmark of libchamfer's Chamfer-Estimate hot path on one GB300 per rank.
 
-Workload (one step = every stage of the path on one pair of point sets):
-  |A| = |B| = 100,000, d = 128, binary32, l2, eps = 0.1 (T = 4606 samples),
-  100-cluster Gaussian mixture (centres U[-10,10]^128, unit std; B's centres
-  moved by N(0, 0.5^2)), L = 10 scales, k = 16 embedding width.
+Default workload (one step = every stage of the path on one pair of point sets):
+  |A| = |B| = 1,000,000, d = 384, stored bfloat16, l2, eps = 0.1 (T = 5527
+  samples), unit-norm 1000-cluster mixture (stand-in for the paper's DEEP1B /
+  MS-Turing setting), L = 10 scales, k = 16 embedding width, BF16 tensor-core
+  screen with a canonical binary32 rerank.
 A step registers both sets from resident device memory (ingest), runs CrudeNN,
 the importance draws, the sampled scans and the combine, and ends with the
 estimate on the host (ch_set_create x2 + ch_estimate + ch_set_destroy x2).
@@ -13,6 +14,7 @@ metric = (|A| + |B|) points per second of estimates within (1 +- 0.1) of the
 exact GPU brute force (ch_exact); steps outside that band count zero points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config precision|precision_fp8|mid|batched|batched_d64|curves|serving]
 
 With N > 1 (torchrun, one process per GPU) every rank runs its own pair
 (independent replicas, no data-path collective); value = all points / max time.
@@ -44,6 +46,7 @@ PROJ = 16
 FLUSH_BYTES = 256 << 20  # > 126 MB L2
 DTYPE = "f32"            # storage type of the sets ("f32", "bf16", "fp8")
 CONFIG = "mid"
+DEFAULT_CONFIG = "precision"
 
 WORKLOADS = {
     "mid": dict(n=100_000, d=128, dtype="f32",
@@ -129,7 +132,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=200, help="0 skips the serving sample")
-    ap.add_argument("--config", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default=DEFAULT_CONFIG, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-scan-fraction", type=int, default=32,
+                    help="the CPU baseline runs T/f of the sampled scans and scales their time by f")
     return ap.parse_args()
 
 
@@ -193,9 +198,10 @@ def screen_traffic(kind):
     return None
 
 
-def cpu_oracle_step(A, B, T, seed, scan_fraction=1):
+def cpu_oracle_step(A, B, T, seed, scan_fraction=1, details=False):
     """One oracle Chamfer-Estimate on the full sets; with scan_fraction f > 1 only
-    T/f sampled scans run and their time is scaled by f.  Returns (seconds, eta)."""
+    the first ceil(T/f) sampled scans run and their time is scaled by T/Ts.
+    Returns (seconds, eta over the Ts scans that ran[, details])."""
     import oracle
     t0 = time.perf_counter()
     r = oracle.crude_nn(A, B, oracle.L2, hash_seed=seed, L=LEVELS, proj_dim=PROJ)
@@ -206,7 +212,31 @@ def cpu_oracle_step(A, B, T, seed, scan_fraction=1):
     m, _ = oracle.scan(A, idx[:Ts], B, oracle.L2)
     t2 = time.perf_counter()
     eta = oracle.combine(m, idx[:Ts], w, W)
-    return (t1 - t0) + (t2 - t1) * (T / Ts), eta
+    sec = (t1 - t0) + (t2 - t1) * (T / Ts)
+    if details:
+        return sec, eta, {"crude": r, "w": w, "W": W, "idx": idx, "Ts": Ts, "m": m,
+                          "t_crude_weights_draws_s": t1 - t0, "t_scans_s": t2 - t1}
+    return sec, eta
+
+
+def slice_oracle_step(A, B, T, seed, slices, k, scans):
+    """A bounded sample of one oracle Chamfer-Estimate: CrudeNN, weights and draws
+    on slice k of `slices` equal row slices of A and of B (every stage is linear
+    in the points it sees), then `scans` sampled scans against B's slice.  Each
+    part's time is scaled to the whole estimate: x slices for CrudeNN, weights
+    and draws; x slices * T / scans for the scans.  Returns seconds."""
+    import oracle
+    nA, nB = A.shape[0] // slices, B.shape[0] // slices
+    a = A[k * nA:(k + 1) * nA]
+    b = B[k * nB:(k + 1) * nB]
+    t0 = time.perf_counter()
+    r = oracle.crude_nn(a, b, oracle.L2, hash_seed=seed, L=LEVELS, proj_dim=PROJ)
+    w, prefix, W, _ = oracle.weights(r["D"])
+    idx = oracle.draws(prefix, W, scans, seed)
+    t1 = time.perf_counter()
+    oracle.scan(a, idx, b, oracle.L2)
+    t2 = time.perf_counter()
+    return (t1 - t0) * slices + (t2 - t1) * slices * (T / scans)
 
 
 def serving_sample(ch, ctx, rank, n_req=200, seed=7):
@@ -570,38 +600,43 @@ def run_reference_batched(args):
     }))
 
 
+REF_SLICES = {"mid": 1, "precision": 8, "precision_fp8": 8}
+REF_SCANS = {"mid": 576, "precision": 64, "precision_fp8": 64}
+
+
 def run_reference(args):
-    """The oracle, as it stands, on the host cores (rank 0 only)."""
+    """The oracle, as it stands, on the host cores (rank 0 only), on the same
+    seeded data as this arm's own line (rank 0's pair)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
-    from paper_2307_03043_gb300 import workloads
     if CONFIG in BATCHED:
         run_reference_batched(args)
         return
-    if CONFIG in ("curves", "serving"):  # not a points/s workload: the reference arm times the mid one
-        select_workload("mid")
-    A, B = workloads.gaussian_mixture(NA, NB, DIM, 0)
+    if CONFIG in ("curves", "serving"):  # not a points/s workload: the reference arm times the default one
+        select_workload(DEFAULT_CONFIG)
+    A, B = make_data(0)[:2]
     T = oracle.default_T(NA, NB, EPS)
-    frac = 8
+    slices, scans = REF_SLICES[CONFIG], REF_SCANS[CONFIG]
     for w in range(args.warmup):
-        cpu_oracle_step(A, B, T, 1000 + w, frac)
+        slice_oracle_step(A, B, T, 1000 + w, slices, w % slices, scans)
     times, walls = [], []
     for k in range(args.steps):
         w0 = time.perf_counter()
-        t, _ = cpu_oracle_step(A, B, T, k, frac)
+        times.append(slice_oracle_step(A, B, T, k, slices, k % slices, scans))
         walls.append(time.perf_counter() - w0)
-        times.append(t)
-    sec = float(np.mean(times))  # one whole estimate, its scans extrapolated from the sample
+    sec = float(np.mean(times))  # one whole estimate, extrapolated from the sample
     value = (NA + NB) / sec
     cores = oracle.num_threads()
-    sample = (f"each step: oracle CrudeNN + weights + draws on the full 100k x 100k sets, "
-              f"exact scans of T/{frac} samples timed and scaled by {frac}")
+    part = "the full sets" if slices == 1 else f"row slice (k mod {slices}) of 1/{slices} of each set"
+    sample = (f"each step k: oracle CrudeNN + weights + draws on {part}, then {scans} sampled exact scans "
+              f"against B's {'set' if slices == 1 else 'slice'}; times scaled to one whole estimate "
+              f"(x{slices} for CrudeNN/weights/draws, x{slices}*T/{scans} for the scans)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(walls)) * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
         "config": workload_config(T),
         # ms_per_step is the wall time of one sampled step; value counts one whole
         # estimate per extrapolated_ms_per_estimate
@@ -609,6 +644,44 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def oracle_parity(ch, ctx, torch, A, B, scA, scB, cdt, T, det, eta_o, screen):
+    """GPU against the oracle on the timed workload, seed 0 (the seeds of timed
+    step 0), outside the timed region: CrudeNN (b(a), level, D_a bits) and the
+    weights in full, the T draws, and the estimate over the first Ts draws (the
+    ones whose scans the CPU baseline ran)."""
+    r = det["crude"]
+    sA = ch.ch_set_create(ctx, A, 2 if scA is None else 1, NA, DIM, cdt, scA)
+    sB = ch.ch_set_create(ctx, B, 2 if scB is None else 1, NB, DIM, cdt, scB)
+    try:
+        bidx = torch.full((NA,), -1, dtype=torch.int64, device="cuda")
+        D = torch.zeros(NA, dtype=torch.float32, device="cuda")
+        lv = torch.zeros(NA, dtype=torch.uint8, device="cuda")
+        ch.ch_crude_nn(ctx, sA, sB, ch.hash_params(ch.CH_L2, LEVELS, PROJ, None, 0), bidx, D, lv)
+        idx = torch.zeros(T, dtype=torch.int64, device="cuda")
+        w = torch.zeros(NA, dtype=torch.int64, device="cuda")
+        W = ch.ch_sample(ctx, D, NA, T, 0, idx, w, want_total=True)
+        Ts = det["Ts"]
+        eta_g = ch.ch_estimate(ctx, sA, sB, ch.est_params(ch.CH_L2, LEVELS, PROJ, None, 0, eps=EPS, T=Ts,
+                                                          sample_seed=0, screen=screen))
+        D_h = D.cpu().numpy()
+        out = {
+            "seed": 0,
+            "crude_nn_bit_exact": bool(np.array_equal(bidx.cpu().numpy(), r["bidx"])
+                                       and np.array_equal(lv.cpu().numpy(), r["level"])
+                                       and np.array_equal(D_h.view(np.uint32), r["D"].view(np.uint32))),
+            "weights_bit_exact": bool(W == det["W"] and np.array_equal(w.cpu().numpy().view(np.uint64), det["w"])),
+            "draws_bit_exact": bool(np.array_equal(idx.cpu().numpy(), det["idx"])),
+            "T_compared": Ts, "eta_gpu": eta_g, "eta_oracle": eta_o,
+            "rel_vs_oracle": abs(eta_g / eta_o - 1.0) if eta_o else abs(eta_g),
+            "what": f"GPU estimate with T = {Ts} against the oracle's over the same {Ts} draws (seed 0); "
+                    f"CrudeNN, weights and all {T} draws compared in full",
+        }
+    finally:
+        ch.ch_set_destroy(sA)
+        ch.ch_set_destroy(sB)
+    return out
 
 
 def main():
@@ -702,7 +775,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, scan_ms, kern_ms, ok, stages = [], [], [], [], []
+    step_ms, scan_ms, kern_ms, ok, stages, etas = [], [], [], [], [], []
     screen_used = None
     launches0 = ch.ch_kernel_launches()
     for k in range(args.steps):
@@ -718,6 +791,7 @@ def main():
         stages.append((rep.t_crude_ms, rep.t_sample_ms, rep.t_scan_ms, rep.t_total_ms))
         screen_used = rep.screen
         ok.append(abs(eta / exact - 1.0) <= 0.1)
+        etas.append(eta)
         T = rep.T
     torch.cuda.synchronize()
     launches = ch.ch_kernel_launches() - launches0
@@ -775,11 +849,12 @@ def main():
                 "peak_basis": f"of measured: bf16_tflops (burst) x {ratio:.3f} nominal {kind.lower()}:bf16"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel_ms"] = kern_avg
-    # CrudeNN as a whole against HBM: algorithmic bytes = each set read once by the
-    # embedding pass, A and the rows b(a) of B read once by the crude distances,
-    # the k-wide binary32 embedding of both sets written once and read once, D written
+    # CrudeNN as a whole against HBM.  Algorithmic bytes (the measurement plan's
+    # per-point figure): each set read once for its keys, A and the rows b(a) of B
+    # read once by the crude distances, every point's L 8-byte keys written and read
+    # once, and 8 + 4 bytes of (b(a), D_a) per point of A.
     crude_ms = float(np.mean([s[0] for s in stages]))
-    crude_bytes = (NA + NB + 2 * NA) * DIM * elem_bytes() + (NA + NB) * PROJ * 4 * 2 + NA * 4
+    crude_bytes = (NA + NB + 2 * NA) * DIM * elem_bytes() + (NA + NB) * LEVELS * 16 + NA * 12
     hbm = peaks.get("hbm_gbs", 6800.0)
     crude_roof = {"bound": "hbm", "bytes": crude_bytes, "achieved": crude_bytes / (crude_ms / 1e3) / 1e9,
                   "peak": hbm, "unit": "GB/s", "frac": crude_bytes / (crude_ms / 1e3) / 1e9 / hbm,
@@ -788,15 +863,22 @@ def main():
 
     serving = serving_sample(ch, ctx, rank, args.serve_requests) if args.serve_requests > 0 else None
     cpu = None
+    parity = {"rel_vs_exact_per_step": [e / exact - 1.0 for e in etas],
+              "max_abs_rel_vs_exact": float(max(abs(e / exact - 1.0) for e in etas)),
+              "exact_mode": "canonical fp32, all pairs" if exact_mode == 0 else
+                            "tensor-core screen + canonical fp32 rerank, all of A"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        frac = 1 if CONFIG == "mid" else 32
-        sec, _ = cpu_oracle_step(A_np, B_np, T, 0, frac)
+        frac = 1 if CONFIG == "mid" else max(1, args.cpu_scan_fraction)
+        sec, eta_o, det = cpu_oracle_step(A_np, B_np, T, 0, frac, details=True)
         cpu = {"value": (NA + NB) / sec, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": ("one full oracle Chamfer-Estimate of the 100k x 100k workload (all T scans)"
                           if frac == 1 else
-                          f"oracle CrudeNN + weights + draws on the full sets (dequantised values), "
-                          f"exact scans of T/{frac} samples timed and scaled by {frac}")}
+                          f"oracle CrudeNN + weights + draws on the full sets (the stored values widened "
+                          f"to binary32), exact scans of the first {det['Ts']} of T = {T} samples, timed "
+                          f"and scaled by T/{det['Ts']}"),
+               "crude_weights_draws_s": det["t_crude_weights_draws_s"], "scans_s": det["t_scans_s"]}
+        parity.update(oracle_parity(ch, ctx, torch, A, B, scA, scB, cdt, T, det, eta_o, screen))
 
     if rank == 0:
         out = {
@@ -805,6 +887,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
             "config": workload_config(T),
             "accuracy": {"steps_within_10pct": int(sum(ok)), "steps": len(ok), "exact_ch": exact},
+            "parity": parity,
             "exact_gpu": {"mode": "canonical fp32, all pairs" if exact_mode == 0 else
                           "tensor-core screen + canonical fp32 rerank, all of A", "ms": float(np.mean(exact_ms_ev)), "pts_per_s": (NA + NB) / (np.mean(exact_ms_ev) / 1e3),
                           "speedup_estimate_vs_exact": float(np.mean(exact_ms_ev)) / (total_ms / args.steps)},

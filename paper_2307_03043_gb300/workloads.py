@@ -44,29 +44,55 @@ def gaussian_mixture(n_a: int, n_b: int, d: int, seed: int, clusters: int = 100,
     return A, B
 
 
+def _pool_map(fn, items):
+    """Runs fn over items on a thread pool (numpy's random fills and ufuncs
+    release the GIL); results in item order."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    items = list(items)
+    if len(items) <= 1:
+        return [fn(x) for x in items]
+    with ThreadPoolExecutor(max_workers=min(len(items), os.cpu_count() or 1)) as ex:
+        return list(ex.map(fn, items))
+
+
 def unit_mixture(n_a: int, n_b: int, d: int, seed: int, clusters: int = 1000,
-                 sigma: float = 0.3, chunk: int = 1 << 18):
+                 sigma: float = 0.3, chunk: int = 1 << 16):
     """Unit-norm mixture vectors (stand-in for DEEP1B / MS-Turing embeddings).
 
     1000 unit centres (normalised N(0, I)); point = normalise(centre +
     N(0, sigma^2 I / d)); A and B are independent draws of the same mixture.
+    Rows are drawn in chunks of `chunk`, each from its own PCG64 stream spawned
+    from `seed`, in binary32 and on all host threads, so a 1M x 384 set takes
+    seconds; the values depend only on (seed, sizes, chunk), never on the thread
+    count.
     """
     g = _rng(seed)
     C = g.standard_normal((clusters, d))
     C /= np.linalg.norm(C, axis=1, keepdims=True)
-    s = sigma / math.sqrt(d)
+    C32 = C.astype(np.float32)
+    s = np.float32(sigma / math.sqrt(d))
+    streams = np.random.SeedSequence([seed, 0x756E6974]).spawn(2)
 
-    def draw(n):
+    def draw(n, ss):
         out = np.empty((n, d), dtype=np.float32)
-        for lo in range(0, n, chunk):
-            hi = min(n, lo + chunk)
-            lab = g.integers(0, clusters, size=hi - lo)
-            x = C[lab] + s * g.standard_normal((hi - lo, d))
-            x /= np.linalg.norm(x, axis=1, keepdims=True)
-            out[lo:hi] = x
+        spans = [(lo, min(n, lo + chunk)) for lo in range(0, n, chunk)]
+        kids = ss.spawn(len(spans))
+
+        def fill(k):
+            lo, hi = spans[k]
+            gk = np.random.Generator(np.random.PCG64(kids[k]))
+            lab = gk.integers(0, clusters, size=hi - lo)
+            x = out[lo:hi]
+            gk.standard_normal(size=(hi - lo, d), dtype=np.float32, out=x)
+            x *= s
+            x += C32[lab]
+            x /= np.sqrt(np.einsum("ij,ij->i", x, x))[:, None]
+
+        _pool_map(fill, range(len(spans)))
         return out
 
-    return draw(n_a), draw(n_b)
+    return draw(n_a, streams[0]), draw(n_b, streams[1])
 
 
 def shape_surface(n_a: int, n_b: int, seed: int, noise: float = 0.01):
@@ -115,15 +141,37 @@ def log_uniform_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     return np.exp(g.uniform(math.log(lo), math.log(hi), size=count)).astype(np.int64)
 
 
-def to_bf16_bits(X: np.ndarray) -> np.ndarray:
-    """Round binary32 to bfloat16 (nearest even); returns the uint16 bit patterns."""
-    u = np.ascontiguousarray(X, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    r = ((u >> 16) & 1) + 0x7FFF
-    return ((u + r) >> 16).astype(np.uint16)
+def to_bf16_bits(X: np.ndarray, chunk: int = 1 << 22) -> np.ndarray:
+    """Round binary32 to bfloat16 (nearest even); returns the uint16 bit patterns.
+
+    Works on 32-bit words in chunks on all host threads; patterns whose rounding
+    increment would carry out of 32 bits (negative NaNs near 0xFFFFFFFF) wrap to
+    0, as a 64-bit sum truncated to 16 bits would.
+    """
+    u = np.ascontiguousarray(X, dtype=np.float32).reshape(-1).view(np.uint32)
+    out = np.empty(u.shape, dtype=np.uint16)
+
+    def conv(lo):
+        v = u[lo:lo + chunk]
+        r = ((v >> np.uint32(16)) & np.uint32(1)) + np.uint32(0x7FFF)
+        out[lo:lo + chunk] = ((v + r) >> np.uint32(16)).astype(np.uint16)
+
+    with np.errstate(over="ignore"):
+        _pool_map(conv, range(0, u.size, chunk))
+    return out.reshape(np.shape(X))
 
 
 def bf16_bits_to_f32(H: np.ndarray) -> np.ndarray:
-    return (np.asarray(H, dtype=np.uint32) << 16).view(np.float32)
+    H = np.asarray(H, dtype=np.uint16)
+    out = np.empty(H.shape, dtype=np.uint32)
+    flat_in, flat_out = H.reshape(-1), out.reshape(-1)
+    step = 1 << 22
+
+    def conv(lo):
+        flat_out[lo:lo + step] = flat_in[lo:lo + step].astype(np.uint32) << np.uint32(16)
+
+    _pool_map(conv, range(0, flat_in.size, step))
+    return out.view(np.float32)
 
 
 # E4M3 (OCP FP8, 'fn' variant: no infinities, max 448) value table
@@ -145,12 +193,7 @@ def _e4m3_table() -> np.ndarray:
 E4M3_VALUES = _e4m3_table()
 
 
-def to_fp8_e4m3(X: np.ndarray):
-    """Per-row scale = max|x| / 448, codes = nearest E4M3 of x / scale.
-
-    Returns (codes uint8 [n, d], scales float32 [n]).  Ties go to the even code.
-    """
-    X = np.asarray(X, dtype=np.float32)
+def _fp8_rows(X: np.ndarray):
     amax = np.abs(X).max(axis=1)
     scale = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
     Y = (X / scale[:, None]).astype(np.float64)
@@ -166,7 +209,33 @@ def to_fp8_e4m3(X: np.ndarray):
     return code, scale
 
 
-def fp8_dequant(codes: np.ndarray, scales: np.ndarray) -> np.ndarray:
+def to_fp8_e4m3(X: np.ndarray, chunk: int = 1 << 14):
+    """Per-row scale = max|x| / 448, codes = nearest E4M3 of x / scale.
+
+    Returns (codes uint8 [n, d], scales float32 [n]).  Ties go to the even code.
+    Rows are converted in chunks on all host threads (each row on its own).
+    """
+    X = np.asarray(X, dtype=np.float32)
+    n = X.shape[0]
+    code = np.empty(X.shape, dtype=np.uint8)
+    scale = np.empty(n, dtype=np.float32)
+
+    def conv(lo):
+        code[lo:lo + chunk], scale[lo:lo + chunk] = _fp8_rows(X[lo:lo + chunk])
+
+    _pool_map(conv, range(0, n, chunk))
+    return code, scale
+
+
+def fp8_dequant(codes: np.ndarray, scales: np.ndarray, chunk: int = 1 << 14) -> np.ndarray:
     """float32(E4M3 value) * row scale, one binary32 rounding."""
-    v = E4M3_VALUES[np.asarray(codes, dtype=np.uint8)].astype(np.float32)
-    return (v * np.asarray(scales, dtype=np.float32)[:, None]).astype(np.float32)
+    codes = np.asarray(codes, dtype=np.uint8)
+    scales = np.asarray(scales, dtype=np.float32)
+    table = E4M3_VALUES.astype(np.float32)
+    out = np.empty(codes.shape, dtype=np.float32)
+
+    def conv(lo):
+        out[lo:lo + chunk] = table[codes[lo:lo + chunk]] * scales[lo:lo + chunk, None]
+
+    _pool_map(conv, range(0, codes.shape[0], chunk))
+    return out

@@ -6,21 +6,26 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _run(extra_env=None):
+def _run(extra_env=None, config="batched"):
     env = dict(os.environ)
     env.update(extra_env or {})
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "batched",
-                        "--steps", "1", "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=600)
+    args = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0"]
+    if config is not None:
+        args += ["--config", config]
+    r = subprocess.run(args, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     return [ln for ln in r.stdout.splitlines() if ln.strip()]
 
 
-def test_reference_arm_prints_the_contract_line():
-    lines = _run()
+@pytest.mark.parametrize("config", ["batched", "mid", None])
+def test_reference_arm_prints_the_contract_line(config):
+    """None runs the default workload (1M x 1M, d = 384, bf16) on row slices."""
+    lines = _run(config=config)
     assert len(lines) == 1
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference"
@@ -31,6 +36,8 @@ def test_reference_arm_prints_the_contract_line():
     assert rec["steps"] == 1 and rec["warmup"] == 0 and rec["n_gpus"] == 1
     assert rec["higher_is_better"] is True and rec["vs_baseline"] is None
     assert rec["data"] == "synthetic" and "workload" in rec["config"]
+    if config is None:
+        assert rec["config"]["workload"].startswith("precision") and rec["dtype"] == "bf16"
     cpu = rec["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == rec["value"] and cpu["sample"]
     e2e = rec["e2e"]
