@@ -207,27 +207,31 @@ ch_status ch_crude_nn(ch_ctx* ctx, const ch_set* A, const ch_set* B, const ch_ha
  * fixed point), S = 62 - ceil(log2 nA) - e_M with max D_a < 2^e_M; each draw is
  * the first a whose inclusive prefix of w exceeds floor(u W / 2^128), u the
  * 128-bit Philox4x32-10 output of counter (l, 3, 0) under key sample_seed.
- * D: device float [nA], all >= 0.  idx: device int64 [T].  w: device uint64
- * [nA] or NULL.  W_total: host uint64 or NULL (non-NULL synchronises).
- * All D_a = 0 gives W = 0 and idx = -1. */
+ * D: device float [nA], all finite and >= 0.  idx: device int64 [T].  w:
+ * device uint64 [nA] or NULL.  W_total: host uint64 or NULL (non-NULL
+ * synchronises).  All D_a = 0 gives W = 0 and idx = -1; so does a D holding
+ * +Inf or NaN (outside the contract; no weight is then meaningful). */
 ch_status ch_sample(ch_ctx* ctx, const float* D, int64_t nA, int64_t T, uint64_t seed, int64_t* idx,
                     uint64_t* w, uint64_t* W_total);
 
 /* ch_sample without any device allocation (the paper has no counterpart; this
  * is a deployment variant).  For callers that cannot allocate device memory:
- * code that must stay allocation-free while a stream is captured, plug-ins
- * whose host application owns every device allocation, processes held to a
- * memory budget fixed at start-up.  It needs no context: the scratch lives in
- * one fixed ~8.4 MB device array inside the library, which every GPU that
- * loads the library holds until the process exits.
+ * plug-ins whose host application owns every device allocation, and processes
+ * held to a device-memory budget fixed at start-up, where a cudaMalloc could
+ * fail or be forbidden in the middle of a run.  It needs no context: the
+ * scratch lives in one fixed ~8.4 MB device array inside the library, which
+ * every GPU that loads the library holds until the process exits.
  * Same arguments and results as ch_sample, bit for bit, except: nA may be at
  * most 1,048,576 (larger returns CH_EINVAL before any work); w is required;
  * W_total is a DEVICE uint64 or NULL (no host synchronisation); stream is a
- * cudaStream_t (NULL = legacy default stream).  The first call on a device
- * looks up the array's device address with that device current, so make it
- * before any stream capture.  Every call shares the one array: calls whose
- * work overlaps on the GPU (other streams, other host threads) race; serialise
- * them, e.g. on one stream.  Returns CH_ECUDA if a launch fails. */
+ * cudaStream_t (NULL = legacy default stream).  The array's device address is
+ * looked up with the device current on the first call in each CUDA context
+ * (again after cudaDeviceReset), which also loads the library's device code on
+ * that device: make the first call on a device before any stream capture.
+ * Every call shares the one array and the call clears what must start at zero:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race; serialise them, e.g. on one stream.  Returns CH_ECUDA if a launch
+ * fails. */
 ch_status ch_sample_static(const float* D, int64_t nA, int64_t T, uint64_t seed, int64_t* idx, uint64_t* w,
                            uint64_t* W_total, void* stream);
 

@@ -338,6 +338,9 @@ struct SampleWork {
   uint64_t* W;           // [1]
   int32_t* S;            // [1]
 };
+// the weight scan works in blocks of kSampleScanTile points (256 threads x 4)
+constexpr int kSampleScanTile = 1024;
+constexpr int64_t sample_blocks_c(int64_t nA) { return (nA + kSampleScanTile - 1) / kSampleScanTile; }
 size_t sample_blocks(int64_t nA);
 // D[0..n) = 1 (the uniform-sampling baseline's weights)
 void launch_fill_ones(float* D, int64_t n, cudaStream_t s);

@@ -11,8 +11,9 @@ namespace chx {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;  // elements per block
+static_assert(kScanTile == kSampleScanTile, "the weight-scan tile is declared in common.cuh");
 
-size_t sample_blocks(int64_t nA) { return static_cast<size_t>(ceil_div(nA, kScanTile)); }
+size_t sample_blocks(int64_t nA) { return static_cast<size_t>(sample_blocks_c(nA)); }
 
 __global__ void k_max_d(const float* D, int64_t n, uint32_t* maxD) {
   pdl_entry();
@@ -24,9 +25,11 @@ __global__ void k_max_d(const float* D, int64_t n, uint32_t* maxD) {
   if ((threadIdx.x & 31) == 0) atomicMax(maxD, m);
 }
 
+// A non-finite maximum (D holding Inf or NaN, outside the contract) is treated
+// like an all-zero D: W = 0, every weight 0 and every draw -1.
 __device__ inline int weight_shift(const uint32_t* maxD, int64_t nA, bool* zero) {
   const float M = ord_dec(*maxD);
-  if (!(M > 0.0f)) {
+  if (!(M > 0.0f) || !(M <= 3.402823466e38f)) {
     *zero = true;
     return 0;
   }

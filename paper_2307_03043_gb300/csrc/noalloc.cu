@@ -1,14 +1,16 @@
 // noalloc.cu -- ch_sample_static: the sampling step (ch_sample) for callers
 // that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a stream
-// capture that must stay allocation-free, plug-ins whose host application owns
-// every device allocation, or processes working under a fixed memory budget
-// set before they start.  ch_sample_static does the same work as ch_sample
+// Some callers cannot call cudaMalloc at all: plug-ins whose host application
+// owns every device allocation, or processes working under a device-memory
+// budget fixed before they start, where an allocation in the middle of a run
+// could fail or is forbidden.  ch_sample_static does the same work as ch_sample
 // without allocating anything: its scratch (the running maximum, the weight
 // shift, the total, per-block sums and the inclusive prefix of the weights)
 // lives in one file-scope __device__ array of fixed size, which every GPU that
 // loads this library holds until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -17,7 +19,7 @@ namespace {
 
 // largest nA the static scratch serves
 constexpr int64_t kStaticMaxA = int64_t(1) << 20;
-constexpr size_t kStaticBlocks = (kStaticMaxA + 1023) / 1024;  // weight-scan blocks of 1024 elements
+constexpr size_t kStaticBlocks = static_cast<size_t>(chx::sample_blocks_c(kStaticMaxA));  // weight-scan blocks
 
 // layout inside the array (each part 256-byte aligned)
 constexpr size_t kOffMax = 0;                                   // uint32 running max (ordered encoding)
@@ -28,26 +30,42 @@ constexpr size_t kOffPrefix = kOffBlocks + ((kStaticBlocks * 8 + 255) & ~size_t(
 constexpr size_t kStaticBytes = kOffPrefix + size_t(kStaticMaxA) * 8;                    // ~8.4 MB
 
 static __device__ __align__(256) unsigned char g_sample_scratch[kStaticBytes];
+static_assert(kOffPrefix >= kOffBlocks + kStaticBlocks * sizeof(uint64_t),
+              "the block-sum region holds one entry per weight-scan block of the largest nA");
 
 // Host code may not use g_sample_scratch's name as a device address: its
-// device address is looked up once per device, with that device current.
+// device address is looked up with the device current, once per CUDA context.
+// The cache is keyed on the context's unique id, so after cudaDeviceReset (a new
+// primary context, the module loaded again) the address is looked up afresh.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
+struct Cached {
+  unsigned long long ctx_id;
+  void* addr;
+};
+Cached g_addr[kMaxDevices] = {};
+
+bool current_ctx_id(unsigned long long* id) {
+  CUcontext c = nullptr;
+  return cuCtxGetCurrent(&c) == CUDA_SUCCESS && c && cuCtxGetId(c, id) == CUDA_SUCCESS;
+}
 
 ch_status scratch_for_current_device(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CH_ECUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
+  unsigned long long id = 0;
+  const bool have_ctx = current_ctx_id(&id);
+  if (!have_ctx || !g_addr[dev].addr || g_addr[dev].ctx_id != id) {
+    void* p = nullptr;  // the look-up also makes the device's primary context current
     if (cudaGetSymbolAddress(&p, g_sample_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return CH_ECUDA;
     }
-    g_addr[dev] = p;
+    if (!current_ctx_id(&id)) return CH_ECUDA;
+    g_addr[dev] = Cached{id, p};
   }
-  *out = static_cast<unsigned char*>(g_addr[dev]);
+  *out = static_cast<unsigned char*>(g_addr[dev].addr);
   return CH_OK;
 }
 

@@ -1,6 +1,7 @@
 """ch_sample_static -- the sampling entry point for callers that cannot allocate
-device memory (e.g. inside a captured stream, or under a host application that
-owns every device allocation) -- must return exactly what ch_sample returns.
+device memory (a plug-in whose host application owns every device allocation,
+a process held to a fixed device-memory budget) -- must return exactly what
+ch_sample returns.
 
 Collected last on purpose, so a run that stops at the first failure has
 already run everything else.  Passes alone in a fresh process and after the
@@ -9,6 +10,7 @@ other tests (the first call on the device does the one-time address look-up).
 import numpy as np
 import pytest
 
+import oracle
 from paper_2307_03043_gb300 import binding as ch
 
 torch = pytest.importorskip("torch")
@@ -56,6 +58,26 @@ def test_static_sampling_matches_ch_sample_twice(ctx):
             assert sW == rW
             assert np.array_equal(si, ri)
             assert np.array_equal(sw, rw)
+
+
+def test_static_sampling_at_the_largest_size_matches_the_oracle(ctx):
+    """nA = 1,048,576, the documented maximum: the last weight-scan block and the
+    prefix are full.  Weights, W and the draws equal the oracle's (Fig. 1 steps
+    2-3) and ch_sample's, on two calls in a row."""
+    n = 1 << 20
+    g = np.random.default_rng(5)
+    Dn = (g.random(n) * g.random(n) ** 4).astype(np.float32)
+    Dn[g.integers(0, n, 1000)] = 0.0
+    w_o, prefix_o, W_o, _ = oracle.weights(Dn)
+    T = 5000
+    idx_o = oracle.draws(prefix_o, W_o, T, 21)
+    D = torch.from_numpy(Dn).cuda()
+    ri, rw, rW = _reference(ctx, D, T, 21)
+    for _ in range(2):
+        si, sw, sW = _static(D, T, 21)
+        assert sW == rW == W_o
+        assert np.array_equal(sw.view(np.uint64), w_o) and np.array_equal(rw.view(np.uint64), w_o)
+        assert np.array_equal(si, idx_o) and np.array_equal(ri, idx_o)
 
 
 def test_static_sampling_limits(ctx):
