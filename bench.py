@@ -133,7 +133,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=200, help="0 skips the serving sample")
     ap.add_argument("--config", default=DEFAULT_CONFIG, choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-scan-fraction", type=int, default=32,
+    ap.add_argument("--cpu-scan-fraction", type=int, default=8,
                     help="the CPU baseline runs T/f of the sampled scans and scales their time by f")
     return ap.parse_args()
 
