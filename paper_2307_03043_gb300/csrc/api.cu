@@ -21,11 +21,6 @@ namespace chx {
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status,
-                         cudaStream_t s);
-void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
-                        uint8_t* level, cudaStream_t s);
-
 void Arena::reserve(size_t bytes) {
   if (bytes <= cap) return;
   if (borrowed) throw Err{CH_ENOMEM, "lent workspace smaller than the call needs"};
@@ -223,6 +218,11 @@ struct TablePlan {
   uint32_t log_cap;
   int per_group;
 };
+// A scale group after the first runs in reverse (the unresolved a's buckets into
+// small tables, B streamed past them once) once at most this many points of A
+// are left: 1M x 384 unit mixture, 46k points left after the first two scales.
+constexpr int64_t kRevMax = int64_t(1) << 16;
+
 static TablePlan table_plan(int64_t nB, int L) {
   TablePlan p;
   p.log_cap = static_cast<uint32_t>(ceil_log2_i64(std::max<int64_t>(2 * nB, 1024)));
@@ -237,6 +237,18 @@ struct CrudeBufs {
   ScaleTables tab;
   int32_t* e_top;
   ulonglong2* slots;   // CH_GROUP_HASH: bucket tables of one scale group
+  // CH_GROUP_HASH scale-group control: left[0] = points of A no scale group has
+  // resolved yet, left[1 + g] = length of group g's reverse list; mode[g]
+  unsigned long long* left;
+  int32_t* mode;
+  int groups;
+  // reverse groups (g >= 1, once at most rev_max points are left): small tables
+  // [groups - 1][per_group][2^rev_log_cap], the list and its slots
+  unsigned long long rev_max;
+  uint32_t rev_log_cap;
+  ulonglong2* rev;
+  int64_t* lst;
+  uint32_t* lst_pos;
   TablePlan plan;
   uint64_t *keysA, *keysB;  // CH_GROUP_SORT and k x W: keys [L][n] and the sort's scratch
   void* sort_work;
@@ -280,6 +292,24 @@ static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_p
   }
   cb->plan = table_plan(B->n, nl);
   cb->slots = lay.template take<ulonglong2>(size_t(cb->plan.per_group) << cb->plan.log_cap);
+  cb->groups = (nl + cb->plan.per_group - 1) / cb->plan.per_group;
+  cb->left = lay.template take<unsigned long long>(1 + cb->groups);
+  cb->mode = lay.template take<int32_t>(cb->groups);
+  // reverse groups need rows of at most 32 hashed values, at most kRevGroupMax
+  // scales per group and more than one group
+  cb->rev_max = (cb->groups > 1 && dd <= 32 && cb->plan.per_group <= kRevGroupMax)
+                    ? static_cast<unsigned long long>(std::min<int64_t>(kRevMax, A->n))
+                    : 0;
+  cb->rev = nullptr;
+  cb->lst = nullptr;
+  cb->lst_pos = nullptr;
+  cb->rev_log_cap = 0;
+  if (cb->rev_max) {
+    cb->rev_log_cap = static_cast<uint32_t>(ceil_log2_i64(std::max<int64_t>(2 * int64_t(cb->rev_max), 1024)));
+    cb->rev = lay.template take<ulonglong2>((size_t(cb->groups - 1) * cb->plan.per_group) << cb->rev_log_cap);
+    cb->lst = lay.template take<int64_t>(cb->rev_max);
+    cb->lst_pos = lay.template take<uint32_t>(size_t(cb->rev_max) * cb->plan.per_group);
+  }
   cb->keysA = cb->keysB = nullptr;
   cb->sort_work = nullptr;
 }
@@ -340,15 +370,43 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
   const size_t cap = size_t(1) << cb->plan.log_cap;
   const size_t group_bytes0 = size_t(std::min(cb->plan.per_group, L)) * cap * sizeof(ulonglong2);
   const bool fold = group_bytes0 <= (size_t(48) << 20) && L <= cb->plan.per_group;
+  // the launch that builds the scale tables also clears the single small group's
+  // tables, or else the reverse groups' small tables
+  void* zero = fold ? static_cast<void*>(cb->slots) : static_cast<void*>(cb->rev);
+  const size_t zero_bytes = fold ? group_bytes0
+                                 : cb->rev ? ((size_t(cb->groups - 1) * cb->plan.per_group) << cb->rev_log_cap) * 16 : 0;
   launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp, hp->hash_seed,
-                      cb->tab, cb->e_top, status, s, fold ? cb->slots : nullptr, fold ? group_bytes0 : 0,
-                      c->sm_count);
-  for (int L0 = 0; L0 < L; L0 += cb->plan.per_group) {
+                      cb->tab, cb->e_top, status, s, zero, zero_bytes, c->sm_count, cb->left, A->n, cb->groups);
+  // Each group's kernels follow its mode (see HashTable): groups after the one
+  // that resolves the last point of A return at once -- on clustered data the
+  // coarse scales are rarely reached (1M x 384 unit mixture: no point past scale
+  // 4 of 10) -- and once few points are left a group runs in reverse.
+  for (int g = 0, L0 = 0; L0 < L; ++g, L0 += cb->plan.per_group) {
     const int nl = std::min(cb->plan.per_group, L - L0);
-    if (!fold) CHX_CUDA(cudaMemsetAsync(cb->slots, 0, size_t(nl) * cap * sizeof(ulonglong2), s));
-    HashTable h{cb->slots, cb->plan.log_cap};
-    launch_group_insert(cb->hB.src, L, L0, nl, cb->tab, h, status, s);
-    launch_group_probe(cb->hA.src, L, L0, nl, cb->tab, h, bidx, level, s);
+    HashTable h{};
+    h.slots = cb->slots;
+    h.log_cap = cb->plan.log_cap;
+    h.left = cb->left;
+    h.mode = cb->mode;
+    h.group = g;
+    h.first = 1;
+    if (g > 0 && cb->rev_max) {
+      h.rev_max = cb->rev_max;
+      h.rev_log_cap = cb->rev_log_cap;
+      h.rev = cb->rev + ((size_t(g - 1) * cb->plan.per_group) << cb->rev_log_cap);
+      h.lst = cb->lst;
+      h.lst_pos = cb->lst_pos;
+      h.lst_n = cb->left + 1 + g;
+      launch_group_reverse(cb->hA.src, cb->hB.src, L, L0, nl, cb->tab, h, bidx, level, status, c->sm_count, s);
+      h.first = 0;
+    }
+    if (!fold) {
+      launch_table_clear(h, nl, c->sm_count, s);
+      h.first = 0;
+    }
+    launch_group_insert(cb->hB.src, L, L0, nl, cb->tab, h, status, c->sm_count, s);
+    h.first = 0;
+    launch_group_probe(cb->hA.src, L, L0, nl, cb->tab, h, bidx, level, c->sm_count, s);
   }
   launch_crude_dist(A, B, hp->metric, bidx, D, maxD, c->sm_count, s);
 }

@@ -281,10 +281,13 @@ struct ScaleTables {
 
 // computes e_top from the two boxes, each given as partial boxes [parts][2][dd]
 // (or uses top_exp), then fills the tables; with zero (16-byte aligned), further
-// blocks of the same launch set zero_bytes (a multiple of 16) there to zero
+// blocks of the same launch set zero_bytes (a multiple of 16) there to zero; with
+// left, left[0] = n_left (the count of points of A not yet resolved by a scale)
+// and left[1 .. n_zero_words] = 0
 void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
                          int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
-                         cudaStream_t s, void* zero = nullptr, size_t zero_bytes = 0, int sm_count = 1);
+                         cudaStream_t s, void* zero = nullptr, size_t zero_bytes = 0, int sm_count = 1,
+                         unsigned long long* left = nullptr, int64_t n_left = 0, int n_zero_words = 0);
 
 // hashed-space source of a set: DT-typed rows (l1) or the binary32 embedding (l2)
 struct HashSrc {
@@ -296,15 +299,41 @@ struct HashSrc {
 };
 
 struct HashTable {
-  ulonglong2* slots;  // [L][cap] : x = key (0 = empty), y = ~min b index
+  ulonglong2* slots;  // [nl][cap] : x = key (0 = empty), y = ~min b index
   uint32_t log_cap;
+  // Scale-group control (left = NULL: none; every group runs forward).
+  // left: points of A that no scale so far resolved.  The group's first kernel
+  // (first != 0) turns it into the group's mode, mode[group], which its later
+  // kernels read: nothing left (skip), more than rev_max left (forward: B into
+  // the tables above), else reverse (below).
+  unsigned long long* left;
+  int32_t* mode;
+  int group;
+  int first;
+  unsigned long long rev_max;  // 0: no reverse groups
+  // reverse groups: small tables [nl][2^rev_log_cap] of the unresolved a's
+  // buckets (cleared before the groups run), the list of those a, each list
+  // entry's slot per scale [rev_max][nl], and the list's length (zeroed before)
+  ulonglong2* rev;
+  uint32_t rev_log_cap;
+  int64_t* lst;
+  uint32_t* lst_pos;
+  unsigned long long* lst_n;
 };
 
+// reverse groups hold at most this many scales
+constexpr int kRevGroupMax = 16;
+
+// zeroes the tables of nl scales (forward groups only)
+void launch_table_clear(HashTable h, int nl, int sm_count, cudaStream_t s);
 // bucket tables of the scales [L0, L0+nl) (one table of 2^log_cap slots per scale)
-void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status,
+void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status, int sm_count,
                          cudaStream_t s);
 void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
-                        uint8_t* level, cudaStream_t s);
+                        uint8_t* level, int sm_count, cudaStream_t s);
+// the reverse form of a scale group (its three kernels return unless the group's mode is reverse)
+void launch_group_reverse(HashSrc A, HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
+                          uint8_t* level, uint32_t* status, int sm_count, cudaStream_t s);
 void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStream_t s);
 // SimHash keys [L][n] of embedded rows Y [n][K] (K <= 64)
 void launch_simhash_keys(const float* Y, int64_t n, int K, int L, uint64_t seed, uint64_t* keys, cudaStream_t s);

@@ -513,6 +513,24 @@ __device__ __forceinline__ float pt_xreduce(float (&v)[KP], int lane) {
   return r;
 }
 
+// Packed binary32 pairs for the projection's FMA chains: fma.rn.f32x2 rounds each
+// half exactly as fmaf does (IEEE fused multiply-add, round to nearest even), at
+// one issue slot per two chains.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+// c = a * b + c, per half
+__device__ __forceinline__ void f2_fma(uint64_t& c, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
+}
+
 template <int DT, int KP>
 __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
     k_project_tma(const __grid_constant__ CUtensorMap map, const void* X, const float* scales, int64_t n, int d,
@@ -548,10 +566,13 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
   // producer (lane 0) runs two items ahead of the consumers
   int64_t pt = gw;  // producer's next tile and slice
   int psl = 0;
+  // the set streams through once: its lines go first, so that the embeddings
+  // and bucket tables that follow keep their place in L2
+  const uint64_t pol = l2_evict_first_policy();
   auto issue = [&](int64_t it) {  // lane 0: item it -> stage it & 1
     uint64_t* b = &bar[it & 1];
     mbar_expect_tx(b, kPTStage);
-    tma_load_2d(stage + (it & 1) * kPTStage, &map, psl * kPTBox, static_cast<int>(pt * kPTRows), b);
+    tma_load_2d_hint(stage + (it & 1) * kPTStage, &map, psl * kPTBox, static_cast<int>(pt * kPTRows), b, pol);
     if (++psl == slices) {
       psl = 0;
       pt += stride;
@@ -566,13 +587,12 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
   for (int t = threadIdx.x; t < d * KP; t += blockDim.x) sG[t] = gauss_entry(seed, k, t / KP, t % KP);
   __syncthreads();
 
-  float acc[2][KP], sq[2];
+  // acc2[r][h] holds outputs 2h and 2h + 1 of row r; sq2 holds |x|^2 of rows 0 and 1
+  uint64_t acc2[2][KP / 2], sq2 = 0;
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    sq[r] = 0.0f;
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
-    for (int i = 0; i < KP; ++i) acc[r][i] = 0.0f;
-  }
+    for (int h = 0; h < KP / 2; ++h) acc2[r][h] = 0;
   float run_lo = __int_as_float(0x7F800000), run_hi = __int_as_float(0xFF800000);
   bool ok = true;
   int64_t it = 0;
@@ -620,18 +640,17 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
 #pragma unroll
       for (int e = 0; e < PER; ++e) {
         if (e < lim) {
-#pragma unroll
-          for (int r = 0; r < 2; ++r) sq[r] = fmaf(xv[r][e], xv[r][e], sq[r]);
-          const float4* g4 = reinterpret_cast<const float4*>(sG + (j0 + c * PER + e) * KP);
+          const uint64_t xx = f2_pack(xv[0][e], xv[1][e]);
+          f2_fma(sq2, xx, xx);
+          const uint64_t xb[2] = {f2_pack(xv[0][e], xv[0][e]), f2_pack(xv[1][e], xv[1][e])};
+          const ulonglong2* g2 = reinterpret_cast<const ulonglong2*>(sG + (j0 + c * PER + e) * KP);
 #pragma unroll
           for (int i4 = 0; i4 < KP / 4; ++i4) {
-            const float4 gv = g4[i4];
+            const ulonglong2 gv = g2[i4];  // outputs 4 i4 .. 4 i4 + 3 of G's row j
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-              acc[r][4 * i4 + 0] = __fmaf_rn(gv.x, xv[r][e], acc[r][4 * i4 + 0]);
-              acc[r][4 * i4 + 1] = __fmaf_rn(gv.y, xv[r][e], acc[r][4 * i4 + 1]);
-              acc[r][4 * i4 + 2] = __fmaf_rn(gv.z, xv[r][e], acc[r][4 * i4 + 2]);
-              acc[r][4 * i4 + 3] = __fmaf_rn(gv.w, xv[r][e], acc[r][4 * i4 + 3]);
+              f2_fma(acc2[r][2 * i4], gv.x, xb[r]);
+              f2_fma(acc2[r][2 * i4 + 1], gv.y, xb[r]);
             }
           }
         }
@@ -658,6 +677,20 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
       issue(it + 2);
     }
     if (sl == slices - 1) {  // the tile's rows are complete
+      float acc[2][KP], sq[2];
+      {
+        const float2 q = f2_unpack(sq2);
+        sq[0] = q.x;
+        sq[1] = q.y;
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int h = 0; h < KP / 2; ++h) {
+          const float2 q = f2_unpack(acc2[r][h]);
+          acc[r][2 * h] = q.x;
+          acc[r][2 * h + 1] = q.y;
+        }
       float tlo[KP], thi[KP];
 #pragma unroll
       for (int i = 0; i < KP; ++i) {
@@ -691,9 +724,9 @@ __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)
           }
         }
 #pragma unroll
-        for (int i = 0; i < KP; ++i) acc[r][i] = 0.0f;
-        sq[r] = 0.0f;
+        for (int h = 0; h < KP / 2; ++h) acc2[r][h] = 0;
       }
+      sq2 = 0;
       run_lo = fminf(run_lo, pt_xreduce<KP, true>(tlo, lane));
       run_hi = fmaxf(run_hi, pt_xreduce<KP, false>(thi, lane));
     }
@@ -858,8 +891,11 @@ int launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* bo
 // K_j = Philox(j, 0, 4, 0).(y:x) | 1; salt_e = mix64((uint32)e ^ seed).
 __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
                                int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
-                               uint4* zero, int64_t zero16) {
+                               uint4* zero, int64_t zero16, unsigned long long* left, int64_t n_left,
+                               int n_zero_words) {
   pdl_entry();
+  if (left && blockIdx.x == 0 && threadIdx.x <= n_zero_words)
+    left[threadIdx.x] = threadIdx.x == 0 ? static_cast<unsigned long long>(n_left) : 0ull;
   if (blockIdx.x > 0) {  // the other blocks clear the bucket tables meanwhile
     const uint4 z = make_uint4(0, 0, 0, 0);
     for (int64_t i = int64_t(blockIdx.x - 1) * blockDim.x + threadIdx.x; i < zero16;
@@ -945,13 +981,15 @@ __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t*
 
 void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
                          int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
-                         cudaStream_t s, void* zero, size_t zero_bytes, int sm_count) {
+                         cudaStream_t s, void* zero, size_t zero_bytes, int sm_count, unsigned long long* left,
+                         int64_t n_left, int n_zero_words) {
+  CHX_CHECK(n_zero_words < 1024, CH_EINVAL, "too many scale groups");
   CHX_CHECK((partsA <= 1 && partsB <= 1) || dd <= kMaxProj, CH_EINVAL, "partial boxes need dd <= 64");
   // 1024 threads: the partial-box loads of all blocks are in flight at once
   const int64_t zero16 = zero ? static_cast<int64_t>(zero_bytes / 16) : 0;
   const int zblocks = zero16 ? static_cast<int>(std::min<int64_t>(ceil_div(zero16, 1024 * 4), 2 * sm_count)) : 0;
   launch_k(k_scale_tables, 1 + zblocks, 1024, 0, s, boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out,
-           status, static_cast<uint4*>(zero), zero16);
+           status, static_cast<uint4*>(zero), zero16, left, n_left, n_zero_words);
   launch_check("scale_tables");
 }
 
@@ -1010,6 +1048,123 @@ __global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* 
   }
 }
 
+// Vector form for rows of a multiple of 16 bytes on 16-byte aligned bases (A and B
+// of one storage type): rows move in 16-byte chunks of C = 16 / ES coordinates.
+// A row group of LPR = 32 / C lanes reads one a and its b(a); lane l of the group
+// owns partials p_{lC} .. p_{lC + C - 1} and takes chunks m = l, l + LPR, ... in
+// increasing m, so partial r still collects the coordinates j = r (mod 32) in
+// increasing j.  The tree p_q += p_{q+s} for s = 16 .. 1 runs by shuffles inside
+// the group for s >= C and in registers below: the same sums, in the same order,
+// as the lane-per-partial form.
+template <int DT>
+__device__ __forceinline__ void chunk_vals(const uint4 raw, float sc, float (&v)[16 / (DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1)]) {
+  if constexpr (DT == CH_F32) {
+    v[0] = __uint_as_float(raw.x);
+    v[1] = __uint_as_float(raw.y);
+    v[2] = __uint_as_float(raw.z);
+    v[3] = __uint_as_float(raw.w);
+  } else if constexpr (DT == CH_BF16) {
+    const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      v[2 * e] = __uint_as_float(w4[e] << 16);
+      v[2 * e + 1] = __uint_as_float(w4[e] & 0xFFFF0000u);
+    }
+  } else {
+    const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __fmul_rn(e4m3_to_f32(static_cast<uint8_t>(w4[e / 4] >> (8 * (e % 4)))), sc);
+  }
+}
+
+template <int DT, int METRIC>
+__global__ void __launch_bounds__(256) k_crude_dist_v(const void* A, const float* scA, int64_t nA, const void* B,
+                                                      const float* scB, int d, const int64_t* bidx, float* D,
+                                                      uint32_t* maxD) {
+  pdl_entry();
+  constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
+  constexpr int C = 16 / ES;    // coordinates per chunk
+  constexpr int LPR = 32 / C;   // lanes per row
+  constexpr int RPW = 32 / LPR; // rows per warp
+  constexpr int U = 4;          // chunks of A and of B in flight per lane
+  __shared__ uint32_t s_max[8];
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % LPR, grp = lane / LPR;
+  const int chunks = d / C;
+  const size_t rowq = size_t(d) / C;  // 16-byte words per row
+  const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t wstep = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  uint32_t mx = 0;
+  // every lane runs the same number of rounds (the shuffles need the whole warp)
+  for (int64_t a0 = warp0 * RPW; a0 < nA; a0 += wstep * RPW) {
+    const int64_t a = a0 + grp;
+    const bool live = a < nA;
+    float p[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) p[i] = 0.0f;
+    if (live) {
+      const int64_t b = bidx[a];
+      const uint4* ra = static_cast<const uint4*>(A) + size_t(a) * rowq;
+      const uint4* rb = static_cast<const uint4*>(B) + size_t(b) * rowq;
+      const float sa = DT == CH_FP8E4M3 ? scA[a] : 1.0f;
+      const float sb = DT == CH_FP8E4M3 ? scB[b] : 1.0f;
+      for (int m0 = sub; m0 < chunks; m0 += LPR * U) {
+        uint4 qa[U], qb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int m = m0 + u * LPR;
+          if (m < chunks) {
+            qa[u] = __ldcs(ra + m);  // A is read once: evict first
+            qb[u] = rb[m];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (m0 + u * LPR < chunks) {
+            float va[C], vb[C];
+            chunk_vals<DT>(qa[u], sa, va);
+            chunk_vals<DT>(qb[u], sb, vb);
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+              const float t = __fsub_rn(va[i], vb[i]);
+              if (METRIC == CH_L1)
+                p[i] = __fadd_rn(p[i], fabsf(t));
+              else
+                p[i] = __fmaf_rn(t, t, p[i]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 16; s >= C; s >>= 1) {
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const float o = __shfl_down_sync(0xFFFFFFFFu, p[i], s / C, LPR);
+        p[i] = __fadd_rn(p[i], o);
+      }
+    }
+#pragma unroll
+    for (int s = C / 2; s >= 1; s >>= 1)
+#pragma unroll
+      for (int i = 0; i < s; ++i) p[i] = __fadd_rn(p[i], p[i + s]);
+    if (live && sub == 0) {
+      const float v = (METRIC == CH_L1) ? p[0] : __fsqrt_rn(p[0]);
+      D[a] = v;
+      mx = max(mx, ord_enc(v));
+    }
+  }
+  if (!maxD) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  if (lane == 0) s_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) mx = max(mx, s_max[w]);
+    if (mx) atomicMax(maxD, mx);
+  }
+}
+
 template <int DTA, int DTB>
 static void crude_dist_2(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D,
                          uint32_t* maxD, int G, int grid, cudaStream_t s) {
@@ -1035,6 +1190,30 @@ void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64
                        int sm_count, cudaStream_t s) {
   if (maxD) CHX_CUDA(cudaMemsetAsync(maxD, 0, sizeof(uint32_t), s));
   if (A->n == 0) return;
+  const size_t es = elem_size(A->dtype);
+  if (A->dtype == B->dtype && (size_t(A->d) * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(B->data) & 15) == 0) {
+    // rows per warp: 32 / (lanes per row) = 16 / es coordinates... one row group per 32 / (16 / es) lanes
+    const int64_t rpw = int64_t(16 / es);
+    const int grid = static_cast<int>(std::min<int64_t>(ceil_div(ceil_div(A->n, rpw) * 32, 256), int64_t(sm_count) * 4));
+#define CHX_CDV(DTV)                                                                                              \
+  do {                                                                                                            \
+    if (metric == CH_L1)                                                                                          \
+      launch_k(k_crude_dist_v<DTV, CH_L1>, grid, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, A->d,  \
+               bidx, D, maxD);                                                                                    \
+    else                                                                                                          \
+      launch_k(k_crude_dist_v<DTV, CH_L2>, grid, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, A->d,  \
+               bidx, D, maxD);                                                                                    \
+  } while (0)
+    switch (A->dtype) {
+      case CH_F32: CHX_CDV(CH_F32); break;
+      case CH_BF16: CHX_CDV(CH_BF16); break;
+      default: CHX_CDV(CH_FP8E4M3); break;
+    }
+#undef CHX_CDV
+    launch_check("crude_dist");
+    return;
+  }
   int G = 1;
   while (G < A->d && G < 32) G <<= 1;
   // 8 resident blocks of 256 per SM; each block merges its maximum once

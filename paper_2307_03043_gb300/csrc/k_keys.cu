@@ -10,7 +10,9 @@
 // Bucket tables: one open-addressing table (linear probing, 16-byte slots
 // {key, ~min b}) per scale; B inserts, then each a probes its scales in
 // increasing order and stops at the first bucket that holds a b.
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -31,7 +33,8 @@ __device__ inline void load_row(const HashSrc& src, int64_t r, float (&y)[W]) {
       const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(src.base) + r * W);
 #pragma unroll
       for (int q = 0; q < W / 4; ++q) {
-        const float4 v = p[q];
+        // evict-first: the rows stream past the bucket tables, which are to stay in L2
+        const float4 v = __ldcs(p + q);
         y[4 * q] = v.x;
         y[4 * q + 1] = v.y;
         y[4 * q + 2] = v.z;
@@ -148,29 +151,76 @@ __device__ inline int64_t table_find(const ulonglong2* tab, uint32_t log_cap, ui
   return -1;
 }
 
+// ------------------------------------------------------------------ scale groups
+// The scales run in groups whose tables stay L2-resident.  The first kernel a
+// group launches reads *h.left (the points of A no finer scale resolved; it does
+// not change while that kernel runs, so all its blocks agree) and records the
+// group's mode for the group's later kernels:
+//   GM_SKIP  nothing left: every launch of the group returns at once;
+//   GM_FWD   B's points go into tables sized for B, the unresolved a probe them;
+//   GM_REV   few points left (*left <= h.rev_max): the unresolved a's buckets go
+//            into small tables, B streams past them once, marking each bucket
+//            with its smallest b, and the a read their buckets back.
+// Both forward and reverse give, for each a, the first scale of the group at
+// which some b shares its bucket and the smallest such b (Fig. 2, step 3).
+enum : int32_t { GM_SKIP = 0, GM_FWD = 1, GM_REV = 2 };
+
+__device__ __forceinline__ int group_mode(const HashTable& h) {
+  if (!h.left) return GM_FWD;
+  if (h.first) {
+    const unsigned long long v = *h.left;
+    const int m = v == 0 ? GM_SKIP : (v <= h.rev_max ? GM_REV : GM_FWD);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) h.mode[h.group] = m;
+    return m;
+  }
+  return h.mode[h.group];
+}
+
+// takes n resolved points off *h.left: one atomic per block (every thread of the
+// block calls this)
+__device__ __forceinline__ void take_off_left(const HashTable& h, unsigned n) {
+  __shared__ unsigned s_n;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  const unsigned w = __reduce_add_sync(0xFFFFFFFFu, n);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_n, w);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_n) atomicAdd(h.left, 0ull - static_cast<unsigned long long>(s_n));
+}
+
+__global__ void k_table_clear(HashTable h, int64_t n16) {
+  pdl_entry();
+  if (group_mode(h) != GM_FWD) return;
+  uint4* z = reinterpret_cast<uint4*>(h.slots);
+  const uint4 zero = make_uint4(0, 0, 0, 0);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n16; i += int64_t(gridDim.x) * blockDim.x)
+    z[i] = zero;
+}
+
 // Narrow rows: one thread per (point, scale) (blockIdx.y = scale), so the
-// scales' insert round trips overlap instead of forming one chain per point.
+// scales' insert round trips overlap instead of forming one chain per point;
+// grid-stride over the points, so that a skipped group costs a short launch.
 template <int DT, int W>
 __global__ void __launch_bounds__(128) k_table_insert_ps(HashSrc src, int L, int L0, int nl, ScaleTables t,
                                                          HashTable h, uint32_t* status) {
   pdl_entry();
-  const int l = blockIdx.y;  // scale; blocks run scale by scale, as the flat order t = l * n + r did
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= src.n) return;
-  float y[W];
-  load_row<DT, W>(src, r, y);
+  if (group_mode(h) != GM_FWD) return;
+  const int l = blockIdx.y;
   const size_t cap = size_t(1) << h.log_cap;
-  table_insert(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t), r, status);
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
+    float y[W];
+    load_row<DT, W>(src, r, y);
+    table_insert(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t), r, status);
+  }
 }
 
 template <int DT>
 __global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
                                                       uint32_t* status) {
   pdl_entry();
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= src.n) return;
+  if (group_mode(h) != GM_FWD) return;
   const size_t cap = size_t(1) << h.log_cap;
-  {
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
     for (int b0 = 0; b0 < nl; b0 += kLevelBlock) {
       uint64_t key[kLevelBlock];
       const int nb = min(kLevelBlock, nl - b0);
@@ -182,49 +232,148 @@ __global__ void __launch_bounds__(128) k_table_insert(HashSrc src, int L, int L0
   }
 }
 
+// Reverse group, step 1: the unresolved a's (level = L) buckets at the group's
+// scales go into the small tables (one per scale), with no b yet (y = 0).
+template <int DT, int W>
+__global__ void __launch_bounds__(128) k_rev_insert(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
+                                                    const uint8_t* level, uint32_t* status) {
+  pdl_entry();
+  if (group_mode(h) != GM_REV) return;
+  const uint32_t rcap = 1u << h.rev_log_cap;
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
+    if (level[r] < L) continue;
+    float y[W];
+    load_row<DT, W>(src, r, y);
+    for (int l = 0; l < nl; ++l) {
+      ulonglong2* tab = h.rev + size_t(l) * rcap;
+      const uint64_t key = reg_key(y, src.dd, L, L0 + l, t);
+      uint32_t pos = slot_home(key, h.rev_log_cap);
+      uint32_t it = 0;
+      for (; it < rcap; ++it) {
+        const unsigned long long cur = atomicCAS(&tab[pos].x, 0ull, static_cast<unsigned long long>(key));
+        if (cur == 0ull || cur == key) break;
+        pos = (pos + 1) & (rcap - 1);
+      }
+      if (it == rcap) atomicOr(status, ST_TABLE_FULL);
+    }
+  }
+}
+
+// Reverse group, step 2: every b looks its buckets up in the small tables and
+// marks the ones present with its index (smallest b wins); one thread per
+// (b, scale), as for the forward insert.
+template <int DT, int W>
+__global__ void __launch_bounds__(128) k_rev_stream(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h) {
+  pdl_entry();
+  if (group_mode(h) != GM_REV) return;
+  const uint32_t rcap = 1u << h.rev_log_cap;
+  const int l = blockIdx.y;
+  ulonglong2* tab = h.rev + size_t(l) * rcap;
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
+    float y[W];
+    load_row<DT, W>(src, r, y);
+    const uint64_t key = reg_key(y, src.dd, L, L0 + l, t);
+    const unsigned long long want = ~static_cast<unsigned long long>(r);
+    uint32_t pos = slot_home(key, h.rev_log_cap);
+    for (uint32_t it = 0; it < rcap; ++it) {
+      const ulonglong2 sl = tab[pos];
+      if (sl.x == key) {
+        if (sl.y < want) atomicMax(&tab[pos].y, want);
+        break;
+      }
+      if (sl.x == 0ull) break;
+      pos = (pos + 1) & (rcap - 1);
+    }
+  }
+}
+
+// Reverse group, step 3: each unresolved a takes the first of its buckets (in
+// scale order) that some b marked; the points resolved come off *h.left.
+template <int DT, int W>
+__global__ void __launch_bounds__(128) k_rev_resolve(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
+                                                     int64_t* bidx, uint8_t* level) {
+  pdl_entry();
+  if (group_mode(h) != GM_REV) return;
+  const uint32_t rcap = 1u << h.rev_log_cap;
+  unsigned resolved = 0;
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
+    if (level[r] < L) continue;
+    float y[W];
+    load_row<DT, W>(src, r, y);
+    for (int l = 0; l < nl; ++l) {
+      const ulonglong2* tab = h.rev + size_t(l) * rcap;
+      const uint64_t key = reg_key(y, src.dd, L, L0 + l, t);
+      uint32_t pos = slot_home(key, h.rev_log_cap);
+      unsigned long long yb = 0;
+      for (uint32_t it = 0; it < rcap; ++it) {
+        const ulonglong2 sl = tab[pos];
+        if (sl.x == key) {
+          yb = sl.y;
+          break;
+        }
+        if (sl.x == 0ull) break;
+        pos = (pos + 1) & (rcap - 1);
+      }
+      if (yb) {
+        bidx[r] = static_cast<int64_t>(~yb);
+        level[r] = static_cast<uint8_t>(L0 + l);
+        ++resolved;
+        break;
+      }
+    }
+  }
+  take_off_left(h, resolved);
+}
+
 // Each unresolved a walks the scales of the group in increasing order and
-// stops at the first bucket that holds a b (Fig. 2, step 3).
+// stops at the first bucket that holds a b (Fig. 2, step 3); the points this
+// group resolves come off *h.left.
 template <int DT, int W, bool WIDE>
 __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h,
                                                      int64_t* bidx, uint8_t* level) {
   pdl_entry();
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= src.n) return;
-  if (L0 > 0 && level[r] < L) return;  // resolved at a finer scale group
-  if (L0 == 0) {
-    // first group: start from "no scale collides" (b = 0, level = L)
-    bidx[r] = 0;
-    level[r] = static_cast<uint8_t>(L);
-  }
+  if (group_mode(h) != GM_FWD) return;
   const size_t cap = size_t(1) << h.log_cap;
-  if (!WIDE) {  // rows in registers (dd <= W); the wide form is compiled only where needed
-    float y[W];
-    load_row<DT, W>(src, r, y);
-    for (int l = 0; l < nl; ++l) {
-      const int64_t b = table_find(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t));
-      if (b >= 0) {
-        bidx[r] = b;
-        level[r] = static_cast<uint8_t>(L0 + l);
-        return;
-      }
+  unsigned resolved = 0;
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
+    if (L0 > 0 && level[r] < L) continue;  // resolved at a finer scale group
+    if (L0 == 0) {
+      // first group: start from "no scale collides" (b = 0, level = L)
+      bidx[r] = 0;
+      level[r] = static_cast<uint8_t>(L);
     }
-  } else {
-    for (int b0 = 0; b0 < nl; b0 += kLevelBlock) {
-      uint64_t key[kLevelBlock];
-      const int nb = min(kLevelBlock, nl - b0);
-      stream_keys<DT>(src, r, L, L0 + b0, nb, t, key);
-#pragma unroll
-      for (int l = 0; l < kLevelBlock; ++l) {
-        if (l >= nb) continue;
-        const int64_t b = table_find(h.slots + size_t(b0 + l) * cap, h.log_cap, key[l]);
+    bool found = false;
+    if (!WIDE) {  // rows in registers (dd <= W); the wide form is compiled only where needed
+      float y[W];
+      load_row<DT, W>(src, r, y);
+      for (int l = 0; l < nl && !found; ++l) {
+        const int64_t b = table_find(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t));
         if (b >= 0) {
           bidx[r] = b;
-          level[r] = static_cast<uint8_t>(L0 + b0 + l);
-          return;
+          level[r] = static_cast<uint8_t>(L0 + l);
+          found = true;
+        }
+      }
+    } else {
+      for (int b0 = 0; b0 < nl && !found; b0 += kLevelBlock) {
+        uint64_t key[kLevelBlock];
+        const int nb = min(kLevelBlock, nl - b0);
+        stream_keys<DT>(src, r, L, L0 + b0, nb, t, key);
+#pragma unroll
+        for (int l = 0; l < kLevelBlock; ++l) {
+          if (l >= nb || found) continue;
+          const int64_t b = table_find(h.slots + size_t(b0 + l) * cap, h.log_cap, key[l]);
+          if (b >= 0) {
+            bidx[r] = b;
+            level[r] = static_cast<uint8_t>(L0 + b0 + l);
+            found = true;
+          }
         }
       }
     }
+    resolved += found;
   }
+  if (h.left) take_off_left(h, resolved);
 }
 
 template <int DT, int W>
@@ -266,6 +415,8 @@ void dispatch_dt_w(int dtype, int dd, F&& f) {
 
 }  // namespace
 
+// SimHash keys}  // namespace
+
 // SimHash keys (random hyperplanes at every scale): bit i of a point is 1 unless
 // y_i < 0; level l keeps the first max(1, K >> l) bits; key = mix64(bits +
 // mix64((l << 32) ^ seed)), 0 replaced by 1.  One thread per point, all levels.
@@ -299,39 +450,106 @@ void launch_keys_write(HashSrc X, int L, ScaleTables t, uint64_t* keys, cudaStre
   launch_check("keys_write");
 }
 
-void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status,
+// Grids of the table kernels: grid-stride over the points, two waves of the
+// blocks that fit on the SMs at once (a skipped group then costs a short launch;
+// 1M x 384 CrudeNN: 1.070 ms at one wave, 1.039 ms at two, 1.111 ms with a block
+// per 128 points).
+template <class K>
+static int table_grid(K kernel, int64_t n, int sm_count) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> per_sm_of;  // resident 128-thread blocks per SM, per kernel
+  int per_sm;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = per_sm_of.find(reinterpret_cast<const void*>(kernel));
+    if (it == per_sm_of.end()) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 128, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 4;
+      }
+      it = per_sm_of.emplace(reinterpret_cast<const void*>(kernel), b).first;
+    }
+    per_sm = it->second;
+  }
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 128), int64_t(sm_count) * per_sm * 2)));
+}
+
+void launch_table_clear(HashTable h, int nl, int sm_count, cudaStream_t s) {
+  const int64_t n16 = int64_t(nl) << h.log_cap;  // 16-byte slots
+  const int grid = static_cast<int>(std::min<int64_t>(ceil_div(n16, 1024), int64_t(sm_count) * 2));
+  launch_k(k_table_clear, grid, 1024, 0, s, h, n16);
+  launch_check("table_clear");
+}
+
+void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status, int sm_count,
                          cudaStream_t s) {
   if (B.n == 0) return;
   if (B.dd <= kRegRow) {
-    const dim3 grid_ps(static_cast<unsigned>(ceil_div(B.n, 128)), static_cast<unsigned>(nl));
     dispatch_dt_w(B.dtype, B.dd, [&](auto dtc, auto wc) {
-      launch_k(k_table_insert_ps<decltype(dtc)::value, decltype(wc)::value>, grid_ps, 128, 0, s, B, L, L0, nl, t, h,
-                                                                                            status);
+      auto kern = k_table_insert_ps<decltype(dtc)::value, decltype(wc)::value>;
+      // the nl scales share one wave
+      const int gx = std::max(1, table_grid(kern, B.n, sm_count) / nl);
+      launch_k(kern, dim3(static_cast<unsigned>(gx), static_cast<unsigned>(nl)), 128, 0, s, B, L, L0, nl, t, h,
+               status);
     });
     launch_check("table_insert");
     return;
   }
-  const int grid = static_cast<int>(ceil_div(B.n, 128));
   switch (B.dtype) {
-    case CH_F32: launch_k(k_table_insert<CH_F32>, grid, 128, 0, s, B, L, L0, nl, t, h, status); break;
-    case CH_BF16: launch_k(k_table_insert<CH_BF16>, grid, 128, 0, s, B, L, L0, nl, t, h, status); break;
-    default: launch_k(k_table_insert<CH_FP8E4M3>, grid, 128, 0, s, B, L, L0, nl, t, h, status); break;
+    case CH_F32:
+      launch_k(k_table_insert<CH_F32>, table_grid(k_table_insert<CH_F32>, B.n, sm_count), 128, 0, s, B, L, L0, nl, t,
+               h, status);
+      break;
+    case CH_BF16:
+      launch_k(k_table_insert<CH_BF16>, table_grid(k_table_insert<CH_BF16>, B.n, sm_count), 128, 0, s, B, L, L0, nl,
+               t, h, status);
+      break;
+    default:
+      launch_k(k_table_insert<CH_FP8E4M3>, table_grid(k_table_insert<CH_FP8E4M3>, B.n, sm_count), 128, 0, s, B, L,
+               L0, nl, t, h, status);
+      break;
   }
   launch_check("table_insert");
 }
 
 void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx, uint8_t* level,
-                        cudaStream_t s) {
+                        int sm_count, cudaStream_t s) {
   if (A.n == 0) return;
-  const int grid = static_cast<int>(ceil_div(A.n, 128));
+
   dispatch_dt_w(A.dtype, A.dd, [&](auto dtc, auto wc) {
     constexpr int DT = decltype(dtc)::value, W = decltype(wc)::value;
-    if (A.dd <= W)  // the register form alone: 32-odd registers instead of 115, so 4x the resident warps
-      launch_k(k_table_probe<DT, W, false>, grid, 128, 0, s, A, L, L0, nl, t, h, bidx, level);
+    if (A.dd <= W)  // the register form alone: 48 registers instead of 127, so 2.5x the resident warps
+      launch_k(k_table_probe<DT, W, false>, table_grid(k_table_probe<DT, W, false>, A.n, sm_count), 128, 0, s, A, L,
+               L0, nl, t, h, bidx, level);
     else
-      launch_k(k_table_probe<DT, W, true>, grid, 128, 0, s, A, L, L0, nl, t, h, bidx, level);
+      launch_k(k_table_probe<DT, W, true>, table_grid(k_table_probe<DT, W, true>, A.n, sm_count), 128, 0, s, A, L,
+               L0, nl, t, h, bidx, level);
   });
   launch_check("table_probe");
+}
+
+void launch_group_reverse(HashSrc A, HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
+                          uint8_t* level, uint32_t* status, int sm_count, cudaStream_t s) {
+  CHX_CHECK(A.dd <= kRegRow && B.dd <= kRegRow, CH_EINVAL, "reverse scale groups need hashed rows of <= 32 values");
+  dispatch_dt_w(A.dtype, A.dd, [&](auto dtc, auto wc) {
+    auto kern = k_rev_insert<decltype(dtc)::value, decltype(wc)::value>;
+    launch_k(kern, table_grid(kern, A.n, sm_count), 128, 0, s, A, L, L0, nl, t, h, level, status);
+  });
+  launch_check("rev_insert");
+  HashTable later = h;
+  later.first = 0;
+  dispatch_dt_w(B.dtype, B.dd, [&](auto dtc, auto wc) {
+    auto kern = k_rev_stream<decltype(dtc)::value, decltype(wc)::value>;
+    const int gx = std::max(1, table_grid(kern, B.n, sm_count) / nl);
+    launch_k(kern, dim3(static_cast<unsigned>(gx), static_cast<unsigned>(nl)), 128, 0, s, B, L, L0, nl, t, later);
+  });
+  launch_check("rev_stream");
+  dispatch_dt_w(A.dtype, A.dd, [&](auto dtc, auto wc) {
+    auto kern = k_rev_resolve<decltype(dtc)::value, decltype(wc)::value>;
+    launch_k(kern, table_grid(kern, A.n, sm_count), 128, 0, s, A, L, L0, nl, t, later, bidx, level);
+  });
+  launch_check("rev_resolve");
 }
 
 }  // namespace chx

@@ -45,9 +45,29 @@ struct Cached {
 };
 Cached g_addr[kMaxDevices] = {};
 
+// driver calls through the runtime's entry-point table, so that the library
+// loads (and its CPU-side checks run) on machines without the driver
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+template <class F>
+F driver_fn(const char* name, int version) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return reinterpret_cast<F>(p);
+}
+
 bool current_ctx_id(unsigned long long* id) {
+  static const CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 4000);
+  static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId", 12000);
+  if (!get_current || !get_id) return false;
   CUcontext c = nullptr;
-  return cuCtxGetCurrent(&c) == CUDA_SUCCESS && c && cuCtxGetId(c, id) == CUDA_SUCCESS;
+  return get_current(&c) == CUDA_SUCCESS && c && get_id(c, id) == CUDA_SUCCESS;
 }
 
 ch_status scratch_for_current_device(unsigned char** out) {

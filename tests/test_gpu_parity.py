@@ -193,6 +193,39 @@ def test_crude_nn_bit_exact_two_table_groups(ctx, pair_factory, metric):
     assert lv.max() >= 5  # some points resolve in the second group
 
 
+@pytest.mark.parametrize("top_exp,expect", [(4, "forward"), (6, "reverse")])
+def test_crude_nn_later_group_forward_and_reverse(ctx, pair_factory, top_exp, expect):
+    """|A| = 100k, |B| = 300k: two groups of five scales.  The first group
+    resolves a number of points set by the top scale: with top_exp = 4 one point,
+    leaving more than 65536 for the second group (B into its tables, as the
+    first); with top_exp = 6 about 69k, leaving about 31k, so the second group
+    runs in reverse (the unresolved a's buckets into small tables, B streamed past
+    them).  Either way b(a), the scale and D_a equal the oracle's bit for bit."""
+    A, B = workloads.uniform(100_000, 300_000, 16, 5)
+    p = pair_factory(A, B)
+    bidx, D, lv = gpu_crude(ctx, p, L2, 3, top_exp=top_exp)
+    r = oracle.crude_nn(A, B, L2, hash_seed=3, top_exp=top_exp)
+    assert np.array_equal(bidx, r["bidx"])
+    assert np.array_equal(lv, r["level"])
+    assert np.array_equal(D.view(np.uint32), r["D"].view(np.uint32))
+    left = int(np.sum(r["level"] >= 5))
+    assert (left > 65536) == (expect == "forward") and left > 0
+
+
+def test_crude_nn_five_groups_l1_surface(ctx, pair_factory):
+    """d = 3 surfaces, l1, |B| = 600k: 32 MB tables, five groups of two scales;
+    the first resolves all but a few points, the second resolves them in reverse,
+    the other three return at once."""
+    A, B = workloads.shape_surface(60_000, 600_000, 9)
+    p = pair_factory(A, B)
+    bidx, D, lv = gpu_crude(ctx, p, L1, 3)
+    r = oracle.crude_nn(A, B, L1, hash_seed=3)
+    assert np.array_equal(bidx, r["bidx"])
+    assert np.array_equal(lv, r["level"])
+    assert np.array_equal(D.view(np.uint32), r["D"].view(np.uint32))
+    assert 0 < int(np.sum(r["level"] >= 2)) < 100
+
+
 @pytest.mark.parametrize("group", GROUPS, ids=["hash", "sort"])
 def test_crude_nn_few_levels_and_fallback(ctx, pair_factory, group):
     A, B = workloads.uniform(400, 600, 6, 5)
