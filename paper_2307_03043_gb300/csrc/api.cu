@@ -166,6 +166,14 @@ static void run_hashed(ch_ctx* c, const ch_set* X, const ch_hash_params* hp, Has
     ensure_ingest(const_cast<ch_set*>(X), c->stream);
 }
 
+// the context's side stream and its fork / join events, made on first use
+static void ensure_side(ch_ctx* c) {
+  if (c->side) return;
+  CHX_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CHX_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+  CHX_CUDA(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+}
+
 // Both sets' hashed-space passes.  Where each l2 projection is bound by its
 // start-up (generating the Gaussian matrix, filling the copy pipeline: sets of
 // 2M to 64M coordinates) the two run side by side, A's on the context's stream
@@ -182,11 +190,7 @@ static void run_hashed_pair(ch_ctx* c, const ch_set* A, const ch_set* B, const c
     run_hashed(c, B, hp, hB, status);
     return;
   }
-  if (!c->side) {
-    CHX_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-    CHX_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
-    CHX_CUDA(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
-  }
+  ensure_side(c);
   const int k = static_cast<int>(hp->proj_dim);
   const int half = c->sm_count / 2;
   CHX_CUDA(cudaEventRecord(c->fork_ev, c->stream));
@@ -238,17 +242,15 @@ struct CrudeBufs {
   int32_t* e_top;
   ulonglong2* slots;   // CH_GROUP_HASH: bucket tables of one scale group
   // CH_GROUP_HASH scale-group control: left[0] = points of A no scale group has
-  // resolved yet, left[1 + g] = length of group g's reverse list; mode[g]
+  // resolved yet; mode[g] = group g's mode
   unsigned long long* left;
   int32_t* mode;
   int groups;
   // reverse groups (g >= 1, once at most rev_max points are left): small tables
-  // [groups - 1][per_group][2^rev_log_cap], the list and its slots
+  // [groups - 1][per_group][2^rev_log_cap]
   unsigned long long rev_max;
   uint32_t rev_log_cap;
   ulonglong2* rev;
-  int64_t* lst;
-  uint32_t* lst_pos;
   TablePlan plan;
   uint64_t *keysA, *keysB;  // CH_GROUP_SORT and k x W: keys [L][n] and the sort's scratch
   void* sort_work;
@@ -293,7 +295,7 @@ static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_p
   cb->plan = table_plan(B->n, nl);
   cb->slots = lay.template take<ulonglong2>(size_t(cb->plan.per_group) << cb->plan.log_cap);
   cb->groups = (nl + cb->plan.per_group - 1) / cb->plan.per_group;
-  cb->left = lay.template take<unsigned long long>(1 + cb->groups);
+  cb->left = lay.template take<unsigned long long>(1);
   cb->mode = lay.template take<int32_t>(cb->groups);
   // reverse groups need rows of at most 32 hashed values, at most kRevGroupMax
   // scales per group and more than one group
@@ -301,14 +303,10 @@ static void take_crude(L& lay, const ch_set* A, const ch_set* B, const ch_hash_p
                     ? static_cast<unsigned long long>(std::min<int64_t>(kRevMax, A->n))
                     : 0;
   cb->rev = nullptr;
-  cb->lst = nullptr;
-  cb->lst_pos = nullptr;
   cb->rev_log_cap = 0;
   if (cb->rev_max) {
     cb->rev_log_cap = static_cast<uint32_t>(ceil_log2_i64(std::max<int64_t>(2 * int64_t(cb->rev_max), 1024)));
     cb->rev = lay.template take<ulonglong2>((size_t(cb->groups - 1) * cb->plan.per_group) << cb->rev_log_cap);
-    cb->lst = lay.template take<int64_t>(cb->rev_max);
-    cb->lst_pos = lay.template take<uint32_t>(size_t(cb->rev_max) * cb->plan.per_group);
   }
   cb->keysA = cb->keysB = nullptr;
   cb->sort_work = nullptr;
@@ -376,12 +374,26 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
   const size_t zero_bytes = fold ? group_bytes0
                                  : cb->rev ? ((size_t(cb->groups - 1) * cb->plan.per_group) << cb->rev_log_cap) * 16 : 0;
   launch_scale_tables(cb->hA.box, cb->hA.box_parts, cb->hB.box, cb->hB.box_parts, dd, L, hp->top_exp, hp->hash_seed,
-                      cb->tab, cb->e_top, status, s, zero, zero_bytes, c->sm_count, cb->left, A->n, cb->groups);
+                      cb->tab, cb->e_top, status, s, zero, zero_bytes, c->sm_count, cb->left, A->n, 0);
   // Each group's kernels follow its mode (see HashTable): groups after the one
   // that resolves the last point of A return at once -- on clustered data the
   // coarse scales are rarely reached (1M x 384 unit mixture: no point past scale
   // 4 of 10) -- and once few points are left a group runs in reverse.
+  // Every point of A resolved by the first group has its final b(a): with later
+  // groups to run, the crude distances of those points go on the side stream
+  // right after the first group, beside the later groups' latency-bound table
+  // work, and the rest follow the last group.
+  const bool split = cb->groups > 1 && crude_dist_vector_ok(A, B) && c->sm_count >= 2;
   for (int g = 0, L0 = 0; L0 < L; ++g, L0 += cb->plan.per_group) {
+    if (split && g == 1) {
+      ensure_side(c);
+      if (maxD) CHX_CUDA(cudaMemsetAsync(maxD, 0, sizeof(uint32_t), s));
+      CHX_CUDA(cudaEventRecord(c->fork_ev, s));
+      CHX_CUDA(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+      // two of the four resident blocks per SM: room for the table kernels beside it
+      launch_crude_dist_part(A, B, hp->metric, bidx, D, maxD, level, L0, true, c->sm_count, c->side, 2);
+      CHX_CUDA(cudaEventRecord(c->join_ev, c->side));
+    }
     const int nl = std::min(cb->plan.per_group, L - L0);
     HashTable h{};
     h.slots = cb->slots;
@@ -394,9 +406,6 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
       h.rev_max = cb->rev_max;
       h.rev_log_cap = cb->rev_log_cap;
       h.rev = cb->rev + ((size_t(g - 1) * cb->plan.per_group) << cb->rev_log_cap);
-      h.lst = cb->lst;
-      h.lst_pos = cb->lst_pos;
-      h.lst_n = cb->left + 1 + g;
       launch_group_reverse(cb->hA.src, cb->hB.src, L, L0, nl, cb->tab, h, bidx, level, status, c->sm_count, s);
       h.first = 0;
     }
@@ -407,6 +416,11 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
     launch_group_insert(cb->hB.src, L, L0, nl, cb->tab, h, status, c->sm_count, s);
     h.first = 0;
     launch_group_probe(cb->hA.src, L, L0, nl, cb->tab, h, bidx, level, c->sm_count, s);
+  }
+  if (split) {
+    CHX_CUDA(cudaStreamWaitEvent(s, c->join_ev, 0));
+    launch_crude_dist_part(A, B, hp->metric, bidx, D, maxD, level, cb->plan.per_group, false, c->sm_count, s, 4);
+    return;
   }
   launch_crude_dist(A, B, hp->metric, bidx, D, maxD, c->sm_count, s);
 }

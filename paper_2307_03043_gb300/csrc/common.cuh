@@ -312,13 +312,9 @@ struct HashTable {
   int first;
   unsigned long long rev_max;  // 0: no reverse groups
   // reverse groups: small tables [nl][2^rev_log_cap] of the unresolved a's
-  // buckets (cleared before the groups run), the list of those a, each list
-  // entry's slot per scale [rev_max][nl], and the list's length (zeroed before)
+  // buckets, cleared before the groups run
   ulonglong2* rev;
   uint32_t rev_log_cap;
-  int64_t* lst;
-  uint32_t* lst_pos;
-  unsigned long long* lst_n;
 };
 
 // reverse groups hold at most this many scales
@@ -356,9 +352,17 @@ void launch_cand_dist(const ch_set* A, const ch_set* B, int metric, const int32_
 void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB, int64_t nB, int L,
                        void* work, int64_t* bidx, uint8_t* level, cudaStream_t s);
 
-// D_a = canonical d(a, B[b(a)]); with maxD non-null also max_a D_a (ordered-encoded)
+// D_a = canonical d(a, B[b(a)]); with maxD non-null also max_a D_a (ordered-encoded;
+// *maxD is cleared first unless keep_max)
 void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, uint32_t* maxD,
                        int sm_count, cudaStream_t s);
+// The same for the a with level[a] < split (below = true) or level[a] >= split
+// (below = false) only, folding into *maxD without clearing it; false (nothing
+// launched) where the vector form does not apply
+bool crude_dist_vector_ok(const ch_set* A, const ch_set* B);
+bool launch_crude_dist_part(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D,
+                            uint32_t* maxD, const uint8_t* level, int split, bool below, int sm_count, cudaStream_t s,
+                            int blocks_per_sm = 4);
 
 // sampling
 struct SampleWork {

@@ -1077,81 +1077,126 @@ __device__ __forceinline__ void chunk_vals(const uint4 raw, float sc, float (&v)
   }
 }
 
+// resident blocks of the vector crude-distance kernel per SM (fp8 decodes 16 codes
+// per chunk and needs the registers of three)
+template <int DT>
+constexpr int kCrudeDistBlocks = DT == CH_FP8E4M3 ? 3 : 4;
+
+// D_a for the row group's a (a < 0: none; every lane of the warp calls this);
+// folds D_a into mx on the group's first lane
 template <int DT, int METRIC>
-__global__ void __launch_bounds__(256) k_crude_dist_v(const void* A, const float* scA, int64_t nA, const void* B,
-                                                      const float* scB, int d, const int64_t* bidx, float* D,
-                                                      uint32_t* maxD) {
-  pdl_entry();
+__device__ __forceinline__ void crude_row(const void* A, const float* scA, const void* B, const float* scB, int d,
+                                          const int64_t* bidx, float* D, int64_t a, uint32_t& mx) {
   constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
   constexpr int C = 16 / ES;    // coordinates per chunk
   constexpr int LPR = 32 / C;   // lanes per row
-  constexpr int RPW = 32 / LPR; // rows per warp
   constexpr int U = 4;          // chunks of A and of B in flight per lane
-  __shared__ uint32_t s_max[8];
-  const int lane = threadIdx.x & 31;
-  const int sub = lane % LPR, grp = lane / LPR;
+  const int sub = (threadIdx.x & 31) % LPR;
   const int chunks = d / C;
   const size_t rowq = size_t(d) / C;  // 16-byte words per row
+  const bool live = a >= 0;
+  float p[C];
+#pragma unroll
+  for (int i = 0; i < C; ++i) p[i] = 0.0f;
+  if (live) {
+    const int64_t b = bidx[a];
+    const uint4* ra = static_cast<const uint4*>(A) + size_t(a) * rowq;
+    const uint4* rb = static_cast<const uint4*>(B) + size_t(b) * rowq;
+    const float sa = DT == CH_FP8E4M3 ? scA[a] : 1.0f;
+    const float sb = DT == CH_FP8E4M3 ? scB[b] : 1.0f;
+    for (int m0 = sub; m0 < chunks; m0 += LPR * U) {
+      uint4 qa[U], qb[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int m = m0 + u * LPR;
+        if (m < chunks) {
+          qa[u] = __ldcs(ra + m);  // A is read once: evict first
+          qb[u] = rb[m];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (m0 + u * LPR < chunks) {
+          float va[C], vb[C];
+          chunk_vals<DT>(qa[u], sa, va);
+          chunk_vals<DT>(qb[u], sb, vb);
+#pragma unroll
+          for (int i = 0; i < C; ++i) {
+            const float t = __fsub_rn(va[i], vb[i]);
+            if (METRIC == CH_L1)
+              p[i] = __fadd_rn(p[i], fabsf(t));
+            else
+              p[i] = __fmaf_rn(t, t, p[i]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 16; s >= C; s >>= 1) {
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const float o = __shfl_down_sync(0xFFFFFFFFu, p[i], s / C, LPR);
+      p[i] = __fadd_rn(p[i], o);
+    }
+  }
+#pragma unroll
+  for (int s = C / 2; s >= 1; s >>= 1)
+#pragma unroll
+    for (int i = 0; i < s; ++i) p[i] = __fadd_rn(p[i], p[i + s]);
+  if (live && sub == 0) {
+    const float v = (METRIC == CH_L1) ? p[0] : __fsqrt_rn(p[0]);
+    D[a] = v;
+    mx = max(mx, ord_enc(v));
+  }
+}
+
+// With level, only the a whose level is below split (below != 0) or not: each
+// warp takes spans of 256 points, lists the ones that pass from the span's level
+// bytes (eight coalesced reads, ballots), and runs its row groups over the list.
+template <int DT, int METRIC>
+__global__ void __launch_bounds__(256, kCrudeDistBlocks<DT>) k_crude_dist_v(const void* A, const float* scA, int64_t nA, const void* B,
+                                                      const float* scB, int d, const int64_t* bidx, float* D,
+                                                      uint32_t* maxD, const uint8_t* level, int split, int below) {
+  pdl_entry();
+  constexpr int ES = DT == CH_F32 ? 4 : DT == CH_BF16 ? 2 : 1;
+  constexpr int LPR = 32 / (16 / ES);  // lanes per row
+  constexpr int RPW = 32 / LPR;        // rows per warp
+  constexpr int kSpan = 256;
+  __shared__ uint32_t s_max[8];
+  __shared__ uint16_t s_list[8][kSpan];  // blocks of 256 threads: 8 warps
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int grp = lane / LPR;
   const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t wstep = (int64_t(gridDim.x) * blockDim.x) >> 5;
   uint32_t mx = 0;
-  // every lane runs the same number of rounds (the shuffles need the whole warp)
-  for (int64_t a0 = warp0 * RPW; a0 < nA; a0 += wstep * RPW) {
-    const int64_t a = a0 + grp;
-    const bool live = a < nA;
-    float p[C];
-#pragma unroll
-    for (int i = 0; i < C; ++i) p[i] = 0.0f;
-    if (live) {
-      const int64_t b = bidx[a];
-      const uint4* ra = static_cast<const uint4*>(A) + size_t(a) * rowq;
-      const uint4* rb = static_cast<const uint4*>(B) + size_t(b) * rowq;
-      const float sa = DT == CH_FP8E4M3 ? scA[a] : 1.0f;
-      const float sb = DT == CH_FP8E4M3 ? scB[b] : 1.0f;
-      for (int m0 = sub; m0 < chunks; m0 += LPR * U) {
-        uint4 qa[U], qb[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int m = m0 + u * LPR;
-          if (m < chunks) {
-            qa[u] = __ldcs(ra + m);  // A is read once: evict first
-            qb[u] = rb[m];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (m0 + u * LPR < chunks) {
-            float va[C], vb[C];
-            chunk_vals<DT>(qa[u], sa, va);
-            chunk_vals<DT>(qb[u], sb, vb);
-#pragma unroll
-            for (int i = 0; i < C; ++i) {
-              const float t = __fsub_rn(va[i], vb[i]);
-              if (METRIC == CH_L1)
-                p[i] = __fadd_rn(p[i], fabsf(t));
-              else
-                p[i] = __fmaf_rn(t, t, p[i]);
-            }
-          }
-        }
-      }
+  if (!level) {
+    // every lane runs the same number of rounds (the shuffles need the whole warp)
+    for (int64_t a0 = warp0 * RPW; a0 < nA; a0 += wstep * RPW) {
+      const int64_t a = a0 + grp;
+      crude_row<DT, METRIC>(A, scA, B, scB, d, bidx, D, a < nA ? a : -1, mx);
     }
+  } else {
+    for (int64_t s0 = warp0 * kSpan; s0 < nA; s0 += wstep * kSpan) {
+      bool ok[kSpan / 32];
 #pragma unroll
-    for (int s = 16; s >= C; s >>= 1) {
-#pragma unroll
-      for (int i = 0; i < C; ++i) {
-        const float o = __shfl_down_sync(0xFFFFFFFFu, p[i], s / C, LPR);
-        p[i] = __fadd_rn(p[i], o);
+      for (int k = 0; k < kSpan / 32; ++k) {
+        const int64_t a = s0 + 32 * k + lane;
+        ok[k] = a < nA && ((level[a] < split) == (below != 0));
       }
-    }
+      int cnt = 0;
 #pragma unroll
-    for (int s = C / 2; s >= 1; s >>= 1)
-#pragma unroll
-      for (int i = 0; i < s; ++i) p[i] = __fadd_rn(p[i], p[i + s]);
-    if (live && sub == 0) {
-      const float v = (METRIC == CH_L1) ? p[0] : __fsqrt_rn(p[0]);
-      D[a] = v;
-      mx = max(mx, ord_enc(v));
+      for (int k = 0; k < kSpan / 32; ++k) {
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, ok[k]);
+        if (ok[k]) s_list[w][cnt + __popc(m & ((1u << lane) - 1))] = static_cast<uint16_t>(32 * k + lane);
+        cnt += __popc(m);
+      }
+      __syncwarp();
+      for (int i0 = 0; i0 < cnt; i0 += RPW) {
+        const int i = i0 + grp;
+        crude_row<DT, METRIC>(A, scA, B, scB, d, bidx, D, i < cnt ? s0 + s_list[w][i] : -1, mx);
+      }
+      __syncwarp();
     }
   }
   if (!maxD) return;
@@ -1186,34 +1231,48 @@ static void crude_dist_1(const ch_set* A, const ch_set* B, int metric, const int
   }
 }
 
-void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, uint32_t* maxD,
-                       int sm_count, cudaStream_t s) {
-  if (maxD) CHX_CUDA(cudaMemsetAsync(maxD, 0, sizeof(uint32_t), s));
-  if (A->n == 0) return;
+// the vector form applies: one storage type, rows of a multiple of 16 bytes on 16-byte aligned bases
+bool crude_dist_vector_ok(const ch_set* A, const ch_set* B) {
   const size_t es = elem_size(A->dtype);
-  if (A->dtype == B->dtype && (size_t(A->d) * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
-      (reinterpret_cast<uintptr_t>(B->data) & 15) == 0) {
-    // rows per warp: 32 / (lanes per row) = 16 / es coordinates... one row group per 32 / (16 / es) lanes
-    const int64_t rpw = int64_t(16 / es);
-    const int grid = static_cast<int>(std::min<int64_t>(ceil_div(ceil_div(A->n, rpw) * 32, 256), int64_t(sm_count) * 4));
+  return A->dtype == B->dtype && (size_t(A->d) * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(A->data) & 15) == 0 &&
+         (reinterpret_cast<uintptr_t>(B->data) & 15) == 0;
+}
+
+bool launch_crude_dist_part(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D,
+                            uint32_t* maxD, const uint8_t* level, int split, bool below, int sm_count, cudaStream_t s,
+                            int blocks_per_sm) {
+  const size_t es = elem_size(A->dtype);
+  if (!crude_dist_vector_ok(A, B)) return false;
+  if (A->n == 0) return true;
+  // a row group of 32 / (16 / es) lanes per a: 16 / es rows per warp
+  const int64_t rpw = int64_t(16 / es);
+  const int per_sm = std::min(blocks_per_sm, A->dtype == CH_FP8E4M3 ? kCrudeDistBlocks<CH_FP8E4M3> : 4);
+  const int grid = static_cast<int>(std::min<int64_t>(ceil_div(ceil_div(A->n, rpw) * 32, 256), int64_t(sm_count) * per_sm));
+  const int bl = below ? 1 : 0;
 #define CHX_CDV(DTV)                                                                                              \
   do {                                                                                                            \
     if (metric == CH_L1)                                                                                          \
       launch_k(k_crude_dist_v<DTV, CH_L1>, grid, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, A->d,  \
-               bidx, D, maxD);                                                                                    \
+               bidx, D, maxD, level, split, bl);                                                                  \
     else                                                                                                          \
       launch_k(k_crude_dist_v<DTV, CH_L2>, grid, 256, 0, s, A->data, A->scales, A->n, B->data, B->scales, A->d,  \
-               bidx, D, maxD);                                                                                    \
+               bidx, D, maxD, level, split, bl);                                                                  \
   } while (0)
-    switch (A->dtype) {
-      case CH_F32: CHX_CDV(CH_F32); break;
-      case CH_BF16: CHX_CDV(CH_BF16); break;
-      default: CHX_CDV(CH_FP8E4M3); break;
-    }
-#undef CHX_CDV
-    launch_check("crude_dist");
-    return;
+  switch (A->dtype) {
+    case CH_F32: CHX_CDV(CH_F32); break;
+    case CH_BF16: CHX_CDV(CH_BF16); break;
+    default: CHX_CDV(CH_FP8E4M3); break;
   }
+#undef CHX_CDV
+  launch_check("crude_dist");
+  return true;
+}
+
+void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, uint32_t* maxD,
+                       int sm_count, cudaStream_t s) {
+  if (maxD) CHX_CUDA(cudaMemsetAsync(maxD, 0, sizeof(uint32_t), s));
+  if (A->n == 0) return;
+  if (launch_crude_dist_part(A, B, metric, bidx, D, maxD, nullptr, 0, true, sm_count, s, 4)) return;
   int G = 1;
   while (G < A->d && G < 32) G <<= 1;
   // 8 resident blocks of 256 per SM; each block merges its maximum once

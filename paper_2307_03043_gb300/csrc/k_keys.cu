@@ -10,6 +10,7 @@
 // Bucket tables: one open-addressing table (linear probing, 16-byte slots
 // {key, ~min b}) per scale; B inserts, then each a probes its scales in
 // increasing order and stops at the first bucket that holds a b.
+#include <cstddef>
 #include <mutex>
 #include <type_traits>
 #include <unordered_map>
@@ -70,6 +71,61 @@ __device__ inline uint64_t reg_key(const float (&y)[W], int dd, int L, int lvl, 
       cell_acc(y[j], __ldg(&t.shift[j * L + lvl]), inv_r,
                __ldg(reinterpret_cast<const unsigned long long*>(&t.mult[j])), h);
   return finish_key(h, t, lvl);
+}
+
+// The scale constants of a group, staged in shared memory once per block
+// (the table kernels are grid-stride, so a block keys many points): the shifts
+// of each scale contiguous in the coordinate, so a key reads them and the
+// multipliers as 16-byte words instead of one scalar global load per term.
+// 16-byte aligned: group_key reads the shifts and the multipliers as 16-byte words
+template <int W>
+struct __align__(16) GroupConsts {
+  float z[kMaxLevels][W];  // z_{e,j} of scale L0 + l, l < nl <= kMaxLevels
+  uint64_t K[W];           // multipliers
+  float inv_r[kMaxLevels];
+  uint64_t salt[kMaxLevels];
+};
+static_assert(alignof(GroupConsts<4>) == 16 && alignof(GroupConsts<16>) == 16 && alignof(GroupConsts<32>) == 16,
+              "vector reads of the staged constants need 16-byte alignment");
+static_assert(offsetof(GroupConsts<16>, K) % 16 == 0 && offsetof(GroupConsts<32>, K) % 16 == 0 &&
+                  offsetof(GroupConsts<4>, K) % 16 == 0,
+              "the multipliers start on a 16-byte boundary");
+
+// fills c for the scales L0 .. L0 + nl - 1 (nl <= kMaxLevels, the bound every
+// caller's hash parameters were checked against); every thread of the block calls it
+template <int W>
+__device__ void load_group_consts(GroupConsts<W>& c, const ScaleTables& t, int dd, int L, int L0, int nl) {
+  for (int i = threadIdx.x; i < kMaxLevels * W; i += blockDim.x) {
+    const int l = i / W, j = i % W;
+    c.z[l][j] = (l < nl && j < dd) ? __ldg(&t.shift[j * L + L0 + l]) : 0.0f;
+  }
+  for (int j = threadIdx.x; j < W; j += blockDim.x)
+    c.K[j] = j < dd ? __ldg(reinterpret_cast<const unsigned long long*>(&t.mult[j])) : 0ull;
+  for (int l = threadIdx.x; l < kMaxLevels; l += blockDim.x) {
+    c.inv_r[l] = l < nl ? __ldg(&t.inv_r[L0 + l]) : 1.0f;
+    c.salt[l] = l < nl ? __ldg(reinterpret_cast<const unsigned long long*>(&t.salt[L0 + l])) : 0ull;
+  }
+  __syncthreads();
+}
+
+// key of a register-resident row at the group's scale l (the same key as reg_key at L0 + l)
+template <int W>
+__device__ inline uint64_t group_key(const float (&y)[W], int dd, int l, const GroupConsts<W>& c) {
+  const float inv_r = c.inv_r[l];
+  uint64_t h = 0;
+#pragma unroll
+  for (int j4 = 0; j4 < W / 4; ++j4) {
+    const float4 z4 = *reinterpret_cast<const float4*>(&c.z[l][4 * j4]);
+    const ulonglong2 k01 = *reinterpret_cast<const ulonglong2*>(&c.K[4 * j4]);
+    const ulonglong2 k23 = *reinterpret_cast<const ulonglong2*>(&c.K[4 * j4 + 2]);
+    const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
+    const uint64_t kk[4] = {k01.x, k01.y, k23.x, k23.y};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (4 * j4 + q < dd) cell_acc(y[4 * j4 + q], zz[q], inv_r, kk[q], h);
+  }
+  const uint64_t k = mix64(h + c.salt[l]);
+  return k == 0 ? 1 : k;
 }
 
 // keys of a streamed row at scales L0 .. L0+nl-1 (nl <= 16)
@@ -205,12 +261,14 @@ __global__ void __launch_bounds__(128) k_table_insert_ps(HashSrc src, int L, int
                                                          HashTable h, uint32_t* status) {
   pdl_entry();
   if (group_mode(h) != GM_FWD) return;
+  __shared__ GroupConsts<W> gc;
+  load_group_consts(gc, t, src.dd, L, L0, nl);
   const int l = blockIdx.y;
   const size_t cap = size_t(1) << h.log_cap;
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
     float y[W];
     load_row<DT, W>(src, r, y);
-    table_insert(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t), r, status);
+    table_insert(h.slots + size_t(l) * cap, h.log_cap, group_key(y, src.dd, l, gc), r, status);
   }
 }
 
@@ -239,6 +297,8 @@ __global__ void __launch_bounds__(128) k_rev_insert(HashSrc src, int L, int L0, 
                                                     const uint8_t* level, uint32_t* status) {
   pdl_entry();
   if (group_mode(h) != GM_REV) return;
+  __shared__ GroupConsts<W> gc;
+  load_group_consts(gc, t, src.dd, L, L0, nl);
   const uint32_t rcap = 1u << h.rev_log_cap;
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
     if (level[r] < L) continue;
@@ -246,7 +306,7 @@ __global__ void __launch_bounds__(128) k_rev_insert(HashSrc src, int L, int L0, 
     load_row<DT, W>(src, r, y);
     for (int l = 0; l < nl; ++l) {
       ulonglong2* tab = h.rev + size_t(l) * rcap;
-      const uint64_t key = reg_key(y, src.dd, L, L0 + l, t);
+      const uint64_t key = group_key(y, src.dd, l, gc);
       uint32_t pos = slot_home(key, h.rev_log_cap);
       uint32_t it = 0;
       for (; it < rcap; ++it) {
@@ -266,13 +326,15 @@ template <int DT, int W>
 __global__ void __launch_bounds__(128) k_rev_stream(HashSrc src, int L, int L0, int nl, ScaleTables t, HashTable h) {
   pdl_entry();
   if (group_mode(h) != GM_REV) return;
+  __shared__ GroupConsts<W> gc;
+  load_group_consts(gc, t, src.dd, L, L0, nl);
   const uint32_t rcap = 1u << h.rev_log_cap;
   const int l = blockIdx.y;
   ulonglong2* tab = h.rev + size_t(l) * rcap;
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
     float y[W];
     load_row<DT, W>(src, r, y);
-    const uint64_t key = reg_key(y, src.dd, L, L0 + l, t);
+    const uint64_t key = group_key(y, src.dd, l, gc);
     const unsigned long long want = ~static_cast<unsigned long long>(r);
     uint32_t pos = slot_home(key, h.rev_log_cap);
     for (uint32_t it = 0; it < rcap; ++it) {
@@ -294,6 +356,8 @@ __global__ void __launch_bounds__(128) k_rev_resolve(HashSrc src, int L, int L0,
                                                      int64_t* bidx, uint8_t* level) {
   pdl_entry();
   if (group_mode(h) != GM_REV) return;
+  __shared__ GroupConsts<W> gc;
+  load_group_consts(gc, t, src.dd, L, L0, nl);
   const uint32_t rcap = 1u << h.rev_log_cap;
   unsigned resolved = 0;
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
@@ -302,7 +366,7 @@ __global__ void __launch_bounds__(128) k_rev_resolve(HashSrc src, int L, int L0,
     load_row<DT, W>(src, r, y);
     for (int l = 0; l < nl; ++l) {
       const ulonglong2* tab = h.rev + size_t(l) * rcap;
-      const uint64_t key = reg_key(y, src.dd, L, L0 + l, t);
+      const uint64_t key = group_key(y, src.dd, l, gc);
       uint32_t pos = slot_home(key, h.rev_log_cap);
       unsigned long long yb = 0;
       for (uint32_t it = 0; it < rcap; ++it) {
@@ -333,6 +397,8 @@ __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0,
                                                      int64_t* bidx, uint8_t* level) {
   pdl_entry();
   if (group_mode(h) != GM_FWD) return;
+  __shared__ GroupConsts<WIDE ? 4 : W> gc;
+  if constexpr (!WIDE) load_group_consts(gc, t, src.dd, L, L0, nl);
   const size_t cap = size_t(1) << h.log_cap;
   unsigned resolved = 0;
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gridDim.x) * blockDim.x) {
@@ -343,11 +409,11 @@ __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0,
       level[r] = static_cast<uint8_t>(L);
     }
     bool found = false;
-    if (!WIDE) {  // rows in registers (dd <= W); the wide form is compiled only where needed
+    if constexpr (!WIDE) {  // rows in registers (dd <= W); the wide form is compiled only where needed
       float y[W];
       load_row<DT, W>(src, r, y);
       for (int l = 0; l < nl && !found; ++l) {
-        const int64_t b = table_find(h.slots + size_t(l) * cap, h.log_cap, reg_key(y, src.dd, L, L0 + l, t));
+        const int64_t b = table_find(h.slots + size_t(l) * cap, h.log_cap, group_key(y, src.dd, l, gc));
         if (b >= 0) {
           bidx[r] = b;
           level[r] = static_cast<uint8_t>(L0 + l);
