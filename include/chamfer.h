@@ -158,6 +158,15 @@ ch_status ch_ctx_sync(ch_ctx* ctx);
 int64_t ch_kernel_launches(void);
 /* Bytes currently held by the context's workspace arena. */
 int64_t ch_ctx_workspace_bytes(const ch_ctx* ctx);
+/* Budget of every pipeline wait inside the tensor-core screen (Fig. 1 step 3's
+ * l2 scan), in SM clock cycles; 0 (the default) means about 2 s.  A wait that
+ * runs out stops the kernel's work; the kernel still waits, within the default
+ * bound, for every copy and tensor-core operation it issued before it frees its
+ * memory, and the call returns CH_ETIMEOUT with the context still usable.  A
+ * small budget turns a stalled pipeline into that error quickly.  Applies to the
+ * context's later calls (and to the lanes of its batched calls).  CH_EINVAL for
+ * a negative value or a NULL context. */
+ch_status ch_ctx_set_wait_cycles(ch_ctx* ctx, int64_t cycles);
 
 /* ------------------------------------------------------------ point sets
  * mode 0: data is HOST memory, copied to the device;

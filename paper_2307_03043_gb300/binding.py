@@ -79,6 +79,7 @@ SIGNATURES = {
     "ch_last_error": (ctypes.c_char_p, [_vp]),
     "ch_ctx_sync": (_i32, [_vp]),
     "ch_ctx_workspace_bytes": (_i64, [_vp]),
+    "ch_ctx_set_wait_cycles": (_i32, [_vp, _i64]),
     "ch_kernel_launches": (_i64, []),
     "ch_set_create": (_i32, [_vp, _vp, ctypes.c_int, _i64, _i32, _i32, _vp, _P(_vp)]),
     "ch_set_destroy": (None, [_vp]),
@@ -191,6 +192,10 @@ def ch_ctx_sync(ctx):
 
 def ch_ctx_workspace_bytes(ctx) -> int:
     return int(lib().ch_ctx_workspace_bytes(ctx))
+
+
+def ch_ctx_set_wait_cycles(ctx, cycles: int):
+    _check(lib().ch_ctx_set_wait_cycles(ctx, cycles), "ch_ctx_set_wait_cycles", ctx)
 
 
 def ch_kernel_launches() -> int:

@@ -482,7 +482,7 @@ static void run_scan(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t T, 
   } else {
     ensure_norms(const_cast<ch_set*>(B), c->stream);
     launch_screen_l2(A, idx, T, B, sb->screen, static_cast<int>(R), sb->screen_work, m, argmin, status, c->sm_count,
-                     c->screen_chunk_sms, c->stream, timer);
+                     c->screen_chunk_sms, c->stream, timer, c->wait_cycles);
   }
 }
 
@@ -647,6 +647,16 @@ ch_status ch_ctx_sync(ch_ctx* c) {
 }
 
 int64_t ch_ctx_workspace_bytes(const ch_ctx* c) { return c ? static_cast<int64_t>(c->ws.cap) : 0; }
+
+ch_status ch_ctx_set_wait_cycles(ch_ctx* c, int64_t cycles) {
+  if (!c) return CH_EINVAL;
+  if (cycles < 0) {
+    c->err = "wait budget must be >= 0";
+    return CH_EINVAL;
+  }
+  c->wait_cycles = cycles;
+  return CH_OK;
+}
 
 ch_status ch_set_create(ch_ctx* c, const void* data, int mode, int64_t n, int32_t d, int32_t dtype,
                         const float* row_scales, ch_set** out) {
@@ -1036,7 +1046,10 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
   }
   // K lanes run at once, so each screen splits B for its share of the SMs only
   // (fewer chunks, fewer rerank candidates per sample)
-  for (int k = 0; k < K; ++k) c->lanes[k]->screen_chunk_sms = std::max(1, c->sm_count / K);
+  for (int k = 0; k < K; ++k) {
+    c->lanes[k]->screen_chunk_sms = std::max(1, c->sm_count / K);
+    c->lanes[k]->wait_cycles = c->wait_cycles;
+  }
   // the lazy set passes run here, on c's stream, so that no two lanes race on them
   for (int64_t i = 0; i < count; ++i) {
     if (st[i] != CH_OK) continue;

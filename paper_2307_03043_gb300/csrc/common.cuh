@@ -128,6 +128,7 @@ struct ch_ctx {
   bool own_stream = false;
   int sm_count = 0;
   int screen_chunk_sms = 0;  // SMs the screen's B split aims to fill (0: all); a batch lane's share
+  long long wait_cycles = 0;  // budget of the tensor-core screen's pipeline waits, SM cycles (0: about 2 s)
   chx::Arena ws;
   cudaMemPool_t pool = nullptr;  // stream-ordered pool for sets; keeps freed memory
   void* host_pin = nullptr;   // pinned page for small readbacks
@@ -426,7 +427,7 @@ bool screen_supported(int screen, const ch_set* A, const ch_set* B);
 size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int chunk_sms, int screen);
 void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R,
                       void* work, float* min_d, int64_t* argmin, uint32_t* status, int sm_count, int chunk_sms,
-                      cudaStream_t s, const KernelTimer& timer);
+                      cudaStream_t s, const KernelTimer& timer, long long wait_cycles = 0);
 
 // result block copied to the host at the end of a synchronising call
 struct ResBlock {

@@ -19,9 +19,11 @@
 // canonical binary32 distance on the columns each stands for, so the reported
 // minimum is exact whenever the true nearest point survives the screen.
 //
-// Every mbarrier wait is bounded (about 2 s of SM clock); on expiry the CTA
-// raises ST_TIMEOUT, stops issuing work, lets in-flight copies and MMAs drain
-// and frees its tensor memory before returning.
+// Every mbarrier wait is bounded (about 2 s of SM clock, or the context's own
+// budget); on expiry the CTA raises ST_TIMEOUT and stops issuing work.  Before
+// its tensor memory is freed and it returns, the producer waits (with the full
+// 2 s bound) for every copy it issued to land, and the MMA thread commits once
+// more and waits for that commit, so no copy or MMA is still in flight.
 #include "tma.cuh"
 
 namespace chx {
@@ -145,6 +147,7 @@ struct ScreenArgs {
   float* part_s;        // [chunks][T][R]
   int32_t* part_i;
   uint32_t* status;
+  long long wait_cycles;  // budget of each pipeline wait (SM cycles)
 };
 
 template <int SCREEN, bool STREAMQ>
@@ -169,7 +172,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* q_empty = q_full + 1;   // [1]
   uint64_t* acc_full = q_empty + 1; // [2]
   uint64_t* acc_empty = acc_full + 2;  // [2]
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* drain = acc_empty + 2;     // [1] the MMA thread's last commit
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -184,6 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], 32 * kEpiWarps);
     }
+    mbar_init(drain, 1);
     *abort_flag = 0;
     mbar_init_fence();
   }
@@ -198,28 +203,36 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
   const int n_items = args.row_tiles * args.chunks;
+  const long long budget = args.wait_cycles;
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0, qphase = 0;
+      // the stages (bit s) and the sample tile (q_issued) this thread has loaded,
+      // and the barrier phase of each one's last copy
+      uint32_t issued = 0, last_par = 0;
+      bool q_issued = false;
+      uint32_t q_par = 0;
       for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
         const int mt = item % args.row_tiles, ck = item / args.row_tiles;
         const int64_t b_begin = int64_t(ck) * args.chunk_len;
         const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
         constexpr int kEs = SCREEN == CH_SCREEN_TF32 ? 4 : SCREEN == CH_SCREEN_BF16 ? 2 : 1;
         if (!streamq) {
-          if (!mbar_wait(q_empty, qphase ^ 1, abort_flag)) break;
-          qphase ^= 1;
+          if (!mbar_wait(q_empty, qphase ^ 1, abort_flag, budget)) break;
           mbar_expect_tx(q_full, uint32_t(KB) * kBM * kKB);
           for (int kb = 0; kb < KB; ++kb)
             tma_load_2d(q_smem + size_t(kb) * kBM * kKB, &tmQ, kb * kKB / kEs, mt * kBM, q_full);
+          q_issued = true;
+          q_par = qphase;
+          qphase ^= 1;
         }
         bool ok = true;
         for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += kBN) {
           for (int kb = 0; kb < KB; ++kb) {
-            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, budget)) {
               ok = false;
               break;
             }
@@ -228,6 +241,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               tma_load_2d(q_smem + size_t(stage) * kBM * kKB, &tmQ, kb * kKB / kEs, mt * kBM, &full[stage]);
             tma_load_2d(b_smem + size_t(stage) * kBN * kKB, &tmB, kb * kKB / kEs, static_cast<int>(b0),
                         &full[stage]);
+            issued |= 1u << stage;
+            last_par = (last_par & ~(1u << stage)) | (phase << stage);
             if (++stage == S) {
               stage = 0;
               phase ^= 1;
@@ -235,6 +250,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      // drain: every copy issued has landed before the CTA's memory is released
+      // (at once after a normal run, whose copies the MMAs have consumed)
+      for (int st = 0; st < S; ++st)
+        if (issued >> st & 1u) mbar_wait_bounded(&full[st], last_par >> st & 1u);
+      if (q_issued) mbar_wait_bounded(q_full, q_par);
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
@@ -247,17 +267,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t b_begin = int64_t(ck) * args.chunk_len;
         const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
         if (!streamq) {
-          if (!mbar_wait(q_full, qphase, abort_flag)) break;
+          if (!mbar_wait(q_full, qphase, abort_flag, budget)) break;
           qphase ^= 1;
           tc_fence_after();
         }
         bool ok = true;
         for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += kBN) {
-          if (!mbar_wait(&acc_empty[acc], accphase ^ 1, abort_flag)) break;
+          if (!mbar_wait(&acc_empty[acc], accphase ^ 1, abort_flag, budget)) break;
           tc_fence_after();
           const uint32_t dtmem = tmem_base + acc * kBN;
           for (int kb = 0; kb < KB; ++kb) {
-            if (!mbar_wait(&full[stage], phase, abort_flag)) {
+            if (!mbar_wait(&full[stage], phase, abort_flag, budget)) {
               ok = false;
               break;
             }
@@ -281,6 +301,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!streamq) tc_commit(q_empty);
         if (!ok) break;
       }
+      // drain: this commit arrives once every MMA this thread issued has completed
+      tc_commit(drain);
+      mbar_wait_bounded(drain, 0);
     }
   } else {
     // ------------------------------------------------ epilogue: one sample row per thread
@@ -338,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
         prefetch_norms(b0 + kBN);  // next tile's, consumed one tile from now
-        const bool got = mbar_wait(&acc_full[acc], accphase, abort_flag);
+        const bool got = mbar_wait(&acc_full[acc], accphase, abort_flag, budget);
         if (!__all_sync(0xFFFFFFFFu, got)) {
           ok = false;
           break;
@@ -418,14 +441,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   // ------------------------------------------------ teardown
+  // (the producer and the MMA thread have drained their copies and MMAs above)
   __syncwarp();
-  if (*abort_flag) {
-    if (threadIdx.x == 0) atomicOr(args.status, ST_TIMEOUT);
-    // let in-flight copies and MMAs drain before the CTA's memory is released
-    const long long t0 = clock64();
-    while (clock64() - t0 < 20000000ll) {
-    }
-  }
+  if (*abort_flag && threadIdx.x == 0) atomicOr(args.status, ST_TIMEOUT);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -554,7 +572,7 @@ size_t screen_workspace(int64_t T, int64_t nB, int d, int R, int sm_count, int c
 
 void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, int screen, int R, void* work,
                       float* min_d, int64_t* argmin, uint32_t* status, int sm_count, int chunk_sms,
-                      cudaStream_t s, const KernelTimer& timer) {
+                      cudaStream_t s, const KernelTimer& timer, long long wait_cycles) {
   if (T == 0) return;
   const Plan p = make_plan(T, B->n, A->d, R, sm_count, chunk_sms, screen);
   const int es = static_cast<int>(elem_size(A->dtype));
@@ -591,6 +609,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
   a.part_s = part_s;
   a.part_i = part_i;
   a.status = status;
+  a.wait_cycles = wait_cycles > 0 ? wait_cycles : kTimeoutCycles;
 
 #define CHX_SCREEN_LAUNCH(SCR)                                                                              \
   do {                                                                                                      \

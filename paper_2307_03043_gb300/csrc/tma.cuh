@@ -36,13 +36,15 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; false if it expired or another role gave up (abort_flag set)
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+// bounded wait (budget: SM cycles); false if it expired or another role gave up
+// (abort_flag set)
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                          long long budget = kTimeoutCycles) {
   if (mbar_try(b, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(b, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kTimeoutCycles) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1;
       return false;
     }
