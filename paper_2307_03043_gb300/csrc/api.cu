@@ -334,8 +334,11 @@ static void bucket_keys(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_ha
 
 // CrudeNN (Fig. 2): embedding, scales, per-scale bucket tables of B, probes of A,
 // then D_a = d(a, b(a)).
+// With hashed_ready, cb->hA / hB already hold both sets' hashed spaces (the other
+// direction of a symmetric estimate made them) and the set passes are skipped.
 static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash_params* hp, CrudeBufs* cb,
-                      int64_t* bidx, uint8_t* level, float* D, uint32_t* status, uint32_t* maxD = nullptr) {
+                      int64_t* bidx, uint8_t* level, float* D, uint32_t* status, uint32_t* maxD = nullptr,
+                      bool hashed_ready = false) {
   const int L = static_cast<int>(hp->levels);
   const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
   cudaStream_t s = c->stream;
@@ -354,7 +357,7 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
     launch_cand_dist(A, B, hp->metric, cb->cand, k * W, bidx, D, maxD, s);
     return;
   }
-  run_hashed_pair(c, A, B, hp, &cb->hA, &cb->hB, status);
+  if (!hashed_ready) run_hashed_pair(c, A, B, hp, &cb->hA, &cb->hB, status);
   if (hp->group == CH_GROUP_SORT || hp->family == CH_FAMILY_SIMHASH) {
     bucket_keys(c, A, B, hp, cb, true, status);
     launch_sort_group(cb->keysA, A->n, cb->keysB, B->n, L, cb->sort_work, bidx, level, s);
@@ -916,15 +919,13 @@ static void check_estimate(ch_ctx* c, const ch_set* A, const ch_set* B, const ch
   *T = p->T > 0 ? p->T : default_T(A->n, B->n, p->eps);
 }
 
-// Enqueues the whole estimate of (A, B) on c's stream, carving c's workspace; the
-// result block lands in res_out (or in the workspace when null).  With events,
-// records stage boundaries in c->ev.  Returns the result block and the screen used.
-static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t T,
-                                  uint32_t R, ResBlock* res_out, bool events, int* screen_used,
-                                  ResBlock* host_out = nullptr, bool lone = false) {
+// Runs the estimate of (A, B) on c's stream in the buffers eb (carved from c's
+// workspace by the caller); with hashed_ready, eb.cb.hA / hB already hold both
+// sets' hashed spaces.
+static ResBlock* estimate_run(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t T,
+                              uint32_t R, EstBufs& eb, ResBlock* res_out, bool events, int* screen_used,
+                              ResBlock* host_out, bool lone, bool hashed_ready) {
   const int64_t nA = A->n;
-  EstBufs eb;
-  carve(c, [&](auto& lay) { take_estimate(lay, c, A, B, p, T, R, &eb); });
   if (res_out) eb.res = res_out;
   CrudeBufs& cb = eb.cb;
   SampleBufs& sb = eb.sb;
@@ -943,7 +944,7 @@ static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, c
     }
     launch_fill_ones(eb.D, nA, s);
   } else {
-    run_crude(c, A, B, &p->hash, &cb, eb.bidx, eb.level, eb.D, &res->status, sb.sw.maxD);
+    run_crude(c, A, B, &p->hash, &cb, eb.bidx, eb.level, eb.D, &res->status, sb.sw.maxD, hashed_ready);
   }
   if (events) CHX_CUDA(cudaEventRecord(c->ev[1], s));
   launch_weights(eb.D, nA, eb.w, sb.prefix, sb.sw, s, !uniform, true);
@@ -962,6 +963,17 @@ static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, c
   if (events) CHX_CUDA(cudaEventRecord(c->ev[4], s));
   if (screen_used) *screen_used = sc.screen;
   return res;
+}
+
+// Enqueues the whole estimate of (A, B) on c's stream, carving c's workspace; the
+// result block lands in res_out (or in the workspace when null).  With events,
+// records stage boundaries in c->ev.  Returns the result block and the screen used.
+static ResBlock* estimate_enqueue(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_est_params* p, int64_t T,
+                                  uint32_t R, ResBlock* res_out, bool events, int* screen_used,
+                                  ResBlock* host_out = nullptr, bool lone = false) {
+  EstBufs eb;
+  carve(c, [&](auto& lay) { take_estimate(lay, c, A, B, p, T, R, &eb); });
+  return estimate_run(c, A, B, p, T, R, eb, res_out, events, screen_used, host_out, lone, false);
 }
 
 // the workspace bytes estimate_enqueue carves for (A, B, p)
@@ -1130,23 +1142,56 @@ ch_status ch_estimate_sym(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_
   if (!c || !p || !eta) return CH_EINVAL;
   CHX_GUARD_BEGIN(c)
   CHX_CHECK(A && B, CH_EINVAL, "set NULL");
-  const ch_set* As[2] = {A, B};
-  const ch_set* Bs[2] = {B, A};
-  ch_est_params ps[2] = {*p, *p};
-  ps[1].sample_seed ^= 0x9E3779B97F4A7C15ull;
-  double e[2] = {0.0, 0.0};
-  ch_status st[2] = {CH_OK, CH_OK};
-  const ch_status r = ch_estimate_batch(c, 2, As, Bs, ps, e, st);
-  if (r != CH_OK) {
-    if (st[0] != CH_OK || st[1] != CH_OK) {
-      c->err = st[0] != CH_OK ? "direction (A, B) failed" : "direction (B, A) failed";
-      return st[0] != CH_OK ? st[0] : st[1];
+  ch_est_params pb = *p;  // the (B, A) direction: its own draws
+  pb.sample_seed ^= 0x9E3779B97F4A7C15ull;
+  const bool shared = p->sampling != CH_SAMPLING_UNIFORM && !crude_kw(&p->hash) && p->hash.group == CH_GROUP_HASH &&
+                      p->hash.family != CH_FAMILY_SIMHASH && A->n > 0 && B->n > 0;
+  if (!shared) {
+    // the variants without shared set passes: the two directions as a batch of two
+    const ch_set* As[2] = {A, B};
+    const ch_set* Bs[2] = {B, A};
+    ch_est_params ps[2] = {*p, pb};
+    double e[2] = {0.0, 0.0};
+    ch_status st[2] = {CH_OK, CH_OK};
+    const ch_status r = ch_estimate_batch(c, 2, As, Bs, ps, e, st);
+    if (r != CH_OK) {
+      if (st[0] != CH_OK || st[1] != CH_OK) {
+        c->err = st[0] != CH_OK ? "direction (A, B) failed" : "direction (B, A) failed";
+        return st[0] != CH_OK ? st[0] : st[1];
+      }
+      return r;
     }
-    return r;
+    *eta = e[0] + e[1];
+    if (eta_ab) *eta_ab = e[0];
+    if (eta_ba) *eta_ba = e[1];
+    return CH_OK;
   }
-  *eta = e[0] + e[1];
-  if (eta_ab) *eta_ab = e[0];
-  if (eta_ba) *eta_ba = e[1];
+  // CH(A, B) + CH(B, A) sharing the set passes: both directions use the same hash
+  // parameters, so A's and B's hashed spaces (the l2 embedding under the one
+  // Gaussian matrix, or the rows and boxes for l1), the joint box and the scales
+  // are the same; they are computed once, then each direction builds its own
+  // bucket tables, draws and scans.
+  int64_t Tab, Tba;
+  uint32_t R, Rb;
+  check_estimate(c, A, B, p, &Tab, &R);
+  check_estimate(c, B, A, &pb, &Tba, &Rb);
+  CHX_CUDA(cudaSetDevice(c->device));
+  EstBufs e1, e2;
+  carve(c, [&](auto& lay) {
+    take_estimate(lay, c, A, B, p, Tab, R, &e1);
+    take_estimate(lay, c, B, A, &pb, Tba, Rb, &e2);
+  });
+  ResBlock* h = static_cast<ResBlock*>(c->host_pin);  // [0]: (A, B), [1]: (B, A)
+  estimate_run(c, A, B, p, Tab, R, e1, nullptr, false, nullptr, h, true, false);
+  e2.cb.hA = e1.cb.hB;
+  e2.cb.hB = e1.cb.hA;
+  estimate_run(c, B, A, &pb, Tba, Rb, e2, nullptr, false, nullptr, h + 1, true, true);
+  CHX_CUDA(cudaStreamSynchronize(c->stream));
+  check_result(h);
+  check_result(h + 1);
+  *eta = h[0].eta + h[1].eta;
+  if (eta_ab) *eta_ab = h[0].eta;
+  if (eta_ba) *eta_ba = h[1].eta;
   return CH_OK;
   CHX_GUARD_END
 }

@@ -506,7 +506,30 @@ def test_symmetric_estimate_matches_oracle(ctx, pair_factory, metric, uniform):
     tot_o, ab_o, ba_o = oracle.estimate_sym(A, B, metric, 3, 4, T=T, uniform=uniform)
     assert abs(ab / ab_o - 1) < 1e-5 and abs(ba / ba_o - 1) < 1e-5
     assert tot == ab + ba
+    # each direction equals the one-sided estimate exactly (importance sampling
+    # shares the set passes between the directions; that changes no bit)
     assert ab == ch.ch_estimate(ctx, p.sA, p.sB, prm)
+    prm_ba = ch.est_params(metric, 10, 16, None, 3, T=T, sample_seed=4 ^ 0x9E3779B97F4A7C15, screen=ch.CH_SCREEN_EXACT,
+                           sampling=ch.CH_SAMPLING_UNIFORM if uniform else ch.CH_SAMPLING_IMPORTANCE)
+    assert ba == ch.ch_estimate(ctx, p.sB, p.sA, prm_ba)
+
+
+@pytest.mark.parametrize("n_a,n_b,d", [(100_000, 100_000, 128), (60_000, 300_000, 16)])
+def test_symmetric_estimate_shared_passes_large(ctx, pair_factory, n_a, n_b, d):
+    """The symmetric form on the l2 path with the tensor-core screen: the 100k
+    mixture (one scale group, the two projections side by side) and |B| = 300k
+    (two scale groups, the second in reverse for one direction): each direction
+    equals its one-sided estimate bit for bit and the oracle's within 1e-5
+    (T = 400 draws per direction)."""
+    A, B = workloads.gaussian_mixture(n_a, n_b, d, 43, clusters=40)
+    p = pair_factory(A, B)
+    prm = ch.est_params(L2, 10, 16, None, 8, T=400, sample_seed=9)
+    tot, ab, ba = ch.ch_estimate_sym(ctx, p.sA, p.sB, prm)
+    assert ab == ch.ch_estimate(ctx, p.sA, p.sB, prm)
+    prm_ba = ch.est_params(L2, 10, 16, None, 8, T=400, sample_seed=9 ^ 0x9E3779B97F4A7C15)
+    assert ba == ch.ch_estimate(ctx, p.sB, p.sA, prm_ba)
+    tot_o, ab_o, ba_o = oracle.estimate_sym(A, B, L2, 8, 9, T=400)
+    assert abs(ab / ab_o - 1) < 1e-5 and abs(ba / ba_o - 1) < 1e-5
 
 
 def test_estimate_edge_cases(ctx, pair_factory):
