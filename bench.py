@@ -44,6 +44,7 @@ EPS = 0.1
 LEVELS = 10
 PROJ = 16
 FLUSH_BYTES = 256 << 20  # > 126 MB L2
+SERVE_HASH_SEED = 7      # the serving index's hash functions (fixed per server)
 DTYPE = "f32"            # storage type of the sets ("f32", "bf16", "fp8")
 CONFIG = "mid"
 DEFAULT_CONFIG = "precision"
@@ -68,9 +69,10 @@ WORKLOADS = {
                         "per T, on the 100k x 100k d=128 mixture and on two 100k d=16 Gaussian clouds with one "
                         "far outlier in A (l2)"),
     "serving": dict(n=0, d=768, dtype="f32",
-                    desc="serving: resident sets of log-uniform 1k-500k points, d uniform in {3,128,768}, fp32 or "
-                         "bf16 uniform, l2, eps=0.1; requests pick a (d, type) pool and two of its sets; a closed "
-                         "burst measures saturation, then Poisson arrivals at 0.5/0.8/0.95x of it"),
+                    desc="serving: resident sets of log-uniform 1k-500k points (l2 embeddings resident under the "
+                         "server's hash seed), d uniform in {3,128,768}, fp32 or bf16 uniform, l2, eps=0.1; requests "
+                         "pick a (d, type) pool and two of its sets; a closed burst measures saturation, then Poisson "
+                         "arrivals at 0.5/0.8/0.95x of it"),
 }
 BATCHED = ("batched", "batched_d64")
 
@@ -247,6 +249,10 @@ def serving_sample(ch, ctx, rank, n_req=200, seed=7):
     from paper_2307_03043_gb300 import workloads
     rng = np.random.default_rng(seed + rank)
     srv = ch.ch_serve_create(ctx, 32 << 30, 8, 4096)
+    # an index: the sets' l2 embeddings under one hash seed stay resident; each
+    # request draws its own samples
+    index = ch.hash_params(ch.CH_L2, LEVELS, PROJ, None, SERVE_HASH_SEED)
+    ch.ch_serve_index(srv, index)
     by_dim = {3: [], 128: []}
     sizes = workloads.log_uniform_sizes(12, 1000, 100_000, seed + rank)
     for i, n in enumerate(sizes):
@@ -257,7 +263,7 @@ def serving_sample(ch, ctx, rank, n_req=200, seed=7):
     def req(k):
         pool = by_dim[3] if rng.random() < 0.5 else by_dim[128]
         a, b = pool[rng.integers(len(pool))], pool[rng.integers(len(pool))]
-        p = ch.est_params(ch.CH_L2, LEVELS, PROJ, None, k, eps=EPS, sample_seed=k)
+        p = ch.est_params(ch.CH_L2, LEVELS, PROJ, None, SERVE_HASH_SEED, eps=EPS, sample_seed=k)
         st, t = ch.ch_serve_submit(srv, a[0], b[0], p)
         return st, t, a[1] + b[1]
 
@@ -268,6 +274,7 @@ def serving_sample(ch, ctx, rank, n_req=200, seed=7):
     rate = len(burst) / (time.perf_counter() - t0)
     ch.ch_serve_destroy(srv)
     srv = ch.ch_serve_create(ctx, 32 << 30, 8, 4096)
+    ch.ch_serve_index(srv, index)
     by_dim = {3: [], 128: []}
     for i, n in enumerate(sizes):
         d = 3 if i % 2 == 0 else 128
@@ -290,8 +297,8 @@ def serving_sample(ch, ctx, rank, n_req=200, seed=7):
     wall = time.perf_counter() - t0
     s = ch.ch_serve_stats_get(srv)
     ch.ch_serve_destroy(srv)
-    return {"workload": "12 resident sets, log-uniform 1k-100k points, d in {3,128}, fp32, l2, eps=0.1, "
-                        "Poisson arrivals at 0.8x saturation, 8 slots",
+    return {"workload": "12 resident sets (l2 embeddings resident under the server's hash seed), log-uniform "
+                        "1k-100k points, d in {3,128}, fp32, l2, eps=0.1, Poisson arrivals at 0.8x saturation, 8 slots",
             "requests": n_req, "completed": ok, "p50_us": s.p50_us, "p99_us": s.p99_us,
             "saturation_rps": rate, "offered_rps": 0.8 * rate, "throughput_rps": ok / wall,
             "pts_per_s": pts / wall, "peak_bytes": s.peak_bytes}
@@ -482,6 +489,7 @@ def run_serving(args, ch, ctx, torch):
     rng = np.random.default_rng(11)
     total_req = args.serve_requests if args.serve_requests > 0 else 20_000
     srv = ch.ch_serve_create(ctx, 48 << 30, 8, 8192)
+    ch.ch_serve_index(srv, ch.hash_params(ch.CH_L2, LEVELS, PROJ, None, SERVE_HASH_SEED))
     pools = {}
     k = 0
     for d in (3, 128, 768):
@@ -501,7 +509,7 @@ def run_serving(args, ch, ctx, torch):
     def req(seed):
         pool = pools[keys[rng.integers(len(keys))]]
         a, b = pool[rng.integers(len(pool))], pool[rng.integers(len(pool))]
-        p = ch.est_params(ch.CH_L2, LEVELS, PROJ, None, seed, eps=EPS, sample_seed=seed)
+        p = ch.est_params(ch.CH_L2, LEVELS, PROJ, None, SERVE_HASH_SEED, eps=EPS, sample_seed=seed)
         st, t = ch.ch_serve_submit(srv, a[0], b[0], p)
         return st, t, a[1] + b[1]
 

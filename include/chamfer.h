@@ -188,6 +188,17 @@ void ch_set_destroy(ch_set* set);
  * concurrently (every call only requires the set to live on the context's
  * device). */
 ch_status ch_set_prepare(ch_ctx* ctx, ch_set* set);
+/* Keeps the set's l2 embedding under hp resident (the k = proj_dim wide Gaussian
+ * projection of the hashed space, Appendix A.2's l2 family, and its bounding
+ * box): every later l2 call whose hash parameters have the same hash_seed and
+ * proj_dim reads it instead of projecting the set again (k x W structures other
+ * than the first still project under their own seeds), with the same results
+ * bit for bit.  The embedding (n * proj_dim binary32 plus its boxes) is owned by
+ * the set and freed with it; a second call with other parameters replaces it.
+ * Synchronises (reports non-finite data as CH_EINVAL).  For hp->metric = CH_L1
+ * it does nothing: the l1 family hashes the rows themselves.  Not thread-safe
+ * against calls that read the set at the same time. */
+ch_status ch_set_embed(ch_ctx* ctx, ch_set* set, const ch_hash_params* hp);
 int64_t ch_set_size(const ch_set* set);
 int32_t ch_set_dim(const ch_set* set);
 
@@ -315,6 +326,13 @@ typedef struct {
 } ch_serve_stats;
 
 ch_status ch_serve_create(ch_ctx* ctx, const ch_serve_config* cfg, ch_server** out);
+/* Makes the server an index under hp: every set registered from now on keeps
+ * its l2 embedding under hp resident (ch_set_embed), so requests whose hash
+ * parameters share hp's hash_seed and proj_dim skip the projection of both sets
+ * (their results are the same bits as without the index).  Call it before the
+ * first registration; CH_EBUSY once sets are registered, CH_EINVAL for invalid
+ * hash parameters. */
+ch_status ch_serve_index(ch_server* s, const ch_hash_params* hp);
 /* Registers a point set (same arguments as ch_set_create); *set_id identifies it. */
 ch_status ch_serve_register(ch_server* s, const void* data, int mode, int64_t n, int32_t d, int32_t dtype,
                             const float* row_scales, uint64_t* set_id);

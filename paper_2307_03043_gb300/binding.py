@@ -98,6 +98,8 @@ SIGNATURES = {
                                _P(ctypes.c_double)]),
     "ch_exact": (_i32, [_vp, _vp, _vp, _i32, _i32, _P(ctypes.c_double), _vp]),
     "ch_serve_create": (_i32, [_vp, _P(ch_serve_config), _P(_vp)]),
+    "ch_serve_index": (_i32, [_vp, _P(ch_hash_params)]),
+    "ch_set_embed": (_i32, [_vp, _vp, _P(ch_hash_params)]),
     "ch_serve_register": (_i32, [_vp, _vp, ctypes.c_int, _i64, _i32, _i32, _vp, _P(_u64)]),
     "ch_serve_submit": (_i32, [_vp, _u64, _u64, _P(ch_est_params), _P(_u64)]),
     "ch_serve_poll": (_i32, [_vp, _u64, _P(ctypes.c_double), _P(_i32)]),
@@ -307,6 +309,14 @@ def ch_serve_create(ctx, hbm_budget_bytes: int, max_slots: int = 8, max_queue: i
     cfg = ch_serve_config(hbm_budget_bytes, max_slots, max_queue)
     _check(lib().ch_serve_create(ctx, ctypes.byref(cfg), ctypes.byref(h)), "ch_serve_create", ctx)
     return h
+
+
+def ch_serve_index(srv, hp: ch_hash_params):
+    _check(lib().ch_serve_index(srv, ctypes.byref(hp)), "ch_serve_index")
+
+
+def ch_set_embed(ctx, s, hp: ch_hash_params):
+    _check(lib().ch_set_embed(ctx, s, ctypes.byref(hp)), "ch_set_embed", ctx)
 
 
 def ch_serve_register(srv, data, mode: int, n: int, d: int, dtype: int = CH_F32, row_scales=None) -> int:

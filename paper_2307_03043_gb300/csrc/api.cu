@@ -138,6 +138,14 @@ struct Hashed {
 
 static int proj_pad(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64; }
 
+// k x W CrudeNN (Section 3's large-scale variant) is asked for
+static bool crude_kw(const ch_hash_params* hp) { return hp->window > 1 || hp->repeats > 1; }
+
+// the set's resident embedding serves hp (made by ch_set_embed under the same seed and width)
+static bool resident_hashed(const ch_set* X, const ch_hash_params* hp) {
+  return hp->metric == CH_L2 && X->hs.valid && X->hs.seed == hp->hash_seed && X->hs.k == static_cast<int>(hp->proj_dim);
+}
+
 template <class L>
 static void take_hashed(L& lay, const ch_set* X, const ch_hash_params* hp, Hashed* h) {
   if (hp->metric == CH_L1) {
@@ -148,8 +156,11 @@ static void take_hashed(L& lay, const ch_set* X, const ch_hash_params* hp, Hashe
     h->boxY = nullptr;
   } else {
     const int k = static_cast<int>(hp->proj_dim);
-    h->Y = lay.template take<float>(size_t(X->n) * k + 4 + size_t(proj_pad(k)) * X->d);
-    h->boxY = lay.template take<uint32_t>(size_t(2) * k * kMaxBoxParts);
+    // no buffers where the set's resident embedding serves every pass of the call
+    // (k x W structures other than the first project under their own seeds)
+    const bool resident = resident_hashed(X, hp) && !crude_kw(hp);
+    h->Y = resident ? nullptr : lay.template take<float>(size_t(X->n) * k + 4 + size_t(proj_pad(k)) * X->d);
+    h->boxY = resident ? nullptr : lay.template take<uint32_t>(size_t(2) * k * kMaxBoxParts);
     h->src = HashSrc{h->Y, CH_F32, X->n, k, nullptr};
     h->box = h->boxY;
     h->box_parts = 1;  // set by the projection
@@ -158,12 +169,22 @@ static void take_hashed(L& lay, const ch_set* X, const ch_hash_params* hp, Hashe
 
 // the hashed space's pass over a set: the l2 projection (which also yields
 // |x|^2 and the finite check) or, for l1, the ingest pass (box of x)
+// The hashed space h reads: the set's resident embedding where it serves hp,
+// else the workspace buffers h->Y / h->boxY (which stay the call's own, so a
+// later pass under another seed never writes into the resident one).
 static void run_hashed(ch_ctx* c, const ch_set* X, const ch_hash_params* hp, Hashed* h, uint32_t* status) {
-  if (hp->metric == CH_L2)
+  if (resident_hashed(X, hp)) {
+    h->src = HashSrc{X->hs.Y, CH_F32, X->n, X->hs.k, nullptr};
+    h->box = X->hs.box;
+    h->box_parts = X->hs.parts;
+  } else if (hp->metric == CH_L2) {
+    h->src = HashSrc{h->Y, CH_F32, X->n, static_cast<int>(hp->proj_dim), nullptr};
+    h->box = h->boxY;
     h->box_parts = launch_project(X, hp->hash_seed, static_cast<int>(hp->proj_dim), h->Y, h->boxY, status,
                                   c->sm_count, c->stream);
-  else
+  } else {
     ensure_ingest(const_cast<ch_set*>(X), c->stream);
+  }
 }
 
 // the context's side stream and its fork / join events, made on first use
@@ -185,13 +206,17 @@ static void run_hashed_pair(ch_ctx* c, const ch_set* A, const ch_set* B, const c
                             Hashed* hB, uint32_t* status) {
   const int64_t wA = A->n * A->d, wB = B->n * B->d;
   const bool side_by_side = std::min(wA, wB) >= (int64_t(1) << 21) && std::max(wA, wB) <= (int64_t(1) << 26);
-  if (hp->metric != CH_L2 || c->sm_count < 2 || !side_by_side) {
+  if (hp->metric != CH_L2 || c->sm_count < 2 || !side_by_side || resident_hashed(A, hp) || resident_hashed(B, hp)) {
     run_hashed(c, A, hp, hA, status);
     run_hashed(c, B, hp, hB, status);
     return;
   }
   ensure_side(c);
   const int k = static_cast<int>(hp->proj_dim);
+  hA->src = HashSrc{hA->Y, CH_F32, A->n, k, nullptr};
+  hA->box = hA->boxY;
+  hB->src = HashSrc{hB->Y, CH_F32, B->n, k, nullptr};
+  hB->box = hB->boxY;
   const int half = c->sm_count / 2;
   CHX_CUDA(cudaEventRecord(c->fork_ev, c->stream));
   CHX_CUDA(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
@@ -257,8 +282,6 @@ struct CrudeBufs {
   int32_t* cand;  // k x W: [nA][k W] candidate indices
 };
 
-// k x W CrudeNN (Section 3's large-scale variant) is asked for
-static bool crude_kw(const ch_hash_params* hp) { return hp->window > 1 || hp->repeats > 1; }
 static int kw_k(const ch_hash_params* hp) { return hp->repeats ? static_cast<int>(hp->repeats) : 1; }
 static int kw_w(const ch_hash_params* hp) { return hp->window ? static_cast<int>(hp->window) : 1; }
 // hash seed of structure r (r = 0: the base structure)
@@ -321,8 +344,8 @@ static void bucket_keys(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_ha
   if (hp->family == CH_FAMILY_SIMHASH) {
     const int K = static_cast<int>(hp->proj_dim);
     if (report_top) CHX_CUDA(cudaMemsetAsync(cb->e_top, 0, sizeof(int32_t), s));  // no scales: reported as 0
-    launch_simhash_keys(cb->hB.Y, B->n, K, L, hp->hash_seed, cb->keysB, s);
-    launch_simhash_keys(cb->hA.Y, A->n, K, L, hp->hash_seed, cb->keysA, s);
+    launch_simhash_keys(static_cast<const float*>(cb->hB.src.base), B->n, K, L, hp->hash_seed, cb->keysB, s);
+    launch_simhash_keys(static_cast<const float*>(cb->hA.src.base), A->n, K, L, hp->hash_seed, cb->keysA, s);
     return;
   }
   const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
@@ -724,7 +747,41 @@ void ch_set_destroy(ch_set* X) {
   cudaSetDevice(c->device);
   if (X->owned && X->data) cudaFreeAsync(X->data, c->stream);
   if (X->norms) cudaFreeAsync(X->norms, c->stream);
+  if (X->hs.Y) cudaFreeAsync(X->hs.Y, c->stream);
   delete X;
+}
+
+ch_status ch_set_embed(ch_ctx* c, ch_set* X, const ch_hash_params* hp) {
+  if (!c || !X || !hp) return CH_EINVAL;
+  CHX_GUARD_BEGIN(c)
+  check_hash(hp);
+  CHX_CHECK(X->ctx->device == c->device, CH_EINVAL, "set lives on another device");
+  if (hp->metric != CH_L2) return CH_OK;  // l1 hashes the rows themselves; their box is cached with the set
+  if (resident_hashed(X, hp)) return CH_OK;
+  CHX_CUDA(cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const int k = static_cast<int>(hp->proj_dim);
+  // the projection's layout: [n][k] plus the width-padded Gaussian-matrix tail, then the partial boxes
+  const size_t ybytes = ((size_t(X->n) * k + 4 + size_t(proj_pad(k)) * X->d) * 4 + 255) & ~size_t(255);
+  const size_t bbytes = size_t(2) * k * kMaxBoxParts * 4;
+  char* mem = nullptr;
+  CHX_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&mem), ybytes + bbytes, c->pool, s));
+  if (X->hs.Y) CHX_CUDA(cudaFreeAsync(X->hs.Y, s));  // an embedding under other parameters
+  X->hs.valid = false;
+  X->hs.Y = reinterpret_cast<float*>(mem);
+  X->hs.box = reinterpret_cast<uint32_t*>(mem + ybytes);
+  ResBlock* res = nullptr;
+  carve(c, [&](auto& lay) { res = lay.template take<ResBlock>(1); });
+  CHX_CUDA(cudaMemsetAsync(res, 0, sizeof(ResBlock), s));
+  X->hs.parts = launch_project(X, hp->hash_seed, k, X->hs.Y, X->hs.box, &res->status, c->sm_count, s);
+  launch_k(k_collect, 1, 32, 0, s, res, X->status, nullptr, nullptr, nullptr, nullptr, nullptr);
+  launch_check("collect");
+  finish(c, res, static_cast<ResBlock*>(c->host_pin));
+  X->hs.seed = hp->hash_seed;
+  X->hs.k = k;
+  X->hs.valid = true;
+  return CH_OK;
+  CHX_GUARD_END
 }
 
 ch_status ch_set_prepare(ch_ctx* c, ch_set* X) {

@@ -112,14 +112,14 @@ struct Arena {
 
 }  // namespace chx
 
-// hashed representation of a set for one (metric, seed, k)
+// a set's resident l2 embedding under one (hash seed, width k), made by ch_set_embed
 struct chx_hashed {
   bool valid = false;
-  int metric = 0;
   uint64_t seed = 0;
   int k = 0;
-  float* Y = nullptr;         // l2: projection [n][k]; l1: unused (the set's own data)
-  uint32_t* box = nullptr;    // ordered-encoded [2][dd]: min then max per hashed coordinate
+  float* Y = nullptr;         // projection [n][k] (+ the width-padded Gaussian-matrix tail), owned by the set
+  uint32_t* box = nullptr;    // ordered-encoded partial boxes [parts][2][k] of Y
+  int parts = 0;
 };
 
 struct ch_ctx {

@@ -2,7 +2,8 @@
 // point sets (host C++; the device work is ch_estimate on per-slot streams).
 //
 //  * Sets are registered once, prepared eagerly (bounding box, |x|^2, finite
-//    check) and never written again, so every slot may read them at once.
+//    check; with ch_serve_index also the l2 embedding under the index's hash
+//    parameters) and never written again, so every slot may read them at once.
 //  * Each request's device footprint is the exact workspace ch_estimate needs
 //    for its sizes and parameters; a scheduler thread admits queued requests in
 //    arrival order while a slot is free and the admitted footprints stay within
@@ -84,6 +85,8 @@ struct ch_server {
   std::vector<double> lat_us;
   int64_t completed = 0, failed = 0, rejected = 0, launched = 0;
   Clock::time_point t_create;
+  bool indexed = false;  // registered sets keep their l2 embedding under index_hp resident
+  ch_hash_params index_hp{};
 };
 
 namespace {
@@ -224,6 +227,7 @@ ch_status ch_serve_register(ch_server* s, const void* data, int mode, int64_t n,
   ch_status st = ch_set_create(s->main, data, mode, n, d, dtype, row_scales, &X);
   if (st != CH_OK) return st;
   st = ch_set_prepare(s->main, X);
+  if (st == CH_OK && s->indexed) st = ch_set_embed(s->main, X, &s->index_hp);
   if (st != CH_OK) {
     ch_set_destroy(X);
     return st;
@@ -231,6 +235,18 @@ ch_status ch_serve_register(ch_server* s, const void* data, int mode, int64_t n,
   std::lock_guard<std::mutex> lk(s->mu);
   *set_id = s->next_set++;
   s->sets[*set_id] = X;
+  return CH_OK;
+}
+
+ch_status ch_serve_index(ch_server* s, const ch_hash_params* hp) {
+  if (!s || !hp) return CH_EINVAL;
+  if (hp->metric != CH_L1 && hp->metric != CH_L2) return CH_EINVAL;
+  if (hp->proj_dim < 1 || hp->proj_dim > 64) return CH_EINVAL;
+  std::lock_guard<std::mutex> reg(s->reg_mu);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->sets.empty()) return CH_EBUSY;
+  s->indexed = true;
+  s->index_hp = *hp;
   return CH_OK;
 }
 

@@ -118,7 +118,7 @@ def test_binding_structs_match_the_c_layout(tmp_path):
 
 NULL_CTX_CALLS = ["ch_ctx_sync", "ch_set_create", "ch_set_prepare", "ch_top_exp", "ch_hash_keys", "ch_crude_nn",
                   "ch_sample", "ch_sampled_nn", "ch_estimate", "ch_estimate_batch", "ch_estimate_sym", "ch_exact",
-                  "ch_ctx_set_wait_cycles"]
+                  "ch_ctx_set_wait_cycles", "ch_set_embed"]
 
 
 @pytest.mark.parametrize("name", NULL_CTX_CALLS)

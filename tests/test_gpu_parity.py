@@ -607,3 +607,47 @@ def test_mid_workload_sampled_parity(ctx, pair_factory):
     eta = ch.ch_estimate(ctx, p.sA, p.sB, ch.est_params(L2, eps=0.1, hash_seed=0, sample_seed=1, T=512))
     eta_o = oracle.estimate(A, B, L2, 0, 1, T=512)
     assert abs(eta / eta_o - 1) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_resident_embedding_changes_no_bit(ctx, pair_factory, dtype):
+    """ch_set_embed keeps a set's l2 embedding resident (Appendix A.2's l2
+    family under one hash seed and width): CrudeNN, the estimate, the symmetric
+    form, k x W and SimHash then read it instead of projecting, with the same
+    results bit for bit; other seeds still project; l1 ignores it."""
+    A, B = workloads.gaussian_mixture(6000, 9000, 48, 51, clusters=9)
+    if dtype == "bf16":
+        A = workloads.bf16_bits_to_f32(workloads.to_bf16_bits(A))
+        B = workloads.bf16_bits_to_f32(workloads.to_bf16_bits(B))
+        hA, hB = workloads.to_bf16_bits(A), workloads.to_bf16_bits(B)
+        sA = ch.ch_set_create(ctx, hA, 0, A.shape[0], 48, ch.CH_BF16)
+        sB = ch.ch_set_create(ctx, hB, 0, B.shape[0], 48, ch.CH_BF16)
+    else:
+        sA = ch.ch_set_create(ctx, A, 0, A.shape[0], 48)
+        sB = ch.ch_set_create(ctx, B, 0, B.shape[0], 48)
+    try:
+        prms = [ch.est_params(L2, 10, 16, None, 12, T=900, sample_seed=2),
+                ch.est_params(L2, 10, 16, None, 12, T=900, sample_seed=2, repeats=2, window=3),
+                ch.est_params(L2, 10, 16, None, 12, T=900, sample_seed=2, family=ch.CH_FAMILY_SIMHASH),
+                ch.est_params(L2, 10, 16, None, 13, T=900, sample_seed=2),
+                ch.est_params(L1, 10, 16, None, 12, T=900, sample_seed=2)]
+        before = [ch.ch_estimate(ctx, sA, sB, p) for p in prms]
+        sym_before = ch.ch_estimate_sym(ctx, sA, sB, prms[0])
+        bidx0 = torch.zeros(6000, dtype=torch.int64, device="cuda")
+        D0 = torch.zeros(6000, dtype=torch.float32, device="cuda")
+        ch.ch_crude_nn(ctx, sA, sB, ch.hash_params(L2, 10, 16, None, 12), bidx0, D0)
+        for s_ in (sA, sB):
+            ch.ch_set_embed(ctx, s_, ch.hash_params(L2, 10, 16, None, 12))
+            ch.ch_set_embed(ctx, s_, ch.hash_params(L1, 10, 16, None, 12))  # l1: nothing to keep
+        after = [ch.ch_estimate(ctx, sA, sB, p) for p in prms]
+        assert after == before
+        assert ch.ch_estimate_sym(ctx, sA, sB, prms[0]) == sym_before
+        bidx1 = torch.zeros(6000, dtype=torch.int64, device="cuda")
+        D1 = torch.zeros(6000, dtype=torch.float32, device="cuda")
+        ch.ch_crude_nn(ctx, sA, sB, ch.hash_params(L2, 10, 16, None, 12), bidx1, D1)
+        assert torch.equal(bidx0, bidx1) and torch.equal(D0.view(torch.int32), D1.view(torch.int32))
+        r = oracle.crude_nn(A, B, L2, hash_seed=12)
+        assert np.array_equal(bidx1.cpu().numpy(), r["bidx"])
+    finally:
+        ch.ch_set_destroy(sA)
+        ch.ch_set_destroy(sB)

@@ -155,3 +155,41 @@ def test_register_rejects_non_finite(ctx):
         ch.ch_serve_register(srv, A, 0, 10, 8)
     assert ei.value.status == ch.CH_EINVAL
     ch.ch_serve_destroy(srv)
+
+
+def test_indexed_server_same_bits_as_plain_estimates(ctx):
+    """A server made an index (ch_serve_index): every registered set keeps its
+    l2 embedding under the index's hash seed resident; requests with that seed
+    skip both projections, others project as before.  Every result, alone or
+    mixed, is the plain ch_estimate's bit for bit; registering before indexing is
+    refused with CH_EBUSY."""
+    data = _sets(5, seed=3)
+    srv = _server(ctx)
+    hp = ch.hash_params(ch.CH_L2, 10, 16, None, 77)
+    ch.ch_serve_index(srv, hp)
+    ids = [ch.ch_serve_register(srv, X, 0, X.shape[0], 64) for X in data]
+    with pytest.raises(ch.ChamferError) as ei:
+        ch.ch_serve_index(srv, hp)
+    assert ei.value.status == ch.CH_EBUSY
+    rng = np.random.default_rng(5)
+    jobs = []
+    for k in range(20):
+        a, b = rng.integers(0, len(ids), 2)
+        seed = 77 if k % 4 else 1000 + k  # most on the index's seed, some off it
+        p = ch.est_params(ch.CH_L2, 10, 16, None, seed, eps=0.2, sample_seed=300 + k)
+        st, t = ch.ch_serve_submit(srv, ids[a], ids[b], p)
+        assert st == ch.CH_OK
+        jobs.append((t, a, b, p))
+    got = {}
+    for t, a, b, p in jobs:
+        st, eta, rs = ch.ch_serve_wait(srv, t, 60000)
+        assert st == ch.CH_OK and rs == ch.CH_OK
+        got[t] = eta
+    ch.ch_serve_destroy(srv)
+    c2 = ch.ch_ctx_create(0, None)
+    sets = [ch.ch_set_create(c2, X, 0, X.shape[0], 64) for X in data]
+    for t, a, b, p in jobs:
+        assert ch.ch_estimate(c2, sets[a], sets[b], p) == got[t]
+    for x in sets:
+        ch.ch_set_destroy(x)
+    ch.ch_ctx_destroy(c2)
