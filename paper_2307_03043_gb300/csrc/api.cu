@@ -14,7 +14,11 @@
 using namespace chx;
 
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <thread>
+#include <tuple>
+#include <unordered_map>
 
 namespace chx {
 
@@ -958,6 +962,111 @@ ch_status ch_sampled_nn(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t 
 
 namespace chx {
 
+// ------------------------------------------------------------------ batched small scans
+// Chunk length of the batched small scan, tuned per (storage type, metric, d,
+// size class of B) by timing candidate lengths on the first batch that needs it
+// (every candidate computes the same minima, so the tuning runs are the batch's
+// own scans); the choice is kept for the process.
+struct ScanTuneKey {
+  int dtype, metric, d, cls;
+  bool operator==(const ScanTuneKey& o) const {
+    return dtype == o.dtype && metric == o.metric && d == o.d && cls == o.cls;
+  }
+};
+struct ScanTuneHash {
+  size_t operator()(const ScanTuneKey& k) const {
+    return (size_t(k.dtype) * 1315423911u) ^ (size_t(k.metric) << 8) ^ (size_t(k.d) << 16) ^ (size_t(k.cls) << 24);
+  }
+};
+static std::mutex g_tune_mu;
+static std::unordered_map<ScanTuneKey, int64_t, ScanTuneHash> g_tuned;
+constexpr int64_t kScanChunkCandidates[] = {2048, 4096, 8192, 16384, 32768};
+
+static int size_class(int64_t n) { return ceil_log2_i64(std::max<int64_t>(n, 1)); }
+
+static int64_t tuned_chunk(const ScanTuneKey& k) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(k);
+  return it == g_tuned.end() ? 0 : it->second;
+}
+
+static void run_small_scans(ch_ctx* c, const std::vector<int64_t>& run, const std::vector<char>& small,
+                            const ch_set* const* A, const ch_set* const* B, const ch_est_params* params,
+                            const std::vector<int64_t>& Ts, const std::vector<int64_t*>& idxp,
+                            const std::vector<unsigned long long*>& bestp) {
+  // groups of one storage type, metric and dimension
+  std::map<std::tuple<int, int, int>, std::vector<int64_t>> groups;
+  for (int64_t i : run)
+    if (small[i]) groups[{A[i]->dtype, params[i].hash.metric, A[i]->d}].push_back(i);
+  const int spi = small_scan_samples_per_item();
+  for (auto& g : groups) {
+    const auto& ids = g.second;
+    const int dtype = std::get<0>(g.first), metric = std::get<1>(g.first), d = std::get<2>(g.first);
+    int64_t sum_nB = 0;
+    for (int64_t i : ids) sum_nB += B[i]->n;
+    const ScanTuneKey key{dtype, metric, d, size_class(sum_nB / static_cast<int64_t>(ids.size()))};
+    std::vector<SmallScanPair> pairs(ids.size());
+    for (size_t j = 0; j < ids.size(); ++j) {
+      const int64_t i = ids[j];
+      pairs[j] = SmallScanPair{A[i]->data, A[i]->scales, A[i]->n, idxp[i], Ts[i], B[i]->data, B[i]->scales, B[i]->n,
+                               bestp[i]};
+    }
+    auto items_for = [&](int64_t cl) {
+      std::vector<SmallScanItem> it;
+      for (size_t j = 0; j < ids.size(); ++j) {
+        const int64_t i = ids[j];
+        const int64_t sb = ceil_div(Ts[i], int64_t(spi));
+        for (int64_t b0 = 0; b0 < B[i]->n; b0 += cl)
+          for (int64_t q = 0; q < sb; ++q) it.push_back(SmallScanItem{int32_t(j), int32_t(q), b0});
+      }
+      return it;
+    };
+    // device buffers: the pair list and the largest item list of the candidates
+    const int64_t tuned = tuned_chunk(key);
+    const std::vector<int64_t> cands =
+        tuned ? std::vector<int64_t>{tuned}
+              : std::vector<int64_t>(std::begin(kScanChunkCandidates), std::end(kScanChunkCandidates));
+    size_t max_items = 0;
+    std::vector<std::vector<SmallScanItem>> lists;
+    for (int64_t cl : cands) {
+      lists.push_back(items_for(cl));
+      max_items = std::max(max_items, lists.back().size());
+    }
+    char* dmem = nullptr;
+    const size_t pbytes = (sizeof(SmallScanPair) * pairs.size() + 255) & ~size_t(255);
+    CHX_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dmem), pbytes + sizeof(SmallScanItem) * max_items,
+                                     c->pool, c->stream));
+    SmallScanPair* dp = reinterpret_cast<SmallScanPair*>(dmem);
+    SmallScanItem* di = reinterpret_cast<SmallScanItem*>(dmem + pbytes);
+    CHX_CUDA(cudaMemcpyAsync(dp, pairs.data(), sizeof(SmallScanPair) * pairs.size(), cudaMemcpyHostToDevice,
+                             c->stream));
+    float best_ms = 0.0f;
+    int64_t best_cl = cands[0];
+    for (size_t k = 0; k < cands.size(); ++k) {
+      CHX_CUDA(cudaMemcpyAsync(di, lists[k].data(), sizeof(SmallScanItem) * lists[k].size(), cudaMemcpyHostToDevice,
+                               c->stream));
+      if (cands.size() > 1) CHX_CUDA(cudaEventRecord(c->ev[5], c->stream));
+      launch_scan_small_batch(dp, di, static_cast<int64_t>(lists[k].size()), cands[k], dtype, metric, d, c->sm_count,
+                              c->stream);
+      if (cands.size() > 1) {
+        CHX_CUDA(cudaEventRecord(c->ev[6], c->stream));
+        CHX_CUDA(cudaEventSynchronize(c->ev[6]));
+        float ms = 0.0f;
+        CHX_CUDA(cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]));
+        if (k == 0 || ms < best_ms) {
+          best_ms = ms;
+          best_cl = cands[k];
+        }
+      }
+    }
+    if (cands.size() > 1) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[key] = best_cl;
+    }
+    CHX_CUDA(cudaFreeAsync(dmem, c->stream));
+  }
+}
+
 constexpr int kBatchLanes = 8;  // concurrent streams (and host threads) of a batched call
 
 // argument checks of one estimate; returns (T, R)
@@ -1128,28 +1237,117 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
       else ensure_ingest(const_cast<ch_set*>(x), c->stream);
     }
   }
-  // workspaces sized once, for the largest pair of each lane
-  std::vector<size_t> need(K, 0);
+  // The pairs run in four phases, so that the small per-pair steps become one
+  // launch each for the whole batch:
+  //   1. CrudeNN of every pair on the lanes (pair i on lane i mod K);
+  //   2. one launch: weights, prefix, W and draws of every pair (a CTA per pair);
+  //   3. the sampled scans on the lanes;
+  //   4. one launch: the combine of every pair, in the single-pair summation order.
+  // Each pair's D, w, prefix, draws and minima live in one batch allocation; a
+  // lane's workspace holds the scratch of one pair's CrudeNN or scan at a time.
+  std::vector<int64_t> run;
   for (int64_t i = 0; i < count; ++i)
-    if (st[i] == CH_OK && A[i]->n > 0)
-      need[i % K] = std::max(need[i % K], estimate_need(c->lanes[i % K], A[i], B[i], &params[i], Ts[i], Rs[i]));
+    if (st[i] == CH_OK && A[i]->n > 0) run.push_back(i);
+  // pairs whose sampled scan is the exact scan of d <= 4: one persistent launch
+  // for all of them (per storage type and metric) instead of a scan per pair
+  std::vector<char> small(count, 0);
+  for (int64_t i : run)
+    small[i] = A[i]->d <= kBatchScanMaxD && Ts[i] > 0 && B[i]->n < (int64_t(1) << 32) - 1 &&
+               screen_choice(params[i].screen, params[i].hash.metric, A[i], B[i]) == CH_SCREEN_EXACT;
+  std::vector<size_t> need(K, 0);
+  for (int64_t i : run) {
+    const ch_est_params* p = &params[i];
+    ch_ctx* lane = c->lanes[i % K];
+    Layout mc, ms;
+    CrudeBufs cb;
+    take_crude(mc, A[i], B[i], &p->hash, &cb);
+    mc.template take<int64_t>(A[i]->n);  // b(a)
+    mc.template take<uint8_t>(A[i]->n);  // level
+    ScanBufs sc;
+    if (!small[i]) take_scan(ms, lane, A[i], B[i], Ts[i], p->hash.metric, p->screen, Rs[i], &sc);
+    need[i % K] = std::max(need[i % K], std::max(mc.need, ms.need) + 256);
+  }
   for (int k = 0; k < K; ++k) c->lanes[k]->ws.reserve(need[k]);
-  ResBlock* dres = nullptr;
-  CHX_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&dres), sizeof(ResBlock) * count, c->pool, c->stream));
-  CHX_CUDA(cudaMemsetAsync(dres, 0, sizeof(ResBlock) * count, c->stream));
-  CHX_CUDA(cudaEventRecord(c->ev[7], c->stream));
-  for (int k = 0; k < K; ++k) CHX_CUDA(cudaStreamWaitEvent(c->lanes[k]->stream, c->ev[7], 0));
-  // one host thread per lane enqueues that lane's pairs (kernel launches are
-  // the host-side cost of small pairs); the sets' lazy state is already final
+  // the batch allocation: result blocks, the work list, then each pair's arrays
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t arena = al(sizeof(ResBlock) * count) + al(sizeof(BatchItem) * std::max<size_t>(run.size(), 1));
+  size_t best_bytes = 0;  // the small pairs' packed minima, one block (cleared together)
+  for (int64_t i : run) {
+    arena += al(size_t(A[i]->n) * 4) + 2 * al(size_t(A[i]->n) * 8) + al(size_t(Ts[i]) * 8) + al(size_t(Ts[i]) * 4);
+    if (small[i]) best_bytes += al(size_t(Ts[i]) * 8);
+  }
+  arena += best_bytes;
+  char* mem = nullptr;
+  CHX_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&mem), arena, c->pool, c->stream));
+  ResBlock* dres = reinterpret_cast<ResBlock*>(mem);
+  BatchItem* ditems = reinterpret_cast<BatchItem*>(mem + al(sizeof(ResBlock) * count));
+  char* cur = mem + al(sizeof(ResBlock) * count) + al(sizeof(BatchItem) * std::max<size_t>(run.size(), 1));
+  std::vector<BatchItem> items(run.size());
+  std::vector<float*> Dp(count, nullptr), mp(count, nullptr);
+  std::vector<int64_t*> idxp(count, nullptr);
+  std::vector<unsigned long long*> bestp(count, nullptr);
+  char* best_base = cur;
+  cur += best_bytes;
   {
+    char* b = best_base;
+    for (int64_t i : run)
+      if (small[i]) {
+        bestp[i] = reinterpret_cast<unsigned long long*>(b);
+        b += al(size_t(Ts[i]) * 8);
+      }
+  }
+  for (size_t j = 0; j < run.size(); ++j) {
+    const int64_t i = run[j];
+    BatchItem& it = items[j];
+    float* D = reinterpret_cast<float*>(cur);
+    cur += al(size_t(A[i]->n) * 4);
+    it.w = reinterpret_cast<uint64_t*>(cur);
+    cur += al(size_t(A[i]->n) * 8);
+    it.prefix = reinterpret_cast<uint64_t*>(cur);
+    cur += al(size_t(A[i]->n) * 8);
+    it.idx = reinterpret_cast<int64_t*>(cur);
+    cur += al(size_t(Ts[i]) * 8);
+    float* m = reinterpret_cast<float*>(cur);
+    cur += al(size_t(Ts[i]) * 4);
+    it.D = D;
+    it.m = m;
+    it.mpk = bestp[i];
+    it.res = dres + i;
+    it.statusA = A[i]->status;
+    it.statusB = B[i]->status;
+    it.nA = A[i]->n;
+    it.T = Ts[i];
+    it.seed = params[i].sample_seed;
+    Dp[i] = D;
+    mp[i] = m;
+    idxp[i] = it.idx;
+  }
+  CHX_CUDA(cudaMemsetAsync(dres, 0, sizeof(ResBlock) * count, c->stream));
+  if (!items.empty())
+    CHX_CUDA(cudaMemcpyAsync(ditems, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                             c->stream));
+  // c's stream -> every lane, and back
+  auto fork = [&] {
+    CHX_CUDA(cudaEventRecord(c->ev[7], c->stream));
+    for (int k = 0; k < K; ++k) CHX_CUDA(cudaStreamWaitEvent(c->lanes[k]->stream, c->ev[7], 0));
+  };
+  auto join = [&] {
+    for (int k = 0; k < K; ++k) {
+      CHX_CUDA(cudaEventRecord(c->lanes[k]->ev[7], c->lanes[k]->stream));
+      CHX_CUDA(cudaStreamWaitEvent(c->stream, c->lanes[k]->ev[7], 0));
+    }
+  };
+  // one host thread per lane enqueues that lane's pairs (kernel launches are the
+  // host-side cost of small pairs); the sets' lazy state is already final
+  auto on_lanes = [&](auto&& body) {
     std::vector<std::thread> th;
     for (int k = 0; k < K; ++k)
       th.emplace_back([&, k] {
         cudaSetDevice(c->device);
-        for (int64_t i = k; i < count; i += K) {
-          if (st[i] != CH_OK || A[i]->n == 0) continue;
+        for (int64_t i : run) {
+          if (i % K != k || st[i] != CH_OK) continue;
           try {
-            estimate_enqueue(c->lanes[k], A[i], B[i], &params[i], Ts[i], Rs[i], dres + i, false, nullptr);
+            body(c->lanes[k], i);
           } catch (const Err& e) {
             st[i] = e.st;
           } catch (...) {
@@ -1158,11 +1356,40 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
         }
       });
     for (auto& t : th) t.join();
+  };
+  fork();
+  on_lanes([&](ch_ctx* lane, int64_t i) {  // 1. CrudeNN (or the uniform baseline's equal weights)
+    const ch_est_params* p = &params[i];
+    if (p->sampling == CH_SAMPLING_UNIFORM) {
+      launch_fill_ones(Dp[i], A[i]->n, lane->stream);
+      return;
+    }
+    CrudeBufs cb;
+    int64_t* bidx = nullptr;
+    uint8_t* level = nullptr;
+    carve(lane, [&](auto& lay) {
+      take_crude(lay, A[i], B[i], &p->hash, &cb);
+      bidx = lay.template take<int64_t>(A[i]->n);
+      level = lay.template take<uint8_t>(A[i]->n);
+    });
+    run_crude(lane, A[i], B[i], &p->hash, &cb, bidx, level, Dp[i], &dres[i].status, nullptr);
+  });
+  join();
+  launch_batch_sample(ditems, static_cast<int64_t>(run.size()), c->stream);  // 2.
+  fork();
+  on_lanes([&](ch_ctx* lane, int64_t i) {  // 3. the sampled scans (the small pairs' below)
+    if (small[i]) return;
+    const ch_est_params* p = &params[i];
+    ScanBufs sc;
+    carve(lane, [&](auto& lay) { take_scan(lay, lane, A[i], B[i], Ts[i], p->hash.metric, p->screen, Rs[i], &sc); });
+    run_scan(lane, A[i], idxp[i], Ts[i], B[i], p->hash.metric, Rs[i], &sc, mp[i], nullptr, &dres[i].status);
+  });
+  if (best_bytes) {
+    CHX_CUDA(cudaMemsetAsync(best_base, 0xFF, best_bytes, c->stream));
+    run_small_scans(c, run, small, A, B, params, Ts, idxp, bestp);
   }
-  for (int k = 0; k < K; ++k) {
-    CHX_CUDA(cudaEventRecord(c->lanes[k]->ev[7], c->lanes[k]->stream));
-    CHX_CUDA(cudaStreamWaitEvent(c->stream, c->lanes[k]->ev[7], 0));
-  }
+  join();
+  launch_batch_combine(ditems, static_cast<int64_t>(run.size()), c->stream);  // 4.
   const size_t bytes = sizeof(ResBlock) * count;
   if (c->batch_pin_cap < bytes) {
     if (c->batch_pin) cudaFreeHost(c->batch_pin);
@@ -1173,7 +1400,7 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
   }
   ResBlock* h = static_cast<ResBlock*>(c->batch_pin);
   CHX_CUDA(cudaMemcpyAsync(h, dres, bytes, cudaMemcpyDeviceToHost, c->stream));
-  CHX_CUDA(cudaFreeAsync(dres, c->stream));
+  CHX_CUDA(cudaFreeAsync(mem, c->stream));
   CHX_CUDA(cudaStreamSynchronize(c->stream));
   ch_status first = CH_OK;
   for (int64_t i = 0; i < count; ++i) {

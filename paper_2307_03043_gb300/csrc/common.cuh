@@ -420,6 +420,31 @@ void launch_scan_merge(ScanPart part, int64_t T, const int64_t* qidx, float* min
                        cudaStream_t s);
 int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count);
 
+// ---- batched exact scan of small dimensions (d <= 4) over many pairs at once
+constexpr int kBatchScanMaxD = 4;
+struct SmallScanPair {
+  const void* A;
+  const float* scA;
+  int64_t nA;
+  const int64_t* qidx;  // [T] draws (< 0: none)
+  int64_t T;
+  const void* B;
+  const float* scB;
+  int64_t nB;
+  unsigned long long* best;  // [T] min over B of (canonical distance bits << 32 | index), preset to all ones
+};
+struct SmallScanItem {
+  int32_t pair;    // index into the pair list
+  int32_t sblock;  // block of samples
+  int64_t b0;      // first point of B of the item's chunk
+};
+// samples per item of the batched small scan
+int small_scan_samples_per_item();
+// one persistent launch over every item (all pairs of one storage type, metric
+// and dimension d <= 4); each item's minima fold into best[] by atomicMin
+void launch_scan_small_batch(const SmallScanPair* pairs, const SmallScanItem* items, int64_t n_items,
+                             int64_t chunk_len, int dtype, int metric, int d, int sm_count, cudaStream_t s);
+
 // tensor-core screen + rerank (l2)
 bool screen_supported(int screen, const ch_set* A, const ch_set* B);
 // chunk_sms: the SM count the split of B into chunks aims to fill (the grid still
@@ -458,6 +483,28 @@ struct CollectArgs {
 // the result's bits) do not depend on the GPU.
 constexpr int kCombineBlocks = 128;
 constexpr int kCombineDoubles = 2 + 2 * kCombineBlocks;
+
+// One pair of a batched call in the work lists of the batched sampling and
+// combine kernels (device memory; one CTA per entry).
+struct BatchItem {
+  const float* D;    // [nA] crude distances
+  uint64_t* w;       // [nA] weights
+  uint64_t* prefix;  // [nA] inclusive prefix of w
+  int64_t* idx;      // [T] draws
+  const float* m;    // [T] sampled minima (the combine's input), or
+  const unsigned long long* mpk;  // [T] the minima packed by the batched small scan (distance bits in the high word)
+  ResBlock* res;     // the pair's result block (W, S, eta, D_total, set status words)
+  const uint32_t* statusA;
+  const uint32_t* statusB;
+  int64_t nA, T;
+  uint64_t seed;
+};
+// weights, their exact inclusive prefix, W and the T draws of every listed pair
+// (the same integers as launch_weights + launch_draws)
+void launch_batch_sample(const BatchItem* items, int64_t count, cudaStream_t s);
+// eta and sum D of every listed pair, in the summation order of launch_combine
+// (so the same bits), into its result block
+void launch_batch_combine(const BatchItem* items, int64_t count, cudaStream_t s);
 void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const uint64_t* W, int64_t T,
                     const float* D, int64_t nA, double* out, cudaStream_t s, CollectArgs collect = CollectArgs());
 // sum of per-a minima (binary64): out[1] = sum (same layout as launch_combine)

@@ -414,6 +414,167 @@ void launch_combine(const float* m, const int64_t* idx, const uint64_t* w, const
   launch_check("combine_final");
 }
 
+// ------------------------------------------------------------------ batched work lists
+// One CTA per listed pair (a work list of BatchItem): the pairs of a batched call
+// take their weights, prefix and draws in one launch, and their combine in
+// another, instead of five launches each.
+
+constexpr int kBatchThreads = 1024;
+
+// block-wide max of non-negative ordered-encoded values (every thread calls it)
+__device__ inline uint32_t block_max_u32(uint32_t v, uint32_t* s_w) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = 0;
+  for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) v = max(v, s_w[i]);
+  __syncthreads();
+  return v;
+}
+
+// Per pair: S from max D (as k_max_d + weight_shift), w_a = ceil(D_a 2^S), the
+// inclusive prefix in chunks of blockDim x kScanItems points carried across
+// chunks (exact integers, so any grouping gives the same sums), W, then the draws
+// by binary search over the whole prefix.
+__global__ void __launch_bounds__(kBatchThreads) k_batch_sample(const BatchItem* items) {
+  pdl_entry();
+  __shared__ uint32_t s_m[32];
+  __shared__ uint64_t s_warp[32];
+  __shared__ uint64_t s_carry;
+  const BatchItem it = items[blockIdx.x];
+  const int64_t nA = it.nA;
+  uint32_t mx = 0;
+  for (int64_t a = threadIdx.x; a < nA; a += blockDim.x) mx = max(mx, ord_enc(it.D[a]));
+  const uint32_t maxD = block_max_u32(mx, s_m);
+  bool zero;
+  const int S = weight_shift(&maxD, nA, &zero);
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tile = int64_t(blockDim.x) * kScanItems;
+  for (int64_t c0 = 0; c0 < nA; c0 += tile) {
+    const int64_t base = c0 + int64_t(threadIdx.x) * kScanItems;
+    uint64_t v[kScanItems];
+    uint64_t run = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      const int64_t a = base + i;
+      uint64_t wa = 0;
+      if (a < nA && !zero) {
+        const float Da = it.D[a];
+        if (Da > 0.0f) wa = ceil_scaled(Da, S);
+      }
+      if (a < nA) it.w[a] = wa;
+      run += wa;
+      v[i] = run;
+    }
+    uint64_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint64_t woff = 0;
+    for (int i = 0; i < warp; ++i) woff += s_warp[i];
+    const uint64_t carry = s_carry;
+    const uint64_t off = carry + woff + x - run;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      const int64_t a = base + i;
+      if (a < nA) it.prefix[a] = v[i] + off;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = off + run;
+    __syncthreads();
+  }
+  const uint64_t W = nA > 0 ? s_carry : 0;
+  if (threadIdx.x == 0) {
+    it.res->W = W;
+    it.res->S = nA > 0 ? S : 0;
+  }
+  // the prefix written above is read back by other threads of this CTA
+  __threadfence_block();
+  __syncthreads();
+  for (int64_t l = threadIdx.x; l < it.T; l += blockDim.x) {
+    if (W == 0) {
+      it.idx[l] = -1;
+      continue;
+    }
+    const uint64_t t = draw_point(l, it.seed, W);
+    int64_t lo = 0, hi = nA;  // first a with prefix[a] > t
+    while (lo < hi) {
+      const int64_t m = lo + ((hi - lo) >> 1);
+      if (it.prefix[m] > t)
+        hi = m;
+      else
+        lo = m + 1;
+    }
+    it.idx[l] = lo;
+  }
+}
+
+// Per pair, 256 threads: the kCombineBlocks partial sums of k_combine_part (block
+// b's thread t sums the strided elements of slice b, then the block's tree), and
+// their final tree with the upper half of the threads adding zeros: the same
+// binary64 operations in the same order, so the same bits.
+__global__ void __launch_bounds__(256) k_batch_combine(const BatchItem* items) {
+  pdl_entry();
+  __shared__ double s_a[256], s_b[256];
+  __shared__ double p_a[kCombineBlocks], p_b[kCombineBlocks];
+  const BatchItem it = items[blockIdx.x];
+  const uint64_t W = it.res->W;
+  const int64_t T = it.T, nA = it.nA;
+  const int64_t lt = ceil_div_dev(T, kCombineBlocks), la = ceil_div_dev(nA, kCombineBlocks);
+  const double Wd = static_cast<double>(W);
+  for (int b = 0; b < kCombineBlocks; ++b) {
+    double acc = 0.0, accD = 0.0;
+    if (W != 0) {
+      const int64_t end = min(T, (b + 1) * lt);
+      for (int64_t l = b * lt + threadIdx.x; l < end; l += blockDim.x) {
+        const float ml = it.mpk ? __uint_as_float(static_cast<uint32_t>(it.mpk[l] >> 32)) : it.m[l];
+        acc += static_cast<double>(ml) * (Wd / static_cast<double>(it.w[it.idx[l]]));
+      }
+    }
+    const int64_t endA = min(nA, (b + 1) * la);
+    for (int64_t a = b * la + threadIdx.x; a < endA; a += blockDim.x) accD += static_cast<double>(it.D[a]);
+    block_sum2(acc, accD, s_a, s_b);
+    if (threadIdx.x == 0) {
+      p_a[b] = acc;
+      p_b[b] = accD;
+    }
+    __syncthreads();  // s_a / s_b are reused
+  }
+  double a = 0.0, bsum = 0.0;
+  if (threadIdx.x < kCombineBlocks) {
+    a = p_a[threadIdx.x];
+    bsum = p_b[threadIdx.x];
+  }
+  __syncthreads();
+  block_sum2(a, bsum, s_a, s_b);
+  if (threadIdx.x == 0) {
+    ResBlock* r = it.res;
+    r->eta = (W != 0 && T > 0) ? a / static_cast<double>(T) : 0.0;
+    r->D_total = bsum;
+    if (it.statusA) r->statusA = *it.statusA;
+    if (it.statusB) r->statusB = *it.statusB;
+  }
+}
+
+void launch_batch_sample(const BatchItem* items, int64_t count, cudaStream_t s) {
+  if (count == 0) return;
+  launch_k(k_batch_sample, static_cast<int>(count), kBatchThreads, 0, s, items);
+  launch_check("batch_sample");
+}
+
+void launch_batch_combine(const BatchItem* items, int64_t count, cudaStream_t s) {
+  if (count == 0) return;
+  launch_k(k_batch_combine, static_cast<int>(count), 256, 0, s, items);
+  launch_check("batch_combine");
+}
+
 void launch_sum_f32(const float* v, int64_t n, double* out, cudaStream_t s) {
   // out[1] = sum v (binary64), out[0] = 0: the combine reduction with no samples
   launch_combine(nullptr, nullptr, nullptr, nullptr, 0, v, n, out, s);

@@ -321,6 +321,83 @@ __global__ void __launch_bounds__(256) k_scan_small(const void* __restrict__ A, 
   }
 }
 
+// The batched form: one persistent launch over items (pair, sample block, chunk
+// of B) of many pairs of one storage type, metric and dimension; each item walks
+// its chunk exactly as k_scan_small does and folds each sample's minimum into the
+// pair's best[] as (canonical distance bits << 32 | b), so the smallest distance
+// wins and, among equal distances, the smallest index (the merge's rule).
+template <int DT, int METRIC, int D>
+__global__ void __launch_bounds__(256) k_scan_small_batch(const SmallScanPair* __restrict__ pairs,
+                                                          const SmallScanItem* __restrict__ items, int64_t n_items,
+                                                          int64_t chunk_len) {
+  pdl_entry();
+  __shared__ float Bs[kSmallBT * D];
+  for (int64_t w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const SmallScanItem it = items[w];
+    const SmallScanPair pr = pairs[it.pair];
+    const int64_t l0 = int64_t(it.sblock) * kSmallQ + threadIdx.x;
+    const int64_t b_begin = it.b0;
+    const int64_t b_end = min(pr.nB, b_begin + chunk_len);
+    float q[kSmallPQ][D];
+    float best_val[kSmallPQ], best_p0[kSmallPQ];
+    int64_t best_idx[kSmallPQ];
+#pragma unroll
+    for (int p = 0; p < kSmallPQ; ++p) {
+      const int64_t l = l0 + 256 * p;
+      int64_t a = -1;
+      if (l < pr.T) a = pr.qidx[l];
+#pragma unroll
+      for (int j = 0; j < D; ++j) q[p][j] = (a >= 0 && a < pr.nA) ? load_elem<DT>(pr.A, a, D, j, pr.scA) : 0.0f;
+      best_val[p] = __int_as_float(0x7F800000);
+      best_p0[p] = __int_as_float(0x7F800000);
+      best_idx[p] = INT64_MAX;
+    }
+    for (int64_t b0 = b_begin; b0 < b_end; b0 += kSmallBT) {
+      const int rows = static_cast<int>(min(static_cast<int64_t>(kSmallBT), b_end - b0));
+      __syncthreads();
+      for (int f = threadIdx.x; f < rows * D; f += 256) Bs[f] = load_elem<DT>(pr.B, b0 + f / D, D, f % D, pr.scB);
+      __syncthreads();
+      for (int r = 0; r < rows; ++r) {
+        float bv[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) bv[j] = Bs[r * D + j];
+#pragma unroll
+        for (int p = 0; p < kSmallPQ; ++p) {
+          float leaf[D];
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            const float t = __fsub_rn(q[p][j], bv[j]);
+            leaf[j] = (METRIC == CH_L1) ? fabsf(t) : __fmul_rn(t, t);
+          }
+          const float v = small_node<D, 0, 1>(leaf);
+          if (METRIC == CH_L1) {
+            if (v < best_val[p]) {
+              best_val[p] = v;
+              best_idx[p] = b0 + r;
+            }
+          } else if (v < best_p0[p]) {
+            best_p0[p] = v;
+            const float sv = __fsqrt_rn(v);
+            if (sv < best_val[p]) {
+              best_val[p] = sv;
+              best_idx[p] = b0 + r;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < kSmallPQ; ++p) {
+      const int64_t l = l0 + 256 * p;
+      // (no point below +inf: +inf with index bits all ones, still below the preset)
+      if (l < pr.T)
+        atomicMin(&pr.best[l], (static_cast<unsigned long long>(__float_as_uint(best_val[p])) << 32) |
+                                   static_cast<unsigned long long>(static_cast<uint32_t>(best_idx[p])));
+    }
+    __syncthreads();  // Bs is refilled by the next item
+  }
+}
+
 __global__ void k_scan_merge(const float* part_val, const int64_t* part_idx, int chunks, int64_t T,
                              const int64_t* qidx, float* min_d, int64_t* argmin) {
   pdl_entry();
@@ -482,6 +559,42 @@ void launch_scan_merge(ScanPart part, int64_t T, const int64_t* qidx, float* min
   launch_k(k_scan_merge, static_cast<int>(ceil_div(T, 256)), 256, 0, s, part.val, part.idx, part.chunks, T, qidx, min_d,
                                                                   argmin);
   launch_check("scan_merge");
+}
+
+int small_scan_samples_per_item() { return kSmallQ; }
+
+template <int DT, int METRIC>
+static void small_batch_d(const SmallScanPair* pairs, const SmallScanItem* items, int64_t n, int64_t chunk_len, int d,
+                          int grid, cudaStream_t s) {
+  switch (d) {
+    case 1: launch_k(k_scan_small_batch<DT, METRIC, 1>, grid, 256, 0, s, pairs, items, n, chunk_len); break;
+    case 2: launch_k(k_scan_small_batch<DT, METRIC, 2>, grid, 256, 0, s, pairs, items, n, chunk_len); break;
+    case 3: launch_k(k_scan_small_batch<DT, METRIC, 3>, grid, 256, 0, s, pairs, items, n, chunk_len); break;
+    default: launch_k(k_scan_small_batch<DT, METRIC, 4>, grid, 256, 0, s, pairs, items, n, chunk_len); break;
+  }
+}
+
+template <int DT>
+static void small_batch_m(const SmallScanPair* pairs, const SmallScanItem* items, int64_t n, int64_t chunk_len,
+                          int metric, int d, int grid, cudaStream_t s) {
+  if (metric == CH_L1)
+    small_batch_d<DT, CH_L1>(pairs, items, n, chunk_len, d, grid, s);
+  else
+    small_batch_d<DT, CH_L2>(pairs, items, n, chunk_len, d, grid, s);
+}
+
+void launch_scan_small_batch(const SmallScanPair* pairs, const SmallScanItem* items, int64_t n_items,
+                             int64_t chunk_len, int dtype, int metric, int d, int sm_count, cudaStream_t s) {
+  if (n_items == 0) return;
+  CHX_CHECK(d >= 1 && d <= kSmallMaxD, CH_EINVAL, "batched small scan: d must be in 1..4");
+  // a persistent grid: about four resident blocks per SM
+  const int grid = static_cast<int>(std::min<int64_t>(n_items, int64_t(sm_count) * 4));
+  switch (dtype) {
+    case CH_F32: small_batch_m<CH_F32>(pairs, items, n_items, chunk_len, metric, d, grid, s); break;
+    case CH_BF16: small_batch_m<CH_BF16>(pairs, items, n_items, chunk_len, metric, d, grid, s); break;
+    default: small_batch_m<CH_FP8E4M3>(pairs, items, n_items, chunk_len, metric, d, grid, s); break;
+  }
+  launch_check("scan_small_batch");
 }
 
 }  // namespace chx

@@ -150,6 +150,160 @@ struct ScreenArgs {
   long long wait_cycles;  // budget of each pipeline wait (SM cycles)
 };
 
+// arrive on this CTA's mbarrier at shared address addr; relaxed: what it
+// publishes (the tensor-memory reads) is ordered by the tcgen05 fences around it
+__device__ __forceinline__ void mbar_arrive_relaxed(uint32_t addr) {
+  asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// The epilogue (eight warps: warps 2 .. 9 of the block): one sample row per
+// thread.  Warp w reads TMEM lane quadrant w % 4 (the only one it may access) and
+// one 128-column slice of each accumulator tile, forms the scores and keeps, per
+// residue class of columns, the running minimum and the tile it came from.  Work
+// item `item` covers sample tile tile_of(item) and chunk item / items_per_chunk.
+// After reading an accumulator each warp arrives once on acc_empty[acc] (given by
+// its shared address).
+template <int SCREEN, class TileOf>
+__device__ __forceinline__ void screen_epilogue(const ScreenArgs& args, int first_item, int item_stride, int n_items,
+                                              int items_per_chunk, TileOf tile_of, uint32_t tmem_base,
+                                              float* nb_s, float* sb_s, uint64_t* acc_full,
+                                              const uint32_t (&acc_empty_c)[2], volatile int* abort_flag,
+                                              long long budget) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ew = warp & 3;
+  const int qs = (warp - 2) >> 2;  // column slice
+  const int row = ew * 32 + lane;
+  uint32_t acc = 0, accphase = 0;
+  for (int item = first_item; item < n_items && !*abort_flag; item += item_stride) {
+    const int mt = tile_of(item), ck = item / items_per_chunk;
+    const int64_t b_begin = int64_t(ck) * args.chunk_len;
+    const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
+    const int64_t grow = int64_t(mt) * kBM + row;
+    float sq = 1.0f;
+    if constexpr (SCREEN == CH_SCREEN_FP8) sq = (grow < args.T) ? args.scaleQ[grow] : 1.0f;
+    // running minima per residue class of this warp's slice; best_c holds the
+    // tile (within the chunk) of each minimum
+    float best_s[kClasses];
+    int32_t best_c[kClasses];
+#pragma unroll
+    for (int i = 0; i < kClasses; ++i) {
+      best_s[i] = __int_as_float(0x7F800000);
+      best_c[i] = -1;
+    }
+    int32_t tile = 0;  // tile index within the chunk
+    // |b|^2 (and -2 x FP8 scale) of this lane's columns of a tile slice,
+    // fetched one tile ahead so the load latency hides behind a tile of work;
+    // +inf past the end of the chunk
+    constexpr int kPer = kSliceCols / 32;
+    float pn[kPer], ps[kPer];
+    auto prefetch_norms = [&](int64_t t0) {
+      const int64_t base = t0 + qs * kSliceCols;
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int64_t b = base + lane + 32 * k;
+        pn[k] = (b < b_end) ? __ldg(&args.normB[b]) : __int_as_float(0x7F800000);
+        ps[k] = 0.0f;
+        if constexpr (SCREEN == CH_SCREEN_FP8) ps[k] = (b < b_end) ? -2.0f * __ldg(&args.scaleB[b]) : 0.0f;
+      }
+    };
+    prefetch_norms(b_begin);
+    bool ok = true;
+    for (int64_t b0 = b_begin; b0 < b_end; b0 += kBN) {
+      // stage |b|^2 (and -2 x FP8 scale) of this tile in this warp's own buffer;
+      // +inf past the end of B.  Only __syncwarp is used inside the epilogue, so
+      // a warp that gives up on a wait can never strand another one.
+      float* nb = nb_s + ((warp - 2) * 2 + acc) * kSliceCols;
+      float* sb = sb_s + ((warp - 2) * 2 + acc) * kSliceCols;
+      // this tile's norms were fetched into registers during the previous tile
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        nb[lane + 32 * k] = pn[k];
+        if constexpr (SCREEN == CH_SCREEN_FP8) sb[lane + 32 * k] = ps[k];
+      }
+      __syncwarp();
+      prefetch_norms(b0 + kBN);  // next tile's, consumed one tile from now
+      const bool got = mbar_wait(&acc_full[acc], accphase, abort_flag, budget);
+      if (!__all_sync(0xFFFFFFFFu, got)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + qs * kSliceCols;
+      // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 16 columns
+      // (chunk ch = slice columns ch*16 .. ch*16+15: classes (ch*16) mod
+      // kClasses + i, occurrence ch*16 / kClasses), folded into the tile minima tm
+      float tm[kClasses];
+      auto process = [&](uint32_t(&r)[16], int ch) {
+        const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 16);
+        const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 n = nb4[q];
+          float4 m = make_float4(-2.0f, -2.0f, -2.0f, -2.0f);
+          if constexpr (SCREEN == CH_SCREEN_FP8) {
+            m = sb4[q];  // -2 x column scale, times this row's sample scale
+            m.x *= sq;
+            m.y *= sq;
+            m.z *= sq;
+            m.w *= sq;
+          }
+          r[4 * q + 0] = __float_as_uint(fmaf(m.x, __uint_as_float(r[4 * q + 0]), n.x));
+          r[4 * q + 1] = __float_as_uint(fmaf(m.y, __uint_as_float(r[4 * q + 1]), n.y));
+          r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
+          r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
+        }
+        const int c0 = (ch * 16) % kClasses;
+        const bool first = ch * 16 < kClasses;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          tm[c0 + i] = first ? __uint_as_float(r[i]) : fminf(tm[c0 + i], __uint_as_float(r[i]));
+      };
+      // two 16-column register buffers: the next chunk loads while this one is processed
+      uint32_t ra[16], rb[16];
+      tmem_ld16_async(taddr, ra);
+      tmem_wait_ld();
+#pragma unroll
+      for (int ch = 0; ch < kSliceCols / 16; ch += 2) {
+        tmem_ld16_async(taddr + (ch + 1) * 16, rb);
+        process(ra, ch);
+        tmem_wait_ld();
+        if (ch + 2 < kSliceCols / 16) tmem_ld16_async(taddr + (ch + 2) * 16, ra);
+        process(rb, ch + 1);
+        tmem_wait_ld();
+      }
+      // the warp's tensor-memory reads are complete (tcgen05.wait::ld is warp-wide):
+      // one arrival per warp frees the accumulator
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_relaxed(acc_empty_c[acc]);
+      // one running-minimum update per class and tile
+#pragma unroll
+      for (int i = 0; i < kClasses; ++i) {
+        const bool lt = tm[i] < best_s[i];
+        best_s[i] = lt ? tm[i] : best_s[i];
+        best_c[i] = lt ? tile : best_c[i];
+      }
+      ++tile;
+      acc ^= 1;
+      if (acc == 0) accphase ^= 1;
+      __syncwarp();  // this warp's staging buffer is rewritten two tiles later
+    }
+    if (!ok) break;
+    if (grow < args.T) {
+      // entry (tile t, class i) stands for columns
+      // b_begin + t*256 + slice*kSliceCols + o*kClasses + i, o = 0 .. kOcc-1
+      const size_t base = (size_t(ck * kSlices + qs) * args.T + grow) * kClasses;
+#pragma unroll
+      for (int i = 0; i < kClasses; ++i) {
+        const int32_t t = best_c[i];
+        args.part_s[base + i] = best_s[i];
+        args.part_i[base + i] =
+            t < 0 ? -1 : static_cast<int32_t>(b_begin + int64_t(t) * kBN + qs * kSliceCols + i);
+      }
+    }
+  }
+  }
+
 template <int SCREEN, bool STREAMQ>
 __global__ void __launch_bounds__(kThreads, 1)
     k_screen(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmB, ScreenArgs args) {
@@ -186,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(q_empty, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 32 * kEpiWarps);
+      mbar_init(&acc_empty[i], kEpiWarps);  // one arrival per epilogue warp
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -306,138 +460,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait_bounded(drain, 0);
     }
   } else {
-    // ------------------------------------------------ epilogue: one sample row per thread
-    // Eight warps: warp w reads TMEM lane quadrant w % 4 (the only one it may
-    // access) and one 128-column slice of each accumulator tile.
-    const int ew = warp & 3;
-    const int qs = (warp - 2) >> 2;  // column slice
-    const int row = ew * 32 + lane;
-    uint32_t acc = 0, accphase = 0;
-    for (int item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
-      const int mt = item % args.row_tiles, ck = item / args.row_tiles;
-      const int64_t b_begin = int64_t(ck) * args.chunk_len;
-      const int64_t b_end = min(args.nB, b_begin + args.chunk_len);
-      const int64_t grow = int64_t(mt) * kBM + row;
-      float sq = 1.0f;
-      if constexpr (SCREEN == CH_SCREEN_FP8) sq = (grow < args.T) ? args.scaleQ[grow] : 1.0f;
-      // running minima per residue class of this warp's slice; best_c holds the
-      // tile (within the chunk) of each minimum
-      float best_s[kClasses];
-      int32_t best_c[kClasses];
-#pragma unroll
-      for (int i = 0; i < kClasses; ++i) {
-        best_s[i] = __int_as_float(0x7F800000);
-        best_c[i] = -1;
-      }
-      int32_t tile = 0;  // tile index within the chunk
-      // |b|^2 (and -2 x FP8 scale) of this lane's columns of a tile slice,
-      // fetched one tile ahead so the load latency hides behind a tile of work;
-      // +inf past the end of the chunk
-      constexpr int kPer = kSliceCols / 32;
-      float pn[kPer], ps[kPer];
-      auto prefetch_norms = [&](int64_t t0) {
-        const int64_t base = t0 + qs * kSliceCols;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-          const int64_t b = base + lane + 32 * k;
-          pn[k] = (b < b_end) ? __ldg(&args.normB[b]) : __int_as_float(0x7F800000);
-          ps[k] = 0.0f;
-          if constexpr (SCREEN == CH_SCREEN_FP8) ps[k] = (b < b_end) ? -2.0f * __ldg(&args.scaleB[b]) : 0.0f;
-        }
-      };
-      prefetch_norms(b_begin);
-      bool ok = true;
-      for (int64_t b0 = b_begin; b0 < b_end; b0 += kBN) {
-        // stage |b|^2 (and -2 x FP8 scale) of this tile in this warp's own buffer;
-        // +inf past the end of B.  Only __syncwarp is used inside the epilogue, so
-        // a warp that gives up on a wait can never strand another one.
-        float* nb = nb_s + ((warp - 2) * 2 + acc) * kSliceCols;
-        float* sb = sb_s + ((warp - 2) * 2 + acc) * kSliceCols;
-        // this tile's norms were fetched into registers during the previous tile
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-          nb[lane + 32 * k] = pn[k];
-          if constexpr (SCREEN == CH_SCREEN_FP8) sb[lane + 32 * k] = ps[k];
-        }
-        __syncwarp();
-        prefetch_norms(b0 + kBN);  // next tile's, consumed one tile from now
-        const bool got = mbar_wait(&acc_full[acc], accphase, abort_flag, budget);
-        if (!__all_sync(0xFFFFFFFFu, got)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + qs * kSliceCols;
-        // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 16 columns
-        // (chunk ch = slice columns ch*16 .. ch*16+15: classes (ch*16) mod
-        // kClasses + i, occurrence ch*16 / kClasses), folded into the tile minima tm
-        float tm[kClasses];
-        auto process = [&](uint32_t(&r)[16], int ch) {
-          const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 16);
-          const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 16);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 n = nb4[q];
-            float4 m = make_float4(-2.0f, -2.0f, -2.0f, -2.0f);
-            if constexpr (SCREEN == CH_SCREEN_FP8) {
-              m = sb4[q];  // -2 x column scale, times this row's sample scale
-              m.x *= sq;
-              m.y *= sq;
-              m.z *= sq;
-              m.w *= sq;
-            }
-            r[4 * q + 0] = __float_as_uint(fmaf(m.x, __uint_as_float(r[4 * q + 0]), n.x));
-            r[4 * q + 1] = __float_as_uint(fmaf(m.y, __uint_as_float(r[4 * q + 1]), n.y));
-            r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
-            r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
-          }
-          const int c0 = (ch * 16) % kClasses;
-          const bool first = ch * 16 < kClasses;
-#pragma unroll
-          for (int i = 0; i < 16; ++i)
-            tm[c0 + i] = first ? __uint_as_float(r[i]) : fminf(tm[c0 + i], __uint_as_float(r[i]));
-        };
-        // two 16-column register buffers: the next chunk loads while this one is processed
-        uint32_t ra[16], rb[16];
-        tmem_ld16_async(taddr, ra);
-        tmem_wait_ld();
-#pragma unroll
-        for (int ch = 0; ch < kSliceCols / 16; ch += 2) {
-          tmem_ld16_async(taddr + (ch + 1) * 16, rb);
-          process(ra, ch);
-          tmem_wait_ld();
-          if (ch + 2 < kSliceCols / 16) tmem_ld16_async(taddr + (ch + 2) * 16, ra);
-          process(rb, ch + 1);
-          tmem_wait_ld();
-        }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[acc]);
-        // one running-minimum update per class and tile
-#pragma unroll
-        for (int i = 0; i < kClasses; ++i) {
-          const bool lt = tm[i] < best_s[i];
-          best_s[i] = lt ? tm[i] : best_s[i];
-          best_c[i] = lt ? tile : best_c[i];
-        }
-        ++tile;
-        acc ^= 1;
-        if (acc == 0) accphase ^= 1;
-        __syncwarp();  // this warp's staging buffer is rewritten two tiles later
-      }
-      if (!ok) break;
-      if (grow < args.T) {
-        // entry (tile t, class i) stands for columns
-        // b_begin + t*256 + slice*kSliceCols + o*kClasses + i, o = 0 .. kOcc-1
-        const size_t base = (size_t(ck * kSlices + qs) * args.T + grow) * kClasses;
-#pragma unroll
-        for (int i = 0; i < kClasses; ++i) {
-          const int32_t t = best_c[i];
-          args.part_s[base + i] = best_s[i];
-          args.part_i[base + i] =
-              t < 0 ? -1 : static_cast<int32_t>(b_begin + int64_t(t) * kBN + qs * kSliceCols + i);
-        }
-      }
-    }
+    uint32_t acc_empty_c[2] = {su32(&acc_empty[0]), su32(&acc_empty[1])};
+    screen_epilogue<SCREEN>(args, blockIdx.x, gridDim.x, n_items, args.row_tiles,
+                            [&](int item) { return item % args.row_tiles; }, tmem_base, nb_s, sb_s, acc_full,
+                            acc_empty_c, abort_flag, budget);
   }
 
   // ------------------------------------------------ teardown
@@ -508,9 +534,9 @@ Plan make_plan(int64_t T, int64_t nB, int d, int R, int sm_count, int chunk_sms,
   // resident tile leaves three, and the bf16 d = 384 screen ran 3.01 ms resident
   // against 2.81 ms streamed on 1M x 1M)
   p.stream_q = int64_t(p.kblocks) * kBM * kKB >= 96 * 1024;
+  const size_t limit = 227 * 1024;
   const size_t fixed = 1024 + (p.stream_q ? 0 : size_t(p.kblocks) * kBM * kKB) + 16 * kBN * sizeof(float) + 256;
   const size_t per_stage = size_t(kBN) * kKB + (p.stream_q ? size_t(kBM) * kKB : 0);
-  const size_t limit = 227 * 1024;
   p.stages = static_cast<int>(std::min<size_t>(6, (limit - std::min(limit, fixed)) / per_stage));
   p.smem = fixed + size_t(p.stages) * per_stage;
   // chunks: smallest count whose items fill chunk_sms SMs to >= 90 % (at most
@@ -616,7 +642,7 @@ void launch_screen_l2(const ch_set* A, const int64_t* qidx, int64_t T, const ch_
     auto kern = p.stream_q ? k_screen<SCR, true> : k_screen<SCR, false>;                                    \
     CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)); /* constant */ \
     timer.start(s);                                                                                         \
-    launch_k(kern, p.grid, kThreads, p.smem, s, tmQ, tmB, a);                                                     \
+    launch_k(kern, p.grid, kThreads, p.smem, s, tmQ, tmB, a);                                               \
     timer.stop(s);                                                                                          \
   } while (0)
   if (screen == CH_SCREEN_TF32) CHX_SCREEN_LAUNCH(CH_SCREEN_TF32);

@@ -73,3 +73,44 @@ def test_batch_failures_and_empty(ctx):
     assert ch.ch_estimate_batch(ctx, [], [], []) == ([], [])
     for s in (sX, sY, sE, sBad):
         ch.ch_set_destroy(s)
+
+
+@pytest.mark.parametrize("d", [1, 2, 4])
+def test_batch_small_d_all_storage_types(ctx, d):
+    """Pairs of d <= 4 go through one batched exact scan per (storage type,
+    metric, d); the first call tunes its chunk length, the second reuses it, and
+    both equal the single-pair estimates bit for bit."""
+    sizes = workloads.log_uniform_sizes(12, 50, 30_000, 40 + d)
+    made, A, B, P = [], [], [], []
+    for i in range(6):
+        X, _ = workloads.gaussian_mixture(int(sizes[2 * i]), 1, d, 500 + i, clusters=5)
+        Y, _ = workloads.gaussian_mixture(int(sizes[2 * i + 1]), 1, d, 600 + i, clusters=5)
+        for kind in ("f32", "bf16", "fp8"):
+            if kind == "f32":
+                sX = ch.ch_set_create(ctx, X, 0, X.shape[0], d)
+                sY = ch.ch_set_create(ctx, Y, 0, Y.shape[0], d)
+            elif kind == "bf16":
+                sX = ch.ch_set_create(ctx, torch.from_numpy(workloads.to_bf16_bits(X)).cuda(), 1, X.shape[0], d,
+                                      ch.CH_BF16)
+                sY = ch.ch_set_create(ctx, torch.from_numpy(workloads.to_bf16_bits(Y)).cuda(), 1, Y.shape[0], d,
+                                      ch.CH_BF16)
+            else:
+                cx, sx = workloads.to_fp8_e4m3(X)
+                cy, sy = workloads.to_fp8_e4m3(Y)
+                sX = ch.ch_set_create(ctx, torch.from_numpy(cx).cuda(), 1, X.shape[0], d, ch.CH_FP8E4M3,
+                                      torch.from_numpy(sx).cuda())
+                sY = ch.ch_set_create(ctx, torch.from_numpy(cy).cuda(), 1, Y.shape[0], d, ch.CH_FP8E4M3,
+                                      torch.from_numpy(sy).cuda())
+            made += [sX, sY]
+            for metric in (ch.CH_L1, ch.CH_L2):
+                A.append(sX)
+                B.append(sY)
+                P.append(ch.est_params(metric, hash_seed=i, sample_seed=10 * i + metric, eps=0.2))
+    single = [ch.ch_estimate(ctx, A[i], B[i], P[i]) for i in range(len(A))]
+    for _ in range(2):
+        eta, st = ch.ch_estimate_batch(ctx, A, B, P)
+        assert all(s == ch.CH_OK for s in st)
+        assert eta == single
+    torch.cuda.synchronize()
+    for s in made:
+        ch.ch_set_destroy(s)
