@@ -250,6 +250,37 @@ __host__ __device__ inline int ceil_log2_i64(int64_t n) {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __device__ inline int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Packed binary32 pairs (sm_100 and later): fma.rn.f32x2 and mul.rn.f32x2 round
+// each half exactly as fmaf and __fmul_rn do (IEEE, round to nearest even), at one
+// issue slot per two lanes of work.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+// c = a * b + c, per half
+__device__ __forceinline__ void f2_fma(uint64_t& c, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
+}
+// a * b, per half
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// min(a, b, c) in one instruction (sm_100 and later); like fminf, a NaN operand
+// is ignored when another is a number
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
 inline uint32_t next_pow2_u32(uint64_t x) {
   uint32_t p = 1;
   while (p < x) p <<= 1;

@@ -513,23 +513,6 @@ __device__ __forceinline__ float pt_xreduce(float (&v)[KP], int lane) {
   return r;
 }
 
-// Packed binary32 pairs for the projection's FMA chains: fma.rn.f32x2 rounds each
-// half exactly as fmaf does (IEEE fused multiply-add, round to nearest even), at
-// one issue slot per two chains.
-__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-  return r;
-}
-// c = a * b + c, per half
-__device__ __forceinline__ void f2_fma(uint64_t& c, uint64_t a, uint64_t b) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
-}
 
 template <int DT, int KP>
 __global__ void __launch_bounds__(pt_max_warps<DT>() * 32, 1)

@@ -109,6 +109,15 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// the wait, with the 16 registers of a tmem_ld16_async tied to it so that no read
+// of them is scheduled before it
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
 
 // 16 columns; valid after tmem_wait_ld()
 __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
@@ -181,6 +190,8 @@ __device__ __forceinline__ void screen_epilogue(const ScreenArgs& args, int firs
     const int64_t grow = int64_t(mt) * kBM + row;
     float sq = 1.0f;
     if constexpr (SCREEN == CH_SCREEN_FP8) sq = (grow < args.T) ? args.scaleQ[grow] : 1.0f;
+    const uint64_t sq2 = f2_pack(sq, sq);
+    const uint64_t neg2 = f2_pack(-2.0f, -2.0f);
     // running minima per residue class of this warp's slice; best_c holds the
     // tile (within the chunk) of each minimum
     float best_s[kClasses];
@@ -229,60 +240,80 @@ __device__ __forceinline__ void screen_epilogue(const ScreenArgs& args, int firs
       }
       tc_fence_after();
       const uint32_t taddr = tmem_base + (static_cast<uint32_t>(ew * 32) << 16) + acc * kBN + qs * kSliceCols;
-      // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of 16 columns
-      // (chunk ch = slice columns ch*16 .. ch*16+15: classes (ch*16) mod
-      // kClasses + i, occurrence ch*16 / kClasses), folded into the tile minima tm
-      float tm[kClasses];
-      auto process = [&](uint32_t(&r)[16], int ch) {
+      // scores s = |b|^2 - 2 q.b (FP8: |b|^2 - 2 s_q s_b q8.b8) of the 16 columns
+      // ch*16 .. ch*16+15 of the slice, two columns per packed instruction (each
+      // half rounded as fmaf and __fmul_rn round)
+      auto scores = [&](const uint32_t(&r)[16], int ch, float(&o)[16]) {
         const float4* nb4 = reinterpret_cast<const float4*>(nb + ch * 16);
         const float4* sb4 = reinterpret_cast<const float4*>(sb + ch * 16);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const float4 n = nb4[q];
-          float4 m = make_float4(-2.0f, -2.0f, -2.0f, -2.0f);
+          uint64_t m01 = neg2, m23 = neg2;
           if constexpr (SCREEN == CH_SCREEN_FP8) {
-            m = sb4[q];  // -2 x column scale, times this row's sample scale
-            m.x *= sq;
-            m.y *= sq;
-            m.z *= sq;
-            m.w *= sq;
+            const float4 m = sb4[q];  // -2 x column scale, times this row's sample scale
+            m01 = f2_mul(f2_pack(m.x, m.y), sq2);
+            m23 = f2_mul(f2_pack(m.z, m.w), sq2);
           }
-          r[4 * q + 0] = __float_as_uint(fmaf(m.x, __uint_as_float(r[4 * q + 0]), n.x));
-          r[4 * q + 1] = __float_as_uint(fmaf(m.y, __uint_as_float(r[4 * q + 1]), n.y));
-          r[4 * q + 2] = __float_as_uint(fmaf(m.z, __uint_as_float(r[4 * q + 2]), n.z));
-          r[4 * q + 3] = __float_as_uint(fmaf(m.w, __uint_as_float(r[4 * q + 3]), n.w));
+          uint64_t s01 = f2_pack(n.x, n.y), s23 = f2_pack(n.z, n.w);
+          f2_fma(s01, m01, f2_pack(__uint_as_float(r[4 * q + 0]), __uint_as_float(r[4 * q + 1])));
+          f2_fma(s23, m23, f2_pack(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3])));
+          const float2 a = f2_unpack(s01), b = f2_unpack(s23);
+          o[4 * q + 0] = a.x;
+          o[4 * q + 1] = a.y;
+          o[4 * q + 2] = b.x;
+          o[4 * q + 3] = b.y;
         }
-        const int c0 = (ch * 16) % kClasses;
-        const bool first = ch * 16 < kClasses;
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          tm[c0 + i] = first ? __uint_as_float(r[i]) : fminf(tm[c0 + i], __uint_as_float(r[i]));
       };
-      // two 16-column register buffers: the next chunk loads while this one is processed
+      // Chunk ch holds classes (ch*16) mod kClasses + i (occurrence ch*16 / kClasses),
+      // so chunks 0, 2, 4, 6 cover classes 0..15 and 1, 3, 5, 7 classes 16..31.  The
+      // chunks are read in that order, two 16-column register buffers deep (the next
+      // chunk loads while this one is scored); per half, the tile minimum of a class
+      // is min(min(s0, s2), s4, s6), then the class's running (value, tile) pair
+      // takes one update.
+      static_assert(kSliceCols == 128 && kClasses == 32 && kOcc == 4, "chunk order below assumes 8 x 16 columns");
+      constexpr int kOrder[8] = {0, 2, 4, 6, 1, 3, 5, 7};
       uint32_t ra[16], rb[16];
-      tmem_ld16_async(taddr, ra);
-      tmem_wait_ld();
+      float tm[16], pend[16], sc[16];
+      // one running-minimum update per class and tile (classes h .. h+15)
+      auto update = [&](int h) {
 #pragma unroll
-      for (int ch = 0; ch < kSliceCols / 16; ch += 2) {
-        tmem_ld16_async(taddr + (ch + 1) * 16, rb);
-        process(ra, ch);
-        tmem_wait_ld();
-        if (ch + 2 < kSliceCols / 16) tmem_ld16_async(taddr + (ch + 2) * 16, ra);
-        process(rb, ch + 1);
-        tmem_wait_ld();
+        for (int i = 0; i < 16; ++i) {
+          const bool lt = tm[i] < best_s[h + i];
+          best_s[h + i] = lt ? tm[i] : best_s[h + i];
+          best_c[h + i] = lt ? tile : best_c[h + i];
+        }
+      };
+      tmem_ld16_async(taddr + kOrder[0] * 16, ra);
+      tmem_wait_ld16(ra);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        uint32_t(&cur)[16] = (k & 1) ? rb : ra;
+        uint32_t(&nxt)[16] = (k & 1) ? ra : rb;
+        if (k + 1 < 8) tmem_ld16_async(taddr + kOrder[k + 1] * 16, nxt);
+        const int occ = k & 3;
+        if (occ == 0) {
+          scores(cur, kOrder[k], tm);
+        } else if (occ == 1) {
+          scores(cur, kOrder[k], sc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) tm[i] = fminf(tm[i], sc[i]);
+        } else if (occ == 2) {
+          scores(cur, kOrder[k], pend);
+        } else {
+          scores(cur, kOrder[k], sc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) tm[i] = fmin3(tm[i], pend[i], sc[i]);
+          if (k == 3) update(0);  // the second half's update follows the arrival below
+        }
+        if (k + 1 < 8) tmem_wait_ld16(nxt);
       }
       // the warp's tensor-memory reads are complete (tcgen05.wait::ld is warp-wide):
       // one arrival per warp frees the accumulator
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_relaxed(acc_empty_c[acc]);
-      // one running-minimum update per class and tile
-#pragma unroll
-      for (int i = 0; i < kClasses; ++i) {
-        const bool lt = tm[i] < best_s[i];
-        best_s[i] = lt ? tm[i] : best_s[i];
-        best_c[i] = lt ? tile : best_c[i];
-      }
+      update(16);
       ++tile;
       acc ^= 1;
       if (acc == 0) accphase ^= 1;
