@@ -408,22 +408,13 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
   // Each group's kernels follow its mode (see HashTable): groups after the one
   // that resolves the last point of A return at once -- on clustered data the
   // coarse scales are rarely reached (1M x 384 unit mixture: no point past scale
-  // 4 of 10) -- and once few points are left a group runs in reverse.
-  // Every point of A resolved by the first group has its final b(a): with later
-  // groups to run, the crude distances of those points go on the side stream
-  // right after the first group, beside the later groups' latency-bound table
-  // work, and the rest follow the last group.
-  const bool split = cb->groups > 1 && crude_dist_vector_ok(A, B) && c->sm_count >= 2;
+  // 4 of 10) -- and once few points are left a group runs in reverse.  The crude
+  // distances follow the last group in one pass over A.  (Running those of the
+  // first group's points on a side stream beside the later groups was faster
+  // with a distance kernel of four memory round trips per row; with the whole
+  // row in flight the single pass is faster: 1M x 384 bf16, four hash seeds,
+  // CrudeNN 1.06-1.28 -> 0.97-1.06 ms.)
   for (int g = 0, L0 = 0; L0 < L; ++g, L0 += cb->plan.per_group) {
-    if (split && g == 1) {
-      ensure_side(c);
-      if (maxD) CHX_CUDA(cudaMemsetAsync(maxD, 0, sizeof(uint32_t), s));
-      CHX_CUDA(cudaEventRecord(c->fork_ev, s));
-      CHX_CUDA(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
-      // two of the four resident blocks per SM: room for the table kernels beside it
-      launch_crude_dist_part(A, B, hp->metric, bidx, D, maxD, level, L0, true, c->sm_count, c->side, 2);
-      CHX_CUDA(cudaEventRecord(c->join_ev, c->side));
-    }
     const int nl = std::min(cb->plan.per_group, L - L0);
     HashTable h{};
     h.slots = cb->slots;
@@ -446,11 +437,6 @@ static void run_crude(ch_ctx* c, const ch_set* A, const ch_set* B, const ch_hash
     launch_group_insert(cb->hB.src, L, L0, nl, cb->tab, h, status, c->sm_count, s);
     h.first = 0;
     launch_group_probe(cb->hA.src, L, L0, nl, cb->tab, h, bidx, level, c->sm_count, s);
-  }
-  if (split) {
-    CHX_CUDA(cudaStreamWaitEvent(s, c->join_ev, 0));
-    launch_crude_dist_part(A, B, hp->metric, bidx, D, maxD, level, cb->plan.per_group, false, c->sm_count, s, 4);
-    return;
   }
   launch_crude_dist(A, B, hp->metric, bidx, D, maxD, c->sm_count, s);
 }

@@ -388,13 +388,6 @@ void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB,
 // *maxD is cleared first unless keep_max)
 void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, uint32_t* maxD,
                        int sm_count, cudaStream_t s);
-// The same for the a with level[a] < split (below = true) or level[a] >= split
-// (below = false) only, folding into *maxD without clearing it; false (nothing
-// launched) where the vector form does not apply
-bool crude_dist_vector_ok(const ch_set* A, const ch_set* B);
-bool launch_crude_dist_part(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D,
-                            uint32_t* maxD, const uint8_t* level, int split, bool below, int sm_count, cudaStream_t s,
-                            int blocks_per_sm = 4);
 
 // sampling
 struct SampleWork {
