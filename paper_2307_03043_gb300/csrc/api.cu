@@ -474,7 +474,7 @@ static void take_scan(L& lay, ch_ctx* c, const ch_set* A, const ch_set* B, int64
                       uint32_t R, ScanBufs* sb) {
   sb->screen = screen_choice(screen, metric, A, B);
   if (sb->screen == CH_SCREEN_EXACT) {
-    sb->part.chunks = scan_exact_chunks(T, B->n, A->d, c->sm_count);
+    sb->part.chunks = scan_exact_chunks(T, B->n, A->d, A->dtype, c->sm_count);
     sb->part.val = lay.template take<float>(size_t(sb->part.chunks) * std::max<int64_t>(T, 1));
     sb->part.idx = lay.template take<int64_t>(size_t(sb->part.chunks) * std::max<int64_t>(T, 1));
     sb->screen_work = nullptr;

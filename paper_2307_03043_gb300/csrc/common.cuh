@@ -442,7 +442,7 @@ void launch_scan_exact(const ch_set* A, const int64_t* qidx, int64_t T, const ch
                        int sm_count, cudaStream_t s);
 void launch_scan_merge(ScanPart part, int64_t T, const int64_t* qidx, float* min_d, int64_t* argmin,
                        cudaStream_t s);
-int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count);
+int scan_exact_chunks(int64_t T, int64_t nB, int d, int dtype, int sm_count);
 
 // ---- batched exact scan of small dimensions (d <= 4) over many pairs at once
 constexpr int kBatchScanMaxD = 4;

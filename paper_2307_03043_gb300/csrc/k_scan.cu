@@ -116,10 +116,36 @@ __device__ __forceinline__ void stage_row(float* __restrict__ Ts, int r, const v
   }
 }
 
+// The binary32 form of stage_row as asynchronous 4-byte copies (cp.async, no
+// register round trip): row < 0 fills zeros (source size 0).  The copies land
+// after cp.async.wait_group.
+template <int S, int NJ>
+__device__ __forceinline__ void stage_row_async(float* __restrict__ Ts, int r, const float* __restrict__ base,
+                                                int64_t row, int d, int jl) {
+  static_assert(S % 8 == 4, "conflict-free staging needs S = 4 mod 8");
+  const float* src = base + (row >= 0 ? row : 0) * int64_t(d);
+  const uint32_t n = row >= 0 ? 4u : 0u;
+  auto one = [&](int j) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(static_cast<uint32_t>(
+                     __cvta_generic_to_shared(Ts + j * S + r))),
+                 "l"(src + j), "r"(n)
+                 : "memory");
+  };
+  if constexpr (NJ > 0) {
+#pragma unroll
+    for (int k = 0; k < 4 * NJ; ++k) {
+      const int j = jl + 8 * k;
+      if (k < 4 * (NJ - 1) || j < d) one(j);
+    }
+  } else {
+    for (int j = jl; j < d; j += 8) one(j);
+  }
+}
+
 // One block: QT samples against a chunk of B, staged SUB x BT rows at a time
 // (one pair of barriers per stage); each thread owns PQ samples x PB rows of
 // every BT-row sub-tile.
-template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ, int SUB>
+template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ, int SUB, bool DB>
 __global__ void __launch_bounds__(256, kScanBlocksPerSM)
     k_scan_exact(const void* __restrict__ A, const float* __restrict__ scA, const int64_t* __restrict__ qidx, int64_t T,
                  int64_t nA, const void* __restrict__ B, const float* __restrict__ scB, int64_t nB, int d,
@@ -132,7 +158,7 @@ __global__ void __launch_bounds__(256, kScanBlocksPerSM)
   constexpr int QS = QT + 4, BS = ST + 4;
   extern __shared__ __align__(16) float smem[];
   float* Qs = smem;
-  float* Bs = smem + size_t(d) * QS;
+  float* Bs = smem + size_t(d) * QS;  // DB: two stages, the next one in flight during this one's arithmetic
   __shared__ float r_val[NTB][QT];
   __shared__ int64_t r_idx[NTB][QT];
 
@@ -161,16 +187,40 @@ __global__ void __launch_bounds__(256, kScanBlocksPerSM)
     best_idx[p] = INT64_MAX;
   }
   const float* Qt = Qs + tq * PQ;
-  const float* Bt = Bs + tb * PB;
-
-  for (int64_t b0 = b_begin; b0 < b_end; b0 += ST) {
-    __syncthreads();
+  // stage `st` (rows b0 .. b0 + ST - 1 of the chunk) into buffer `buf`
+  auto stage_async = [&](int64_t b0, int buf) {
     const int64_t rows = min(static_cast<int64_t>(ST), b_end - b0);
+    float* dst = Bs + size_t(buf) * d * BS;
     for (int g = warp; g < ST / 4; g += 8) {
       const int r = 4 * g + rl;
-      stage_row<DT, BS, NJ>(Bs, r, B, scB, r < rows ? b0 + r : int64_t(-1), d, jl);
+      stage_row_async<BS, NJ>(dst, r, static_cast<const float*>(B), r < rows ? b0 + r : int64_t(-1), d, jl);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if constexpr (DB) {
+    if (b_begin < b_end) stage_async(b_begin, 0);
+  }
+  int buf = 0;
+  for (int64_t b0 = b_begin; b0 < b_end; b0 += ST, buf ^= 1) {
+    __syncthreads();
+    const int64_t rows = min(static_cast<int64_t>(ST), b_end - b0);
+    if constexpr (DB) {
+      // the next stage goes into the other buffer (its last readers passed the
+      // barrier above); then this stage's copies are waited for
+      if (b0 + ST < b_end) {
+        stage_async(b0 + ST, buf ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+    } else {
+      for (int g = warp; g < ST / 4; g += 8) {
+        const int r = 4 * g + rl;
+        stage_row<DT, BS, NJ>(Bs, r, B, scB, r < rows ? b0 + r : int64_t(-1), d, jl);
+      }
     }
     __syncthreads();
+    const float* Bt = Bs + (DB ? size_t(buf) * d * BS : 0) + tb * PB;
     // distances of this thread's pairs in sub-tile `sub`, folded into its minima
     auto scan_sub = [&](int sub) {
       float out[PQ][PB];
@@ -431,21 +481,28 @@ static TileShape tile_for(int d) {
   return {16, 16, 1};
 }
 
-static size_t scan_smem(int d) {
+// Binary32 rows of d <= 64 stage B through two buffers with asynchronous copies,
+// the next stage in flight during this one's arithmetic (100k x 100k, T = 4606:
+// d = 8 l1 0.82 -> 0.74 ms, d = 16 l1 1.22 -> 1.06 ms, d = 64 l1 3.12 -> 2.90 ms,
+// l2 3.35 -> 2.99 ms).  At d = 128 the second buffer leaves room for two blocks
+// per SM instead of three, and the scan was slower (5.0 -> 5.5 ms).
+static bool scan_double_buffered(int dtype, int d) { return dtype == CH_F32 && d <= 64; }
+
+static size_t scan_smem(int d, bool db) {
   const TileShape t = tile_for(d);
-  return size_t(d) * ((t.QT + 4) + (t.BT * t.SUB + 4)) * sizeof(float);
+  return size_t(d) * ((t.QT + 4) + (db ? 2 : 1) * (t.BT * t.SUB + 4)) * sizeof(float);
 }
 
 // Blocks of k_scan_exact one SM holds at once for dimension d: the dynamic
 // tiles, the static per-row minima (16 thread rows x QT x (4 + 8) bytes) and
 // the 1 KB reserved per block, out of 228 KB of shared memory per SM.
-static int scan_blocks_per_sm(int d) {
+static int scan_blocks_per_sm(int d, bool db) {
   const TileShape t = tile_for(d);
-  const size_t per_block = scan_smem(d) + size_t(16) * t.QT * 12 + 1024;
+  const size_t per_block = scan_smem(d, db) + size_t(16) * t.QT * 12 + 1024;
   return static_cast<int>(std::max<size_t>(1, std::min<size_t>(kScanBlocksPerSM, (228u * 1024u) / per_block)));
 }
 
-int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
+int scan_exact_chunks(int64_t T, int64_t nB, int d, int dtype, int sm_count) {
   if (d <= kSmallMaxD) {  // k_scan_small: about 4 blocks per SM, chunks of >= 256 points
     const int64_t qblocks = ceil_div(std::max<int64_t>(T, 1), kSmallQ);
     int64_t chunks = ceil_div(int64_t(sm_count) * 4, qblocks);
@@ -457,7 +514,7 @@ int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
   // when every wave runs at the same rate; ties go to fewer chunks (less merging).
   const TileShape t = tile_for(d);
   const int64_t qtiles = ceil_div(std::max<int64_t>(T, 1), t.QT);
-  const int64_t resident = int64_t(sm_count) * scan_blocks_per_sm(d);
+  const int64_t resident = int64_t(sm_count) * scan_blocks_per_sm(d, scan_double_buffered(dtype, d));
   const int64_t btiles = ceil_div(std::max<int64_t>(nB, 1), int64_t(t.BT) * t.SUB);  // stages
   const int64_t max_chunks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(btiles, 4), 4 * resident));
   int64_t best = 1, best_cost = INT64_MAX;
@@ -475,9 +532,11 @@ int scan_exact_chunks(int64_t T, int64_t nB, int d, int sm_count) {
 template <int DT, int METRIC, int QT, int BT, int PQ, int PB, int NJ = 0, int SUB = 1>
 static void scan_launch(const ch_set* A, const int64_t* qidx, int64_t T, const ch_set* B, ScanPart part,
                         cudaStream_t s) {
-  auto kern = k_scan_exact<DT, METRIC, QT, BT, PQ, PB, NJ, SUB>;
+  constexpr bool kDB = DT == CH_F32 && NJ > 0 && NJ <= 2;  // the launches of scan_double_buffered(DT, d)
+  auto kern = k_scan_exact<DT, METRIC, QT, BT, PQ, PB, NJ, SUB, kDB>;
+  const bool db = kDB;
   CHX_CHECK(tile_for(A->d).BT == BT && tile_for(A->d).SUB == SUB, CH_ENOTSUP, "scan tile mismatch");
-  const size_t smem = scan_smem(A->d);
+  const size_t smem = scan_smem(A->d, db);
   // a constant value, so concurrent callers on other threads never race on it
   CHX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
   const int64_t chunk_len = ceil_div(ceil_div(B->n, part.chunks), BT * SUB) * (BT * SUB);
@@ -545,7 +604,7 @@ void launch_scan_exact(const ch_set* A, const int64_t* qidx, int64_t T, const ch
                        int sm_count, cudaStream_t s) {
   (void)sm_count;
   if (T == 0) return;
-  CHX_CHECK(scan_smem(A->d) <= 220 * 1024, CH_ENOTSUP, "dimension too large for the exact scan");
+  CHX_CHECK(scan_smem(A->d, false) <= 220 * 1024, CH_ENOTSUP, "dimension too large for the exact scan");
   switch (A->dtype) {
     case CH_F32: scan_metric<CH_F32>(A, qidx, T, B, metric, part, s); break;
     case CH_BF16: scan_metric<CH_BF16>(A, qidx, T, B, metric, part, s); break;
