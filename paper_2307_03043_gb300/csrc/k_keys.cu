@@ -554,10 +554,9 @@ void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTa
   if (B.dd <= kRegRow) {
     dispatch_dt_w(B.dtype, B.dd, [&](auto dtc, auto wc) {
       auto kern = k_table_insert_ps<decltype(dtc)::value, decltype(wc)::value>;
-      // the nl scales share one wave
-      // nl blocks rows (one per scale) share the grid's two waves: a row count of
-      // n * nl, so a group of many scales keeps every row in its own thread where
-      // the waves allow (100k x 128, 10 scales: CrudeNN 0.163 -> 0.110 ms; 4096 d = 3
+      // the nl block rows (one per scale) share the grid's two waves: sized for a
+      // row count of n * nl, so a group of many scales keeps every row in its own
+      // thread where the waves allow (100k x 128, 10 scales: CrudeNN 0.163 -> 0.110 ms; 4096 d = 3
       // pairs: l2 149.3 -> 139.9 ms per batch)
       const int gx = std::max(1, table_grid(kern, B.n * nl, sm_count) / nl);
       launch_k(kern, dim3(static_cast<unsigned>(gx), static_cast<unsigned>(nl)), 128, 0, s, B, L, L0, nl, t, h,
