@@ -293,6 +293,85 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
   }
 }
 
+// Small dimensions (d <= 8, known at compile time): one fused launch per set.
+// Each block generates its own copy of G (d x KP entries, at most one per
+// thread) in shared memory, a thread keys rows in grid-stride order with the
+// same fmaf chains in coordinate order as k_project, and the block writes one
+// partial box (as k_project_tma does), so neither a separate G launch nor the
+// box initialisation is needed.
+constexpr int kProjSmallMaxD = 8;
+template <int DT, int KP, int D>
+__global__ void __launch_bounds__(128) k_project_small(const void* X, const float* scales, int64_t n, uint64_t seed,
+                                                       int k, float* Y, uint32_t* box, float* norms,
+                                                       uint32_t* status) {
+  pdl_entry();
+  static_assert(D * KP <= 128, "one G entry per thread");
+  __shared__ __align__(16) float s_g[D][KP];
+  __shared__ uint32_t s_box[2 * KP];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < D * KP) s_g[tid / KP][tid % KP] = gauss_entry(seed, k, tid / KP, tid % KP);
+  if (tid < 2 * KP) s_box[tid] = tid < KP ? 0xFFFFFFFFu : 0u;
+  __syncthreads();
+  uint32_t lo[KP], hi[KP];  // ordered-encoded, as k_project keeps them
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    lo[i] = 0xFFFFFFFFu;
+    hi[i] = 0u;
+  }
+  bool bad = false;
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + tid; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    float xv[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) xv[j] = load_elem<DT>(X, r, D, j, scales);
+    float acc[KP], sq = 0.0f;
+#pragma unroll
+    for (int i = 0; i < KP; ++i) acc[i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      sq = fmaf(xv[j], xv[j], sq);
+      bad |= !isfinite(xv[j]);
+#pragma unroll
+      for (int i = 0; i < KP; ++i) acc[i] = __fmaf_rn(s_g[j][i], xv[j], acc[i]);
+    }
+    if (KP == 16 && k == 16) {
+      float4* y4 = reinterpret_cast<float4*>(Y + r * 16);
+#pragma unroll
+      for (int i4 = 0; i4 < 4; ++i4) y4[i4] = make_float4(acc[4 * i4], acc[4 * i4 + 1], acc[4 * i4 + 2], acc[4 * i4 + 3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < KP; ++i)
+        if (i < k) Y[r * k + i] = acc[i];
+    }
+    if (norms) norms[r] = sq;
+#pragma unroll
+    for (int i = 0; i < KP; ++i) {
+      lo[i] = min(lo[i], ord_enc(acc[i]));
+      hi[i] = max(hi[i], ord_enc(acc[i]));
+    }
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    if (i < k) {
+      uint32_t l = lo[i], h = hi[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        l = min(l, __shfl_xor_sync(0xFFFFFFFFu, l, o));
+        h = max(h, __shfl_xor_sync(0xFFFFFFFFu, h, o));
+      }
+      if (lane == 0 && l <= h) {
+        atomicMin(&s_box[i], l);
+        atomicMax(&s_box[KP + i], h);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < 2 * k) {
+    const int i = tid < k ? tid : KP + tid - k;
+    box[size_t(blockIdx.x) * 2 * k + tid] = s_box[i];
+  }
+}
+
 // Asynchronous variant for rows whose byte length is a multiple of 16: each
 // 32-coordinate slice of the block's rows (and of G) is copied with 16-byte
 // cp.async into a double buffer, so the next slice is in flight while the
@@ -824,9 +903,30 @@ static int launch_project_tma(const ch_set* X, uint64_t seed, int k, float* Y, u
   return grid;
 }
 
+template <int DT, int KP>
+static int launch_project_small(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, float* norms,
+                                int sm_count, cudaStream_t s) {
+  const int grid = static_cast<int>(std::min<int64_t>(ceil_div(X->n, 128), std::min(sm_count, kMaxBoxParts)));
+  switch (X->d) {
+#define CHX_PS(DV)                                                                                              \
+  case DV:                                                                                                      \
+    launch_k(k_project_small<DT, KP, DV>, grid, 128, 0, s, X->data, X->scales, X->n, seed, k, Y, box, norms,  \
+             X->status);                                                                                        \
+    break;
+    CHX_PS(1) CHX_PS(2) CHX_PS(3) CHX_PS(4) CHX_PS(5) CHX_PS(6) CHX_PS(7) CHX_PS(8)
+#undef CHX_PS
+    default: CHX_CHECK(false, CH_EINVAL, "small projection: d must be in 1..8");
+  }
+  return grid;
+}
+
 template <int DT>
 static int project_any(const ch_set* X, uint64_t seed, int k, int kp, float* Y, uint32_t* box, float* norms,
                        int sm_count, cudaStream_t s) {
+  if (X->d <= kProjSmallMaxD && kp <= 16) {
+    if (kp == 8) return launch_project_small<DT, 8>(X, seed, k, Y, box, norms, sm_count, s);
+    return launch_project_small<DT, 16>(X, seed, k, Y, box, norms, sm_count, s);
+  }
   const int warps = project_tma_warps<DT>(X, kp);
   if (warps > 0) {
     if (kp == 8) return launch_project_tma<DT, 8>(X, seed, k, Y, box, norms, warps, sm_count, s);
