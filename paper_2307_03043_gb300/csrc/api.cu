@@ -948,6 +948,158 @@ ch_status ch_sampled_nn(ch_ctx* c, const ch_set* A, const int64_t* idx, int64_t 
 
 namespace chx {
 
+// ------------------------------------------------------------------ batched CrudeNN
+// A pair's CrudeNN runs in the batched launches when its scales fit one group of
+// bucket tables, its hashed rows fit registers and it uses the default grid
+// family with hash tables (the single-pair path's forward group, kernel for kernel).
+static bool crude_batchable(const ch_set* A, const ch_set* B, const ch_est_params* p) {
+  const ch_hash_params* hp = &p->hash;
+  if (p->sampling == CH_SAMPLING_UNIFORM || crude_kw(hp)) return false;
+  if (hp->group != CH_GROUP_HASH || hp->family != CH_FAMILY_GRID) return false;
+  if (A->dtype != B->dtype || A->n == 0 || B->n == 0) return false;
+  const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
+  if (dd > 32) return false;
+  const int L = static_cast<int>(hp->levels);
+  return table_plan(B->n, L).per_group >= L;
+}
+
+// bytes of bucket tables of one batched chunk
+static size_t crude_chunk_budget() { return size_t(1) << 30; }
+
+struct CrudeChunkPair {
+  int64_t i;  // index of the pair in the batch
+  Hashed hA, hB;
+  CrudePair d;
+};
+
+// CrudeNN of the listed pairs (all batchable, one metric, hashed type and
+// width, and storage type): per chunk of pairs, the l2 projections on the
+// lanes, then on c's stream one launch each of scale tables, inserts, probes and
+// crude distances for the whole chunk.  D_a goes to Dp[i].
+template <class OnLanes>
+static void run_crude_batched(ch_ctx* c, const std::vector<int64_t>& ids, const ch_set* const* A,
+                              const ch_set* const* B, const ch_est_params* params, const std::vector<float*>& Dp,
+                              ResBlock* dres, OnLanes&& on_lanes_of, int K) {
+  size_t at = 0;
+  while (at < ids.size()) {
+    // the chunk: pairs in order until the tables reach the budget
+    std::vector<CrudeChunkPair> ch;
+    size_t tab_bytes = 0;
+    while (at < ids.size()) {
+      const int64_t i = ids[at];
+      const int L = static_cast<int>(params[i].hash.levels);
+      const size_t tb = (size_t(L) << table_plan(B[i]->n, L).log_cap) * sizeof(ulonglong2);
+      if (!ch.empty() && tab_bytes + tb > crude_chunk_budget()) break;
+      tab_bytes += tb;
+      CrudeChunkPair cp;
+      cp.i = i;
+      ch.push_back(cp);
+      ++at;
+    }
+    const int np = static_cast<int>(ch.size());
+    // layout: descriptors and block prefixes, tables, then each pair's buffers
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    auto lay_pairs = [&](auto& lay) {
+      for (auto& cp : ch) {
+        const int64_t i = cp.i;
+        const ch_hash_params* hp = &params[i].hash;
+        const int L = static_cast<int>(hp->levels);
+        const int dd = hp->metric == CH_L1 ? A[i]->d : static_cast<int>(hp->proj_dim);
+        take_hashed(lay, A[i], hp, &cp.hA);
+        take_hashed(lay, B[i], hp, &cp.hB);
+        cp.d.t = take_tables(lay, dd, L);
+        cp.d.bidx = lay.template take<int64_t>(A[i]->n);
+        cp.d.level = lay.template take<uint8_t>(A[i]->n);
+      }
+    };
+    Layout m;
+    lay_pairs(m);
+    const size_t head = al(sizeof(CrudePair) * np) + 3 * al(sizeof(int) * (np + 1));
+    const size_t bytes = head + al(tab_bytes) + m.need + 256;
+    char* mem = nullptr;
+    CHX_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&mem), bytes, c->pool, c->stream));
+    CrudePair* dP = reinterpret_cast<CrudePair*>(mem);
+    int* dblk = reinterpret_cast<int*>(mem + al(sizeof(CrudePair) * np));
+    const size_t blk_stride = al(sizeof(int) * (np + 1)) / sizeof(int);
+    char* tables = mem + head;
+    Arena ar;
+    ar.base = tables + al(tab_bytes);
+    ar.cap = bytes - head - al(tab_bytes);
+    ar.borrowed = true;
+    Layout t;
+    t.measure = false;
+    t.a = &ar;
+    lay_pairs(t);
+    // the projections (l2) on the lanes; l1 rows are the sets' own
+    if (params[ch[0].i].hash.metric == CH_L2) {
+      std::vector<int64_t> which(np);
+      for (int j = 0; j < np; ++j) which[j] = j;
+      on_lanes_of(which, [&](ch_ctx* lane, int64_t j) {
+        CrudeChunkPair& cp = ch[j];
+        const ch_hash_params* hp = &params[cp.i].hash;
+        run_hashed(lane, A[cp.i], hp, &cp.hA, &dres[cp.i].status);
+        run_hashed(lane, B[cp.i], hp, &cp.hB, &dres[cp.i].status);
+      });
+    } else {
+      for (auto& cp : ch) {
+        run_hashed(c, A[cp.i], &params[cp.i].hash, &cp.hA, &dres[cp.i].status);
+        run_hashed(c, B[cp.i], &params[cp.i].hash, &cp.hB, &dres[cp.i].status);
+      }
+    }
+    // descriptors and block runs
+    std::vector<CrudePair> hP(np);
+    std::vector<int> b_ins(np + 1, 0), b_prb(np + 1, 0), b_dst(np + 1, 0);
+    char* tab = tables;
+    for (int j = 0; j < np; ++j) {
+      CrudeChunkPair& cp = ch[j];
+      const int64_t i = cp.i;
+      const ch_hash_params* hp = &params[i].hash;
+      const int L = static_cast<int>(hp->levels);
+      CrudePair& d = cp.d;
+      d.A = cp.hA.src;
+      d.B = cp.hB.src;
+      d.boxA = cp.hA.box;
+      d.boxB = cp.hB.box;
+      d.partsA = cp.hA.box_parts;
+      d.partsB = cp.hB.box_parts;
+      d.log_cap = table_plan(B[i]->n, L).log_cap;
+      d.slots = reinterpret_cast<ulonglong2*>(tab);
+      tab += (size_t(L) << d.log_cap) * sizeof(ulonglong2);
+      d.L = L;
+      d.top_exp = hp->top_exp;
+      d.seed = hp->hash_seed;
+      d.rawA = A[i]->data;
+      d.scA = A[i]->scales;
+      d.rawB = B[i]->data;
+      d.scB = B[i]->scales;
+      d.d = A[i]->d;
+      d.gx_insert = static_cast<int>(std::min<int64_t>(ceil_div(B[i]->n, 128), 64));
+      d.gx_probe = static_cast<int>(std::min<int64_t>(ceil_div(A[i]->n, 128), 256));
+      d.gx_dist = static_cast<int>(std::min<int64_t>(ceil_div(A[i]->n * crude_dist_lanes(A[i]->d), 256), 256));
+      d.D = Dp[i];
+      d.status = &dres[i].status;
+      hP[j] = d;
+      b_ins[j + 1] = b_ins[j] + d.gx_insert * L;
+      b_prb[j + 1] = b_prb[j] + d.gx_probe;
+      b_dst[j + 1] = b_dst[j] + d.gx_dist;
+    }
+    cudaStream_t s = c->stream;
+    CHX_CUDA(cudaMemcpyAsync(dP, hP.data(), sizeof(CrudePair) * np, cudaMemcpyHostToDevice, s));
+    CHX_CUDA(cudaMemcpyAsync(dblk, b_ins.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, s));
+    CHX_CUDA(cudaMemcpyAsync(dblk + blk_stride, b_prb.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, s));
+    CHX_CUDA(cudaMemcpyAsync(dblk + 2 * blk_stride, b_dst.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, s));
+    CHX_CUDA(cudaMemsetAsync(tables, 0, tab_bytes, s));
+    const ch_set* A0 = A[ch[0].i];
+    const ch_hash_params* hp0 = &params[ch[0].i].hash;
+    launch_scale_tables_batch(dP, np, s);
+    launch_insert_batch(dP, dblk, np, b_ins[np], hP[0].B.dtype, hP[0].B.dd, s);
+    launch_probe_batch(dP, dblk + blk_stride, np, b_prb[np], hP[0].A.dtype, hP[0].A.dd, s);
+    launch_crude_dist_batch(dP, dblk + 2 * blk_stride, np, b_dst[np], A0->dtype, hp0->metric, A0->d, s);
+    CHX_CUDA(cudaFreeAsync(mem, s));
+  }
+  (void)K;
+}
+
 // ------------------------------------------------------------------ batched small scans
 // Chunk length of the batched small scan, tuned per (storage type, metric, d,
 // size class of B) by timing candidate lengths on the first batch that needs it
@@ -1240,15 +1392,20 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
   for (int64_t i : run)
     small[i] = A[i]->d <= kBatchScanMaxD && Ts[i] > 0 && B[i]->n < (int64_t(1) << 32) - 1 &&
                screen_choice(params[i].screen, params[i].hash.metric, A[i], B[i]) == CH_SCREEN_EXACT;
+  // pairs whose CrudeNN runs in the batched launches (the others on the lanes)
+  std::vector<char> bcr(count, 0);
+  for (int64_t i : run) bcr[i] = crude_batchable(A[i], B[i], &params[i]);
   std::vector<size_t> need(K, 0);
   for (int64_t i : run) {
     const ch_est_params* p = &params[i];
     ch_ctx* lane = c->lanes[i % K];
     Layout mc, ms;
     CrudeBufs cb;
-    take_crude(mc, A[i], B[i], &p->hash, &cb);
-    mc.template take<int64_t>(A[i]->n);  // b(a)
-    mc.template take<uint8_t>(A[i]->n);  // level
+    if (!bcr[i]) {
+      take_crude(mc, A[i], B[i], &p->hash, &cb);
+      mc.template take<int64_t>(A[i]->n);  // b(a)
+      mc.template take<uint8_t>(A[i]->n);  // level
+    }
     ScanBufs sc;
     if (!small[i]) take_scan(ms, lane, A[i], B[i], Ts[i], p->hash.metric, p->screen, Rs[i], &sc);
     need[i % K] = std::max(need[i % K], std::max(mc.need, ms.need) + 256);
@@ -1346,6 +1503,7 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
   fork();
   on_lanes([&](ch_ctx* lane, int64_t i) {  // 1. CrudeNN (or the uniform baseline's equal weights)
     const ch_est_params* p = &params[i];
+    if (bcr[i]) return;  // below, in the batched launches
     if (p->sampling == CH_SAMPLING_UNIFORM) {
       launch_fill_ones(Dp[i], A[i]->n, lane->stream);
       return;
@@ -1361,6 +1519,39 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
     run_crude(lane, A[i], B[i], &p->hash, &cb, bidx, level, Dp[i], &dres[i].status, nullptr);
   });
   join();
+  {
+    // the batched CrudeNN, one run per (metric, hashed type and width, storage type)
+    std::map<std::tuple<int, int, int, int>, std::vector<int64_t>> groups;
+    for (int64_t i : run) {
+      if (!bcr[i]) continue;
+      const ch_hash_params* hp = &params[i].hash;
+      const int dd = hp->metric == CH_L1 ? A[i]->d : static_cast<int>(hp->proj_dim);
+      const int hdt = hp->metric == CH_L1 ? A[i]->dtype : CH_F32;
+      groups[{hp->metric, hdt, dd, A[i]->dtype}].push_back(i);
+    }
+    // body(lane, j) for j in which, j on lane j mod K; c's stream -> lanes -> c's stream
+    auto on_lanes_of = [&](const std::vector<int64_t>& which, auto&& body) {
+      fork();
+      std::vector<std::thread> th;
+      std::vector<ch_status> err(K, CH_OK);
+      for (int k = 0; k < K; ++k)
+        th.emplace_back([&, k] {
+          cudaSetDevice(c->device);
+          try {
+            for (int64_t j : which)
+              if (j % K == k) body(c->lanes[k], j);
+          } catch (const Err& e) {
+            err[k] = e.st;
+          } catch (...) {
+            err[k] = CH_ECUDA;
+          }
+        });
+      for (auto& t : th) t.join();
+      join();
+      for (int k = 0; k < K; ++k) CHX_CHECK(err[k] == CH_OK, err[k], "batched CrudeNN: a projection failed");
+    };
+    for (auto& g : groups) run_crude_batched(c, g.second, A, B, params, Dp, dres, on_lanes_of, K);
+  }
   launch_batch_sample(ditems, static_cast<int64_t>(run.size()), c->stream);  // 2.
   fork();
   on_lanes([&](ch_ctx* lane, int64_t i) {  // 3. the sampled scans (the small pairs' below)

@@ -389,6 +389,55 @@ void launch_sort_group(const uint64_t* keysA, int64_t nA, const uint64_t* keysB,
 void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64_t* bidx, float* D, uint32_t* maxD,
                        int sm_count, cudaStream_t s);
 
+// CrudeNN of many pairs in one launch per step (batched estimates): every pair's
+// scales fit one group of bucket tables, its hashed rows fit registers (dd <= 32)
+// and A and B share one storage type.  Each kernel's blocks are cut into
+// consecutive runs, one per pair (blk0[p] .. blk0[p + 1] - 1); a block finds its
+// pair by binary search and then does exactly what the single-pair kernel's
+// block of the same index does.
+struct CrudePair {
+  HashSrc A, B;                      // hashed rows of the two sets
+  const uint32_t* boxA;              // [partsA][2][dd] partial boxes of A's hashed rows
+  const uint32_t* boxB;
+  int partsA, partsB;
+  ScaleTables t;
+  ulonglong2* slots;                 // [L][2^log_cap] bucket tables, zeroed before the launches
+  uint32_t log_cap;
+  int L, top_exp;
+  uint64_t seed;
+  const void* rawA;                  // the stored rows, for D_a
+  const float* scA;
+  const void* rawB;
+  const float* scB;
+  int d;
+  int gx_insert, gx_probe, gx_dist;  // blocks per pair: insert (per scale), probe, crude distance
+  int64_t* bidx;
+  uint8_t* level;
+  float* D;
+  uint32_t* status;
+};
+// the pair whose run of blocks holds block b: the largest p with blk0[p] <= b
+__device__ __forceinline__ int find_pair(const int* __restrict__ blk0, int np, int b) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&blk0[mid]) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+// scale tables of every pair (a block per pair; e_top is not reported)
+void launch_scale_tables_batch(const CrudePair* P, int np, cudaStream_t s);
+// B into the tables at every scale, then A's probes: blk0 [np + 1] prefix of
+// the per-pair block counts (insert: gx_insert * L, probe: gx_probe)
+void launch_insert_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int dd, cudaStream_t s);
+void launch_probe_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int dd, cudaStream_t s);
+// D_a of every pair (G lanes per a, as launch_crude_dist's lane form; blocks gx_dist)
+void launch_crude_dist_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int metric, int d,
+                             cudaStream_t s);
+// lanes per a of the batched crude distance for dimension d
+int crude_dist_lanes(int d);
+
 // sampling
 struct SampleWork {
   uint32_t* maxD;        // [1] ordered-encoded max

@@ -972,20 +972,10 @@ int launch_project(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* bo
 // e_top = ceil(log2 Delta) + 1 (0 if Delta = 0); scales 2^e, e = e_top-L+1..e_top.
 // Shift z_{e,j} = (w0 >> 8) 2^(e-24), w0 = Philox(j, e, 1, 0).x; multiplier
 // K_j = Philox(j, 0, 4, 0).(y:x) | 1; salt_e = mix64((uint32)e ^ seed).
-__global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
-                               int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
-                               uint4* zero, int64_t zero16, unsigned long long* left, int64_t n_left,
-                               int n_zero_words) {
-  pdl_entry();
-  if (left && blockIdx.x == 0 && threadIdx.x <= n_zero_words)
-    left[threadIdx.x] = threadIdx.x == 0 ? static_cast<unsigned long long>(n_left) : 0ull;
-  if (blockIdx.x > 0) {  // the other blocks clear the bucket tables meanwhile
-    const uint4 z = make_uint4(0, 0, 0, 0);
-    for (int64_t i = int64_t(blockIdx.x - 1) * blockDim.x + threadIdx.x; i < zero16;
-         i += int64_t(gridDim.x - 1) * blockDim.x)
-      zero[i] = z;
-    return;
-  }
+// the scale tables of one pair, by one whole block
+__device__ void scale_tables_block(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
+                                   int top_exp_in, uint64_t seed, const ScaleTables& t, int32_t* e_top_out,
+                                   uint32_t* status) {
   __shared__ int s_elo;
   __shared__ uint32_t s_box[2 * kMaxProj];  // merged partial boxes (partial boxes only come with dd <= kMaxProj)
   const bool merge = partsA > 1 || partsB > 1;
@@ -1062,6 +1052,35 @@ __global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t*
   }
 }
 
+__global__ void k_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
+                               int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
+                               uint4* zero, int64_t zero16, unsigned long long* left, int64_t n_left,
+                               int n_zero_words) {
+  pdl_entry();
+  if (left && blockIdx.x == 0 && threadIdx.x <= n_zero_words)
+    left[threadIdx.x] = threadIdx.x == 0 ? static_cast<unsigned long long>(n_left) : 0ull;
+  if (blockIdx.x > 0) {  // the other blocks clear the bucket tables meanwhile
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int64_t i = int64_t(blockIdx.x - 1) * blockDim.x + threadIdx.x; i < zero16;
+         i += int64_t(gridDim.x - 1) * blockDim.x)
+      zero[i] = z;
+    return;
+  }
+  scale_tables_block(boxA, partsA, boxB, partsB, dd, L, top_exp_in, seed, t, e_top_out, status);
+}
+
+__global__ void k_scale_tables_batch(const CrudePair* P) {
+  pdl_entry();
+  const CrudePair& p = P[blockIdx.x];
+  scale_tables_block(p.boxA, p.partsA, p.boxB, p.partsB, p.A.dd, p.L, p.top_exp, p.seed, p.t, nullptr, p.status);
+}
+
+void launch_scale_tables_batch(const CrudePair* P, int np, cudaStream_t s) {
+  if (np == 0) return;
+  launch_k(k_scale_tables_batch, np, 256, 0, s, P);
+  launch_check("scale_tables_batch");
+}
+
 void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB, int partsB, int dd, int L,
                          int top_exp_in, uint64_t seed, ScaleTables t, int32_t* e_top_out, uint32_t* status,
                          cudaStream_t s, void* zero, size_t zero_bytes, int sm_count, unsigned long long* left,
@@ -1083,18 +1102,16 @@ void launch_scale_tables(const uint32_t* boxA, int partsA, const uint32_t* boxB,
 // for s = G/2 .. 1 via shuffles (steps s >= G would add +0).  Grid-stride; with
 // maxD set, each block also folds max_a D_a into *maxD (ordered-encoded) with a
 // single atomic, which saves the sampler its own pass over D.
+// D_a of one pair's points by the warps of a block run: lane group of G lanes
+// per a, first = this block's first lane index, step = the run's lanes
 template <int DTA, int DTB, int METRIC>
-__global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* scA, int64_t nA, const void* B,
-                                                    const float* scB, int d, int G, const int64_t* bidx,
-                                                    float* D, uint32_t* maxD) {
-  pdl_entry();
+__device__ __forceinline__ void crude_dist_span(const void* A, const float* scA, int64_t nA, const void* B,
+                                                const float* scB, int d, int G, const int64_t* bidx, float* D,
+                                                int64_t first, int64_t step, uint32_t& mx) {
   const int gshift = __ffs(G) - 1;
-  __shared__ uint32_t s_max[8];
-  uint32_t mx = 0;
   const int64_t total = nA * G;
-  const int64_t step = int64_t(gridDim.x) * blockDim.x;
   // every lane runs the same number of rounds (the shuffles need the whole warp)
-  for (int64_t g0 = int64_t(blockIdx.x) * blockDim.x; g0 < total; g0 += step) {
+  for (int64_t g0 = first; g0 < total; g0 += step) {
     const int64_t gt = g0 + threadIdx.x;
     const int64_t a = gt >> gshift;  // G is a power of two: no 64-bit division
     const int q = static_cast<int>(gt & (G - 1));
@@ -1120,6 +1137,17 @@ __global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* 
       mx = max(mx, ord_enc(v));
     }
   }
+}
+
+template <int DTA, int DTB, int METRIC>
+__global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* scA, int64_t nA, const void* B,
+                                                    const float* scB, int d, int G, const int64_t* bidx,
+                                                    float* D, uint32_t* maxD) {
+  pdl_entry();
+  __shared__ uint32_t s_max[8];
+  uint32_t mx = 0;
+  crude_dist_span<DTA, DTB, METRIC>(A, scA, nA, B, scB, d, G, bidx, D, int64_t(blockIdx.x) * blockDim.x,
+                                    int64_t(gridDim.x) * blockDim.x, mx);
   if (!maxD) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
@@ -1129,6 +1157,45 @@ __global__ void __launch_bounds__(256) k_crude_dist(const void* A, const float* 
     for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) mx = max(mx, s_max[w]);
     if (mx) atomicMax(maxD, mx);
   }
+}
+
+int crude_dist_lanes(int d) {
+  int G = 1;
+  while (G < d && G < 32) G <<= 1;
+  return G;
+}
+
+template <int DT, int METRIC>
+__global__ void __launch_bounds__(256) k_crude_dist_batch(const CrudePair* P, const int* blk0, int np) {
+  pdl_entry();
+  const int pi = find_pair(blk0, np, blockIdx.x);
+  const CrudePair& p = P[pi];
+  int G = 1;
+  while (G < p.d && G < 32) G <<= 1;
+  uint32_t mx = 0;
+  const int64_t local = blockIdx.x - blk0[pi];
+  crude_dist_span<DT, DT, METRIC>(p.rawA, p.scA, p.A.n, p.rawB, p.scB, p.d, G, p.bidx, p.D, local * blockDim.x,
+                                  int64_t(p.gx_dist) * blockDim.x, mx);
+}
+
+void launch_crude_dist_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int metric, int d,
+                             cudaStream_t s) {
+  (void)d;
+  if (np == 0 || blocks == 0) return;
+#define CHX_CDB(DTV)                                                                                         \
+  do {                                                                                                       \
+    if (metric == CH_L1)                                                                                     \
+      launch_k(k_crude_dist_batch<DTV, CH_L1>, blocks, 256, 0, s, P, blk0, np);                              \
+    else                                                                                                     \
+      launch_k(k_crude_dist_batch<DTV, CH_L2>, blocks, 256, 0, s, P, blk0, np);                              \
+  } while (0)
+  switch (dtype) {
+    case CH_F32: CHX_CDB(CH_F32); break;
+    case CH_BF16: CHX_CDB(CH_BF16); break;
+    default: CHX_CDB(CH_FP8E4M3); break;
+  }
+#undef CHX_CDB
+  launch_check("crude_dist_batch");
 }
 
 // Vector form for rows of a multiple of 16 bytes on 16-byte aligned bases (A and B

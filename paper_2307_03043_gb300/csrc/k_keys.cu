@@ -442,6 +442,60 @@ __global__ void __launch_bounds__(128) k_table_probe(HashSrc src, int L, int L0,
   if (h.left) take_off_left(h, resolved);
 }
 
+// Batched forms (one launch for many pairs, each pair's scales in one group):
+// block run of pair p, local block i = (scale l, x) with x < gx_insert inserts
+// B's rows x, x + gx_insert * 128, ... at scale l, as k_table_insert_ps does.
+template <int DT, int W>
+__global__ void __launch_bounds__(128) k_table_insert_batch(const CrudePair* P, const int* blk0, int np) {
+  pdl_entry();
+  const int pi = find_pair(blk0, np, blockIdx.x);
+  const CrudePair& p = P[pi];
+  const int local = blockIdx.x - __ldg(&blk0[pi]);
+  const int gx = p.gx_insert;
+  const int l = local / gx;
+  __shared__ GroupConsts<W> gc;
+  load_group_consts(gc, p.t, p.B.dd, p.L, 0, p.L);
+  const HashSrc src = p.B;
+  const size_t cap = size_t(1) << p.log_cap;
+  for (int64_t r = int64_t(local % gx) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gx) * blockDim.x) {
+    float y[W];
+    load_row<DT, W>(src, r, y);
+    table_insert(p.slots + size_t(l) * cap, p.log_cap, group_key(y, src.dd, l, gc), r, p.status);
+  }
+}
+
+// block run of pair p: each a walks the pair's scales in increasing order and
+// stops at the first bucket that holds a b, as k_table_probe does for a single group
+template <int DT, int W>
+__global__ void __launch_bounds__(128) k_table_probe_batch(const CrudePair* P, const int* blk0, int np) {
+  pdl_entry();
+  const int pi = find_pair(blk0, np, blockIdx.x);
+  const CrudePair& p = P[pi];
+  const int local = blockIdx.x - __ldg(&blk0[pi]);
+  const int gx = p.gx_probe;
+  __shared__ GroupConsts<W> gc;
+  load_group_consts(gc, p.t, p.A.dd, p.L, 0, p.L);
+  const HashSrc src = p.A;
+  const int L = p.L;
+  const size_t cap = size_t(1) << p.log_cap;
+  for (int64_t r = int64_t(local) * blockDim.x + threadIdx.x; r < src.n; r += int64_t(gx) * blockDim.x) {
+    int64_t bb = 0;
+    int lv = L;
+    float y[W];
+    load_row<DT, W>(src, r, y);
+    for (int l = 0; l < L; ++l) {
+      const int64_t b = table_find(p.slots + size_t(l) * cap, p.log_cap, group_key(y, src.dd, l, gc));
+      if (b >= 0) {
+        bb = b;
+        lv = l;
+        break;
+      }
+    }
+    p.bidx[r] = bb;
+    p.level[r] = static_cast<uint8_t>(lv);
+  }
+}
+
 template <int DT, int W>
 __global__ void __launch_bounds__(128) k_keys_write(HashSrc src, int L, ScaleTables t, uint64_t* keys) {
   pdl_entry();
@@ -480,8 +534,6 @@ void dispatch_dt_w(int dtype, int dd, F&& f) {
 }
 
 }  // namespace
-
-// SimHash keys}  // namespace
 
 // SimHash keys (random hyperplanes at every scale): bit i of a point is 1 unless
 // y_i < 0; level l keeps the first max(1, K >> l) bits; key = mix64(bits +
@@ -596,6 +648,24 @@ void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTab
                L0, nl, t, h, bidx, level);
   });
   launch_check("table_probe");
+}
+
+void launch_insert_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int dd, cudaStream_t s) {
+  if (np == 0 || blocks == 0) return;
+  CHX_CHECK(dd <= kRegRow, CH_EINVAL, "batched insert: hashed rows of <= 32 values");
+  dispatch_dt_w(dtype, dd, [&](auto dtc, auto wc) {
+    launch_k(k_table_insert_batch<decltype(dtc)::value, decltype(wc)::value>, blocks, 128, 0, s, P, blk0, np);
+  });
+  launch_check("table_insert_batch");
+}
+
+void launch_probe_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int dd, cudaStream_t s) {
+  if (np == 0 || blocks == 0) return;
+  CHX_CHECK(dd <= kRegRow, CH_EINVAL, "batched probe: hashed rows of <= 32 values");
+  dispatch_dt_w(dtype, dd, [&](auto dtc, auto wc) {
+    launch_k(k_table_probe_batch<decltype(dtc)::value, decltype(wc)::value>, blocks, 128, 0, s, P, blk0, np);
+  });
+  launch_check("table_probe_batch");
 }
 
 void launch_group_reverse(HashSrc A, HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, int64_t* bidx,
