@@ -1414,7 +1414,7 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
   // the batch allocation: result blocks, the work list, then each pair's arrays
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   size_t arena = al(sizeof(ResBlock) * count) + al(sizeof(BatchItem) * std::max<size_t>(run.size(), 1));
-  size_t best_bytes = 0;  // the small pairs' packed minima, one block (cleared together)
+  size_t best_bytes = 0;  // the small pairs' minima (distance bits << 32), one block (cleared together)
   for (int64_t i : run) {
     arena += al(size_t(A[i]->n) * 4) + 2 * al(size_t(A[i]->n) * 8) + al(size_t(Ts[i]) * 8) + al(size_t(Ts[i]) * 4);
     if (small[i]) best_bytes += al(size_t(Ts[i]) * 8);

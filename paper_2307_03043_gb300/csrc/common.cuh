@@ -504,7 +504,7 @@ struct SmallScanPair {
   const void* B;
   const float* scB;
   int64_t nB;
-  unsigned long long* best;  // [T] min over B of (canonical distance bits << 32 | index), preset to all ones
+  unsigned long long* best;  // [T] min over B of canonical distance bits << 32, preset to all ones
 };
 struct SmallScanItem {
   int32_t pair;    // index into the pair list
@@ -514,7 +514,7 @@ struct SmallScanItem {
 // samples per item of the batched small scan
 int small_scan_samples_per_item();
 // one persistent launch over every item (all pairs of one storage type, metric
-// and dimension d <= 4); each item's minima fold into best[] by atomicMin
+// and dimension d <= 4); each item's minimum distances fold into best[] by atomicMin
 void launch_scan_small_batch(const SmallScanPair* pairs, const SmallScanItem* items, int64_t n_items,
                              int64_t chunk_len, int dtype, int metric, int d, int sm_count, cudaStream_t s);
 

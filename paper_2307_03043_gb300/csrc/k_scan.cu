@@ -372,10 +372,16 @@ __global__ void __launch_bounds__(256) k_scan_small(const void* __restrict__ A, 
 }
 
 // The batched form: one persistent launch over items (pair, sample block, chunk
-// of B) of many pairs of one storage type, metric and dimension; each item walks
-// its chunk exactly as k_scan_small does and folds each sample's minimum into the
-// pair's best[] as (canonical distance bits << 32 | b), so the smallest distance
-// wins and, among equal distances, the smallest index (the merge's rule).
+// of B) of many pairs of one storage type, metric and dimension.  The estimate
+// needs only each sample's minimum distance, not the point attaining it, so an
+// item keeps the minimum of the canonical l1 sum or squared l2 sum per sample
+// (one min per pair instead of a compare and two selects) and folds it, after
+// one square root for l2 (sqrt is monotone, so sqrt(min) = min(sqrt)), into the
+// pair's best[] as canonical distance bits << 32 by atomicMin.  kBatchPQ samples
+// per thread amortise the broadcast reads of each B row.
+constexpr int kBatchPQ = 8;
+constexpr int kBatchQ = 256 * kBatchPQ;  // samples per item
+
 template <int DT, int METRIC, int D>
 __global__ void __launch_bounds__(256) k_scan_small_batch(const SmallScanPair* __restrict__ pairs,
                                                           const SmallScanItem* __restrict__ items, int64_t n_items,
@@ -385,22 +391,19 @@ __global__ void __launch_bounds__(256) k_scan_small_batch(const SmallScanPair* _
   for (int64_t w = blockIdx.x; w < n_items; w += gridDim.x) {
     const SmallScanItem it = items[w];
     const SmallScanPair pr = pairs[it.pair];
-    const int64_t l0 = int64_t(it.sblock) * kSmallQ + threadIdx.x;
+    const int64_t l0 = int64_t(it.sblock) * kBatchQ + threadIdx.x;
     const int64_t b_begin = it.b0;
     const int64_t b_end = min(pr.nB, b_begin + chunk_len);
-    float q[kSmallPQ][D];
-    float best_val[kSmallPQ], best_p0[kSmallPQ];
-    int64_t best_idx[kSmallPQ];
+    float q[kBatchPQ][D];
+    float best[kBatchPQ];
 #pragma unroll
-    for (int p = 0; p < kSmallPQ; ++p) {
+    for (int p = 0; p < kBatchPQ; ++p) {
       const int64_t l = l0 + 256 * p;
       int64_t a = -1;
       if (l < pr.T) a = pr.qidx[l];
 #pragma unroll
       for (int j = 0; j < D; ++j) q[p][j] = (a >= 0 && a < pr.nA) ? load_elem<DT>(pr.A, a, D, j, pr.scA) : 0.0f;
-      best_val[p] = __int_as_float(0x7F800000);
-      best_p0[p] = __int_as_float(0x7F800000);
-      best_idx[p] = INT64_MAX;
+      best[p] = __int_as_float(0x7F800000);
     }
     for (int64_t b0 = b_begin; b0 < b_end; b0 += kSmallBT) {
       const int rows = static_cast<int>(min(static_cast<int64_t>(kSmallBT), b_end - b0));
@@ -412,37 +415,24 @@ __global__ void __launch_bounds__(256) k_scan_small_batch(const SmallScanPair* _
 #pragma unroll
         for (int j = 0; j < D; ++j) bv[j] = Bs[r * D + j];
 #pragma unroll
-        for (int p = 0; p < kSmallPQ; ++p) {
+        for (int p = 0; p < kBatchPQ; ++p) {
           float leaf[D];
 #pragma unroll
           for (int j = 0; j < D; ++j) {
             const float t = __fsub_rn(q[p][j], bv[j]);
             leaf[j] = (METRIC == CH_L1) ? fabsf(t) : __fmul_rn(t, t);
           }
-          const float v = small_node<D, 0, 1>(leaf);
-          if (METRIC == CH_L1) {
-            if (v < best_val[p]) {
-              best_val[p] = v;
-              best_idx[p] = b0 + r;
-            }
-          } else if (v < best_p0[p]) {
-            best_p0[p] = v;
-            const float sv = __fsqrt_rn(v);
-            if (sv < best_val[p]) {
-              best_val[p] = sv;
-              best_idx[p] = b0 + r;
-            }
-          }
+          best[p] = fminf(best[p], small_node<D, 0, 1>(leaf));
         }
       }
     }
 #pragma unroll
-    for (int p = 0; p < kSmallPQ; ++p) {
+    for (int p = 0; p < kBatchPQ; ++p) {
       const int64_t l = l0 + 256 * p;
-      // (no point below +inf: +inf with index bits all ones, still below the preset)
-      if (l < pr.T)
-        atomicMin(&pr.best[l], (static_cast<unsigned long long>(__float_as_uint(best_val[p])) << 32) |
-                                   static_cast<unsigned long long>(static_cast<uint32_t>(best_idx[p])));
+      if (l < pr.T) {
+        const float m = (METRIC == CH_L1) ? best[p] : __fsqrt_rn(best[p]);
+        atomicMin(&pr.best[l], static_cast<unsigned long long>(__float_as_uint(m)) << 32);
+      }
     }
     __syncthreads();  // Bs is refilled by the next item
   }
@@ -620,7 +610,7 @@ void launch_scan_merge(ScanPart part, int64_t T, const int64_t* qidx, float* min
   launch_check("scan_merge");
 }
 
-int small_scan_samples_per_item() { return kSmallQ; }
+int small_scan_samples_per_item() { return kBatchQ; }
 
 template <int DT, int METRIC>
 static void small_batch_d(const SmallScanPair* pairs, const SmallScanItem* items, int64_t n, int64_t chunk_len, int d,
