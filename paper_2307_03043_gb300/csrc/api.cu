@@ -1014,13 +1014,17 @@ static void run_crude_batched(ch_ctx* c, const std::vector<int64_t>& ids, const 
     };
     Layout m;
     lay_pairs(m);
-    const size_t head = al(sizeof(CrudePair) * np) + 3 * al(sizeof(int) * (np + 1));
+    // small-d projections: a ProjSet per set and a block-run prefix per (type, d) run
+    const size_t proj_head = al(sizeof(ProjSet) * 2 * np) + al(sizeof(int) * (2 * np + 64));
+    const size_t head = al(sizeof(CrudePair) * np) + 3 * al(sizeof(int) * (np + 1)) + proj_head;
     const size_t bytes = head + al(tab_bytes) + m.need + 256;
     char* mem = nullptr;
     CHX_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&mem), bytes, c->pool, c->stream));
     CrudePair* dP = reinterpret_cast<CrudePair*>(mem);
     int* dblk = reinterpret_cast<int*>(mem + al(sizeof(CrudePair) * np));
     const size_t blk_stride = al(sizeof(int) * (np + 1)) / sizeof(int);
+    ProjSet* dS = reinterpret_cast<ProjSet*>(mem + al(sizeof(CrudePair) * np) + 3 * al(sizeof(int) * (np + 1)));
+    int* dSblk = reinterpret_cast<int*>(reinterpret_cast<char*>(dS) + al(sizeof(ProjSet) * 2 * np));
     char* tables = mem + head;
     Arena ar;
     ar.base = tables + al(tab_bytes);
@@ -1030,16 +1034,63 @@ static void run_crude_batched(ch_ctx* c, const std::vector<int64_t>& ids, const 
     t.measure = false;
     t.a = &ar;
     lay_pairs(t);
-    // the projections (l2) on the lanes; l1 rows are the sets' own
+    // the projections (l2): sets of d <= 8 in one launch per (storage type, d),
+    // resident embeddings as they are, the others on the lanes; l1 rows are the
+    // sets' own
     if (params[ch[0].i].hash.metric == CH_L2) {
-      std::vector<int64_t> which(np);
-      for (int j = 0; j < np; ++j) which[j] = j;
-      on_lanes_of(which, [&](ch_ctx* lane, int64_t j) {
-        CrudeChunkPair& cp = ch[j];
-        const ch_hash_params* hp = &params[cp.i].hash;
-        run_hashed(lane, A[cp.i], hp, &cp.hA, &dres[cp.i].status);
-        run_hashed(lane, B[cp.i], hp, &cp.hB, &dres[cp.i].status);
-      });
+      std::vector<int64_t> which;  // 2 j + side: projected on a lane
+      std::map<std::pair<int, int>, std::vector<std::pair<ProjSet, int>>> runs;  // (type, d) -> (set, blocks)
+      const int k = static_cast<int>(params[ch[0].i].hash.proj_dim);
+      for (int j = 0; j < np; ++j)
+        for (int side = 0; side < 2; ++side) {
+          CrudeChunkPair& cp = ch[j];
+          const ch_set* X = side ? B[cp.i] : A[cp.i];
+          Hashed& h = side ? cp.hB : cp.hA;
+          const ch_hash_params* hp = &params[cp.i].hash;
+          if (resident_hashed(X, hp)) {
+            run_hashed(c, X, hp, &h, &dres[cp.i].status);  // no launch: the set's own embedding
+          } else if (X->d <= 8 && k <= 16) {
+            h.src = HashSrc{h.Y, CH_F32, X->n, k, nullptr};
+            h.box = h.boxY;
+            h.box_parts = project_small_blocks(X->n, c->sm_count);
+            runs[{X->dtype, X->d}].push_back(
+                {ProjSet{X->data, X->scales, X->n, hp->hash_seed, h.Y, h.boxY, X->status}, h.box_parts});
+          } else {
+            which.push_back(2 * int64_t(j) + side);
+          }
+        }
+      if (!runs.empty()) {
+        std::vector<ProjSet> hS;
+        std::vector<int> hblk;
+        std::vector<std::tuple<int, int, int, int, int>> launches;  // type, d, first set, first prefix, blocks
+        for (auto& r : runs) {
+          const int first = static_cast<int>(hS.size()), pre = static_cast<int>(hblk.size());
+          int tot = 0;
+          hblk.push_back(0);
+          for (auto& e : r.second) {
+            hS.push_back(e.first);
+            tot += e.second;
+            hblk.push_back(tot);
+          }
+          launches.emplace_back(r.first.first, r.first.second, first, pre, tot);
+        }
+        CHX_CHECK(hblk.size() <= size_t(2 * np + 64), CH_EINVAL, "internal: projection runs");
+        CHX_CUDA(cudaMemcpyAsync(dS, hS.data(), sizeof(ProjSet) * hS.size(), cudaMemcpyHostToDevice, c->stream));
+        CHX_CUDA(cudaMemcpyAsync(dSblk, hblk.data(), sizeof(int) * hblk.size(), cudaMemcpyHostToDevice, c->stream));
+        for (auto& l : launches) {
+          const int first = std::get<2>(l), pre = std::get<3>(l);
+          const int ns = static_cast<int>(runs[{std::get<0>(l), std::get<1>(l)}].size());
+          launch_project_small_batch(dS + first, dSblk + pre, ns, std::get<4>(l), std::get<0>(l), std::get<1>(l), k,
+                                     c->stream);
+        }
+      }
+      if (!which.empty())
+        on_lanes_of(which, [&](ch_ctx* lane, int64_t js) {
+          CrudeChunkPair& cp = ch[js / 2];
+          const ch_hash_params* hp = &params[cp.i].hash;
+          if (js % 2) run_hashed(lane, B[cp.i], hp, &cp.hB, &dres[cp.i].status);
+          else run_hashed(lane, A[cp.i], hp, &cp.hA, &dres[cp.i].status);
+        });
     } else {
       for (auto& cp : ch) {
         run_hashed(c, A[cp.i], &params[cp.i].hash, &cp.hA, &dres[cp.i].status);

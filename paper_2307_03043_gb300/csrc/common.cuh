@@ -426,6 +426,20 @@ __device__ __forceinline__ int find_pair(const int* __restrict__ blk0, int np, i
   }
   return lo;
 }
+// l2 embeddings of many sets of d <= 8 in one launch (batched estimates)
+struct ProjSet {
+  const void* X;
+  const float* scales;
+  int64_t n;
+  uint64_t seed;
+  float* Y;          // [n][k]
+  uint32_t* box;     // [blocks of the set][2][k] partial boxes
+  uint32_t* status;  // the set's status word (non-finite data)
+};
+// blocks (= partial boxes) of a set's small projection
+int project_small_blocks(int64_t n, int sm_count);
+void launch_project_small_batch(const ProjSet* S, const int* blk0, int ns, int blocks, int dtype, int d, int k,
+                                cudaStream_t s);
 // scale tables of every pair (a block per pair; e_top is not reported)
 void launch_scale_tables_batch(const CrudePair* P, int np, cudaStream_t s);
 // B into the tables at every scale, then A's probes: blk0 [np + 1] prefix of

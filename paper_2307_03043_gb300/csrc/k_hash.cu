@@ -300,11 +300,11 @@ __global__ void __launch_bounds__(128) k_project(const void* X, const float* sca
 // partial box (as k_project_tma does), so neither a separate G launch nor the
 // box initialisation is needed.
 constexpr int kProjSmallMaxD = 8;
+// block bx of gx blocks over one set's rows; writes partial box bx
 template <int DT, int KP, int D>
-__global__ void __launch_bounds__(128) k_project_small(const void* X, const float* scales, int64_t n, uint64_t seed,
-                                                       int k, float* Y, uint32_t* box, float* norms,
-                                                       uint32_t* status) {
-  pdl_entry();
+__device__ __forceinline__ void project_small_block(const void* X, const float* scales, int64_t n, uint64_t seed,
+                                                    int k, float* Y, uint32_t* box, float* norms, uint32_t* status,
+                                                    int bx, int gx) {
   static_assert(D * KP <= 128, "one G entry per thread");
   __shared__ __align__(16) float s_g[D][KP];
   __shared__ uint32_t s_box[2 * KP];
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(128) k_project_small(const void* X, const floa
     hi[i] = 0u;
   }
   bool bad = false;
-  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + tid; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t r = int64_t(bx) * blockDim.x + tid; r < n; r += int64_t(gx) * blockDim.x) {
     float xv[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) xv[j] = load_elem<DT>(X, r, D, j, scales);
@@ -368,8 +368,57 @@ __global__ void __launch_bounds__(128) k_project_small(const void* X, const floa
   __syncthreads();
   if (tid < 2 * k) {
     const int i = tid < k ? tid : KP + tid - k;
-    box[size_t(blockIdx.x) * 2 * k + tid] = s_box[i];
+    box[size_t(bx) * 2 * k + tid] = s_box[i];
   }
+}
+
+template <int DT, int KP, int D>
+__global__ void __launch_bounds__(128) k_project_small(const void* X, const float* scales, int64_t n, uint64_t seed,
+                                                       int k, float* Y, uint32_t* box, float* norms,
+                                                       uint32_t* status) {
+  pdl_entry();
+  project_small_block<DT, KP, D>(X, scales, n, seed, k, Y, box, norms, status, blockIdx.x, gridDim.x);
+}
+
+// every listed set of one storage type and d in one launch: the block run of set
+// i (blk0[i] .. blk0[i + 1] - 1) does what k_project_small's grid does for it
+template <int DT, int KP, int D>
+__global__ void __launch_bounds__(128) k_project_small_batch(const ProjSet* S, const int* blk0, int ns, int k) {
+  pdl_entry();
+  const int si = find_pair(blk0, ns, blockIdx.x);
+  const ProjSet& p = S[si];
+  const int local = blockIdx.x - __ldg(&blk0[si]);
+  project_small_block<DT, KP, D>(p.X, p.scales, p.n, p.seed, k, p.Y, p.box, nullptr, p.status, local,
+                                 __ldg(&blk0[si + 1]) - __ldg(&blk0[si]));
+}
+
+int project_small_blocks(int64_t n, int sm_count) {
+  return static_cast<int>(std::min<int64_t>(ceil_div(n, 128), std::min(sm_count, kMaxBoxParts)));
+}
+
+void launch_project_small_batch(const ProjSet* S, const int* blk0, int ns, int blocks, int dtype, int d, int k,
+                                cudaStream_t s) {
+  if (ns == 0 || blocks == 0) return;
+  CHX_CHECK(d >= 1 && d <= kProjSmallMaxD && k <= 16, CH_EINVAL, "batched small projection: d <= 8, k <= 16");
+  auto go = [&](auto dtc) {
+    constexpr int DTV = decltype(dtc)::value;
+    switch (d) {
+#define CHX_PSB(DV)                                                                                          \
+  case DV:                                                                                                   \
+    if (k <= 8) launch_k(k_project_small_batch<DTV, 8, DV>, blocks, 128, 0, s, S, blk0, ns, k);              \
+    else launch_k(k_project_small_batch<DTV, 16, DV>, blocks, 128, 0, s, S, blk0, ns, k);                    \
+    break;
+      CHX_PSB(1) CHX_PSB(2) CHX_PSB(3) CHX_PSB(4) CHX_PSB(5) CHX_PSB(6) CHX_PSB(7) CHX_PSB(8)
+#undef CHX_PSB
+      default: break;
+    }
+  };
+  switch (dtype) {
+    case CH_F32: go(std::integral_constant<int, CH_F32>{}); break;
+    case CH_BF16: go(std::integral_constant<int, CH_BF16>{}); break;
+    default: go(std::integral_constant<int, CH_FP8E4M3>{}); break;
+  }
+  launch_check("project_small_batch");
 }
 
 // Asynchronous variant for rows whose byte length is a multiple of 16: each
@@ -906,7 +955,7 @@ static int launch_project_tma(const ch_set* X, uint64_t seed, int k, float* Y, u
 template <int DT, int KP>
 static int launch_project_small(const ch_set* X, uint64_t seed, int k, float* Y, uint32_t* box, float* norms,
                                 int sm_count, cudaStream_t s) {
-  const int grid = static_cast<int>(std::min<int64_t>(ceil_div(X->n, 128), std::min(sm_count, kMaxBoxParts)));
+  const int grid = project_small_blocks(X->n, sm_count);
   switch (X->d) {
 #define CHX_PS(DV)                                                                                              \
   case DV:                                                                                                      \
