@@ -114,3 +114,33 @@ def test_batch_small_d_all_storage_types(ctx, d):
     torch.cuda.synchronize()
     for s in made:
         ch.ch_set_destroy(s)
+
+
+def test_batch_mixes_batched_and_lane_crude_nn(ctx):
+    """One call holding pairs whose CrudeNN runs in the batched launches (one
+    table group, grid family, hash tables) beside pairs that take the per-pair
+    path (sort grouping, SimHash, k x W, uniform sampling, a pair with several
+    table groups): every estimate equals its lone one."""
+    sets = _pairs(ctx, 6, 8, 21)
+    Xb, Yb = workloads.gaussian_mixture(400_000, 600_000, 8, 5, clusters=50)  # 600k points: several table groups
+    sBig = ch.ch_set_create(ctx, Xb, 0, Xb.shape[0], 8)
+    sBig2 = ch.ch_set_create(ctx, Yb, 0, Yb.shape[0], 8)
+    A, B, P = [], [], []
+    variants = [dict(), dict(group=ch.CH_GROUP_SORT), dict(family=ch.CH_FAMILY_SIMHASH), dict(window=4, repeats=2),
+                dict(sampling=ch.CH_SAMPLING_UNIFORM), dict()]
+    for i, kw in enumerate(variants):
+        for metric in (ch.CH_L1, ch.CH_L2):
+            if kw.get("family") == ch.CH_FAMILY_SIMHASH and metric == ch.CH_L1:
+                continue
+            A.append(sets[2 * i])
+            B.append(sets[2 * i + 1])
+            P.append(ch.est_params(metric, hash_seed=5 * i + metric, sample_seed=3 * i + metric, eps=0.2, **kw))
+    A.append(sBig); B.append(sBig2); P.append(ch.est_params(ch.CH_L2, hash_seed=9, sample_seed=9, eps=0.2))
+    A.append(sBig); B.append(sBig2); P.append(ch.est_params(ch.CH_L1, hash_seed=9, sample_seed=9, eps=0.2))
+    eta, st = ch.ch_estimate_batch(ctx, A, B, P)
+    assert all(s == ch.CH_OK for s in st), st
+    for i in range(len(A)):
+        assert eta[i] == ch.ch_estimate(ctx, A[i], B[i], P[i]), i
+    torch.cuda.synchronize()
+    for s in sets + [sBig, sBig2]:
+        ch.ch_set_destroy(s)
