@@ -950,7 +950,7 @@ namespace chx {
 
 // ------------------------------------------------------------------ batched CrudeNN
 // A pair's CrudeNN runs in the batched launches when its scales fit one group of
-// bucket tables, its hashed rows fit registers and it uses the default grid
+// bucket tables, its hashed rows fit registers (<= 64 values) and it uses the default grid
 // family with hash tables (the single-pair path's forward group, kernel for kernel).
 static bool crude_batchable(const ch_set* A, const ch_set* B, const ch_est_params* p) {
   const ch_hash_params* hp = &p->hash;
@@ -958,7 +958,7 @@ static bool crude_batchable(const ch_set* A, const ch_set* B, const ch_est_param
   if (hp->group != CH_GROUP_HASH || hp->family != CH_FAMILY_GRID) return false;
   if (A->dtype != B->dtype || A->n == 0 || B->n == 0) return false;
   const int dd = hp->metric == CH_L1 ? A->d : static_cast<int>(hp->proj_dim);
-  if (dd > 32) return false;
+  if (dd > 64) return false;
   const int L = static_cast<int>(hp->levels);
   return table_plan(B->n, L).per_group >= L;
 }

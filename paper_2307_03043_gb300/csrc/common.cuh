@@ -390,7 +390,7 @@ void launch_crude_dist(const ch_set* A, const ch_set* B, int metric, const int64
                        int sm_count, cudaStream_t s);
 
 // CrudeNN of many pairs in one launch per step (batched estimates): every pair's
-// scales fit one group of bucket tables, its hashed rows fit registers (dd <= 32)
+// scales fit one group of bucket tables, its hashed rows fit registers (dd <= 64)
 // and A and B share one storage type.  Each kernel's blocks are cut into
 // consecutive runs, one per pair (blk0[p] .. blk0[p + 1] - 1); a block finds its
 // pair by binary search and then does exactly what the single-pair kernel's

@@ -21,10 +21,14 @@ namespace chx {
 
 namespace {
 
-// Rows of up to 32 hashed coordinates are held in registers and keyed one
-// scale at a time; wider rows (l1 in high dimension) stream their coordinates
-// once and accumulate up to 16 scales together.
+// Rows of up to 64 hashed coordinates are held in registers and keyed one
+// scale at a time (the reverse groups up to 32); wider rows (l1 in high
+// dimension) stream their coordinates once and accumulate up to 16 scales
+// together.
 constexpr int kRegRow = 32;
+// forward tables and key writes keep rows of up to 64 values in registers (l1 in
+// d <= 64); the reverse groups stay at kRegRow
+constexpr int kRegRowMax = 64;
 
 // row of width dd <= W into registers (float4 loads for aligned binary32 rows of width W)
 template <int DT, int W>
@@ -523,8 +527,10 @@ void dispatch_dt_w(int dtype, int dd, F&& f) {
   auto with_w = [&](auto dtc) {
     if (dd <= 16)
       f(dtc, std::integral_constant<int, 16>{});
-    else
+    else if (dd <= kRegRow)
       f(dtc, std::integral_constant<int, kRegRow>{});
+    else
+      f(dtc, std::integral_constant<int, kRegRowMax>{});
   };
   switch (dtype) {
     case CH_F32: with_w(std::integral_constant<int, CH_F32>{}); break;
@@ -603,7 +609,7 @@ void launch_table_clear(HashTable h, int nl, int sm_count, cudaStream_t s) {
 void launch_group_insert(HashSrc B, int L, int L0, int nl, ScaleTables t, HashTable h, uint32_t* status, int sm_count,
                          cudaStream_t s) {
   if (B.n == 0) return;
-  if (B.dd <= kRegRow) {
+  if (B.dd <= kRegRowMax) {
     dispatch_dt_w(B.dtype, B.dd, [&](auto dtc, auto wc) {
       auto kern = k_table_insert_ps<decltype(dtc)::value, decltype(wc)::value>;
       // the nl block rows (one per scale) share the grid's two waves: sized for a
@@ -652,7 +658,7 @@ void launch_group_probe(HashSrc A, int L, int L0, int nl, ScaleTables t, HashTab
 
 void launch_insert_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int dd, cudaStream_t s) {
   if (np == 0 || blocks == 0) return;
-  CHX_CHECK(dd <= kRegRow, CH_EINVAL, "batched insert: hashed rows of <= 32 values");
+  CHX_CHECK(dd <= kRegRowMax, CH_EINVAL, "batched insert: hashed rows of <= 64 values");
   dispatch_dt_w(dtype, dd, [&](auto dtc, auto wc) {
     launch_k(k_table_insert_batch<decltype(dtc)::value, decltype(wc)::value>, blocks, 128, 0, s, P, blk0, np);
   });
@@ -661,7 +667,7 @@ void launch_insert_batch(const CrudePair* P, const int* blk0, int np, int blocks
 
 void launch_probe_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int dd, cudaStream_t s) {
   if (np == 0 || blocks == 0) return;
-  CHX_CHECK(dd <= kRegRow, CH_EINVAL, "batched probe: hashed rows of <= 32 values");
+  CHX_CHECK(dd <= kRegRowMax, CH_EINVAL, "batched probe: hashed rows of <= 64 values");
   dispatch_dt_w(dtype, dd, [&](auto dtc, auto wc) {
     launch_k(k_table_probe_batch<decltype(dtc)::value, decltype(wc)::value>, blocks, 128, 0, s, P, blk0, np);
   });
