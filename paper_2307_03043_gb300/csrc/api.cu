@@ -979,7 +979,7 @@ struct CrudeChunkPair {
 template <class OnLanes>
 static void run_crude_batched(ch_ctx* c, const std::vector<int64_t>& ids, const ch_set* const* A,
                               const ch_set* const* B, const ch_est_params* params, const std::vector<float*>& Dp,
-                              ResBlock* dres, OnLanes&& on_lanes_of, int K) {
+                              ResBlock* dres, OnLanes&& on_lanes_of) {
   size_t at = 0;
   while (at < ids.size()) {
     // the chunk: pairs in order until the tables reach the budget
@@ -1148,7 +1148,6 @@ static void run_crude_batched(ch_ctx* c, const std::vector<int64_t>& ids, const 
     launch_crude_dist_batch(dP, dblk + 2 * blk_stride, np, b_dst[np], A0->dtype, hp0->metric, A0->d, s);
     CHX_CUDA(cudaFreeAsync(mem, s));
   }
-  (void)K;
 }
 
 // ------------------------------------------------------------------ batched small scans
@@ -1601,7 +1600,7 @@ ch_status ch_estimate_batch(ch_ctx* c, int64_t count, const ch_set* const* A, co
       join();
       for (int k = 0; k < K; ++k) CHX_CHECK(err[k] == CH_OK, err[k], "batched CrudeNN: a projection failed");
     };
-    for (auto& g : groups) run_crude_batched(c, g.second, A, B, params, Dp, dres, on_lanes_of, K);
+    for (auto& g : groups) run_crude_batched(c, g.second, A, B, params, Dp, dres, on_lanes_of);
   }
   launch_batch_sample(ditems, static_cast<int64_t>(run.size()), c->stream);  // 2.
   fork();
