@@ -170,6 +170,25 @@ def test_projection_fma_chain_close_to_fp64():
     assert np.all(np.abs(Y - ref) <= bound + 1e-30)
 
 
+def test_projection_is_a_fused_chain_in_coordinate_order():
+    """Reading R3 pinned by IEEE binary32 arithmetic worked by hand, with
+    u = 1 + 2^-12 and v = 1 + 2^-11 (u * u = v + 2^-24, a tie between v and its
+    successor that goes to the even v):
+      row (-v, u) . (1, u):  acc = -v, then fma(u, u, -v) = 2^-24 exactly; rounding
+        the product first, or the reverse order, gives 0;
+      row (u, -v) . (u, 1):  acc = round(u * u) = v, then fma(-v, 1, v) = 0; the
+        reverse order gives 2^-24;
+      row (-v, u) . (u, 1):  acc = -(u v) = -(1 + 2^-11 + 2^-12 + 2^-23) exactly, then
+        u - u v = -(2^-11 + 2^-23) exactly."""
+    u, v = 1.0 + 2.0 ** -12, 1.0 + 2.0 ** -11
+    G = np.array([[-v, u], [u, -v]], dtype=np.float32)
+    y = oracle.project(np.array([[1.0, u]], dtype=np.float32), G)
+    assert y[0, 0] == np.float32(2.0 ** -24)
+    y2 = oracle.project(np.array([[u, 1.0]], dtype=np.float32), G)
+    assert y2[0, 1] == np.float32(0.0)
+    assert y2[0, 0] == np.float32(-(2.0 ** -11 + 2.0 ** -23))
+
+
 @pytest.mark.parametrize("case", _hand()["top_exp"]["cases"])
 def test_top_exp_hand_examples(case):
     A, B = np.array(case["A"], np.float32), np.array(case["B"], np.float32)
