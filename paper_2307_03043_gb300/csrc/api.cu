@@ -1145,7 +1145,7 @@ static void run_crude_batched(ch_ctx* c, const std::vector<int64_t>& ids, const 
     launch_scale_tables_batch(dP, np, s);
     launch_insert_batch(dP, dblk, np, b_ins[np], hP[0].B.dtype, hP[0].B.dd, s);
     launch_probe_batch(dP, dblk + blk_stride, np, b_prb[np], hP[0].A.dtype, hP[0].A.dd, s);
-    launch_crude_dist_batch(dP, dblk + 2 * blk_stride, np, b_dst[np], A0->dtype, hp0->metric, A0->d, s);
+    launch_crude_dist_batch(dP, dblk + 2 * blk_stride, np, b_dst[np], A0->dtype, hp0->metric, s);
     CHX_CUDA(cudaFreeAsync(mem, s));
   }
 }

@@ -447,7 +447,7 @@ void launch_scale_tables_batch(const CrudePair* P, int np, cudaStream_t s);
 void launch_insert_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int dd, cudaStream_t s);
 void launch_probe_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int dd, cudaStream_t s);
 // D_a of every pair (G lanes per a, as launch_crude_dist's lane form; blocks gx_dist)
-void launch_crude_dist_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int metric, int d,
+void launch_crude_dist_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int metric,
                              cudaStream_t s);
 // lanes per a of the batched crude distance for dimension d
 int crude_dist_lanes(int d);

@@ -1227,9 +1227,8 @@ __global__ void __launch_bounds__(256) k_crude_dist_batch(const CrudePair* P, co
                                   int64_t(p.gx_dist) * blockDim.x, mx);
 }
 
-void launch_crude_dist_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int metric, int d,
+void launch_crude_dist_batch(const CrudePair* P, const int* blk0, int np, int blocks, int dtype, int metric,
                              cudaStream_t s) {
-  (void)d;
   if (np == 0 || blocks == 0) return;
 #define CHX_CDB(DTV)                                                                                         \
   do {                                                                                                       \
